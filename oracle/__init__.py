@@ -1,0 +1,222 @@
+"""FP64 dense CPU oracle (ctypes wrapper around ``sbg_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+bench's CPU-baseline leg use it to check and time the CUDA library; the
+library itself never imports, links or calls anything here, and this package
+shares no code with it.  The only inputs the two sides share come from the
+``workloads`` package, which holds no arithmetic of the method.
+
+Every function is the plain definition computed on the whole dense box; see
+the C source for the passage of the paper each one follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sbg_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+FLT_EPSILON = float(np.finfo(np.float32).eps)
+
+_lib = None
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, OpenMP, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build_oracle()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        D = ctypes.c_double
+        I = ctypes.c_int
+        lib.oracle_num_threads.restype = I
+        lib.oracle_active_mask.argtypes = [P, I64, ctypes.c_float, P]
+        lib.oracle_fixed_mask.argtypes = [P, P, P, P]
+        lib.oracle_surface_weight.argtypes = [P, P, I64, D, P]
+        lib.oracle_stability_limit.argtypes = [P, P, I, P, P, D, D]
+        lib.oracle_stability_limit.restype = D
+        lib.oracle_step.argtypes = [P, P, P, P, I, P, P, P, D, P, P, D, P]
+        lib.oracle_run.argtypes = [P, P, P, P, I, P, P, D, P, P, D, I64]
+        lib.oracle_run.restype = I
+        lib.oracle_rhs.argtypes = [P, P, P, P, I, P, P, P, P, D, P]
+        lib.oracle_reduce.argtypes = [P, P, P, P, I, P, P, P, P, D, P]
+        lib.oracle_effective_D.argtypes = [P, P, D, D, D, D, D, P, P, P]
+        lib.oracle_steady_cg.argtypes = [P, P, P, P, D, P, D, I64, P]
+        lib.oracle_steady_cg.restype = D
+        lib.oracle_adjoint_step.argtypes = [P, P, P, P, I, P, P, P, P, D, P, P, D, P]
+        lib.oracle_adjoint_run.argtypes = [P, P, P, P, I, P, P, D, P, P, D, I64, P, P, P, P]
+        lib.oracle_adjoint_run.restype = I
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+@dataclass
+class Problem:
+    """A dense problem: phi plus the physics of one run.
+
+    ``phys`` is any object with the fields of ``workloads.Physics``.
+    Derived arrays (active, fixed, w) are computed here by the oracle.
+    """
+    phi: np.ndarray
+    phys: object
+
+    def __post_init__(self):
+        lib = _load()
+        self.phi = np.ascontiguousarray(self.phi, dtype=np.float32)
+        nz, ny, nx = self.phi.shape
+        self.dims = np.array([nx, ny, nz], dtype=np.int64)
+        assert tuple(self.dims) == tuple(self.phys.dims), "phi shape does not match physics dims"
+        self.n = int(nx * ny * nz)
+        self.ns = int(self.phys.nspecies)
+        self.dx = _f64(self.phys.dx)
+        self.D = _f64(list(self.phys.D) + [0.0, 0.0])[:2].copy()
+        self.decay = _f64(list(self.phys.decay) + [0.0, 0.0])[:2].copy()
+        self.k = float(self.phys.k_surf)
+        self.active = np.zeros(self.phi.shape, dtype=np.uint8)
+        lib.oracle_active_mask(_p(self.phi), self.n, ctypes.c_float(FLT_EPSILON), _p(self.active))
+        self.fixed = np.zeros(self.phi.shape, dtype=np.uint8)
+        dirich = np.array([1 if f else 0 for f in self.phys.dirichlet], dtype=np.int32)
+        lib.oracle_fixed_mask(_p(self.dims), _p(self.active), _p(dirich), _p(self.fixed))
+        self.w = np.zeros(self.phi.shape, dtype=np.float64)
+        lib.oracle_surface_weight(_p(self.phi), _p(self.active), self.n, float(self.phys.band_eps),
+                                  _p(self.w))
+
+    # -- state helpers --------------------------------------------------------
+    def shape_state(self, u):
+        u = _f64(u).reshape((self.ns,) + self.phi.shape).copy()
+        u *= self.active[None]  # inactive voxels carry 0
+        return u
+
+    # -- the method ---------------------------------------------------------
+    def stability_limit(self) -> float:
+        return float(_load().oracle_stability_limit(_p(self.dims), _p(self.dx), self.ns, _p(self.D),
+                                                    _p(self.decay), self.k, float(self.phys.band_eps)))
+
+    def step(self, u, dt=None, src=None):
+        u = self.shape_state(u)
+        out = np.empty_like(u)
+        src = None if src is None else _f64(src).reshape(u.shape)
+        _load().oracle_step(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.w), self.ns,
+                            _p(u), _p(out), _p(self.dx), float(self.phys.dt if dt is None else dt),
+                            _p(self.D), _p(self.decay), self.k, _p(src))
+        return out
+
+    def run(self, u, nsteps, dt=None):
+        u = self.shape_state(u)
+        rc = _load().oracle_run(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.w), self.ns,
+                                _p(u), _p(self.dx), float(self.phys.dt if dt is None else dt),
+                                _p(self.D), _p(self.decay), self.k, int(nsteps))
+        if rc != 0:
+            raise MemoryError("oracle_run: allocation failed")
+        return u
+
+    def rhs(self, u):
+        u = self.shape_state(u)
+        out = np.empty_like(u)
+        _load().oracle_rhs(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.w), self.ns,
+                           _p(u), _p(self.dx), _p(self.D), _p(self.decay), self.k, _p(out))
+        return out
+
+    def reduce(self, u):
+        """Per species: dict(mass, J_in, J_out, residual, n_active)."""
+        u = self.shape_state(u)
+        out = np.zeros(self.ns * 5)
+        _load().oracle_reduce(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.w), self.ns,
+                              _p(u), _p(self.dx), _p(self.D), _p(self.decay), self.k, _p(out))
+        keys = ("mass", "J_in", "J_out", "residual", "n_active")
+        return [dict(zip(keys, out[s * 5:(s + 1) * 5])) for s in range(self.ns)]
+
+    def effective_D(self, u):
+        """(D_eff, tau, psi) from the x-face fluxes of species 0 (Eq. 100-102)."""
+        r = self.reduce(u)[0]
+        from workloads import FACE_XHI, FACE_XLO
+        dC = abs(self.phys.face_value[FACE_XLO] - self.phys.face_value[FACE_XHI])
+        d_eff, tau, psi = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _load().oracle_effective_D(_p(self.dims), _p(self.dx), r["J_in"], r["J_out"], dC,
+                                   float(self.D[0]), r["n_active"], ctypes.byref(d_eff),
+                                   ctypes.byref(tau), ctypes.byref(psi))
+        return d_eff.value, tau.value, psi.value
+
+    def steady_cg(self, u0, tol=1e-13, maxit=100000):
+        """FP64 CG steady state of species 0; returns (u, relres, iterations)."""
+        u = self.shape_state(u0)[0].copy()
+        iters = ctypes.c_int64()
+        rel = _load().oracle_steady_cg(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.dx),
+                                       float(self.D[0]), _p(u), float(tol), int(maxit),
+                                       ctypes.byref(iters))
+        return u, float(rel), int(iters.value)
+
+    def adjoint_step(self, u_n, lam_next, dt=None):
+        u_n = self.shape_state(u_n)
+        lam_next = _f64(lam_next).reshape(u_n.shape)
+        lam = np.empty_like(u_n)
+        grad = np.zeros(self.ns + 1)
+        _load().oracle_adjoint_step(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.w),
+                                    self.ns, _p(u_n), _p(lam_next), _p(lam), _p(self.dx),
+                                    float(self.phys.dt if dt is None else dt), _p(self.D),
+                                    _p(self.decay), self.k, _p(grad))
+        return lam, grad
+
+    def adjoint_run(self, u0, nsteps, lam_N, dt=None):
+        """Returns (lambda^0, grad = [dL/dD_s..., dL/dk], u^N)."""
+        u0 = self.shape_state(u0)
+        lam_N = _f64(lam_N).reshape(u0.shape)
+        lam0 = np.empty_like(u0)
+        uN = np.empty_like(u0)
+        grad = np.zeros(self.ns + 1)
+        rc = _load().oracle_adjoint_run(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.w),
+                                        self.ns, _p(u0), _p(self.dx),
+                                        float(self.phys.dt if dt is None else dt), _p(self.D),
+                                        _p(self.decay), self.k, int(nsteps), _p(lam_N), _p(lam0),
+                                        _p(grad), _p(uN))
+        if rc != 0:
+            raise MemoryError("oracle_adjoint_run: cannot store the state history")
+        return lam0, grad, uN
+
+    # -- the gradient workload's loss -------------------------------------------
+    def slab_mask(self, x_cut):
+        m = np.zeros(self.phi.shape, dtype=bool)
+        m[:, :, x_cut + 1:] = True
+        return m & (self.active > 0)
+
+    def slab_loss(self, u, x_cut):
+        """Mean of species 0 over the active voxels with x > x_cut."""
+        u = self.shape_state(u)
+        m = self.slab_mask(x_cut)
+        return float(u[0][m].sum() / m.sum())
+
+    def slab_loss_seed(self, x_cut):
+        """dL/du^N of slab_loss."""
+        m = self.slab_mask(x_cut)
+        lam = np.zeros((self.ns,) + self.phi.shape)
+        lam[0][m] = 1.0 / m.sum()
+        return lam
