@@ -1,0 +1,232 @@
+/*
+ * sbg.h - C ABI of the sparse-block-grid reaction-diffusion library (sm_103a).
+ *
+ * The library advances the reaction-diffusion PDE of Eq. 1 (Sec. 2) with the
+ * FTCS / forward-Euler scheme of Sec. 2.3 on a geometry-adapted sparse block
+ * grid: only the B x B x B voxel blocks that contain pore space (phi > eps,
+ * Eq. 3 sign convention) are stored and updated.  Neighbours outside the pore
+ * space take the centre value (the no-flux rule of Sec. 2.3), the surface
+ * reaction is localised by phi (Sec. 3.5), and FP64 reductions give mass,
+ * fluxes, residual, effective diffusivity and tortuosity (Eq. 2).
+ *
+ * Conventions (every entry point):
+ *  - No exceptions cross the ABI.  Every call returns an sbg_status; on error
+ *    sbg_last_error() holds a message for the calling thread.
+ *  - Dense arrays are [Nz][Ny][Nx], x fastest (a contiguous [Nz, Ny, Nx]
+ *    tensor), with dims[3] = {Nx, Ny, Nz}.  A dims entry need not be a
+ *    multiple of the block edge; the library pads with inactive voxels.
+ *  - Pointers flagged "host or device" are read (or written) during the call
+ *    only; the caller keeps ownership.  Library objects (sbg_grid, sbg_state)
+ *    own their device memory until the matching destroy call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; the call synchronises the stream only
+ *    when it returns host scalars (reductions) or reads/writes host arrays.
+ *  - One grid/state must not be used from two host threads at once.
+ *
+ * Face numbering: 0 = x-low, 1 = x-high, 2 = y-low, 3 = y-high, 4 = z-low,
+ * 5 = z-high.
+ */
+#ifndef SBG_H
+#define SBG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbg_grid_s *sbg_grid;   /* geometry: blocks, hash, neighbour table, masks */
+typedef struct sbg_state_s *sbg_state; /* species fields in block layout, ping-pong pair  */
+
+typedef enum {
+    SBG_OK = 0,
+    SBG_ERR_INVALID_ARG = 1,   /* bad pointer, size, dims, block edge or parameter            */
+    SBG_ERR_OOM = 2,           /* a device or host allocation failed                            */
+    SBG_ERR_CUDA = 3,          /* a CUDA call or kernel launch failed                           */
+    SBG_ERR_UNSTABLE_DT = 4,   /* dt above sbg_stability_limit() and allow_unstable == 0       */
+    SBG_ERR_NONFINITE = 5,     /* a NaN or Inf was found in the state by a reduction           */
+    SBG_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                                 */
+    SBG_ERR_NOT_CONVERGED = 7  /* sbg_run_to_steady reached max_steps first                     */
+} sbg_status;
+
+typedef enum {
+    SBG_F32 = 0,   /* FP32 state and stencil                                                   */
+    SBG_F64 = 1,   /* FP64 state and stencil                                                   */
+    SBG_F32X2 = 2  /* compensated FP32: value = hi + lo, two FP32 arrays, FP32 arithmetic with
+                      error-free sums, so that forward Euler keeps increments far below one
+                      FP32 ulp (needed for steady states to a 1e-8 relative residual)         */
+} sbg_dtype;
+
+enum { SBG_FACE_NOFLUX = 0, SBG_FACE_DIRICHLET = 1 };
+
+/* sbg_build options. */
+typedef struct {
+    int32_t block;          /* block edge B: 4 or 8                                             */
+    int32_t phi_on_device;  /* 1: phi is a device pointer; 0: host pointer                     */
+    float eps_mask;         /* a voxel is in the pore space iff phi > eps_mask (FP32 compare);
+                               0 selects FLT_EPSILON, the paper's insertion bound (Appendix B,
+                               Listings 5 and 6)                                                */
+    float band_eps;         /* half-width eps_b of the surface delta
+                               w = (1 + cos(pi phi / eps_b)) / (2 eps_b) for 0 < phi < eps_b;
+                               0 selects 1.0                                                    */
+} sbg_build_opts;
+
+/* Physics of a run (constant D per species; Eq. 1 with a linear f).
+ * Species 0 (A) loses k_surf * w * A + decay[0] * A per unit time; with two
+ * species, species 1 (B) gains the same k_surf * w * A and loses decay[1] * B. */
+typedef struct {
+    double dx[3];             /* voxel spacing along x, y, z                                   */
+    double dt;                /* forward-Euler step                                             */
+    int32_t nspecies;         /* 1 or 2 (must equal the state's)                               */
+    int32_t face_type[6];     /* SBG_FACE_NOFLUX or SBG_FACE_DIRICHLET per face                */
+    double D[2];              /* diffusion coefficient per species                             */
+    double decay[2];          /* linear bulk loss rate per species                              */
+    double k_surf;            /* surface reaction rate A -> B (a sink of A with one species)    */
+    double face_value[6];     /* value held on Dirichlet faces (species 0); the driving
+                                 difference dC of sbg_effective_D is |value[0] - value[1]|    */
+    int32_t allow_unstable;   /* 1: skip the dt <= limit check                                  */
+} sbg_params;
+
+typedef struct {
+    int64_t dims[3];          /* box size of geometry 0                                          */
+    int32_t block;            /* B                                                              */
+    int32_t n_geoms;          /* 1 for sbg_build                                                */
+    int64_t n_blocks;         /* active blocks (all geometries)                                 */
+    int64_t n_active;         /* active voxels (all geometries)                                 */
+    int64_t n_band_blocks;    /* blocks holding a surface-weight slab                           */
+    double porosity;          /* n_active / box voxels (geometry 0 for a batch)                 */
+    int64_t device_bytes;     /* device memory held by the grid                                 */
+} sbg_grid_info_t;
+
+/* Reduction output layout: out[s * SBG_NRED + q] for species s. */
+enum {
+    SBG_RED_MASS = 0,      /* sum over active voxels of u dV (the mass curve of Sec. 3.4)      */
+    SBG_RED_JIN = 1,       /* x-flux through the plane between x = 0 and x = 1:
+                              sum over (y,z) with both voxels active of
+                              D (u_0 - u_1) / dx * dy dz                                      */
+    SBG_RED_JOUT = 2,      /* same between x = Nx-2 and x = Nx-1                               */
+    SBG_RED_RESIDUAL = 3,  /* ||L_h u||_2 over free active voxels, L_h u the bracketed FTCS
+                              right-hand side, evaluated in FP64                              */
+    SBG_RED_MIN = 4,       /* min of u over active voxels                                       */
+    SBG_RED_MAX = 5,       /* max of u over active voxels                                       */
+    SBG_RED_NONFINITE = 6, /* count of NaN/Inf active voxels                                    */
+    SBG_RED_NACTIVE = 7,   /* count of active voxels                                            */
+    SBG_NRED = 8
+};
+
+/* ---- grid ------------------------------------------------------------------
+ * Block activation and indexing (Sec. 2.3-2.4: chunks stored only if they
+ * hold at least one inserted point; Appendix B Listing 5 for the insertion
+ * test).  Builds, on `stream`: the compact list of active blocks in x-fastest
+ * block order, an open-addressing device hash from block coordinates to block
+ * id, the 26-neighbour table (id or -1), one occupancy bitmap per block and
+ * the surface-weight slabs of blocks that meet the band 0 < phi < eps_b.
+ * phi: dense FP32 [Nz][Ny][Nx], host or device (opts->phi_on_device).
+ * Returns INVALID_ARG for null pointers, dims < 1 or > 65535*B, block not
+ * 4/8; OOM/CUDA on allocation or launch failure.  Synchronises `stream`. */
+sbg_status sbg_build(const float *phi, const int64_t dims[3], const sbg_build_opts *opts,
+                     void *stream, sbg_grid *out);
+
+/* Batched geometries (no counterpart in the paper; a batching pattern of this
+ * library): n geometries, each with its own dims and phi, concatenated into one
+ * block list whose blocks carry their geometry id.  phis[g] as for sbg_build. */
+sbg_status sbg_build_batch(int32_t n, const float *const *phis, const int64_t *dims /* [n][3] */,
+                           const sbg_build_opts *opts, void *stream, sbg_grid *out);
+
+sbg_status sbg_grid_info(sbg_grid grid, sbg_grid_info_t *info);
+
+/* Per-geometry counts of a (batched) grid: n_active[g], first block and
+ * number of blocks of geometry g (blocks are sorted by geometry).  Arrays of
+ * length info.n_geoms, host memory; any may be NULL. */
+sbg_status sbg_grid_geometry_info(sbg_grid grid, int64_t *n_active, int64_t *block_begin,
+                                  int64_t *block_count);
+
+/* Copies the 26-neighbour table ([n_blocks][26] int32, -1 = no block; entry
+ * k enumerates (dz, dy, dx) in {-1,0,1}^3 z-slowest, skipping (0,0,0)) and the
+ * block coordinates ([n_blocks][4] int32: bx, by, bz, geometry) to host
+ * memory; either may be NULL.  For inspection and tests. */
+sbg_status sbg_grid_tables(sbg_grid grid, int32_t *nbr26, int32_t *blocks);
+
+void sbg_grid_destroy(sbg_grid grid);
+
+/* ---- state -----------------------------------------------------------------
+ * nspecies fields in block layout u[s][block * B^3 + (z*B + y)*B + x] plus the
+ * ping-pong partner (the two concentration properties of Appendix B Listing
+ * 7).  Inactive voxels of active blocks hold a NaN sentinel and are never
+ * updated. */
+sbg_status sbg_state_create(sbg_grid grid, int32_t nspecies, sbg_dtype dtype, sbg_state *out);
+
+/* Scatters a dense array into species `species`.  dense: [Nz][Ny][Nx] of
+ * dense_dtype (SBG_F32 or SBG_F64), host or device (on_device).  Values of
+ * inactive voxels are ignored; a NaN input is stored as a canonical NaN so
+ * that reductions report it.  For SBG_F32X2 states the value is split into
+ * hi = fl32(v), lo = fl32(v - hi).  For a batch, `geom` selects the geometry
+ * (0 otherwise).  Synchronises `stream` when dense is host memory. */
+sbg_status sbg_state_set(sbg_grid grid, sbg_state state, int32_t geom, int32_t species,
+                         const void *dense, int32_t dense_dtype, int32_t on_device, void *stream);
+
+/* Gathers species `species` into a dense array (inactive voxels -> 0).  For
+ * SBG_F32X2 states an SBG_F64 output receives hi + lo. */
+sbg_status sbg_state_get(sbg_grid grid, sbg_state state, int32_t geom, int32_t species,
+                         void *dense, int32_t dense_dtype, int32_t on_device, void *stream);
+
+/* Copies all species of `src` into `dst` (same grid, dtype and species). */
+sbg_status sbg_state_copy(sbg_state dst, sbg_state src, void *stream);
+
+void sbg_state_destroy(sbg_state state);
+
+/* ---- time stepping -----------------------------------------------------------
+ * nsteps forward-Euler FTCS steps of Eq. 1 (Sec. 2.3; Appendix B Listing 6
+ * for the per-point update):
+ *   u'_i = u_i + dt ( sum_a D_s/dx_a^2 [(u~_{i+a} - u_i) - (u_i - u~_{i-a})]
+ *                     - decay_s u_i -/+ k_surf w_i u_{A,i} )
+ * with u~_j = u_j if j is an active voxel, else u_i (no-flux rule).  Active
+ * voxels on Dirichlet faces are held.  Each step reads one buffer and writes
+ * the other.  Launches are enqueued on `stream` (replayed from a captured CUDA
+ * graph when nsteps is large); no synchronisation.  Returns UNSTABLE_DT when
+ * dt > sbg_stability_limit() unless params->allow_unstable. */
+sbg_status sbg_step(sbg_grid grid, sbg_state state, const sbg_params *params, int64_t nsteps,
+                    void *stream);
+
+/* Explicit stability limit: Eq. 10 (2-D, pure diffusion) extended to every
+ * axis with more than one voxel, with each species' largest linear loss rate
+ * (decay, plus k_surf / eps_b for species 0) added:
+ *   dt_lim = min_s 1 / (2 D_s sum_a dx_a^-2 + r_s,max).
+ * Returns the limit, or -1 on a null pointer. */
+double sbg_stability_limit(const sbg_params *params, const int64_t dims[3], double band_eps);
+
+/* ---- reductions -------------------------------------------------------------
+ * FP64 reductions over the current state (warp shuffles, per-CTA partials in a
+ * scratch buffer of the grid, then a fixed-order final pass: the result is
+ * deterministic).  out: host double[nspecies * SBG_NRED] (layout above); for a
+ * batch, `geom` selects the geometry (-1 = all geometries together).
+ * Synchronises `stream`. */
+sbg_status sbg_reduce(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom,
+                      double *out, void *stream);
+
+/* Effective diffusivity and diffusive tortuosity (Eq. 2: tau = D / D_eff with
+ * the pore-space D_eff) from the x-face fluxes of species 0:
+ *   D_eff = J L / (dC A), J = (J_in + J_out) / 2, L = (Nx - 1) dx,
+ *   A = Ny dy Nz dz, dC = |face_value[0] - face_value[1]|,
+ *   psi = n_active / (Nx Ny Nz), tau = psi D / D_eff (inf when D_eff <= 0).
+ * D_eff is the superficial value (per box cross-section).  Host outputs. */
+sbg_status sbg_effective_D(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom,
+                           double *D_eff, double *tau, double *psi, void *stream);
+
+/* Steps until the relative residual ||L_h u|| / ||L_h u^0|| of species 0 drops
+ * below tol, checking every check_every steps; *steps_done and *rel_residual
+ * report where it stopped.  Returns NOT_CONVERGED at max_steps and NONFINITE
+ * when a check finds a NaN/Inf. */
+sbg_status sbg_run_to_steady(sbg_grid grid, sbg_state state, const sbg_params *params, double tol,
+                             int64_t check_every, int64_t max_steps, int64_t *steps_done,
+                             double *rel_residual, void *stream);
+
+/* ---- errors -------------------------------------------------------------------- */
+const char *sbg_last_error(void);            /* thread-local; "" when none                      */
+const char *sbg_status_string(sbg_status s);
+int32_t sbg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBG_H */

@@ -156,7 +156,7 @@ class Problem:
         return [dict(zip(keys, out[s * 5:(s + 1) * 5])) for s in range(self.ns)]
 
     def effective_D(self, u):
-        """(D_eff, tau, psi) from the x-face fluxes of species 0 (Eq. 100-102)."""
+        """(D_eff, tau, psi) from the x-face fluxes of species 0 (Eq. 2)."""
         r = self.reduce(u)[0]
         from workloads import FACE_XHI, FACE_XLO
         dC = abs(self.phys.face_value[FACE_XLO] - self.phys.face_value[FACE_XHI])

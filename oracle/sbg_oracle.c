@@ -13,9 +13,10 @@
  * are [S][Nz][Ny][Nx].
  *
  * Readings of the paper taken here (the paper is silent or loose on them):
- *  - active (pore) voxel: phi > FLT_EPSILON, compared in FP32 (insertion rule
- *    of Sec. 2.3's sparse-grid listing with lower bound 0 and no upper cut;
- *    the functor's "outside" test phi <= 0 + eps is its complement);
+ *  - active (pore) voxel: phi > FLT_EPSILON, compared in FP32 (the point
+ *    insertion rule of the sparse-grid construction, Appendix B Listing 5,
+ *    with lower bound 0 and no upper cut; the no-flux test of the functor,
+ *    Appendix B Listing 6, phi <= 0 + eps, is its complement);
  *  - voxels outside the box are outside Omega (mirrored, i.e. no flux through
  *    box faces) unless the face is Dirichlet;
  *  - a Dirichlet face holds its *active* voxels of that voxel plane fixed at
@@ -23,7 +24,7 @@
  *  - surface reaction weight: smoothed delta w = (1 + cos(pi phi / eps_b)) /
  *    (2 eps_b) for active voxels with phi < eps_b, else 0;
  *  - species 0 loses T = k w u0 per unit time, species 1 gains the same T;
- *  - the explicit limit is the 3-D, reactive form of Eq. 238-240.
+ *  - the explicit limit is the 3-D, reactive form of Eq. 10.
  *
  * Sums (mass, fluxes, norms, dot products, gradient sums) are accumulated per
  * z-slice with Kahan compensation, then the slices are added in order, so the
@@ -70,8 +71,8 @@ static double sum_slices(const double *part, int64_t nz)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Geometry: which voxels belong to Omega (Sec. 2.3, point-insertion listing;
- * the functor listing's no-flux test).                                       */
+/* Geometry: which voxels belong to Omega (Sec. 3.2; point insertion in
+ * Appendix B Listing 5; the functor's no-flux test in Listing 6).            */
 void oracle_active_mask(const float *phi, int64_t n, float eps_mask, uint8_t *active)
 {
     for (int64_t i = 0; i < n; ++i) active[i] = (phi[i] > eps_mask) ? 1 : 0;
@@ -105,7 +106,7 @@ void oracle_surface_weight(const float *phi, const uint8_t *active, int64_t n, d
     }
 }
 
-/* Explicit stability limit: Eq. 238-240 gives dt < 1/(2 max D) * 1/sum_a dx_a^-2
+/* Explicit stability limit: Eq. 10 gives dt < 1/(2 max D) * 1/sum_a dx_a^-2
  * for pure diffusion in 2-D.  Here every axis with more than one voxel counts,
  * and each species' largest linear loss rate is added to its diffusive rate;
  * the result is the smallest over species.                                  */
@@ -128,8 +129,8 @@ double oracle_stability_limit(const int64_t dims[3], const double dx[3], int nsp
 /* ------------------------------------------------------------------------ */
 /* Value of the neighbour across axis a, direction dir (+1/-1), with the
  * no-flux rule: a neighbour outside Omega (or outside the box) takes the
- * centre's value, so the gradient towards it is zero (Sec. 2.3; functor
- * listing).                                                                  */
+ * centre's value, so the gradient towards it is zero (Sec. 2.3; Appendix B
+ * Listing 6).                                                                */
 static inline double nbr_value(const double *u, const uint8_t *active, int64_t nx, int64_t ny,
                                int64_t nz, int64_t x, int64_t y, int64_t z, int a, int dir,
                                double uc)
@@ -171,9 +172,9 @@ static double rhs_at(const double *u, const uint8_t *active, const double *w, in
     return lap + react;
 }
 
-/* One forward-Euler FTCS step (Sec. 2.3: FTCS, explicit Euler; Jacobi sweep
- * from the state at step n into a separate output, as the paper's ping-pong
- * of CONC_N -> CONC_NPLUS1).  Inactive voxels are set to 0; Dirichlet-held
+/* One forward-Euler FTCS step of Eq. 1 (Sec. 2.3: FTCS, explicit Euler; a
+ * Jacobi sweep from the state at step n into a separate output, like the
+ * two concentration properties of Appendix B Listing 7).  Inactive voxels are set to 0; Dirichlet-held
  * voxels are copied.  `src` (nullable, [S][N]) is an extra source term added
  * inside the bracket, used by the manufactured-solution check of Sec. 3.1.  */
 void oracle_step(const int64_t dims[3], const uint8_t *active, const uint8_t *fixed,
@@ -296,7 +297,7 @@ void oracle_reduce(const int64_t dims[3], const uint8_t *active, const uint8_t *
     free(part);
 }
 
-/* Effective diffusivity and diffusive tortuosity (Eq. 100-102: tau = D_f / D_eff).
+/* Effective diffusivity and diffusive tortuosity (Eq. 2: tau = D_f / D_eff).
  * D_eff is the superficial value J L / (dC A) with J the mean of the inlet
  * and outlet fluxes, L = (Nx-1) dx the distance between the two held planes
  * and A = Ny dy Nz dz the box cross-section.  The pore-space (intrinsic)

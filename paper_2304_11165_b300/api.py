@@ -1,0 +1,259 @@
+"""Python binding over the C ABI (argument marshalling only: every step of the
+path runs in the library's CUDA kernels).  Device buffers, streams and
+autograd come from PyTorch; dense inputs may be numpy arrays (host) or torch
+tensors (host or CUDA)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import NRED, Params, check, load
+
+_DTYPES = {"f32": _abi.SBG_F32, "f64": _abi.SBG_F64, "f32x2": _abi.SBG_F32X2}
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dense_ptr(a, allow_f32=True):
+    """(pointer, dtype code, on_device, keepalive) for a dense array or tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                a = a.contiguous()
+            if a.dtype == torch.float64:
+                code = _abi.SBG_F64
+            elif a.dtype == torch.float32 and allow_f32:
+                code = _abi.SBG_F32
+            else:
+                raise TypeError("dense tensors must be float32 or float64")
+            return ctypes.c_void_p(a.data_ptr()), code, int(a.is_cuda), a
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a)
+    if arr.dtype == np.float64:
+        code = _abi.SBG_F64
+    elif arr.dtype == np.float32 and allow_f32:
+        code = _abi.SBG_F32
+    else:
+        arr = arr.astype(np.float64)
+        code = _abi.SBG_F64
+    return arr.ctypes.data_as(ctypes.c_void_p), code, 0, arr
+
+
+def make_params(phys, allow_unstable: bool = False, dt=None) -> Params:
+    """Params from any object with the fields of ``workloads.Physics``."""
+    p = Params()
+    for a in range(3):
+        p.dx[a] = float(phys.dx[a])
+    p.dt = float(phys.dt if dt is None else dt)
+    p.nspecies = int(phys.nspecies)
+    for f in range(6):
+        p.face_type[f] = _abi.SBG_FACE_DIRICHLET if phys.dirichlet[f] else _abi.SBG_FACE_NOFLUX
+        p.face_value[f] = float(phys.face_value[f])
+    D = list(phys.D) + [0.0, 0.0]
+    decay = list(phys.decay) + [0.0, 0.0]
+    for s in range(2):
+        p.D[s] = float(D[s])
+        p.decay[s] = float(decay[s])
+    p.k_surf = float(phys.k_surf)
+    p.allow_unstable = int(bool(allow_unstable))
+    return p
+
+
+def stability_limit(params: Params, dims, band_eps: float = 1.0) -> float:
+    d = (ctypes.c_int64 * 3)(*[int(x) for x in dims])
+    return float(load().sbg_stability_limit(ctypes.byref(params), d, float(band_eps)))
+
+
+class Grid:
+    """A sparse block grid built on the device from one or more phi fields."""
+
+    def __init__(self, phi=None, block: int = 8, eps_mask: float = 0.0, band_eps: float = 1.0,
+                 stream=None, _handle=None, _keep=None):
+        lib = load()
+        self._lib = lib
+        if _handle is not None:
+            self.handle = _handle
+        else:
+            opts = _abi.BuildOpts(block, 0, eps_mask, band_eps)
+            ptr, code, on_dev, keep = _phi_ptr(phi)
+            opts.phi_on_device = on_dev
+            nz, ny, nx = phi.shape
+            dims = (ctypes.c_int64 * 3)(nx, ny, nz)
+            h = ctypes.c_void_p()
+            check(lib.sbg_build(ptr, dims, ctypes.byref(opts), _stream_handle(stream), ctypes.byref(h)))
+            self.handle = h
+        self._refresh_info()
+
+    @classmethod
+    def batch(cls, phis, block: int = 8, eps_mask: float = 0.0, band_eps: float = 1.0, stream=None):
+        lib = load()
+        n = len(phis)
+        ptrs = (ctypes.c_void_p * n)()
+        dims = (ctypes.c_int64 * (3 * n))()
+        keep = []
+        on_dev = None
+        for i, phi in enumerate(phis):
+            ptr, code, dev, k = _phi_ptr(phi)
+            if on_dev is None:
+                on_dev = dev
+            elif on_dev != dev:
+                raise ValueError("all phi fields must live on the same side (host or device)")
+            keep.append(k)
+            ptrs[i] = ptr
+            nz, ny, nx = phi.shape
+            dims[3 * i:3 * i + 3] = [nx, ny, nz]
+        opts = _abi.BuildOpts(block, on_dev or 0, eps_mask, band_eps)
+        h = ctypes.c_void_p()
+        check(lib.sbg_build_batch(n, ptrs, dims, ctypes.byref(opts), _stream_handle(stream),
+                                  ctypes.byref(h)))
+        return cls(_handle=h)
+
+    def _refresh_info(self):
+        info = _abi.GridInfo()
+        check(self._lib.sbg_grid_info(self.handle, ctypes.byref(info)))
+        self.info = {f: (list(getattr(info, f)) if f == "dims" else getattr(info, f))
+                     for f, _ in _abi.GridInfo._fields_}
+        self.block = info.block
+        self.n_geoms = info.n_geoms
+        self.n_blocks = info.n_blocks
+        self.n_active = info.n_active
+
+    def geometry_info(self):
+        n = self.n_geoms
+        na, bb, bc = (np.zeros(n, np.int64) for _ in range(3))
+        check(self._lib.sbg_grid_geometry_info(self.handle, na.ctypes.data_as(ctypes.c_void_p),
+                                               bb.ctypes.data_as(ctypes.c_void_p),
+                                               bc.ctypes.data_as(ctypes.c_void_p)))
+        return na, bb, bc
+
+    def tables(self):
+        nbr = np.zeros((self.n_blocks, 26), np.int32)
+        blocks = np.zeros((self.n_blocks, 4), np.int32)
+        check(self._lib.sbg_grid_tables(self.handle, nbr.ctypes.data_as(ctypes.c_void_p),
+                                        blocks.ctypes.data_as(ctypes.c_void_p)))
+        return nbr, blocks
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.sbg_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _phi_ptr(phi):
+    try:
+        import torch
+        if isinstance(phi, torch.Tensor):
+            t = phi.contiguous().to(torch.float32)
+            return ctypes.c_void_p(t.data_ptr()), _abi.SBG_F32, int(t.is_cuda), t
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(phi, dtype=np.float32)
+    return arr.ctypes.data_as(ctypes.c_void_p), _abi.SBG_F32, 0, arr
+
+
+class State:
+    """Species fields of one grid, in block layout, with their ping-pong partner."""
+
+    def __init__(self, grid: Grid, nspecies: int = 1, dtype: str = "f32"):
+        self.grid = grid
+        self.nspecies = nspecies
+        self.dtype = dtype
+        self._lib = grid._lib
+        h = ctypes.c_void_p()
+        check(self._lib.sbg_state_create(grid.handle, nspecies, _DTYPES[dtype], ctypes.byref(h)))
+        self.handle = h
+
+    def set(self, dense, species: int = 0, geom: int = 0, stream=None):
+        ptr, code, on_dev, keep = _dense_ptr(dense)
+        check(self._lib.sbg_state_set(self.grid.handle, self.handle, geom, species, ptr, code, on_dev,
+                                      _stream_handle(stream)))
+        return self
+
+    def set_all(self, dense, geom: int = 0, stream=None):
+        """dense: [S, Nz, Ny, Nx] (or [Nz, Ny, Nx] for one species)."""
+        if self.nspecies == 1 and dense.ndim == 3:
+            return self.set(dense, 0, geom, stream)
+        for s in range(self.nspecies):
+            self.set(dense[s], s, geom, stream)
+        return self
+
+    def get(self, species: int = 0, geom: int = 0, out=None, stream=None):
+        """Dense [Nz, Ny, Nx] copy (float64 numpy by default; or into `out`)."""
+        dims = self.grid.info["dims"] if geom == 0 else None
+        if out is None:
+            if dims is None:
+                raise ValueError("pass `out` for geometries other than 0")
+            out = np.zeros((dims[2], dims[1], dims[0]), np.float64)
+        ptr, code, on_dev, keep = _dense_ptr(out)
+        check(self._lib.sbg_state_get(self.grid.handle, self.handle, geom, species, ptr, code, on_dev,
+                                      _stream_handle(stream)))
+        return out
+
+    def get_all(self, geom: int = 0):
+        return np.stack([self.get(s, geom) for s in range(self.nspecies)])
+
+    def copy_from(self, other: "State", stream=None):
+        check(self._lib.sbg_state_copy(self.handle, other.handle, _stream_handle(stream)))
+        return self
+
+    def step(self, params: Params, nsteps: int, stream=None):
+        check(self._lib.sbg_step(self.grid.handle, self.handle, ctypes.byref(params), int(nsteps),
+                                 _stream_handle(stream)))
+        return self
+
+    def reduce(self, params: Params, geom: int = 0, stream=None):
+        out = np.zeros(self.nspecies * NRED)
+        check(self._lib.sbg_reduce(self.grid.handle, self.handle, ctypes.byref(params), geom,
+                                   out.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)))
+        keys = ("mass", "J_in", "J_out", "residual", "min", "max", "nonfinite", "n_active")
+        return [dict(zip(keys, out[s * NRED:(s + 1) * NRED])) for s in range(self.nspecies)]
+
+    def effective_D(self, params: Params, geom: int = 0, stream=None):
+        d, t, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(self._lib.sbg_effective_D(self.grid.handle, self.handle, ctypes.byref(params), geom,
+                                        ctypes.byref(d), ctypes.byref(t), ctypes.byref(p),
+                                        _stream_handle(stream)))
+        return d.value, t.value, p.value
+
+    def run_to_steady(self, params: Params, tol: float, check_every: int = 1000,
+                      max_steps: int = 10 ** 9, stream=None, raise_on_max=True):
+        steps, rel = ctypes.c_int64(), ctypes.c_double()
+        rc = self._lib.sbg_run_to_steady(self.grid.handle, self.handle, ctypes.byref(params), float(tol),
+                                         int(check_every), int(max_steps), ctypes.byref(steps),
+                                         ctypes.byref(rel), _stream_handle(stream))
+        if rc != _abi.SBG_OK and not (rc == _abi.SBG_ERR_NOT_CONVERGED and not raise_on_max):
+            check(rc)
+        return steps.value, rel.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.sbg_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,133 @@
+// Internal declarations of the sparse-block-grid library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sbg.h"
+
+namespace sbg {
+
+// ---------------------------------------------------------------------------
+// errors
+void set_error(const std::string &msg);
+sbg_status fail(sbg_status s, const std::string &msg);
+sbg_status cuda_fail(cudaError_t e, const char *what);
+
+#define SBG_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return sbg::cuda_fail(e_, #call); \
+    } while (0)
+
+#define SBG_LAUNCH_CHECK(what)                              \
+    do {                                                    \
+        cudaError_t e_ = cudaGetLastError();                \
+        if (e_ != cudaSuccess) return sbg::cuda_fail(e_, what); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// inactive-voxel sentinel: a quiet NaN with a payload that arithmetic never
+// produces (NVIDIA GPUs return the canonical 0x7fffffff for invalid ops), so a
+// stored value is "outside Omega" iff its bits equal the sentinel.
+constexpr uint32_t kSent32 = 0x7fc5b600u;
+constexpr uint64_t kSent64 = 0x7ff8c5b600000000ull;
+
+__host__ __device__ __forceinline__ float sentinel_f32() {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(kSent32);
+#else
+    union { uint32_t u; float f; } c{kSent32};
+    return c.f;
+#endif
+}
+__host__ __device__ __forceinline__ double sentinel_f64() {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)kSent64);
+#else
+    union { uint64_t u; double d; } c{kSent64};
+    return c.d;
+#endif
+}
+__device__ __forceinline__ bool is_sent(float v) { return __float_as_uint(v) == kSent32; }
+__device__ __forceinline__ bool is_sent(double v) {
+    return (uint64_t)__double_as_longlong(v) == kSent64;
+}
+template <typename T> __device__ __forceinline__ T sentinel();
+template <> __device__ __forceinline__ float sentinel<float>() { return sentinel_f32(); }
+template <> __device__ __forceinline__ double sentinel<double>() { return sentinel_f64(); }
+
+// 26-neighbour numbering: k over (dz, dy, dx) in {-1,0,1}^3, z slowest,
+// skipping the centre.  Face entries used by the 7-point stencil:
+constexpr int kNbrXm = 12, kNbrXp = 13, kNbrYm = 10, kNbrYp = 15, kNbrZm = 4, kNbrZp = 21;
+__host__ __device__ __forceinline__ int nbr_slot(int dx, int dy, int dz) {
+    int k = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+    return k > 13 ? k - 1 : k;
+}
+
+constexpr int kNumRed = SBG_NRED;
+constexpr int kRedMaxCtas = 148 * 8;
+
+}  // namespace sbg
+
+// ---------------------------------------------------------------------------
+struct sbg_grid_s {
+    int B = 8;
+    int n_geoms = 1;
+    float eps_mask = 0.f;
+    float band_eps = 1.f;
+    std::vector<int64_t> dims;              // [n_geoms * 3]
+    std::vector<int64_t> geom_nactive;      // [n_geoms]
+    std::vector<int64_t> geom_begin;        // [n_geoms] first block
+    std::vector<int64_t> geom_count;        // [n_geoms] number of blocks
+    int64_t nb = 0;
+    int64_t n_active = 0;
+    int64_t n_band = 0;
+    // device arrays
+    int4 *blocks = nullptr;        // [nb] (bx, by, bz, geometry)
+    int32_t *nbr = nullptr;        // [nb * 26]
+    int32_t *face_nbr = nullptr;   // [nb * 6]: -x, +x, -y, +y, -z, +z
+    unsigned long long *hkeys = nullptr;
+    int32_t *hvals = nullptr;
+    int64_t hcap = 0;
+    uint64_t *bitmap = nullptr;    // [nb * words]
+    int32_t *wslab = nullptr;      // [nb] slab index or -1
+    float *w = nullptr;            // [n_band * B^3]
+    int32_t *gdims = nullptr;      // [n_geoms * 4]: nx, ny, nz, 0
+    double *partials = nullptr;    // reduction scratch [kRedMaxCtas * kNumRed]
+    double *red_dev = nullptr;     // [kNumRed]
+    double *red_host = nullptr;    // pinned [kNumRed]
+    int64_t bytes = 0;
+    int words() const { return (B * B * B + 63) / 64; }
+    int b3() const { return B * B * B; }
+};
+
+struct sbg_state_s {
+    sbg_grid grid = nullptr;
+    int ns = 1;
+    sbg_dtype dtype = SBG_F32;
+    int64_t nslots = 0;            // nb * B^3
+    void *base = nullptr;          // one allocation for everything below
+    void *val[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [buffer][species]
+    float *lo[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // F32X2 low parts
+    int cur = 0;
+    int64_t bytes = 0;
+    // cached CUDA graph of an even number of steps
+    cudaGraphExec_t graph = nullptr;
+    int graph_cur = -1;
+    int64_t graph_steps = 0;
+    sbg_params graph_params{};
+    int graph_variant = -1;
+    size_t elem() const { return dtype == SBG_F64 ? 8 : 4; }
+};
+
+namespace sbg {
+// implemented in sbg_step.cu
+sbg_status validate_params(sbg_grid g, const sbg_params *p, int ns);
+// implemented in sbg_reduce.cu
+sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species,
+                          int which_buffer, double *out_host, cudaStream_t stream);
+}  // namespace sbg

@@ -1,0 +1,331 @@
+// FP64 reductions over the block-layout state: mass (the monitored total of
+// Sec. 3.4), x-face fluxes, the residual ||L_h u||_2 and min/max/non-finite
+// counts; effective diffusivity and tortuosity (Eq. 2); the steady-state
+// driver.
+//
+// Each thread accumulates in FP64, warps combine with __shfl_down_sync, each
+// CTA writes one partial record to the grid's scratch buffer, and a single
+// CTA adds the records in a fixed order, so the result is deterministic for a
+// given grid.  The residual is evaluated in FP64 from the stored values
+// (hi + lo for compensated states), so that a steady-state test at a 1e-8
+// relative residual measures the state, not FP32 rounding of the stencil.
+#include <math.h>
+
+#include <cstring>
+
+#include "sbg_internal.cuh"
+
+namespace sbg {
+
+sbg_status step_n(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, cudaStream_t s);
+
+struct RedArgs {
+    const void *val[2];
+    const float *lo[2];
+    const int4 *blocks;
+    const int32_t *face;
+    const int32_t *wslab;
+    const float *w;
+    const int32_t *gdims;
+    int64_t b_begin, b_count;
+    int species, ns, held_mask;
+    double c[3];
+    double D, decay, k, inv_dx, area, dv;
+    double *partials;
+};
+
+template <typename T, bool X2>
+__device__ __forceinline__ double load_val(const RedArgs &a, int s, int64_t slot, bool &act) {
+    const T v = ((const T *)a.val[s])[slot];
+    act = !is_sent(v);
+    double d = (double)v;
+    if (X2) d += (double)a.lo[s][slot];
+    return d;
+}
+
+// value of the neighbour of (block b, local l) across face f, with the no-flux rule
+template <typename T, bool X2, int B>
+__device__ __forceinline__ double nbr_val(const RedArgs &a, int s, int64_t b, int l, int x, int y,
+                                          int z, int f, double vc, bool *act_out = nullptr) {
+    constexpr int B3 = B * B * B;
+    int64_t nb = b;
+    int ln = l;
+    switch (f) {
+        case 0: if (x > 0) ln = l - 1; else { nb = a.face[b * 6 + 0]; ln = l + (B - 1); } break;
+        case 1: if (x < B - 1) ln = l + 1; else { nb = a.face[b * 6 + 1]; ln = l - (B - 1); } break;
+        case 2: if (y > 0) ln = l - B; else { nb = a.face[b * 6 + 2]; ln = l + (B - 1) * B; } break;
+        case 3: if (y < B - 1) ln = l + B; else { nb = a.face[b * 6 + 3]; ln = l - (B - 1) * B; } break;
+        case 4: if (z > 0) ln = l - B * B; else { nb = a.face[b * 6 + 4]; ln = l + (B - 1) * B * B; } break;
+        default: if (z < B - 1) ln = l + B * B; else { nb = a.face[b * 6 + 5]; ln = l - (B - 1) * B * B; } break;
+    }
+    if (nb < 0) {
+        if (act_out) *act_out = false;
+        return vc;
+    }
+    bool act;
+    double v = load_val<T, X2>(a, s, nb * B3 + ln, act);
+    if (act_out) *act_out = act;
+    return act ? v : vc;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+constexpr int kRedThreads = 256;
+
+template <typename T, bool X2, int B>
+__global__ void __launch_bounds__(kRedThreads) k_reduce(const RedArgs a) {
+    constexpr int B3 = B * B * B;
+    double acc[kNumRed];
+    acc[SBG_RED_MASS] = acc[SBG_RED_JIN] = acc[SBG_RED_JOUT] = acc[SBG_RED_RESIDUAL] = 0.0;
+    acc[SBG_RED_MIN] = INFINITY;
+    acc[SBG_RED_MAX] = -INFINITY;
+    acc[SBG_RED_NONFINITE] = acc[SBG_RED_NACTIVE] = 0.0;
+    const int s = a.species;
+    const int64_t total = a.b_count * B3;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = a.b_begin + t / B3;
+        const int l = (int)(t % B3);
+        bool act;
+        const double v = load_val<T, X2>(a, s, b * B3 + l, act);
+        if (!act) continue;
+        const int x = l % B, y = (l / B) % B, z = l / (B * B);
+        const int4 bc = a.blocks[b];
+        const int nx = a.gdims[bc.w * 4 + 0], ny = a.gdims[bc.w * 4 + 1], nz = a.gdims[bc.w * 4 + 2];
+        const int gx = bc.x * B + x, gy = bc.y * B + y, gz = bc.z * B + z;
+        acc[SBG_RED_NACTIVE] += 1.0;
+        if (!isfinite(v)) {
+            acc[SBG_RED_NONFINITE] += 1.0;
+            continue;
+        }
+        acc[SBG_RED_MASS] += v * a.dv;
+        acc[SBG_RED_MIN] = fmin(acc[SBG_RED_MIN], v);
+        acc[SBG_RED_MAX] = fmax(acc[SBG_RED_MAX], v);
+        const bool held = ((a.held_mask & 1) && gx == 0) || ((a.held_mask & 2) && gx == nx - 1) ||
+                          ((a.held_mask & 4) && gy == 0) || ((a.held_mask & 8) && gy == ny - 1) ||
+                          ((a.held_mask & 16) && gz == 0) || ((a.held_mask & 32) && gz == nz - 1);
+        if (!held) {
+            double lap = 0.0;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                const double vm = nbr_val<T, X2, B>(a, s, b, l, x, y, z, 2 * ax, v);
+                const double vp = nbr_val<T, X2, B>(a, s, b, l, x, y, z, 2 * ax + 1, v);
+                lap += a.c[ax] * ((vp - v) - (v - vm));
+            }
+            double react = -a.decay * v;
+            if (a.k != 0.0) {
+                const int ws = a.wslab[b];
+                const double w = ws >= 0 ? (double)a.w[(int64_t)ws * B3 + l] : 0.0;
+                bool act0;
+                const double ua = (s == 0) ? v : load_val<T, X2>(a, 0, b * B3 + l, act0);
+                const double tr = a.k * w * ua;
+                react += (s == 0) ? -tr : tr;
+            }
+            const double r = lap + react;
+            acc[SBG_RED_RESIDUAL] += r * r;
+        }
+        if (nx >= 2 && (gx == 0 || gx == nx - 2)) {
+            bool act1;
+            const double v1 = nbr_val<T, X2, B>(a, s, b, l, x, y, z, 1, v, &act1);
+            if (act1) {
+                const double j = a.D * (v - v1) * a.inv_dx * a.area;
+                if (gx == 0) acc[SBG_RED_JIN] += j;
+                if (gx == nx - 2) acc[SBG_RED_JOUT] += j;
+            }
+        }
+    }
+    __shared__ double sm[kRedThreads / 32][kNumRed];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kNumRed; ++q) {
+        double v = acc[q];
+        v = (q == SBG_RED_MIN) ? warp_min(v) : (q == SBG_RED_MAX) ? warp_max(v) : warp_sum(v);
+        if (lane == 0) sm[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumRed) {
+        const int q = threadIdx.x;
+        double v = sm[0][q];
+        for (int wi = 1; wi < kRedThreads / 32; ++wi)
+            v = (q == SBG_RED_MIN) ? fmin(v, sm[wi][q]) : (q == SBG_RED_MAX) ? fmax(v, sm[wi][q]) : v + sm[wi][q];
+        a.partials[(int64_t)blockIdx.x * kNumRed + q] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_final(const double *partials, int nctas, double *out) {
+    __shared__ double sm[256][kNumRed];
+    double acc[kNumRed];
+    for (int q = 0; q < kNumRed; ++q)
+        acc[q] = (q == SBG_RED_MIN) ? INFINITY : (q == SBG_RED_MAX) ? -INFINITY : 0.0;
+    for (int c = threadIdx.x; c < nctas; c += blockDim.x)
+        for (int q = 0; q < kNumRed; ++q) {
+            const double v = partials[(int64_t)c * kNumRed + q];
+            acc[q] = (q == SBG_RED_MIN) ? fmin(acc[q], v) : (q == SBG_RED_MAX) ? fmax(acc[q], v) : acc[q] + v;
+        }
+    for (int q = 0; q < kNumRed; ++q) sm[threadIdx.x][q] = acc[q];
+    __syncthreads();
+    for (int stride = 128; stride > 0; stride >>= 1) {
+        if ((int)threadIdx.x < stride)
+            for (int q = 0; q < kNumRed; ++q) {
+                const double o = sm[threadIdx.x + stride][q];
+                double &m = sm[threadIdx.x][q];
+                m = (q == SBG_RED_MIN) ? fmin(m, o) : (q == SBG_RED_MAX) ? fmax(m, o) : m + o;
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < kNumRed) {
+        double v = sm[0][threadIdx.x];
+        if (threadIdx.x == SBG_RED_RESIDUAL) v = sqrt(v);
+        out[threadIdx.x] = v;
+    }
+}
+
+template <typename T, bool X2, int B>
+static void launch_reduce(const RedArgs &a, int nctas, cudaStream_t s) {
+    k_reduce<T, X2, B><<<nctas, kRedThreads, 0, s>>>(a);
+}
+
+// Reduces species `species` of buffer `which` (st->cur when < 0) into out_host[kNumRed].
+sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species,
+                          int which, double *out_host, cudaStream_t s) {
+    const int buf = which < 0 ? st->cur : which;
+    RedArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int sp = 0; sp < st->ns; ++sp) {
+        a.val[sp] = st->val[buf][sp];
+        a.lo[sp] = st->lo[buf][sp];
+    }
+    a.blocks = g->blocks;
+    a.face = g->face_nbr;
+    a.wslab = g->wslab;
+    a.w = g->w;
+    a.gdims = g->gdims;
+    a.b_begin = geom < 0 ? 0 : g->geom_begin[geom];
+    a.b_count = geom < 0 ? g->nb : g->geom_count[geom];
+    a.species = species;
+    a.ns = st->ns;
+    for (int f = 0; f < 6; ++f)
+        if (p->face_type[f] == SBG_FACE_DIRICHLET) a.held_mask |= 1 << f;
+    for (int ax = 0; ax < 3; ++ax) a.c[ax] = p->D[species] / (p->dx[ax] * p->dx[ax]);
+    a.D = p->D[species];
+    a.decay = p->decay[species];
+    a.k = p->k_surf;
+    a.inv_dx = 1.0 / p->dx[0];
+    a.area = p->dx[1] * p->dx[2];
+    a.dv = p->dx[0] * p->dx[1] * p->dx[2];
+    a.partials = g->partials;
+    const int64_t work = a.b_count * g->b3();
+    int nctas = (int)std::min<int64_t>(kRedMaxCtas, (work + kRedThreads - 1) / kRedThreads);
+    if (nctas < 1) nctas = 1;
+    if (st->dtype == SBG_F64) {
+        if (g->B == 8) launch_reduce<double, false, 8>(a, nctas, s);
+        else launch_reduce<double, false, 4>(a, nctas, s);
+    } else if (st->dtype == SBG_F32) {
+        if (g->B == 8) launch_reduce<float, false, 8>(a, nctas, s);
+        else launch_reduce<float, false, 4>(a, nctas, s);
+    } else {
+        if (g->B == 8) launch_reduce<float, true, 8>(a, nctas, s);
+        else launch_reduce<float, true, 4>(a, nctas, s);
+    }
+    k_reduce_final<<<1, 256, 0, s>>>(g->partials, nctas, g->red_dev);
+    SBG_LAUNCH_CHECK("reduction launch");
+    SBG_CUDA(cudaMemcpyAsync(g->red_host, g->red_dev, sizeof(double) * kNumRed, cudaMemcpyDeviceToHost, s));
+    SBG_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(out_host, g->red_host, sizeof(double) * kNumRed);
+    return SBG_OK;
+}
+
+static sbg_status check_common(sbg_grid g, sbg_state st, const sbg_params *p, int geom) {
+    if (!g || !st || !p) return fail(SBG_ERR_INVALID_ARG, "null pointer");
+    if (st->grid != g) return fail(SBG_ERR_INVALID_ARG, "state of another grid");
+    if (geom < -1 || geom >= g->n_geoms) return fail(SBG_ERR_INVALID_ARG, "bad geometry index");
+    if (p->nspecies != st->ns) return fail(SBG_ERR_INVALID_ARG, "params.nspecies differs from the state's");
+    for (int a = 0; a < 3; ++a)
+        if (!(p->dx[a] > 0.0)) return fail(SBG_ERR_INVALID_ARG, "dx must be > 0");
+    return SBG_OK;
+}
+
+}  // namespace sbg
+
+using namespace sbg;
+
+extern "C" sbg_status sbg_reduce(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom,
+                                 double *out, void *stream) {
+    sbg_status rc = check_common(g, st, p, geom);
+    if (rc != SBG_OK) return rc;
+    if (!out) return fail(SBG_ERR_INVALID_ARG, "sbg_reduce: null output");
+    for (int s = 0; s < st->ns; ++s) {
+        rc = reduce_species(g, st, p, geom, s, -1, out + s * kNumRed, (cudaStream_t)stream);
+        if (rc != SBG_OK) return rc;
+    }
+    return SBG_OK;
+}
+
+extern "C" sbg_status sbg_effective_D(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom,
+                                      double *D_eff, double *tau, double *psi, void *stream) {
+    sbg_status rc = check_common(g, st, p, geom);
+    if (rc != SBG_OK) return rc;
+    if (geom < 0) return fail(SBG_ERR_INVALID_ARG, "sbg_effective_D: needs one geometry");
+    if (!D_eff || !tau || !psi) return fail(SBG_ERR_INVALID_ARG, "sbg_effective_D: null output");
+    double r[kNumRed];
+    rc = reduce_species(g, st, p, geom, 0, -1, r, (cudaStream_t)stream);
+    if (rc != SBG_OK) return rc;
+    const int64_t *d = &g->dims[3 * geom];
+    const double L = (double)(d[0] - 1) * p->dx[0];
+    const double A = (double)d[1] * p->dx[1] * (double)d[2] * p->dx[2];
+    const double dC = fabs(p->face_value[0] - p->face_value[1]);
+    const double J = 0.5 * (r[SBG_RED_JIN] + r[SBG_RED_JOUT]);
+    *psi = r[SBG_RED_NACTIVE] / ((double)d[0] * (double)d[1] * (double)d[2]);
+    *D_eff = (dC > 0.0) ? J * L / (dC * A) : NAN;
+    *tau = (*D_eff > 0.0) ? (*psi) * p->D[0] / (*D_eff) : INFINITY;
+    return SBG_OK;
+}
+
+extern "C" sbg_status sbg_run_to_steady(sbg_grid g, sbg_state st, const sbg_params *p, double tol,
+                                        int64_t check_every, int64_t max_steps, int64_t *steps_done,
+                                        double *rel_residual, void *stream) {
+    sbg_status rc = check_common(g, st, p, -1);
+    if (rc != SBG_OK) return rc;
+    if (check_every < 1 || max_steps < 0 || !(tol > 0.0))
+        return fail(SBG_ERR_INVALID_ARG, "sbg_run_to_steady: check_every >= 1, max_steps >= 0, tol > 0");
+    rc = validate_params(g, p, st->ns);
+    if (rc != SBG_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    double r[kNumRed];
+    rc = reduce_species(g, st, p, -1, 0, -1, r, s);
+    if (rc != SBG_OK) return rc;
+    const double r0 = r[SBG_RED_RESIDUAL];
+    int64_t done = 0;
+    double rel = r0 > 0.0 ? 1.0 : 0.0;
+    if (steps_done) *steps_done = 0;
+    if (rel_residual) *rel_residual = rel;
+    if (r[SBG_RED_NONFINITE] > 0) return fail(SBG_ERR_NONFINITE, "sbg_run_to_steady: non-finite initial state");
+    while (rel >= tol && done < max_steps) {
+        const int64_t n = std::min<int64_t>(check_every, max_steps - done);
+        rc = step_n(g, st, p, n, s);
+        if (rc != SBG_OK) return rc;
+        done += n;
+        rc = reduce_species(g, st, p, -1, 0, -1, r, s);
+        if (rc != SBG_OK) return rc;
+        rel = r[SBG_RED_RESIDUAL] / r0;
+        if (steps_done) *steps_done = done;
+        if (rel_residual) *rel_residual = rel;
+        if (r[SBG_RED_NONFINITE] > 0) return fail(SBG_ERR_NONFINITE, "sbg_run_to_steady: non-finite value");
+    }
+    if (rel >= tol) return fail(SBG_ERR_NOT_CONVERGED, "sbg_run_to_steady: max_steps reached");
+    return SBG_OK;
+}

@@ -1,0 +1,208 @@
+// Species state in block layout: u[s][block * B^3 + (z*B + y)*B + x], two
+// buffers (read one, write the other each step, like the two concentration
+// properties of Appendix B Listing 7).  Inactive voxels of active blocks hold
+// the NaN sentinel; the step kernel reads that as "outside Omega".
+#include <math.h>
+
+#include <cstring>
+
+#include "sbg_internal.cuh"
+
+namespace sbg {
+
+template <typename Tin, typename Tst, bool X2, int B>
+__global__ void k_scatter(const Tin *__restrict__ dense, int nx, int ny, int nz,
+                          const int4 *__restrict__ blocks, const uint64_t *__restrict__ bitmap,
+                          int64_t begin, int64_t count, Tst *__restrict__ val, float *__restrict__ lo) {
+    constexpr int B3 = B * B * B;
+    constexpr int W = (B3 + 63) / 64;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count * B3) return;
+    const int64_t b = begin + t / B3;
+    const int l = (int)(t % B3);
+    const int4 bc = blocks[b];
+    const bool act = (bitmap[b * W + l / 64] >> (l % 64)) & 1ull;
+    const int64_t slot = b * B3 + l;
+    if (!act) {
+        val[slot] = sentinel<Tst>();
+        if (X2) lo[slot] = 0.f;
+        return;
+    }
+    const int x = bc.x * B + l % B, y = bc.y * B + (l / B) % B, z = bc.z * B + l / (B * B);
+    double v = (double)dense[((int64_t)z * ny + y) * nx + x];
+    if (isnan(v)) v = __longlong_as_double(0x7fffffffffffffffll);  // canonical NaN, not the sentinel
+    if (X2) {
+        float h = (float)v;
+        if (isnan(v)) h = __uint_as_float(0x7fffffffu);
+        val[slot] = (Tst)h;
+        lo[slot] = isfinite(v) ? (float)(v - (double)h) : 0.f;
+    } else {
+        Tst s = (Tst)v;
+        if (isnan(v)) s = (Tst)__longlong_as_double(0x7fffffffffffffffll);
+        val[slot] = s;
+    }
+}
+
+template <typename Tout, typename Tst, bool X2, int B>
+__global__ void k_gather(Tout *__restrict__ dense, int nx, int ny, int nz,
+                         const int4 *__restrict__ blocks, int64_t begin, int64_t count,
+                         const Tst *__restrict__ val, const float *__restrict__ lo) {
+    constexpr int B3 = B * B * B;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count * B3) return;
+    const int64_t b = begin + t / B3;
+    const int l = (int)(t % B3);
+    const int4 bc = blocks[b];
+    const int x = bc.x * B + l % B, y = bc.y * B + (l / B) % B, z = bc.z * B + l / (B * B);
+    if (x >= nx || y >= ny || z >= nz) return;
+    const int64_t slot = b * B3 + l;
+    Tst v = val[slot];
+    if (is_sent(v)) return;  // dense output was zeroed
+    double d = (double)v;
+    if (X2) d += (double)lo[slot];
+    dense[((int64_t)z * ny + y) * nx + x] = (Tout)d;
+}
+
+template <int B>
+static sbg_status scatter_gather(sbg_grid g, sbg_state st, int geom, int species, void *ddense,
+                                 int dense_dtype, bool to_state, cudaStream_t s) {
+    const int64_t nx = g->dims[3 * geom], ny = g->dims[3 * geom + 1], nz = g->dims[3 * geom + 2];
+    const int64_t begin = g->geom_begin[geom], count = g->geom_count[geom];
+    if (count == 0) return SBG_OK;
+    const unsigned grid = (unsigned)((count * B * B * B + 255) / 256);
+    void *val = st->val[st->cur][species];
+    float *lo = st->lo[st->cur][species];
+#define SG_LAUNCH(TIN, TST, X2)                                                                   \
+    do {                                                                                         \
+        if (to_state)                                                                            \
+            k_scatter<TIN, TST, X2, B><<<grid, 256, 0, s>>>((const TIN *)ddense, (int)nx, (int)ny, \
+                                                          (int)nz, g->blocks, g->bitmap, begin,  \
+                                                          count, (TST *)val, lo);                \
+        else                                                                                     \
+            k_gather<TIN, TST, X2, B><<<grid, 256, 0, s>>>((TIN *)ddense, (int)nx, (int)ny,       \
+                                                         (int)nz, g->blocks, begin, count,       \
+                                                         (const TST *)val, lo);                  \
+    } while (0)
+    const bool in64 = dense_dtype == SBG_F64;
+    if (st->dtype == SBG_F64) {
+        if (in64) SG_LAUNCH(double, double, false);
+        else SG_LAUNCH(float, double, false);
+    } else if (st->dtype == SBG_F32) {
+        if (in64) SG_LAUNCH(double, float, false);
+        else SG_LAUNCH(float, float, false);
+    } else {
+        if (in64) SG_LAUNCH(double, float, true);
+        else SG_LAUNCH(float, float, true);
+    }
+#undef SG_LAUNCH
+    SBG_LAUNCH_CHECK("state scatter/gather");
+    return SBG_OK;
+}
+
+static sbg_status dense_io(sbg_grid g, sbg_state st, int32_t geom, int32_t species, void *dense,
+                           int32_t dense_dtype, int32_t on_device, bool to_state, void *stream) {
+    if (!g || !st || !dense) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set/get: null pointer");
+    if (st->grid != g) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set/get: state of another grid");
+    if (geom < 0 || geom >= g->n_geoms) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set/get: bad geometry");
+    if (species < 0 || species >= st->ns) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set/get: bad species");
+    if (dense_dtype != SBG_F32 && dense_dtype != SBG_F64)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_state_set/get: dense dtype must be SBG_F32 or SBG_F64");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nvox = g->dims[3 * geom] * g->dims[3 * geom + 1] * g->dims[3 * geom + 2];
+    const size_t bytes = (size_t)nvox * (dense_dtype == SBG_F64 ? 8 : 4);
+    void *ddense = dense;
+    if (!on_device) {
+        SBG_CUDA(cudaMallocAsync(&ddense, bytes, s));
+        if (to_state) SBG_CUDA(cudaMemcpyAsync(ddense, dense, bytes, cudaMemcpyHostToDevice, s));
+    }
+    if (!to_state) SBG_CUDA(cudaMemsetAsync(ddense, 0, bytes, s));
+    sbg_status rc = g->B == 8 ? scatter_gather<8>(g, st, geom, species, ddense, dense_dtype, to_state, s)
+                              : scatter_gather<4>(g, st, geom, species, ddense, dense_dtype, to_state, s);
+    if (!on_device) {
+        if (rc == SBG_OK && !to_state)
+            SBG_CUDA(cudaMemcpyAsync(dense, ddense, bytes, cudaMemcpyDeviceToHost, s));
+        SBG_CUDA(cudaFreeAsync(ddense, s));
+        SBG_CUDA(cudaStreamSynchronize(s));
+    }
+    return rc;
+}
+
+}  // namespace sbg
+
+using namespace sbg;
+
+extern "C" sbg_status sbg_state_create(sbg_grid g, int32_t nspecies, sbg_dtype dtype, sbg_state *out) {
+    if (!g || !out) return fail(SBG_ERR_INVALID_ARG, "sbg_state_create: null pointer");
+    if (nspecies < 1 || nspecies > 2) return fail(SBG_ERR_INVALID_ARG, "sbg_state_create: nspecies must be 1 or 2");
+    if (dtype != SBG_F32 && dtype != SBG_F64 && dtype != SBG_F32X2)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_state_create: bad dtype");
+    *out = nullptr;
+    sbg_state st = new sbg_state_s();
+    st->grid = g;
+    st->ns = nspecies;
+    st->dtype = dtype;
+    st->nslots = g->nb * (int64_t)g->b3();
+    const size_t per = (size_t)st->nslots * st->elem();
+    const size_t perlo = dtype == SBG_F32X2 ? (size_t)st->nslots * 4 : 0;
+    const size_t total = 2 * (size_t)nspecies * (per + perlo);
+    cudaError_t e = cudaMalloc(&st->base, total > 0 ? total : 16);
+    if (e != cudaSuccess) {
+        delete st;
+        return cuda_fail(e, "cudaMalloc (state)");
+    }
+    st->bytes = (int64_t)total;
+    char *p = (char *)st->base;
+    for (int b = 0; b < 2; ++b)
+        for (int s = 0; s < nspecies; ++s) {
+            st->val[b][s] = p;
+            p += per;
+            if (perlo) {
+                st->lo[b][s] = (float *)p;
+                p += perlo;
+            }
+        }
+    // every slot starts as the sentinel until sbg_state_set (0xff.. bytes: a NaN, not the sentinel,
+    // so an unset state is reported as non-finite)
+    e = cudaMemset(st->base, 0xff, total > 0 ? total : 16);
+    if (e != cudaSuccess) {
+        cudaFree(st->base);
+        delete st;
+        return cuda_fail(e, "cudaMemset (state)");
+    }
+    *out = st;
+    return SBG_OK;
+}
+
+extern "C" sbg_status sbg_state_set(sbg_grid g, sbg_state st, int32_t geom, int32_t species,
+                                    const void *dense, int32_t dense_dtype, int32_t on_device,
+                                    void *stream) {
+    return dense_io(g, st, geom, species, const_cast<void *>(dense), dense_dtype, on_device, true, stream);
+}
+
+extern "C" sbg_status sbg_state_get(sbg_grid g, sbg_state st, int32_t geom, int32_t species,
+                                    void *dense, int32_t dense_dtype, int32_t on_device, void *stream) {
+    return dense_io(g, st, geom, species, dense, dense_dtype, on_device, false, stream);
+}
+
+extern "C" sbg_status sbg_state_copy(sbg_state dst, sbg_state src, void *stream) {
+    if (!dst || !src) return fail(SBG_ERR_INVALID_ARG, "sbg_state_copy: null pointer");
+    if (dst->grid != src->grid || dst->dtype != src->dtype || dst->ns != src->ns)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_state_copy: grid, dtype or species differ");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t per = (size_t)src->nslots * src->elem();
+    for (int sp = 0; sp < src->ns; ++sp) {
+        SBG_CUDA(cudaMemcpyAsync(dst->val[dst->cur][sp], src->val[src->cur][sp], per,
+                                 cudaMemcpyDeviceToDevice, s));
+        if (src->dtype == SBG_F32X2)
+            SBG_CUDA(cudaMemcpyAsync(dst->lo[dst->cur][sp], src->lo[src->cur][sp],
+                                     (size_t)src->nslots * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    return SBG_OK;
+}
+
+extern "C" void sbg_state_destroy(sbg_state st) {
+    if (!st) return;
+    if (st->graph) cudaGraphExecDestroy(st->graph);
+    cudaFree(st->base);
+    delete st;
+}

@@ -1,0 +1,410 @@
+// The time step: forward-Euler FTCS of Eq. 1 on the sparse block grid
+// (Sec. 2.3), with the no-flux rule applied inside the stencil (a neighbour
+// outside Omega takes the centre value; Appendix B Listing 6), active voxels
+// of Dirichlet faces held, and the linear bulk/surface reactions of Sec. 3.5.
+//
+// Kernel design (one CTA updates BPC blocks, one thread per voxel):
+//  - each thread loads its own voxel (coalesced: a warp reads 128 contiguous
+//    bytes of one block) and stores it in a shared-memory tile;
+//  - threads on a block face load the one-voxel halo from the face
+//    neighbour (id from the precomputed face table; -1 or an inactive voxel
+//    reads as the sentinel, which the mirror rule replaces by the centre);
+//  - after one barrier every interior neighbour comes from shared memory.
+// The update is one expression per voxel, identical for B = 4 and B = 8, so
+// results do not depend on the block size.
+#include <math.h>
+
+#include <cstring>
+
+#include "sbg_internal.cuh"
+
+namespace sbg {
+
+template <typename R>
+struct StepCoef {
+    R c[2][3];       // D_s / dx_a^2
+    R dt;
+    R decay[2];
+    R k;
+};
+
+struct StepArgs {
+    const void *in[2];
+    void *out[2];
+    const float *in_lo[2];
+    float *out_lo[2];
+    const int4 *blocks;
+    const int32_t *face;     // [nb * 6]
+    const int32_t *wslab;
+    const float *w;
+    const int32_t *gdims;
+    int64_t nb;
+    int held_mask;           // bit f: face f is Dirichlet
+    StepCoef<float> cf;
+    StepCoef<double> cd;
+};
+
+template <typename R> __device__ __forceinline__ const StepCoef<R> &coef(const StepArgs &a);
+template <> __device__ __forceinline__ const StepCoef<float> &coef<float>(const StepArgs &a) { return a.cf; }
+template <> __device__ __forceinline__ const StepCoef<double> &coef<double>(const StepArgs &a) { return a.cd; }
+
+__device__ __forceinline__ bool is_held(int mask, int gx, int gy, int gz, int nx, int ny, int nz) {
+    return ((mask & 1) && gx == 0) || ((mask & 2) && gx == nx - 1) || ((mask & 4) && gy == 0) ||
+           ((mask & 8) && gy == ny - 1) || ((mask & 16) && gz == 0) || ((mask & 32) && gz == nz - 1);
+}
+
+template <typename T>
+__device__ __forceinline__ T mirror(T v, T c) { return is_sent(v) ? c : v; }
+
+// Plain FP32 / FP64 state, NS species, optional reaction (REACT: k_surf != 0).
+template <typename T, int B, int BPC, int NS, bool REACT>
+__global__ void __launch_bounds__(BPC * B * B * B, (sizeof(T) == 8 ? 1024 : 2048) / (BPC * B * B * B))
+k_step(const StepArgs a) {
+    constexpr int B3 = B * B * B;
+    __shared__ T tile[NS][BPC * B3];
+    const int tid = threadIdx.x;
+    const int j = tid / B3;
+    const int l = tid - j * B3;
+    const int64_t b = (int64_t)blockIdx.x * BPC + j;
+    const bool valid = b < a.nb;
+    const int x = l % B, y = (l / B) % B, z = l / (B * B);
+
+    T uc[NS], hxm[NS], hxp[NS], hym[NS], hyp[NS], hzm[NS], hzp[NS];
+    int4 bc = make_int4(0, 0, 0, 0);
+    if (valid) {
+        bc = a.blocks[b];
+        const int32_t *fn = a.face + b * 6;
+        const int nxm = (x == 0) ? fn[0] : -1, nxp = (x == B - 1) ? fn[1] : -1;
+        const int nym = (y == 0) ? fn[2] : -1, nyp = (y == B - 1) ? fn[3] : -1;
+        const int nzm = (z == 0) ? fn[4] : -1, nzp = (z == B - 1) ? fn[5] : -1;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const T *in = (const T *)a.in[s];
+            uc[s] = in[b * B3 + l];
+            tile[s][tid] = uc[s];
+            const T sent = sentinel<T>();
+            hxm[s] = (nxm >= 0) ? in[(int64_t)nxm * B3 + l + (B - 1)] : sent;
+            hxp[s] = (nxp >= 0) ? in[(int64_t)nxp * B3 + l - (B - 1)] : sent;
+            hym[s] = (nym >= 0) ? in[(int64_t)nym * B3 + l + (B - 1) * B] : sent;
+            hyp[s] = (nyp >= 0) ? in[(int64_t)nyp * B3 + l - (B - 1) * B] : sent;
+            hzm[s] = (nzm >= 0) ? in[(int64_t)nzm * B3 + l + (B - 1) * B * B] : sent;
+            hzp[s] = (nzp >= 0) ? in[(int64_t)nzp * B3 + l - (B - 1) * B * B] : sent;
+        }
+    }
+    __syncthreads();
+    if (!valid) return;
+
+    const int nx = a.gdims[bc.w * 4 + 0], ny = a.gdims[bc.w * 4 + 1], nz = a.gdims[bc.w * 4 + 2];
+    const bool held = is_held(a.held_mask, bc.x * B + x, bc.y * B + y, bc.z * B + z, nx, ny, nz);
+    const StepCoef<T> &k = coef<T>(a);
+    T w = T(0);
+    if (REACT) {
+        const int ws = a.wslab[b];
+        if (ws >= 0) w = (T)a.w[(int64_t)ws * B3 + l];
+    }
+    const T transfer = REACT ? k.k * w * uc[0] : T(0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const T u = uc[s];
+        T res = u;
+        if (!is_sent(u) && !held) {
+            const T *t = tile[s] + j * B3;
+            const T xm = mirror(x > 0 ? t[l - 1] : hxm[s], u);
+            const T xp = mirror(x < B - 1 ? t[l + 1] : hxp[s], u);
+            const T ym = mirror(y > 0 ? t[l - B] : hym[s], u);
+            const T yp = mirror(y < B - 1 ? t[l + B] : hyp[s], u);
+            const T zm = mirror(z > 0 ? t[l - B * B] : hzm[s], u);
+            const T zp = mirror(z < B - 1 ? t[l + B * B] : hzp[s], u);
+            const T lap = k.c[s][0] * ((xp - u) - (u - xm)) + k.c[s][1] * ((yp - u) - (u - ym)) +
+                          k.c[s][2] * ((zp - u) - (u - zm));
+            T react = -k.decay[s] * u;
+            if (s == 0) react -= transfer;
+            else react += transfer;
+            res = u + k.dt * (lap + react);
+        }
+        ((T *)a.out[s])[b * B3 + l] = res;
+    }
+}
+
+// Compensated FP32 (value = hi + lo), one species.  The Laplacian is
+// evaluated as (differences of hi) + (differences of lo); the increment is
+// added with an error-free two-sum and renormalised, so increments far below
+// one FP32 ulp of the state accumulate in lo instead of being rounded away.
+template <int B, int BPC, bool REACT>
+__global__ void __launch_bounds__(BPC * B * B * B, 2048 / (BPC * B * B * B))
+k_step_x2(const StepArgs a) {
+    constexpr int B3 = B * B * B;
+    __shared__ float th[BPC * B3];
+    __shared__ float tl[BPC * B3];
+    const int tid = threadIdx.x;
+    const int j = tid / B3;
+    const int l = tid - j * B3;
+    const int64_t b = (int64_t)blockIdx.x * BPC + j;
+    const bool valid = b < a.nb;
+    const int x = l % B, y = (l / B) % B, z = l / (B * B);
+    const float *ih = (const float *)a.in[0];
+    const float *il = a.in_lo[0];
+    float hc = 0.f, lc = 0.f;
+    float h[6], lo6[6];
+    int4 bc = make_int4(0, 0, 0, 0);
+    if (valid) {
+        bc = a.blocks[b];
+        const int32_t *fn = a.face + b * 6;
+        hc = ih[b * B3 + l];
+        lc = il[b * B3 + l];
+        th[tid] = hc;
+        tl[tid] = lc;
+        const int nid[6] = {(x == 0) ? fn[0] : -1,     (x == B - 1) ? fn[1] : -1,
+                            (y == 0) ? fn[2] : -1,     (y == B - 1) ? fn[3] : -1,
+                            (z == 0) ? fn[4] : -1,     (z == B - 1) ? fn[5] : -1};
+        const int off[6] = {B - 1, -(B - 1), (B - 1) * B, -(B - 1) * B, (B - 1) * B * B, -(B - 1) * B * B};
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            if (nid[f] >= 0) {
+                h[f] = ih[(int64_t)nid[f] * B3 + l + off[f]];
+                lo6[f] = il[(int64_t)nid[f] * B3 + l + off[f]];
+            } else {
+                h[f] = sentinel_f32();
+                lo6[f] = 0.f;
+            }
+        }
+    }
+    __syncthreads();
+    if (!valid) return;
+    const int nx = a.gdims[bc.w * 4 + 0], ny = a.gdims[bc.w * 4 + 1], nz = a.gdims[bc.w * 4 + 2];
+    const bool held = is_held(a.held_mask, bc.x * B + x, bc.y * B + y, bc.z * B + z, nx, ny, nz);
+    float rh = hc, rl = lc;
+    if (!is_sent(hc) && !held) {
+        const float *t = th + j * B3;
+        const float *u = tl + j * B3;
+        // neighbour (hi, lo) per direction: -x, +x, -y, +y, -z, +z
+        float nh[6], nl[6];
+        nh[0] = x > 0 ? t[l - 1] : h[0];             nl[0] = x > 0 ? u[l - 1] : lo6[0];
+        nh[1] = x < B - 1 ? t[l + 1] : h[1];         nl[1] = x < B - 1 ? u[l + 1] : lo6[1];
+        nh[2] = y > 0 ? t[l - B] : h[2];             nl[2] = y > 0 ? u[l - B] : lo6[2];
+        nh[3] = y < B - 1 ? t[l + B] : h[3];         nl[3] = y < B - 1 ? u[l + B] : lo6[3];
+        nh[4] = z > 0 ? t[l - B * B] : h[4];         nl[4] = z > 0 ? u[l - B * B] : lo6[4];
+        nh[5] = z < B - 1 ? t[l + B * B] : h[5];     nl[5] = z < B - 1 ? u[l + B * B] : lo6[5];
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+            if (is_sent(nh[f])) {
+                nh[f] = hc;
+                nl[f] = lc;
+            }
+        const StepCoef<float> &k = a.cf;
+        float lap = 0.f;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const float dhi = (nh[2 * ax + 1] - hc) - (hc - nh[2 * ax]);
+            const float dlo = (nl[2 * ax + 1] - lc) - (lc - nl[2 * ax]);
+            lap += k.c[0][ax] * (dhi + dlo);
+        }
+        float react = -k.decay[0] * (hc + lc);
+        if (REACT) {
+            const int ws = a.wslab[b];
+            const float w = ws >= 0 ? a.w[(int64_t)ws * B3 + l] : 0.f;
+            react -= k.k * w * (hc + lc);
+        }
+        const float d = k.dt * (lap + react);
+        // two-sum hc + d = s + e exactly
+        const float s = hc + d;
+        const float bb = s - hc;
+        const float e = (hc - (s - bb)) + (d - bb);
+        const float l2 = lc + e;
+        rh = s + l2;
+        rl = l2 - (rh - s);
+    }
+    ((float *)a.out[0])[b * B3 + l] = rh;
+    a.out_lo[0][b * B3 + l] = rl;
+}
+
+// ---------------------------------------------------------------------------
+static void fill_args(sbg_grid g, sbg_state st, const sbg_params *p, int src, StepArgs &a) {
+    std::memset(&a, 0, sizeof(a));
+    for (int s = 0; s < st->ns; ++s) {
+        a.in[s] = st->val[src][s];
+        a.out[s] = st->val[1 - src][s];
+        a.in_lo[s] = st->lo[src][s];
+        a.out_lo[s] = st->lo[1 - src][s];
+    }
+    a.blocks = g->blocks;
+    a.face = g->face_nbr;
+    a.wslab = g->wslab;
+    a.w = g->w;
+    a.gdims = g->gdims;
+    a.nb = g->nb;
+    a.held_mask = 0;
+    for (int f = 0; f < 6; ++f)
+        if (p->face_type[f] == SBG_FACE_DIRICHLET) a.held_mask |= 1 << f;
+    for (int s = 0; s < 2; ++s) {
+        for (int ax = 0; ax < 3; ++ax) {
+            double c = p->D[s] / (p->dx[ax] * p->dx[ax]);
+            a.cd.c[s][ax] = c;
+            a.cf.c[s][ax] = (float)c;
+        }
+        a.cd.decay[s] = p->decay[s];
+        a.cf.decay[s] = (float)p->decay[s];
+    }
+    a.cd.dt = p->dt;
+    a.cf.dt = (float)p->dt;
+    a.cd.k = p->k_surf;
+    a.cf.k = (float)p->k_surf;
+}
+
+template <typename T, int B, int NS>
+static void launch_plain(const StepArgs &a, bool react, cudaStream_t s) {
+    constexpr int BPC = (B == 8) ? 1 : 8;
+    const unsigned grid = (unsigned)((a.nb + BPC - 1) / BPC);
+    if (react) k_step<T, B, BPC, NS, true><<<grid, BPC * B * B * B, 0, s>>>(a);
+    else k_step<T, B, BPC, NS, false><<<grid, BPC * B * B * B, 0, s>>>(a);
+}
+
+template <int B>
+static void launch_x2(const StepArgs &a, bool react, cudaStream_t s) {
+    constexpr int BPC = (B == 8) ? 1 : 8;
+    const unsigned grid = (unsigned)((a.nb + BPC - 1) / BPC);
+    if (react) k_step_x2<B, BPC, true><<<grid, BPC * B * B * B, 0, s>>>(a);
+    else k_step_x2<B, BPC, false><<<grid, BPC * B * B * B, 0, s>>>(a);
+}
+
+// One step from buffer `src` into 1 - src (no state bookkeeping).
+sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, cudaStream_t s) {
+    if (g->nb == 0) return SBG_OK;
+    StepArgs a;
+    fill_args(g, st, p, src, a);
+    const bool react = p->k_surf != 0.0;
+    if (st->dtype == SBG_F32X2) {
+        if (g->B == 8) launch_x2<8>(a, react, s);
+        else launch_x2<4>(a, react, s);
+    } else if (st->dtype == SBG_F32) {
+        if (g->B == 8) {
+            if (st->ns == 1) launch_plain<float, 8, 1>(a, react, s);
+            else launch_plain<float, 8, 2>(a, react, s);
+        } else {
+            if (st->ns == 1) launch_plain<float, 4, 1>(a, react, s);
+            else launch_plain<float, 4, 2>(a, react, s);
+        }
+    } else {
+        if (g->B == 8) {
+            if (st->ns == 1) launch_plain<double, 8, 1>(a, react, s);
+            else launch_plain<double, 8, 2>(a, react, s);
+        } else {
+            if (st->ns == 1) launch_plain<double, 4, 1>(a, react, s);
+            else launch_plain<double, 4, 2>(a, react, s);
+        }
+    }
+    SBG_LAUNCH_CHECK("step kernel launch");
+    return SBG_OK;
+}
+
+double stability_limit(const sbg_params *p, const int64_t dims[3], double band_eps) {
+    double inv2 = 0.0;
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] > 1) inv2 += 1.0 / (p->dx[a] * p->dx[a]);
+    double lim = INFINITY;
+    for (int s = 0; s < p->nspecies; ++s) {
+        double rate = 2.0 * p->D[s] * inv2 + p->decay[s];
+        if (s == 0 && p->k_surf > 0.0) rate += p->k_surf / band_eps;
+        double l = rate > 0.0 ? 1.0 / rate : INFINITY;
+        if (l < lim) lim = l;
+    }
+    return lim;
+}
+
+sbg_status validate_params(sbg_grid g, const sbg_params *p, int ns) {
+    if (!p) return fail(SBG_ERR_INVALID_ARG, "null params");
+    if (p->nspecies != ns) return fail(SBG_ERR_INVALID_ARG, "params.nspecies differs from the state's");
+    for (int a = 0; a < 3; ++a)
+        if (!(p->dx[a] > 0.0) || !isfinite(p->dx[a])) return fail(SBG_ERR_INVALID_ARG, "dx must be finite and > 0");
+    if (!(p->dt > 0.0) || !isfinite(p->dt)) return fail(SBG_ERR_INVALID_ARG, "dt must be finite and > 0");
+    for (int s = 0; s < ns; ++s)
+        if (!(p->D[s] >= 0.0) || !isfinite(p->D[s]) || !(p->decay[s] >= 0.0) || !isfinite(p->decay[s]))
+            return fail(SBG_ERR_INVALID_ARG, "D and decay must be finite and >= 0");
+    if (!(p->k_surf >= 0.0) || !isfinite(p->k_surf)) return fail(SBG_ERR_INVALID_ARG, "k_surf must be finite and >= 0");
+    for (int f = 0; f < 6; ++f)
+        if (p->face_type[f] != SBG_FACE_NOFLUX && p->face_type[f] != SBG_FACE_DIRICHLET)
+            return fail(SBG_ERR_INVALID_ARG, "face_type must be NOFLUX or DIRICHLET");
+    if (!p->allow_unstable) {
+        for (int i = 0; i < g->n_geoms; ++i) {
+            double lim = stability_limit(p, &g->dims[3 * i], g->band_eps);
+            if (p->dt > lim)
+                return fail(SBG_ERR_UNSTABLE_DT, "dt " + std::to_string(p->dt) + " above the explicit limit " +
+                                                     std::to_string(lim));
+        }
+    }
+    return SBG_OK;
+}
+
+constexpr int64_t kGraphSteps = 64;  // steps per captured graph (even: parity preserved)
+
+static sbg_status ensure_graph(sbg_grid g, sbg_state st, const sbg_params *p) {
+    if (st->graph && st->graph_cur == st->cur && std::memcmp(&st->graph_params, p, sizeof(*p)) == 0)
+        return SBG_OK;
+    if (st->graph) {
+        cudaGraphExecDestroy(st->graph);
+        st->graph = nullptr;
+    }
+    cudaStream_t cs;
+    SBG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    sbg_status rc = SBG_OK;
+    if (e == cudaSuccess) {
+        int src = st->cur;
+        for (int64_t i = 0; i < kGraphSteps && rc == SBG_OK; ++i) {
+            rc = launch_step(g, st, p, src, cs);
+            src = 1 - src;
+        }
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (e == cudaSuccess && rc == SBG_OK) e = cudaGraphInstantiate(&st->graph, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (rc != SBG_OK) return rc;
+    if (e != cudaSuccess) {
+        st->graph = nullptr;
+        return cuda_fail(e, "step graph capture");
+    }
+    st->graph_cur = st->cur;
+    st->graph_params = *p;
+    st->graph_steps = kGraphSteps;
+    return SBG_OK;
+}
+
+sbg_status step_n(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, cudaStream_t s) {
+    int64_t done = 0;
+    if (nsteps >= kGraphSteps && g->nb > 0) {
+        sbg_status rc = ensure_graph(g, st, p);
+        if (rc != SBG_OK) return rc;
+        while (nsteps - done >= kGraphSteps) {
+            SBG_CUDA(cudaGraphLaunch(st->graph, s));
+            done += kGraphSteps;
+        }
+    }
+    for (; done < nsteps; ++done) {
+        sbg_status rc = launch_step(g, st, p, st->cur, s);
+        if (rc != SBG_OK) return rc;
+        st->cur = 1 - st->cur;
+    }
+    return SBG_OK;
+}
+
+}  // namespace sbg
+
+using namespace sbg;
+
+extern "C" double sbg_stability_limit(const sbg_params *p, const int64_t dims[3], double band_eps) {
+    if (!p || !dims) return -1.0;
+    return stability_limit(p, dims, band_eps > 0 ? band_eps : 1.0);
+}
+
+extern "C" sbg_status sbg_step(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, void *stream) {
+    if (!g || !st || !p) return fail(SBG_ERR_INVALID_ARG, "sbg_step: null pointer");
+    if (st->grid != g) return fail(SBG_ERR_INVALID_ARG, "sbg_step: state of another grid");
+    if (nsteps < 0) return fail(SBG_ERR_INVALID_ARG, "sbg_step: nsteps < 0");
+    if (st->dtype == SBG_F32X2 && st->ns != 1)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_step: SBG_F32X2 states hold one species");
+    sbg_status rc = validate_params(g, p, st->ns);
+    if (rc != SBG_OK) return rc;
+    return step_n(g, st, p, nsteps, (cudaStream_t)stream);
+}

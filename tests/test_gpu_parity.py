@@ -1,0 +1,212 @@
+"""Parity of the CUDA path with the FP64 oracle, element by element, on small
+seeded inputs that span several blocks and ragged box edges, plus the
+invariances the block layout must respect.  Every call goes through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import Physics, channel_phi, random_blob_phi, spheres64
+from workloads.configs import initial_with_faces
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2304_11165_b300 import Grid, SbgError, State, make_params  # noqa: E402
+from paper_2304_11165_b300 import _abi  # noqa: E402
+
+
+def dirich(*faces, values=None):
+    d = [False] * 6
+    v = [0.0] * 6
+    for i, f in enumerate(faces):
+        d[f] = True
+        if values is not None:
+            v[f] = values[i]
+    return tuple(d), tuple(v)
+
+
+def gpu_run(phi, phys, u0, nsteps, block=8, dtype="f64"):
+    g = Grid(phi, block=block)
+    st = State(g, phys.nspecies, dtype)
+    st.set_all(u0)
+    st.step(make_params(phys), nsteps)
+    out = st.get_all()
+    return out, g, st
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+CASES = [
+    # dims, block, nspecies, k, dirichlet faces
+    ((13, 11, 9), 4, 1, 0.0, (0,)),
+    ((21, 13, 10), 8, 1, 0.0, (0, 1)),
+    ((17, 19, 12), 8, 2, 0.6, (3,)),
+    ((24, 16, 16), 4, 2, 0.6, ()),
+    ((9, 8, 33), 8, 1, 0.3, (5,)),
+]
+
+
+def make_case(dims, ns, k, faces, seed):
+    phi = random_blob_phi(dims, seed, porosity=0.55, ell=1.7)
+    phi = np.where(phi > 0, phi * 0.7, phi).astype(np.float32)
+    d, v = dirich(*faces, values=[1.0] * len(faces))
+    phys = Physics(dims=dims, dt=0.05, nspecies=ns, D=(1.0, 0.45), decay=(0.01, 0.2), k_surf=k,
+                   dx=(1.0, 0.9, 1.1), dirichlet=d, face_value=v)
+    rng = np.random.default_rng(seed)
+    u0 = rng.uniform(0, 1, size=(ns,) + phi.shape)
+    return phi, phys, u0
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_grid_tables_match_brute_force(case):
+    dims, block, ns, k, faces = CASES[case]
+    phi, phys, u0 = make_case(dims, ns, k, faces, 100 + case)
+    P = oracle.Problem(phi, phys)
+    g = Grid(phi, block=block)
+    nbr, blocks = g.tables()
+    nx, ny, nz = dims
+    nbx, nby, nbz = [(n + block - 1) // block for n in dims]
+    act = np.zeros((nbz * block, nby * block, nbx * block), bool)
+    act[:nz, :ny, :nx] = P.active > 0
+    occ = act.reshape(nbz, block, nby, block, nbx, block).any(axis=(1, 3, 5))
+    expect = [(bx, by, bz) for bz in range(nbz) for by in range(nby) for bx in range(nbx) if occ[bz, by, bx]]
+    assert [tuple(b[:3]) for b in blocks] == expect
+    assert g.n_active == int(P.active.sum())
+    index = {c: i for i, c in enumerate(expect)}
+    offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy, dz) != (0, 0, 0)]
+    for i, (bx, by, bz) in enumerate(expect):
+        for kk, (dx, dy, dz) in enumerate(offs):
+            assert nbr[i, kk] == index.get((bx + dx, by + dy, bz + dz), -1)
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_fp64_steps_match_oracle(case):
+    dims, block, ns, k, faces = CASES[case]
+    phi, phys, u0 = make_case(dims, ns, k, faces, 200 + case)
+    P = oracle.Problem(phi, phys)
+    ref = P.run(u0, 40)
+    out, _, _ = gpu_run(phi, phys, u0, 40, block=block, dtype="f64")
+    assert rel_err(out, ref) < 1e-13
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_fp32_steps_match_oracle(case):
+    dims, block, ns, k, faces = CASES[case]
+    phi, phys, u0 = make_case(dims, ns, k, faces, 300 + case)
+    P = oracle.Problem(phi, phys)
+    ref = P.run(u0, 300)
+    out, _, _ = gpu_run(phi, phys, u0, 300, block=block, dtype="f32")
+    assert rel_err(out, ref) < 1e-5
+
+
+def test_block_size_and_graph_path_are_bitwise_identical():
+    phi, phys, u0 = make_case((30, 27, 22), 2, 0.5, (0,), 7)
+    a, _, _ = gpu_run(phi, phys, u0, 130, block=4, dtype="f32")
+    b, _, _ = gpu_run(phi, phys, u0, 130, block=8, dtype="f32")
+    np.testing.assert_array_equal(a, b)
+    # 130 steps = two captured 64-step graphs + 2 single launches; compare with 130 single launches
+    g = Grid(phi, block=8)
+    st = State(g, 2, "f32").set_all(u0)
+    p = make_params(phys)
+    for _ in range(130):
+        st.step(p, 1)
+    np.testing.assert_array_equal(st.get_all(), b)
+
+
+def test_translation_invariance_bitwise():
+    dims = (20, 18, 14)
+    phi, phys, u0 = make_case(dims, 1, 0.0, (), 8)
+    pad = np.full((14 + 10, 18 + 6, 20 + 5), -3.0, np.float32)
+    pad[7:21, 3:21, 3:23] = phi
+    up = np.zeros((1,) + pad.shape)
+    up[:, 7:21, 3:21, 3:23] = u0
+    phys2 = Physics(dims=(25, 24, 24), dt=phys.dt, D=phys.D, decay=phys.decay, dx=phys.dx)
+    a, _, _ = gpu_run(phi, phys, u0, 60, block=8, dtype="f32")
+    b, _, _ = gpu_run(pad, phys2, up, 60, block=8, dtype="f32")
+    np.testing.assert_array_equal(a, b[:, 7:21, 3:21, 3:23])
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_reductions_match_oracle(dtype, tol):
+    phi, phys, u0 = make_case((26, 21, 19), 2, 0.4, (0, 1), 9)
+    P = oracle.Problem(phi, phys)
+    ref_u = P.run(u0, 25)
+    ref = P.reduce(ref_u)
+    g = Grid(phi, block=8)
+    st = State(g, 2, dtype).set_all(u0)
+    p = make_params(phys)
+    st.step(p, 25)
+    red = st.reduce(p)
+    for s in range(2):
+        for key in ("mass", "J_in", "J_out", "residual"):
+            assert abs(red[s][key] - ref[s][key]) <= tol * max(abs(ref[s][key]), 1e-3), (s, key)
+        assert red[s]["n_active"] == ref[s]["n_active"]
+        assert red[s]["nonfinite"] == 0
+
+
+def test_spheres64_fp64_matches_oracle():
+    """64^3, 20 spheres, FP64, c = 1 held on x = 0, D = 1, dt = 0.1, 100 steps."""
+    phi, u0, phys = spheres64()
+    P = oracle.Problem(phi, phys)
+    ref = P.run(u0, phys.steps)
+    out, g, st = gpu_run(phi, phys, u0, phys.steps, block=8, dtype="f64")
+    assert rel_err(out, ref) < 1e-13
+    m_ref = P.reduce(ref)[0]["mass"]
+    m = st.reduce(make_params(phys))[0]["mass"]
+    assert abs(m - m_ref) <= 1e-13 * m_ref
+
+
+def test_channel_steady_state_gives_exact_deff():
+    dims = (40, 12, 12)
+    phi = channel_phi(dims, (3, 8), (4, 9))
+    d, v = dirich(0, 1, values=[1.0, 0.0])
+    phys = Physics(dims=dims, dt=0.15, D=(1.0, 0.0), dirichlet=d, face_value=v)
+    u0 = initial_with_faces(dims, 0.0, phys)
+    g = Grid(phi, block=8)
+    st = State(g, 1, "f32x2").set(u0)
+    p = make_params(phys)
+    steps, rel = st.run_to_steady(p, 1e-10, check_every=500)
+    d_eff, tau, psi = st.effective_D(p)
+    assert abs(psi - 25 / 144) < 1e-15
+    assert abs(d_eff - psi) < 1e-6 * psi
+    assert abs(tau - 1.0) < 1e-6
+
+
+def test_unstable_dt_is_rejected_and_nan_is_reported():
+    phi, phys, u0 = make_case((16, 16, 16), 1, 0.0, (0,), 10)
+    g = Grid(phi, block=8)
+    st = State(g, 1, "f32").set_all(u0)
+    p = make_params(phys, dt=1.0)
+    with pytest.raises(SbgError) as e:
+        st.step(p, 1)
+    assert e.value.status == _abi.SBG_ERR_UNSTABLE_DT
+    u_bad = u0.copy()
+    P = oracle.Problem(phi, phys)
+    z, y, x = np.argwhere((P.active > 0) & (P.fixed == 0))[0]
+    u_bad[0, z, y, x] = np.nan
+    st.set_all(u_bad)
+    p = make_params(phys)
+    assert st.reduce(p)[0]["nonfinite"] == 1
+    with pytest.raises(SbgError) as e:
+        st.run_to_steady(p, 1e-6, check_every=10, max_steps=100)
+    assert e.value.status == _abi.SBG_ERR_NONFINITE
+
+
+def test_empty_and_full_geometries():
+    phys = Physics(dims=(10, 9, 8), dt=0.1)
+    g = Grid(np.full((8, 9, 10), -1.0, np.float32), block=8)
+    assert g.n_blocks == 0 and g.n_active == 0
+    st = State(g, 1, "f32")
+    st.step(make_params(phys), 3)
+    assert st.reduce(make_params(phys))[0]["n_active"] == 0
+    assert np.all(st.get() == 0)
+    full = np.full((8, 9, 10), 2.0, np.float32)
+    u0 = np.random.default_rng(0).uniform(size=(8, 9, 10))
+    ref = oracle.Problem(full, phys).run(u0, 20)
+    out, _, _ = gpu_run(full, phys, u0[None], 20, block=4, dtype="f64")
+    assert rel_err(out, ref) < 1e-13

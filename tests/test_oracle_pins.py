@@ -290,7 +290,7 @@ def test_cg_equals_time_stepping_steady_state():
 
 
 def test_tau_orientation_matches_paper_example():
-    """tau = D / D_eff,intrinsic (Eq. 100-102); the paper's 1.0 / 0.55 = 1.82."""
+    """tau = D / D_eff,intrinsic (Eq. 2); the paper's 1.0 / 0.55 = 1.82."""
     g = GOLDEN["tortuosity_caco3"]
     dims = np.array([11, 4, 5])
     psi = 0.4

@@ -13,7 +13,7 @@ Each workload is named by what it is:
 
 Face numbering: 0 = x-low, 1 = x-high, 2 = y-low, 3 = y-high, 4 = z-low, 5 = z-high.
 Time steps are given as numbers; each one is 0.9 x the explicit limit
-1 / (2 max_s D_s sum_a dx_a^-2 + max rate) (the 3-D form of Eq. 238-240 with the
+1 / (2 max_s D_s sum_a dx_a^-2 + max rate) (the 3-D form of Eq. 10 with the
 largest linear sink rate added), and the tests check them against both
 implementations' limit functions.
 """
