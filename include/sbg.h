@@ -170,6 +170,17 @@ sbg_status sbg_state_set(sbg_grid grid, sbg_state state, int32_t geom, int32_t s
 sbg_status sbg_state_get(sbg_grid grid, sbg_state state, int32_t geom, int32_t species,
                          void *dense, int32_t dense_dtype, int32_t on_device, void *stream);
 
+/* Step-kernel choice for a state (this library's tuning knob; no
+ * counterpart in the paper).  variant: SBG_KERNEL_AUTO (pipelined kernel
+ * where it exists, else the one-thread-per-voxel kernel), SBG_KERNEL_PLAIN
+ * (one thread per voxel, block tile in shared memory, one launch-sized grid)
+ * or SBG_KERNEL_PIPELINED (persistent CTAs streaming 512-voxel groups
+ * through a bulk-copy ring; FP32 and SBG_F32X2 states only).  ctas_per_sm:
+ * persistent CTAs per SM for the pipelined kernel (0 = as many as fit).
+ * Results are bitwise identical across variants. */
+enum { SBG_KERNEL_AUTO = 0, SBG_KERNEL_PLAIN = 1, SBG_KERNEL_PIPELINED = 2 };
+sbg_status sbg_state_set_kernel(sbg_state state, int32_t variant, int32_t ctas_per_sm);
+
 /* Copies all species of `src` into `dst` (same grid, dtype and species). */
 sbg_status sbg_state_copy(sbg_state dst, sbg_state src, void *stream);
 

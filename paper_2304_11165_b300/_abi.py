@@ -22,6 +22,7 @@ SBG_ERR_NOT_CONVERGED = 7
 
 SBG_F32, SBG_F64, SBG_F32X2 = 0, 1, 2
 SBG_FACE_NOFLUX, SBG_FACE_DIRICHLET = 0, 1
+SBG_KERNEL_AUTO, SBG_KERNEL_PLAIN, SBG_KERNEL_PIPELINED = 0, 1, 2
 
 RED_MASS, RED_JIN, RED_JOUT, RED_RESIDUAL, RED_MIN, RED_MAX, RED_NONFINITE, RED_NACTIVE = range(8)
 NRED = 8
@@ -63,6 +64,7 @@ SIGNATURES = [
     ("sbg_state_set", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p]),
     ("sbg_state_get", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p]),
     ("sbg_state_copy", c_int32, [c_void_p, c_void_p, c_void_p]),
+    ("sbg_state_set_kernel", c_int32, [c_void_p, c_int32, c_int32]),
     ("sbg_state_destroy", None, [c_void_p]),
     ("sbg_step", c_int32, [c_void_p, c_void_p, ctypes.POINTER(Params), c_int64, c_void_p]),
     ("sbg_stability_limit", c_double, [ctypes.POINTER(Params), c_void_p, c_double]),

@@ -214,6 +214,12 @@ class State:
     def get_all(self, geom: int = 0):
         return np.stack([self.get(s, geom) for s in range(self.nspecies)])
 
+    def set_kernel(self, variant: str = "auto", ctas_per_sm: int = 0):
+        code = {"auto": _abi.SBG_KERNEL_AUTO, "plain": _abi.SBG_KERNEL_PLAIN,
+                "pipelined": _abi.SBG_KERNEL_PIPELINED}[variant]
+        check(self._lib.sbg_state_set_kernel(self.handle, code, int(ctas_per_sm)))
+        return self
+
     def copy_from(self, other: "State", stream=None):
         check(self._lib.sbg_state_copy(self.handle, other.handle, _stream_handle(stream)))
         return self

@@ -208,7 +208,8 @@ __global__ void k_block_fill(const float *__restrict__ phi, int nx, int ny, int 
 template <int B>
 __global__ void k_fill_w(const float *__restrict__ phi, int nx, int ny, int nz,
                          const int4 *__restrict__ blocks, int64_t begin, int64_t count,
-                         const int32_t *__restrict__ wslab, float eps, double band_eps, float *w) {
+                         const int32_t *__restrict__ wslab, float eps, double band_eps, float *w,
+                         double *w64) {
     constexpr int B3 = B * B * B;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count * B3) return;
@@ -218,15 +219,16 @@ __global__ void k_fill_w(const float *__restrict__ phi, int nx, int ny, int nz,
     if (ws < 0) return;
     const int4 bc = blocks[b];
     int x = bc.x * B + l % B, y = bc.y * B + (l / B) % B, z = bc.z * B + l / (B * B);
-    float val = 0.f;
+    double val = 0.0;
     if (x < nx && y < ny && z < nz) {
         float p = phi[((int64_t)z * ny + y) * nx + x];
         if (p > eps && (double)p < band_eps) {
             const double pi = 3.14159265358979323846;
-            val = (float)((1.0 + cos(pi * (double)p / band_eps)) / (2.0 * band_eps));
+            val = (1.0 + cos(pi * (double)p / band_eps)) / (2.0 * band_eps);
         }
     }
-    w[(int64_t)ws * B3 + l] = val;
+    w[(int64_t)ws * B3 + l] = (float)val;
+    w64[(int64_t)ws * B3 + l] = val;
 }
 
 // wslab[b] = band[b] ? position among band blocks : -1
@@ -328,10 +330,13 @@ static void grid_free(sbg_grid g) {
     cudaFree(g->bitmap);
     cudaFree(g->wslab);
     cudaFree(g->w);
+    cudaFree(g->w64);
     cudaFree(g->gdims);
     cudaFree(g->partials);
     cudaFree(g->red_dev);
     cudaFreeHost(g->red_host);
+    cudaFree(g->err);
+    cudaFreeHost(g->err_host);
     delete g;
 }
 
@@ -413,6 +418,9 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
     TRY(dalloc(g, &g->partials, (size_t)kRedMaxCtas * kNumRed));
     TRY(dalloc(g, &g->red_dev, (size_t)kNumRed));
     TRYC(cudaMallocHost(&g->red_host, sizeof(double) * kNumRed));
+    TRY(dalloc(g, &g->err, 1));
+    TRYC(cudaMemsetAsync(g->err, 0, sizeof(int), st));
+    TRYC(cudaMallocHost(&g->err_host, sizeof(int)));
     TRYC(cudaMalloc(&band, sizeof(int32_t) * std::max<int64_t>(total, 1)));
     TRYC(cudaMalloc(&nact, sizeof(int32_t) * std::max<int64_t>(total, 1)));
     TRYC(cudaMalloc(&wpos, sizeof(int32_t) * std::max<int64_t>(total, 1)));
@@ -459,6 +467,7 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
     TRY(exclusive_scan(band, total, true, wpos, &nband, st));
     g->n_band = nband;
     TRY(dalloc(g, &g->w, (size_t)nband * B3));
+    TRY(dalloc(g, &g->w64, (size_t)nband * B3));
     if (total > 0)
         k_select_slab<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(band, wpos, total, g->wslab);
     for (int i = 0; i < n; ++i) {
@@ -466,7 +475,7 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
         const int64_t nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
         k_fill_w<B><<<(unsigned)((g->geom_count[i] * B3 + 255) / 256), 256, 0, st>>>(
             dphi[i], (int)nx, (int)ny, (int)nz, g->blocks, g->geom_begin[i], g->geom_count[i],
-            g->wslab, g->eps_mask, (double)g->band_eps, g->w);
+            g->wslab, g->eps_mask, (double)g->band_eps, g->w, g->w64);
     }
 
     // hash and neighbour table

@@ -96,10 +96,13 @@ struct sbg_grid_s {
     uint64_t *bitmap = nullptr;    // [nb * words]
     int32_t *wslab = nullptr;      // [nb] slab index or -1
     float *w = nullptr;            // [n_band * B^3]
+    double *w64 = nullptr;         // same weights in FP64 (FP64 states and the reductions)
     int32_t *gdims = nullptr;      // [n_geoms * 4]: nx, ny, nz, 0
     double *partials = nullptr;    // reduction scratch [kRedMaxCtas * kNumRed]
     double *red_dev = nullptr;     // [kNumRed]
     double *red_host = nullptr;    // pinned [kNumRed]
+    int *err = nullptr;            // device error word written by bounded waits (0 = none)
+    int *err_host = nullptr;       // pinned copy
     int64_t bytes = 0;
     int words() const { return (B * B * B + 63) / 64; }
     int b3() const { return B * B * B; }
@@ -121,10 +124,15 @@ struct sbg_state_s {
     int64_t graph_steps = 0;
     sbg_params graph_params{};
     int graph_variant = -1;
+    int graph_ctas = -1;
+    int variant = SBG_KERNEL_AUTO;  // step kernel choice (sbg_state_set_kernel)
+    int ctas_per_sm = 0;
     size_t elem() const { return dtype == SBG_F64 ? 8 : 4; }
 };
 
 namespace sbg {
+// implemented in sbg_reduce.cu: reads and clears the grid's device error word
+sbg_status check_device_error(sbg_grid g, cudaStream_t s);
 // implemented in sbg_step.cu
 sbg_status validate_params(sbg_grid g, const sbg_params *p, int ns);
 // implemented in sbg_reduce.cu

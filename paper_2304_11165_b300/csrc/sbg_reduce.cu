@@ -25,7 +25,7 @@ struct RedArgs {
     const int4 *blocks;
     const int32_t *face;
     const int32_t *wslab;
-    const float *w;
+    const double *w;
     const int32_t *gdims;
     int64_t b_begin, b_count;
     int species, ns, held_mask;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const RedArgs a) {
             double react = -a.decay * v;
             if (a.k != 0.0) {
                 const int ws = a.wslab[b];
-                const double w = ws >= 0 ? (double)a.w[(int64_t)ws * B3 + l] : 0.0;
+                const double w = ws >= 0 ? a.w[(int64_t)ws * B3 + l] : 0.0;
                 bool act0;
                 const double ua = (s == 0) ? v : load_val<T, X2>(a, 0, b * B3 + l, act0);
                 const double tr = a.k * w * ua;
@@ -212,7 +212,7 @@ sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geo
     a.blocks = g->blocks;
     a.face = g->face_nbr;
     a.wslab = g->wslab;
-    a.w = g->w;
+    a.w = g->w64;
     a.gdims = g->gdims;
     a.b_begin = geom < 0 ? 0 : g->geom_begin[geom];
     a.b_count = geom < 0 ? g->nb : g->geom_count[geom];
@@ -246,6 +246,18 @@ sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geo
     SBG_CUDA(cudaMemcpyAsync(g->red_host, g->red_dev, sizeof(double) * kNumRed, cudaMemcpyDeviceToHost, s));
     SBG_CUDA(cudaStreamSynchronize(s));
     std::memcpy(out_host, g->red_host, sizeof(double) * kNumRed);
+    return check_device_error(g, s);
+}
+
+sbg_status check_device_error(sbg_grid g, cudaStream_t s) {
+    SBG_CUDA(cudaMemcpyAsync(g->err_host, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SBG_CUDA(cudaStreamSynchronize(s));
+    if (*g->err_host != 0) {
+        const int code = *g->err_host;
+        SBG_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+        SBG_CUDA(cudaStreamSynchronize(s));
+        return fail((sbg_status)code, "a step kernel gave up a bounded wait (device error word set)");
+    }
     return SBG_OK;
 }
 

@@ -17,44 +17,9 @@
 #include <cstring>
 
 #include "sbg_internal.cuh"
+#include "sbg_step.cuh"
 
 namespace sbg {
-
-template <typename R>
-struct StepCoef {
-    R c[2][3];       // D_s / dx_a^2
-    R dt;
-    R decay[2];
-    R k;
-};
-
-struct StepArgs {
-    const void *in[2];
-    void *out[2];
-    const float *in_lo[2];
-    float *out_lo[2];
-    const int4 *blocks;
-    const int32_t *face;     // [nb * 6]
-    const int32_t *wslab;
-    const float *w;
-    const int32_t *gdims;
-    int64_t nb;
-    int held_mask;           // bit f: face f is Dirichlet
-    StepCoef<float> cf;
-    StepCoef<double> cd;
-};
-
-template <typename R> __device__ __forceinline__ const StepCoef<R> &coef(const StepArgs &a);
-template <> __device__ __forceinline__ const StepCoef<float> &coef<float>(const StepArgs &a) { return a.cf; }
-template <> __device__ __forceinline__ const StepCoef<double> &coef<double>(const StepArgs &a) { return a.cd; }
-
-__device__ __forceinline__ bool is_held(int mask, int gx, int gy, int gz, int nx, int ny, int nz) {
-    return ((mask & 1) && gx == 0) || ((mask & 2) && gx == nx - 1) || ((mask & 4) && gy == 0) ||
-           ((mask & 8) && gy == ny - 1) || ((mask & 16) && gz == 0) || ((mask & 32) && gz == nz - 1);
-}
-
-template <typename T>
-__device__ __forceinline__ T mirror(T v, T c) { return is_sent(v) ? c : v; }
 
 // Plain FP32 / FP64 state, NS species, optional reaction (REACT: k_surf != 0).
 template <typename T, int B, int BPC, int NS, bool REACT>
@@ -100,7 +65,7 @@ k_step(const StepArgs a) {
     T w = T(0);
     if (REACT) {
         const int ws = a.wslab[b];
-        if (ws >= 0) w = (T)a.w[(int64_t)ws * B3 + l];
+        if (ws >= 0) w = sizeof(T) == 8 ? (T)a.w64[(int64_t)ws * B3 + l] : (T)a.w[(int64_t)ws * B3 + l];
     }
     const T transfer = REACT ? k.k * w * uc[0] : T(0);
 #pragma unroll
@@ -115,12 +80,8 @@ k_step(const StepArgs a) {
             const T yp = mirror(y < B - 1 ? t[l + B] : hyp[s], u);
             const T zm = mirror(z > 0 ? t[l - B * B] : hzm[s], u);
             const T zp = mirror(z < B - 1 ? t[l + B * B] : hzp[s], u);
-            const T lap = k.c[s][0] * ((xp - u) - (u - xm)) + k.c[s][1] * ((yp - u) - (u - ym)) +
-                          k.c[s][2] * ((zp - u) - (u - zm));
-            T react = -k.decay[s] * u;
-            if (s == 0) react -= transfer;
-            else react += transfer;
-            res = u + k.dt * (lap + react);
+            res = fused_update(u, xm, xp, ym, yp, zm, zp, k.c[s], k.dt, k.decay[s],
+                               s == 0 ? -transfer : transfer);
         }
         ((T *)a.out[s])[b * B3 + l] = res;
     }
@@ -192,27 +153,12 @@ k_step_x2(const StepArgs a) {
                 nl[f] = lc;
             }
         const StepCoef<float> &k = a.cf;
-        float lap = 0.f;
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            const float dhi = (nh[2 * ax + 1] - hc) - (hc - nh[2 * ax]);
-            const float dlo = (nl[2 * ax + 1] - lc) - (lc - nl[2 * ax]);
-            lap += k.c[0][ax] * (dhi + dlo);
-        }
-        float react = -k.decay[0] * (hc + lc);
+        float rate = k.decay[0];
         if (REACT) {
             const int ws = a.wslab[b];
-            const float w = ws >= 0 ? a.w[(int64_t)ws * B3 + l] : 0.f;
-            react -= k.k * w * (hc + lc);
+            rate = __fmaf_rn(k.k, ws >= 0 ? a.w[(int64_t)ws * B3 + l] : 0.f, rate);
         }
-        const float d = k.dt * (lap + react);
-        // two-sum hc + d = s + e exactly
-        const float s = hc + d;
-        const float bb = s - hc;
-        const float e = (hc - (s - bb)) + (d - bb);
-        const float l2 = lc + e;
-        rh = s + l2;
-        rl = l2 - (rh - s);
+        fused_update_x2(hc, lc, nh, nl, k.c[0], k.dt, rate, rh, rl);
     }
     ((float *)a.out[0])[b * B3 + l] = rh;
     a.out_lo[0][b * B3 + l] = rl;
@@ -231,6 +177,7 @@ static void fill_args(sbg_grid g, sbg_state st, const sbg_params *p, int src, St
     a.face = g->face_nbr;
     a.wslab = g->wslab;
     a.w = g->w;
+    a.w64 = g->w64;
     a.gdims = g->gdims;
     a.nb = g->nb;
     a.held_mask = 0;
@@ -273,6 +220,15 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
     StepArgs a;
     fill_args(g, st, p, src, a);
     const bool react = p->k_surf != 0.0;
+    if (st->variant != SBG_KERNEL_PLAIN) {
+        cudaError_t e = cudaSuccess;
+        if (launch_step_pipe(a, st->dtype, st->ns, g->B, react, st->ctas_per_sm, g->err, s, &e)) {
+            if (e != cudaSuccess) return cuda_fail(e, "pipelined step kernel launch");
+            return SBG_OK;
+        }
+        if (st->variant == SBG_KERNEL_PIPELINED)
+            return fail(SBG_ERR_INVALID_ARG, "the pipelined kernel handles FP32 and SBG_F32X2 states only");
+    }
     if (st->dtype == SBG_F32X2) {
         if (g->B == 8) launch_x2<8>(a, react, s);
         else launch_x2<4>(a, react, s);
@@ -338,7 +294,8 @@ sbg_status validate_params(sbg_grid g, const sbg_params *p, int ns) {
 constexpr int64_t kGraphSteps = 64;  // steps per captured graph (even: parity preserved)
 
 static sbg_status ensure_graph(sbg_grid g, sbg_state st, const sbg_params *p) {
-    if (st->graph && st->graph_cur == st->cur && std::memcmp(&st->graph_params, p, sizeof(*p)) == 0)
+    if (st->graph && st->graph_cur == st->cur && st->graph_variant == st->variant &&
+        st->graph_ctas == st->ctas_per_sm && std::memcmp(&st->graph_params, p, sizeof(*p)) == 0)
         return SBG_OK;
     if (st->graph) {
         cudaGraphExecDestroy(st->graph);
@@ -366,6 +323,8 @@ static sbg_status ensure_graph(sbg_grid g, sbg_state st, const sbg_params *p) {
         return cuda_fail(e, "step graph capture");
     }
     st->graph_cur = st->cur;
+    st->graph_variant = st->variant;
+    st->graph_ctas = st->ctas_per_sm;
     st->graph_params = *p;
     st->graph_steps = kGraphSteps;
     return SBG_OK;
@@ -407,4 +366,15 @@ extern "C" sbg_status sbg_step(sbg_grid g, sbg_state st, const sbg_params *p, in
     sbg_status rc = validate_params(g, p, st->ns);
     if (rc != SBG_OK) return rc;
     return step_n(g, st, p, nsteps, (cudaStream_t)stream);
+}
+
+extern "C" sbg_status sbg_state_set_kernel(sbg_state st, int32_t variant, int32_t ctas_per_sm) {
+    if (!st) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: null state");
+    if (variant < SBG_KERNEL_AUTO || variant > SBG_KERNEL_PIPELINED || ctas_per_sm < 0 || ctas_per_sm > 64)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: bad variant or ctas_per_sm");
+    if (variant == SBG_KERNEL_PIPELINED && st->dtype == SBG_F64)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: no pipelined kernel for FP64 states");
+    st->variant = variant;
+    st->ctas_per_sm = ctas_per_sm;
+    return SBG_OK;
 }

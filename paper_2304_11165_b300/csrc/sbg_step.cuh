@@ -1,0 +1,99 @@
+// Arguments and per-voxel helpers shared by the step kernels.
+#pragma once
+#include "sbg_internal.cuh"
+
+namespace sbg {
+
+template <typename R>
+struct StepCoef {
+    R c[2][3];       // D_s / dx_a^2
+    R dt;
+    R decay[2];
+    R k;
+};
+
+struct StepArgs {
+    const void *in[2];
+    void *out[2];
+    const float *in_lo[2];
+    float *out_lo[2];
+    const int4 *blocks;
+    const int32_t *face;     // [nb * 6]
+    const int32_t *wslab;
+    const float *w;
+    const double *w64;
+    const int32_t *gdims;
+    int64_t nb;
+    int held_mask;           // bit f: face f is Dirichlet
+    StepCoef<float> cf;
+    StepCoef<double> cd;
+};
+
+template <typename R> __device__ __forceinline__ const StepCoef<R> &coef(const StepArgs &a);
+template <> __device__ __forceinline__ const StepCoef<float> &coef<float>(const StepArgs &a) { return a.cf; }
+template <> __device__ __forceinline__ const StepCoef<double> &coef<double>(const StepArgs &a) { return a.cd; }
+
+__device__ __forceinline__ bool is_held(int mask, int gx, int gy, int gz, int nx, int ny, int nz) {
+    return ((mask & 1) && gx == 0) || ((mask & 2) && gx == nx - 1) || ((mask & 4) && gy == 0) ||
+           ((mask & 8) && gy == ny - 1) || ((mask & 16) && gz == 0) || ((mask & 32) && gz == nz - 1);
+}
+
+template <typename T>
+__device__ __forceinline__ T mirror(T v, T c) { return is_sent(v) ? c : v; }
+
+// The per-voxel FTCS update with the rounding of every operation pinned
+// (explicit _rn intrinsics), so that all step kernels produce bitwise the
+// same value for the same neighbourhood whatever their data movement:
+//   u' = u + dt ( sum_a c_a [(u_{+a} - u) - (u - u_{-a})] - decay u + t )
+// with t = -k w u_A for species A and +k w u_A for species B.
+__device__ __forceinline__ float fused_update(float u, float xm, float xp, float ym, float yp, float zm,
+                                              float zp, const float c[3], float dt, float decay,
+                                              float t) {
+    const float dx = __fsub_rn(__fsub_rn(xp, u), __fsub_rn(u, xm));
+    const float dy = __fsub_rn(__fsub_rn(yp, u), __fsub_rn(u, ym));
+    const float dz = __fsub_rn(__fsub_rn(zp, u), __fsub_rn(u, zm));
+    const float lap = __fmaf_rn(c[2], dz, __fmaf_rn(c[1], dy, __fmul_rn(c[0], dx)));
+    const float react = __fmaf_rn(-decay, u, t);
+    return __fmaf_rn(dt, __fadd_rn(lap, react), u);
+}
+__device__ __forceinline__ double fused_update(double u, double xm, double xp, double ym, double yp,
+                                               double zm, double zp, const double c[3], double dt,
+                                               double decay, double t) {
+    const double dx = __dsub_rn(__dsub_rn(xp, u), __dsub_rn(u, xm));
+    const double dy = __dsub_rn(__dsub_rn(yp, u), __dsub_rn(u, ym));
+    const double dz = __dsub_rn(__dsub_rn(zp, u), __dsub_rn(u, zm));
+    const double lap = __fma_rn(c[2], dz, __fma_rn(c[1], dy, __dmul_rn(c[0], dx)));
+    const double react = __fma_rn(-decay, u, t);
+    return __fma_rn(dt, __dadd_rn(lap, react), u);
+}
+
+// Compensated update of one voxel: value = hi + lo.  Differences of hi and
+// of lo are formed separately (the hi differences of neighbouring values are
+// exact when they are within a factor 2), the increment d is added to hi
+// with an error-free two-sum, and the pair is renormalised.
+__device__ __forceinline__ void fused_update_x2(float hc, float lc, const float nh[6], const float nl[6],
+                                                const float c[3], float dt, float rate, float &rh,
+                                                float &rl) {
+    float lap = 0.f;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float dhi = __fsub_rn(__fsub_rn(nh[2 * ax + 1], hc), __fsub_rn(hc, nh[2 * ax]));
+        const float dlo = __fsub_rn(__fsub_rn(nl[2 * ax + 1], lc), __fsub_rn(lc, nl[2 * ax]));
+        lap = __fmaf_rn(c[ax], __fadd_rn(dhi, dlo), lap);
+    }
+    const float react = __fmul_rn(-rate, __fadd_rn(hc, lc));
+    const float d = __fmul_rn(dt, __fadd_rn(lap, react));
+    const float s = __fadd_rn(hc, d);
+    const float bb = __fsub_rn(s, hc);
+    const float e = __fadd_rn(__fsub_rn(hc, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+    const float l2 = __fadd_rn(lc, e);
+    rh = __fadd_rn(s, l2);
+    rl = __fsub_rn(l2, __fsub_rn(rh, s));
+}
+
+// Launches the bulk-copy pipelined kernel (FP32 and compensated-FP32
+// states); returns false when the combination is not handled by it.
+bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, int ctas_per_sm,
+                      int *err_flag, cudaStream_t s, cudaError_t *launch_err);
+
+}  // namespace sbg
