@@ -215,6 +215,28 @@ double sbg_stability_limit(const sbg_params *params, const int64_t dims[3], doub
 sbg_status sbg_reduce(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom,
                       double *out, void *stream);
 
+/* The same FP64 reduction for callers that may not allocate device memory
+ * (their memory belongs to another allocator, such as a framework's caching
+ * allocator or a fixed serving arena, or allocation latency is not allowed in
+ * their loop).  No counterpart in the paper.  It calls no cudaMalloc or
+ * cudaFree: the per-CTA partial records live in a fixed 256 KiB device array
+ * inside the library, held on every GPU that loads it until exit.
+ *   species  reduced species (0 or 1);
+ *   out_dev  caller-owned DEVICE buffer of SBG_NRED doubles, same layout as
+ *            one species of sbg_reduce; written in stream order, no host copy
+ *            and no synchronisation (read it after the stream has run);
+ *   limit    the reduced range (one geometry, or all with geom = -1) may hold
+ *            at most 2^28 voxel slots (blocks x B^3); larger ranges return
+ *            SBG_ERR_INVALID_ARG - use sbg_reduce for them.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls whose kernels may overlap on the GPU
+ * (unordered streams) race and must be serialised by the caller.  Unlike
+ * sbg_reduce it does not read the grid's device error word.  Results equal
+ * sbg_reduce's up to the order of the FP64 sums. */
+sbg_status sbg_reduce_noalloc(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom,
+                              int32_t species, double *out_dev, void *stream);
+
 /* Effective diffusivity and diffusive tortuosity (Eq. 2: tau = D / D_eff with
  * the pore-space D_eff) from the x-face fluxes of species 0:
  *   D_eff = J L / (dC A), J = (J_in + J_out) / 2, L = (Nx - 1) dx,

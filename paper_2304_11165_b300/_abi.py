@@ -69,6 +69,8 @@ SIGNATURES = [
     ("sbg_step", c_int32, [c_void_p, c_void_p, ctypes.POINTER(Params), c_int64, c_void_p]),
     ("sbg_stability_limit", c_double, [ctypes.POINTER(Params), c_void_p, c_double]),
     ("sbg_reduce", c_int32, [c_void_p, c_void_p, ctypes.POINTER(Params), c_int32, c_void_p, c_void_p]),
+    ("sbg_reduce_noalloc", c_int32, [c_void_p, c_void_p, ctypes.POINTER(Params), c_int32, c_int32, c_void_p,
+                                     c_void_p]),
     ("sbg_effective_D", c_int32, [c_void_p, c_void_p, ctypes.POINTER(Params), c_int32, c_void_p, c_void_p,
                                   c_void_p, c_void_p]),
     ("sbg_run_to_steady", c_int32, [c_void_p, c_void_p, ctypes.POINTER(Params), c_double, c_int64, c_int64,

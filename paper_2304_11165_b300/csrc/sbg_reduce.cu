@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include <cstring>
+#include <string>
 
 #include "sbg_internal.cuh"
 
@@ -339,5 +340,114 @@ extern "C" sbg_status sbg_run_to_steady(sbg_grid g, sbg_state st, const sbg_para
         if (r[SBG_RED_NONFINITE] > 0) return fail(SBG_ERR_NONFINITE, "sbg_run_to_steady: non-finite value");
     }
     if (rel >= tol) return fail(SBG_ERR_NOT_CONVERGED, "sbg_run_to_steady: max_steps reached");
+    return SBG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Reduction without any allocation.
+//
+// Some callers cannot call cudaMalloc: a serving process whose device memory
+// is owned and budgeted by another allocator (a framework's caching
+// allocator or a fixed arena), or a hot loop where an allocation's latency
+// or its implicit synchronisation is not acceptable.  sbg_reduce_noalloc runs
+// the same FP64 reduction kernels as sbg_reduce, but its per-CTA partial
+// records live in the fixed array below instead of a buffer owned by the
+// grid, and its result goes to a device buffer the caller owns.
+//
+// The array is `kNoAllocRecords` records of SBG_NRED doubles (256 KiB); every
+// GPU that loads this library keeps it until the process exits.  One record
+// covers up to `kNoAllocSlotsPerCta` voxel slots, so one call reduces at most
+// kNoAllocRecords * kNoAllocSlotsPerCta = 2^28 voxel slots (blocks x B^3);
+// larger ranges are rejected.  Each call's first kernel overwrites every
+// record it uses before the second kernel reads it, so nothing needs
+// clearing between calls; but all calls share the array, so two calls whose
+// kernels overlap on the GPU (different streams, no ordering) race.
+namespace sbg {
+
+constexpr int kNoAllocRecords = 4096;
+constexpr int64_t kNoAllocSlotsPerCta = 65536;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocRecords * kNumRed];
+
+// Device address of g_noalloc_partials on the current device.  In host code
+// the symbol is only a host-side stand-in; the kernels need the address that
+// cudaGetSymbolAddress returns.  Looked up on the first call per device.
+static sbg_status noalloc_scratch(double **out) {
+    static double *ptrs[kNoAllocMaxDevices] = {};
+    int dev = 0;
+    SBG_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_reduce_noalloc: device index out of range");
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (no-allocation reduction scratch)");
+        ptrs[dev] = (double *)p;
+    }
+    *out = ptrs[dev];
+    return SBG_OK;
+}
+
+}  // namespace sbg
+
+extern "C" sbg_status sbg_reduce_noalloc(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom,
+                                         int32_t species, double *out_dev, void *stream) {
+    sbg_status rc = check_common(g, st, p, geom);
+    if (rc != SBG_OK) return rc;
+    if (!out_dev) return fail(SBG_ERR_INVALID_ARG, "sbg_reduce_noalloc: null output");
+    if (species < 0 || species >= st->ns) return fail(SBG_ERR_INVALID_ARG, "sbg_reduce_noalloc: bad species");
+    const int64_t b_begin = geom < 0 ? 0 : g->geom_begin[geom];
+    const int64_t b_count = geom < 0 ? g->nb : g->geom_count[geom];
+    const int64_t work = b_count * g->b3();
+    if (work > (int64_t)kNoAllocRecords * kNoAllocSlotsPerCta)
+        return fail(SBG_ERR_INVALID_ARG,
+                    "sbg_reduce_noalloc: " + std::to_string(work) + " voxel slots exceed the limit of " +
+                        std::to_string((int64_t)kNoAllocRecords * kNoAllocSlotsPerCta) +
+                        " (use sbg_reduce for larger grids)");
+    double *scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc != SBG_OK) return rc;
+
+    RedArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int sp = 0; sp < st->ns; ++sp) {
+        a.val[sp] = st->val[st->cur][sp];
+        a.lo[sp] = st->lo[st->cur][sp];
+    }
+    a.blocks = g->blocks;
+    a.face = g->face_nbr;
+    a.wslab = g->wslab;
+    a.w = g->w64;
+    a.gdims = g->gdims;
+    a.b_begin = b_begin;
+    a.b_count = b_count;
+    a.species = species;
+    a.ns = st->ns;
+    for (int f = 0; f < 6; ++f)
+        if (p->face_type[f] == SBG_FACE_DIRICHLET) a.held_mask |= 1 << f;
+    for (int ax = 0; ax < 3; ++ax) a.c[ax] = p->D[species] / (p->dx[ax] * p->dx[ax]);
+    a.D = p->D[species];
+    a.decay = p->decay[species];
+    a.k = p->k_surf;
+    a.inv_dx = 1.0 / p->dx[0];
+    a.area = p->dx[1] * p->dx[2];
+    a.dv = p->dx[0] * p->dx[1] * p->dx[2];
+    a.partials = scratch;
+    int nctas = (int)((work + kNoAllocSlotsPerCta - 1) / kNoAllocSlotsPerCta);
+    if (nctas < 1) nctas = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (st->dtype == SBG_F64) {
+        if (g->B == 8) launch_reduce<double, false, 8>(a, nctas, s);
+        else launch_reduce<double, false, 4>(a, nctas, s);
+    } else if (st->dtype == SBG_F32) {
+        if (g->B == 8) launch_reduce<float, false, 8>(a, nctas, s);
+        else launch_reduce<float, false, 4>(a, nctas, s);
+    } else {
+        if (g->B == 8) launch_reduce<float, true, 8>(a, nctas, s);
+        else launch_reduce<float, true, 4>(a, nctas, s);
+    }
+    k_reduce_final<<<1, 256, 0, s>>>(scratch, nctas, out_dev);
+    SBG_LAUNCH_CHECK("no-allocation reduction launch");
     return SBG_OK;
 }
