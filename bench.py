@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sbg", choices=["sbg", "reference"])
     ap.add_argument("--n", type=int, default=256, help="box side")
-    ap.add_argument("--block", type=int, default=8)
+    ap.add_argument("--block", type=int, default=4)
     ap.add_argument("--dtype", default="f32x2", choices=["f32", "f32x2", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -174,11 +174,13 @@ sbg_status sbg_state_get(sbg_grid grid, sbg_state state, int32_t geom, int32_t s
  * counterpart in the paper).  variant: SBG_KERNEL_AUTO (pipelined kernel
  * where it exists, else the one-thread-per-voxel kernel), SBG_KERNEL_PLAIN
  * (one thread per voxel, block tile in shared memory, one launch-sized grid)
- * or SBG_KERNEL_PIPELINED (persistent CTAs streaming 512-voxel groups
- * through a bulk-copy ring; FP32 and SBG_F32X2 states only).  ctas_per_sm:
+ * SBG_KERNEL_PIPELINED (persistent CTAs streaming 512-voxel groups
+ * through a bulk-copy ring; FP32 and SBG_F32X2 states only) or
+ * SBG_KERNEL_PIPELINED_PREFETCH (the same, with face halos prefetched one
+ * group ahead in registers: fewer CTAs per SM, less exposed latency).  ctas_per_sm:
  * persistent CTAs per SM for the pipelined kernel (0 = as many as fit).
  * Results are bitwise identical across variants. */
-enum { SBG_KERNEL_AUTO = 0, SBG_KERNEL_PLAIN = 1, SBG_KERNEL_PIPELINED = 2 };
+enum { SBG_KERNEL_AUTO = 0, SBG_KERNEL_PLAIN = 1, SBG_KERNEL_PIPELINED = 2, SBG_KERNEL_PIPELINED_PREFETCH = 3 };
 sbg_status sbg_state_set_kernel(sbg_state state, int32_t variant, int32_t ctas_per_sm);
 
 /* Copies all species of `src` into `dst` (same grid, dtype and species). */

@@ -216,7 +216,8 @@ class State:
 
     def set_kernel(self, variant: str = "auto", ctas_per_sm: int = 0):
         code = {"auto": _abi.SBG_KERNEL_AUTO, "plain": _abi.SBG_KERNEL_PLAIN,
-                "pipelined": _abi.SBG_KERNEL_PIPELINED}[variant]
+                "pipelined": _abi.SBG_KERNEL_PIPELINED,
+                "prefetch": _abi.SBG_KERNEL_PIPELINED_PREFETCH}[variant]
         check(self._lib.sbg_state_set_kernel(self.handle, code, int(ctas_per_sm)))
         return self
 

@@ -336,6 +336,7 @@ static void grid_free(sbg_grid g) {
     cudaFree(g->red_dev);
     cudaFreeHost(g->red_host);
     cudaFree(g->err);
+    cudaFree(g->pad);
     cudaFreeHost(g->err_host);
     delete g;
 }
@@ -419,6 +420,11 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
     TRY(dalloc(g, &g->red_dev, (size_t)kNumRed));
     TRYC(cudaMallocHost(&g->red_host, sizeof(double) * kNumRed));
     TRY(dalloc(g, &g->err, 1));
+    TRY(dalloc(g, &g->pad, 8));
+    {
+        const float hp[8] = {sentinel_f32(), sentinel_f32(), sentinel_f32(), sentinel_f32(), 0.f, 0.f, 0.f, 0.f};
+        TRYC(cudaMemcpy(g->pad, hp, sizeof(hp), cudaMemcpyHostToDevice));
+    }
     TRYC(cudaMemsetAsync(g->err, 0, sizeof(int), st));
     TRYC(cudaMallocHost(&g->err_host, sizeof(int)));
     TRYC(cudaMalloc(&band, sizeof(int32_t) * std::max<int64_t>(total, 1)));

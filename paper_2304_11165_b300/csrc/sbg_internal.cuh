@@ -101,6 +101,7 @@ struct sbg_grid_s {
     double *partials = nullptr;    // reduction scratch [kRedMaxCtas * kNumRed]
     double *red_dev = nullptr;     // [kNumRed]
     double *red_host = nullptr;    // pinned [kNumRed]
+    float *pad = nullptr;          // 16-byte-aligned page: 4 sentinels then 4 zeros (absent halo neighbours)
     int *err = nullptr;            // device error word written by bounded waits (0 = none)
     int *err_host = nullptr;       // pinned copy
     int64_t bytes = 0;

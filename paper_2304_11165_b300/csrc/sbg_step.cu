@@ -178,6 +178,7 @@ static void fill_args(sbg_grid g, sbg_state st, const sbg_params *p, int src, St
     a.wslab = g->wslab;
     a.w = g->w;
     a.w64 = g->w64;
+    a.pad = g->pad;
     a.gdims = g->gdims;
     a.nb = g->nb;
     a.held_mask = 0;
@@ -222,11 +223,12 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
     const bool react = p->k_surf != 0.0;
     if (st->variant != SBG_KERNEL_PLAIN) {
         cudaError_t e = cudaSuccess;
-        if (launch_step_pipe(a, st->dtype, st->ns, g->B, react, st->ctas_per_sm, g->err, s, &e)) {
+        if (launch_step_pipe(a, st->dtype, st->ns, g->B, react, st->variant == SBG_KERNEL_PIPELINED_PREFETCH,
+                             st->ctas_per_sm, g->err, s, &e)) {
             if (e != cudaSuccess) return cuda_fail(e, "pipelined step kernel launch");
             return SBG_OK;
         }
-        if (st->variant == SBG_KERNEL_PIPELINED)
+        if (st->variant >= SBG_KERNEL_PIPELINED)
             return fail(SBG_ERR_INVALID_ARG, "the pipelined kernel handles FP32 and SBG_F32X2 states only");
     }
     if (st->dtype == SBG_F32X2) {
@@ -370,9 +372,9 @@ extern "C" sbg_status sbg_step(sbg_grid g, sbg_state st, const sbg_params *p, in
 
 extern "C" sbg_status sbg_state_set_kernel(sbg_state st, int32_t variant, int32_t ctas_per_sm) {
     if (!st) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: null state");
-    if (variant < SBG_KERNEL_AUTO || variant > SBG_KERNEL_PIPELINED || ctas_per_sm < 0 || ctas_per_sm > 64)
+    if (variant < SBG_KERNEL_AUTO || variant > SBG_KERNEL_PIPELINED_PREFETCH || ctas_per_sm < 0 || ctas_per_sm > 64)
         return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: bad variant or ctas_per_sm");
-    if (variant == SBG_KERNEL_PIPELINED && st->dtype == SBG_F64)
+    if (variant >= SBG_KERNEL_PIPELINED && st->dtype == SBG_F64)
         return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: no pipelined kernel for FP64 states");
     st->variant = variant;
     st->ctas_per_sm = ctas_per_sm;

@@ -22,6 +22,7 @@ struct StepArgs {
     const int32_t *wslab;
     const float *w;
     const double *w64;
+    const float *pad;        // 4 sentinels, then 4 zeros
     const int32_t *gdims;
     int64_t nb;
     int held_mask;           // bit f: face f is Dirichlet
@@ -93,7 +94,8 @@ __device__ __forceinline__ void fused_update_x2(float hc, float lc, const float 
 
 // Launches the bulk-copy pipelined kernel (FP32 and compensated-FP32
 // states); returns false when the combination is not handled by it.
-bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, int ctas_per_sm,
-                      int *err_flag, cudaStream_t s, cudaError_t *launch_err);
+// `prefetch` selects the variant that prefetches halos one group ahead.
+bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, bool prefetch,
+                      int ctas_per_sm, int *err_flag, cudaStream_t s, cudaError_t *launch_err);
 
 }  // namespace sbg

@@ -12,11 +12,14 @@
 //    mbarriers, S groups ahead of the compute; only that thread waits on the
 //    barrier, the others sleep in __syncthreads;
 //  - each thread updates four x-consecutive voxels: its row and the rows
-//    above/below/in front/behind come from shared memory as 16-byte loads;
+//    above/below/in front/behind come from shared memory as 16-byte loads at
+//    per-thread constant offsets from the stage tile or the halo buffer, so
+//    the update has no position-dependent selects of values;
 //  - the one-voxel face halos come from the neighbouring blocks (mostly L2
-//    hits): face ids are prefetched two groups ahead and halo values one
-//    group ahead into registers (two alternating register sets, no copies),
-//    so their latency overlaps the current group's compute;
+//    hits): each thread prefetches the halo values of its own row one group
+//    ahead into registers (face ids two groups ahead; two alternating
+//    register sets, no copies) and parks them in its own slots of a halo
+//    buffer when their group comes up;
 //  - results leave as one 16-byte store per thread and array.
 // Every wait on an mbarrier is bounded: on time-out the CTA sets the grid's
 // error word (reported as SBG_ERR_TIMEOUT), waits (bounded) for its copies in
@@ -33,14 +36,31 @@ __device__ __forceinline__ float f4get(const float4 &v, int i) {
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-template <bool X2, int B, int NS, bool REACT, int S>
-__global__ void __launch_bounds__(kPipeThreads) k_step_pipe(const StepArgs a, int *err) {
-    constexpr int B3 = B * B * B;
-    constexpr int G = kGroupVox / B3;
+// Shared memory of one CTA: an S-stage ring of groups (NA arrays of 512
+// voxels each, written by the bulk copies) and one halo buffer with a B x B
+// face per block of the group and face direction, per array.  Each thread
+// writes the halo values of its own row into its own halo slots and reads
+// them back itself, so the halo buffer needs no extra barrier.  Every
+// neighbour of a thread's row is at a per-thread constant offset from either
+// the stage's tile or the halo buffer; the base is chosen once per group.
+template <int B>
+struct PipeLayout {
+    static constexpr int B3 = B * B * B;
+    static constexpr int G = kGroupVox / B3;
+    static constexpr int kHalo = G * 6 * B * B;  // floats per array
+    __host__ __device__ static constexpr int face(int j, int f) { return (j * 6 + f) * B * B; }
+};
+
+template <bool X2, int B, int NS, bool REACT, int S, int MINB, bool PF>
+__global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs a, int *err) {
+    using L = PipeLayout<B>;
+    constexpr int B3 = L::B3;
+    constexpr int G = L::G;
     constexpr int NA = X2 ? 2 : NS;  // arrays streamed per group
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *stages = reinterpret_cast<float *>(smem_raw);  // [S][NA][512]
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)S * NA * kGroupVox * sizeof(float));
+    float *stages = reinterpret_cast<float *>(smem_raw);   // [S][NA][512]
+    float *halo = stages + (size_t)S * NA * kGroupVox;     // [NA][kHalo]
+    uint64_t *full = reinterpret_cast<uint64_t *>(halo + (size_t)NA * L::kHalo);
 
     const int tid = threadIdx.x;
     const int64_t ngroups = (a.nb + G - 1) / G;
@@ -86,20 +106,30 @@ __global__ void __launch_bounds__(kPipeThreads) k_step_pipe(const StepArgs a, in
     const int j = v0 / B3;
     const int l0 = v0 - j * B3;
     const int x0 = l0 % B, y = (l0 / B) % B, z = l0 / (B * B);
-    const bool dxm = (x0 == 0), dxp = (x0 + 3 == B - 1);  // x-halo duties
-    const int fy = (y == 0) ? 2 : (y == B - 1) ? 3 : -1;
-    const int fz = (z == 0) ? 4 : (z == B - 1) ? 5 : -1;
+    const bool hxm = (x0 == 0), hxp = (x0 + 3 == B - 1);  // which neighbours are halo values
+    const bool hym = (y == 0), hyp = (y == B - 1), hzm = (z == 0), hzp = (z == B - 1);
+    // where, in the neighbouring block, this thread's halo values are
     const int oxm = l0 + (B - 1), oxp = l0 + 3 - (B - 1);
-    const int oy = (fy == 2) ? l0 + (B - 1) * B : l0 - (B - 1) * B;
-    const int oz = (fz == 4) ? l0 + (B - 1) * B * B : l0 - (B - 1) * B * B;
-    const float SENT = sentinel_f32();
+    const int oy = hym ? l0 + (B - 1) * B : l0 - (B - 1) * B;
+    const int oz = hzm ? l0 + (B - 1) * B * B : l0 - (B - 1) * B * B;
+    const int fyy = hym ? 2 : 3, fzz = hzm ? 4 : 5;
+    // neighbour offsets: in the halo buffer when the neighbour is a halo value, else in the tile
+    const int sxm = hxm ? L::face(j, 0) + z * B + y : v0 - 1;
+    const int sxp = hxp ? L::face(j, 1) + z * B + y : v0 + 4;
+    const int sym = hym ? L::face(j, 2) + z * B + x0 : v0 - B;
+    const int syp = hyp ? L::face(j, 3) + z * B + x0 : v0 + B;
+    const int szm = hzm ? L::face(j, 4) + y * B + x0 : v0 - B * B;
+    const int szp = hzp ? L::face(j, 5) + y * B + x0 : v0 + B * B;
+    const int shy = hym ? sym : syp;
+    const int shz = hzm ? szm : szp;
+    const bool dy = hym || hyp, dz = hzm || hzp;
 
     struct Ids {
         int xm, xp, y, z, ws;
     };
     struct Halo {
-        float hxm[NA], hxp[NA];
-        float4 hy[NA], hz[NA];
+        float vxm[NA], vxp[NA];
+        float4 vy[NA], vz[NA];
         float4 w;
         int4 bc;
     };
@@ -108,37 +138,70 @@ __global__ void __launch_bounds__(kPipeThreads) k_step_pipe(const StepArgs a, in
         const int64_t b = gi * G + j;
         if (gi < g1 && b < a.nb) {
             const int32_t *f = a.face + b * 6;
-            if (dxm) r.xm = __ldg(f + 0);
-            if (dxp) r.xp = __ldg(f + 1);
-            if (fy >= 0) r.y = __ldg(f + fy);
-            if (fz >= 0) r.z = __ldg(f + fz);
+            if (hxm) r.xm = __ldg(f + 0);
+            if (hxp) r.xp = __ldg(f + 1);
+            if (dy) r.y = __ldg(f + fyy);
+            if (dz) r.z = __ldg(f + fzz);
             if (REACT) r.ws = __ldg(a.wslab + b);
         }
         return r;
     };
+    // halo values of this thread's row, its surface weights and block coordinates
     auto load_halo = [&](int64_t gi, const Ids &id, Halo &h) {
-        const int64_t b = gi * G + j;
+        const float SENT = sentinel_f32();
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
             const float absent = (X2 && k == 1) ? 0.f : SENT;
-            h.hxm[k] = (id.xm >= 0) ? __ldg(src[k] + (int64_t)id.xm * B3 + oxm) : absent;
-            h.hxp[k] = (id.xp >= 0) ? __ldg(src[k] + (int64_t)id.xp * B3 + oxp) : absent;
-            h.hy[k] = (id.y >= 0) ? __ldg(reinterpret_cast<const float4 *>(src[k] + (int64_t)id.y * B3 + oy))
+            h.vxm[k] = (id.xm >= 0) ? __ldg(src[k] + (int64_t)id.xm * B3 + oxm) : absent;
+            h.vxp[k] = (id.xp >= 0) ? __ldg(src[k] + (int64_t)id.xp * B3 + oxp) : absent;
+            h.vy[k] = (id.y >= 0) ? __ldg(reinterpret_cast<const float4 *>(src[k] + (int64_t)id.y * B3 + oy))
                                   : make_float4(absent, absent, absent, absent);
-            h.hz[k] = (id.z >= 0) ? __ldg(reinterpret_cast<const float4 *>(src[k] + (int64_t)id.z * B3 + oz))
+            h.vz[k] = (id.z >= 0) ? __ldg(reinterpret_cast<const float4 *>(src[k] + (int64_t)id.z * B3 + oz))
                                   : make_float4(absent, absent, absent, absent);
         }
         h.w = make_float4(0.f, 0.f, 0.f, 0.f);
         if (REACT && id.ws >= 0) h.w = __ldg(reinterpret_cast<const float4 *>(a.w + (int64_t)id.ws * B3 + l0));
+        const int64_t b = gi * G + j;
         h.bc = make_int4(0, 0, 0, 0);
         if (a.held_mask && gi < g1 && b < a.nb) h.bc = __ldg(a.blocks + b);
     };
 
-    auto body = [&](int64_t gi, int it, const Halo &cur, Halo &nxt, const Ids &id1, Ids &id2) -> bool {
+    // One group: park this group's prefetched halo values in this thread's
+    // halo slots, prefetch the next group's halos (ids read a group earlier),
+    // wait for the stage, refill the previous stage, update.  The loop below
+    // is unrolled by two with the register sets swapped, so no prefetched
+    // value is copied (a copy would wait for the load every group).
+    auto park = [&](const Halo &h) {
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            float *hb = halo + k * L::kHalo;
+            if (hxm) hb[sxm] = h.vxm[k];
+            if (hxp) hb[sxp] = h.vxp[k];
+            if (dy) *reinterpret_cast<float4 *>(hb + shy) = h.vy[k];
+            if (dz) *reinterpret_cast<float4 *>(hb + shz) = h.vz[k];
+        }
+    };
+
+    // One group.  PF: park this group's halo values (prefetched during the
+    // previous group), prefetch the next group's (ids read a group earlier).
+    // !PF: load this group's halo values now (ids read during the previous
+    // group) and park them after the stage wait, relying on the other CTAs of
+    // the SM to hide their latency.  The loop below is unrolled by two with
+    // the register sets swapped, so no prefetched value is copied (a copy
+    // would wait for the load every group).
+    auto body = [&](int64_t gi, int it, Halo &cur, Halo &nxt, const Ids &id1, Ids &id2) -> bool {
         const int s = it % S;
         const uint32_t par = (uint32_t)((it / S) & 1);
-        id2 = load_ids(gi + 2);
-        load_halo(gi + 1, id1, nxt);
+        const int64_t b = gi * G + j;
+        const bool valid = b < a.nb;
+        if (PF) {
+            if (valid) park(cur);
+            id2 = load_ids(gi + 2);
+            load_halo(gi + 1, id1, nxt);
+        } else {
+            load_halo(gi, id1, cur);
+            id2 = load_ids(gi + 1);
+        }
 
         bool ok = true;
         if (tid == 0) ok = mbar_wait_bounded(&full[s], par);
@@ -153,10 +216,8 @@ __global__ void __launch_bounds__(kPipeThreads) k_step_pipe(const StepArgs a, in
         mbar_try_wait(&full[s], par);  // completed: gives this thread the acquire of the copied data
         // every thread has finished the previous group: refill its stage
         if (tid == 0 && it >= 1 && gi - 1 + S < g1) issue(gi - 1 + S, (it - 1) % S);
-
-        const int64_t b = gi * G + j;
-        if (b >= a.nb) return true;
-        const float *sb = stages + (size_t)s * NA * kGroupVox;
+        if (!valid) return true;
+        if (!PF) park(cur);
 
         // Dirichlet-held voxels
         bool held[4] = {false, false, false, false};
@@ -168,62 +229,57 @@ __global__ void __launch_bounds__(kPipeThreads) k_step_pipe(const StepArgs a, in
 #pragma unroll
             for (int i = 0; i < 4; ++i) held[i] = is_held(a.held_mask, gx + i, gy, gz, nx, ny, nz);
         }
+        const float4 w4 = cur.w;
 
         float4 uc[NA], ym[NA], yp[NA], zm[NA], zp[NA];
         float xm[NA], xp[NA];
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
-            const float *t = sb + k * kGroupVox;
+            const float *t = stages + ((size_t)s * NA + k) * kGroupVox;
+            const float *h = halo + k * L::kHalo;
             uc[k] = *reinterpret_cast<const float4 *>(t + v0);
-            xm[k] = dxm ? cur.hxm[k] : t[v0 - 1];
-            xp[k] = dxp ? cur.hxp[k] : t[v0 + 4];
-            ym[k] = (y > 0) ? *reinterpret_cast<const float4 *>(t + v0 - B) : cur.hy[k];
-            yp[k] = (y < B - 1) ? *reinterpret_cast<const float4 *>(t + v0 + B) : cur.hy[k];
-            zm[k] = (z > 0) ? *reinterpret_cast<const float4 *>(t + v0 - B * B) : cur.hz[k];
-            zp[k] = (z < B - 1) ? *reinterpret_cast<const float4 *>(t + v0 + B * B) : cur.hz[k];
+            xm[k] = (hxm ? h : t)[sxm];
+            xp[k] = (hxp ? h : t)[sxp];
+            ym[k] = *reinterpret_cast<const float4 *>((hym ? h : t) + sym);
+            yp[k] = *reinterpret_cast<const float4 *>((hyp ? h : t) + syp);
+            zm[k] = *reinterpret_cast<const float4 *>((hzm ? h : t) + szm);
+            zp[k] = *reinterpret_cast<const float4 *>((hzp ? h : t) + szp);
         }
         const StepCoef<float> &kc = a.cf;
         float res[NA][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
+            // neighbours of voxel i in array 0 decide the no-flux mirror for every array
+            const float n0[6] = {i == 0 ? xm[0] : f4get(uc[0], i - 1), i == 3 ? xp[0] : f4get(uc[0], i + 1),
+                                 f4get(ym[0], i), f4get(yp[0], i), f4get(zm[0], i), f4get(zp[0], i)};
+            bool out[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) out[f] = is_sent(n0[f]);
+            const float c0 = f4get(uc[0], i);
+            const bool upd = !is_sent(c0) && !held[i];
+#pragma unroll
+            for (int k = 0; k < NA; ++k) res[k][i] = f4get(uc[k], i);
+            if (!upd) continue;
+            float nv[NA][6];
+#pragma unroll
+            for (int k = 0; k < NA; ++k) {
+                const float c = f4get(uc[k], i);
+                const float raw[6] = {i == 0 ? xm[k] : f4get(uc[k], i - 1), i == 3 ? xp[k] : f4get(uc[k], i + 1),
+                                      f4get(ym[k], i), f4get(yp[k], i), f4get(zm[k], i), f4get(zp[k], i)};
+#pragma unroll
+                for (int f = 0; f < 6; ++f) nv[k][f] = out[f] ? c : raw[f];
+            }
             if (X2) {
-                const float hc = f4get(uc[0], i), lc = f4get(uc[NA - 1], i);
-                res[0][i] = hc;
-                res[NA - 1][i] = lc;
-                if (!is_sent(hc) && !held[i]) {
-                    const float hv[6] = {i == 0 ? xm[0] : f4get(uc[0], i - 1), i == 3 ? xp[0] : f4get(uc[0], i + 1),
-                                         f4get(ym[0], i), f4get(yp[0], i), f4get(zm[0], i), f4get(zp[0], i)};
-                    const float lv[6] = {i == 0 ? xm[NA - 1] : f4get(uc[NA - 1], i - 1),
-                                         i == 3 ? xp[NA - 1] : f4get(uc[NA - 1], i + 1),
-                                         f4get(ym[NA - 1], i), f4get(yp[NA - 1], i),
-                                         f4get(zm[NA - 1], i), f4get(zp[NA - 1], i)};
-                    float nh[6], nl[6];
-#pragma unroll
-                    for (int f = 0; f < 6; ++f) {
-                        const bool m = is_sent(hv[f]);
-                        nh[f] = m ? hc : hv[f];
-                        nl[f] = m ? lc : lv[f];
-                    }
-                    float rate = kc.decay[0];
-                    if (REACT) rate = __fmaf_rn(kc.k, f4get(cur.w, i), rate);
-                    fused_update_x2(hc, lc, nh, nl, kc.c[0], kc.dt, rate, res[0][i], res[NA - 1][i]);
-                }
+                float rate = kc.decay[0];
+                if (REACT) rate = __fmaf_rn(kc.k, f4get(w4, i), rate);
+                fused_update_x2(c0, f4get(uc[NA - 1], i), nv[0], nv[NA - 1], kc.c[0], kc.dt, rate, res[0][i],
+                                res[NA - 1][i]);
             } else {
-                const float ua = f4get(uc[0], i);
-                const float t = REACT ? __fmul_rn(__fmul_rn(kc.k, f4get(cur.w, i)), ua) : 0.f;
+                const float t = REACT ? __fmul_rn(__fmul_rn(kc.k, f4get(w4, i)), c0) : 0.f;
 #pragma unroll
-                for (int k = 0; k < NA; ++k) {
-                    const float c = f4get(uc[k], i);
-                    res[k][i] = c;
-                    if (!is_sent(c) && !held[i]) {
-                        const float vxm = i == 0 ? xm[k] : f4get(uc[k], i - 1);
-                        const float vxp = i == 3 ? xp[k] : f4get(uc[k], i + 1);
-                        res[k][i] = fused_update(c, mirror(vxm, c), mirror(vxp, c), mirror(f4get(ym[k], i), c),
-                                                 mirror(f4get(yp[k], i), c), mirror(f4get(zm[k], i), c),
-                                                 mirror(f4get(zp[k], i), c), kc.c[k], kc.dt, kc.decay[k],
-                                                 k == 0 ? -t : t);
-                    }
-                }
+                for (int k = 0; k < NA; ++k)
+                    res[k][i] = fused_update(f4get(uc[k], i), nv[k][0], nv[k][1], nv[k][2], nv[k][3], nv[k][4],
+                                             nv[k][5], kc.c[k], kc.dt, kc.decay[k], k == 0 ? -t : t);
             }
         }
 #pragma unroll
@@ -234,8 +290,10 @@ __global__ void __launch_bounds__(kPipeThreads) k_step_pipe(const StepArgs a, in
 
     Ids idA = load_ids(g0), idB;
     Halo hA, hB;
-    load_halo(g0, idA, hA);
-    idA = load_ids(g0 + 1);
+    if (PF) {
+        load_halo(g0, idA, hA);
+        idA = load_ids(g0 + 1);
+    }
     int it = 0;
     for (int64_t gi = g0; gi < g1; gi += 2, it += 2) {
         if (!body(gi, it, hA, hB, idA, idB)) return;
@@ -244,12 +302,18 @@ __global__ void __launch_bounds__(kPipeThreads) k_step_pipe(const StepArgs a, in
     }
 }
 
-template <bool X2, int B, int NS, bool REACT>
-static cudaError_t launch_pipe_t(const StepArgs &a, int ctas_per_sm, int *err, cudaStream_t s) {
-    constexpr int S = 8;
+template <bool X2, int B, int NS, bool REACT, bool PF>
+static cudaError_t launch_pipe_pf(const StepArgs &a, int ctas_per_sm, int *err, cudaStream_t s) {
     constexpr int NA = X2 ? 2 : NS;
-    constexpr size_t smem = (size_t)S * NA * kGroupVox * sizeof(float) + S * sizeof(uint64_t);
-    auto kern = k_step_pipe<X2, B, NS, REACT, S>;
+    constexpr int S = NA == 1 ? 6 : 4;
+    constexpr size_t smem = ((size_t)S * NA * kGroupVox + (size_t)NA * PipeLayout<B>::kHalo) * sizeof(float) +
+                            S * sizeof(uint64_t);
+    constexpr int G = kGroupVox / (B * B * B);
+    // Without prefetch: 64 registers per thread (8 CTAs of 128 threads per SM)
+    // with one array, 80 (6 CTAs) with two.  With prefetch the two register
+    // sets need up to 128 registers (4 CTAs per SM).
+    constexpr int MINB = PF ? 4 : (NA == 1 ? 8 : 6);
+    auto kern = k_step_pipe<X2, B, NS, REACT, S, MINB, PF>;
     static int occ = -1, nsm = 0;
     if (occ < 0) {
         int dev = 0;
@@ -260,7 +324,6 @@ static cudaError_t launch_pipe_t(const StepArgs &a, int ctas_per_sm, int *err, c
         if (occ < 1) occ = 1;
     }
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-    constexpr int G = kGroupVox / (B * B * B);
     const int64_t ngroups = (a.nb + G - 1) / G;
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ngroups) grid = ngroups;
@@ -269,9 +332,18 @@ static cudaError_t launch_pipe_t(const StepArgs &a, int ctas_per_sm, int *err, c
     return cudaGetLastError();
 }
 
-bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, int ctas_per_sm,
-                      int *err_flag, cudaStream_t s, cudaError_t *launch_err) {
+// Halo prefetch on or off: chosen by the kernel variant of the state.
+static thread_local bool t_prefetch = false;
+template <bool X2, int B, int NS, bool REACT>
+static cudaError_t launch_pipe_t(const StepArgs &a, int ctas_per_sm, int *err, cudaStream_t s) {
+    return t_prefetch ? launch_pipe_pf<X2, B, NS, REACT, true>(a, ctas_per_sm, err, s)
+                      : launch_pipe_pf<X2, B, NS, REACT, false>(a, ctas_per_sm, err, s);
+}
+
+bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, bool prefetch,
+                      int ctas_per_sm, int *err_flag, cudaStream_t s, cudaError_t *launch_err) {
     cudaError_t e = cudaSuccess;
+    t_prefetch = prefetch;
     if (dtype == SBG_F32X2 && ns == 1) {
         if (B == 8) e = react ? launch_pipe_t<true, 8, 1, true>(a, ctas_per_sm, err_flag, s)
                               : launch_pipe_t<true, 8, 1, false>(a, ctas_per_sm, err_flag, s);
