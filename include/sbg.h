@@ -37,6 +37,7 @@ extern "C" {
 
 typedef struct sbg_grid_s *sbg_grid;   /* geometry: blocks, hash, neighbour table, masks */
 typedef struct sbg_state_s *sbg_state; /* species fields in block layout, ping-pong pair  */
+typedef struct sbg_tape_s *sbg_tape;   /* forward checkpoints for the adjoint             */
 
 typedef enum {
     SBG_OK = 0,
@@ -255,6 +256,37 @@ sbg_status sbg_effective_D(sbg_grid grid, sbg_state state, const sbg_params *par
 sbg_status sbg_run_to_steady(sbg_grid grid, sbg_state state, const sbg_params *params, double tol,
                              int64_t check_every, int64_t max_steps, int64_t *steps_done,
                              double *rel_residual, void *stream);
+
+/* ---- adjoint (no counterpart in the paper: this library's differentiation) -------
+ * The step is linear, u^{n+1} = M u^n, so the gradient of a loss L(u^N) runs
+ * lambda^n = M^T lambda^{n+1} backwards from lambda^N = dL/du^N: the
+ * transposed masked stencil (an inactive neighbour contributes nothing, a
+ * Dirichlet-held neighbour counts in the diagonal but carries lambda = 0)
+ * plus the transposed A -> B coupling.  Held values are not free parameters:
+ * lambda is 0 on held voxels.
+ *
+ * sbg_forward_record advances `state` (SBG_F32 or SBG_F64) by nsteps like
+ * sbg_step and keeps a device copy of the state every checkpoint_every steps
+ * (ceil(nsteps / K) copies) in a new tape, which owns that memory.
+ * Synchronises nothing. */
+sbg_status sbg_forward_record(sbg_grid grid, sbg_state state, const sbg_params *params, int64_t nsteps,
+                              int64_t checkpoint_every, void *stream, sbg_tape *out);
+
+/* Runs the adjoint over the recorded steps: segments are taken last to first,
+ * the K states of a segment are recomputed from its checkpoint (a buffer of K
+ * states, allocated on the first call), and K adjoint steps run over them.
+ * lam: in: dL/du^N; out: dL/du^0 (0 on held and inactive voxels); same grid,
+ * dtype and species as the recorded state.  grad (host, 3 doubles):
+ *   grad[0] = dL/dD_0, grad[1] = dL/dD_1 (0 with one species),
+ *   grad[2] = dL/dk_surf,
+ * each accumulated over steps and voxels in FP64 (per-CTA partials added in a
+ * fixed order).  Synchronises `stream`. */
+sbg_status sbg_adjoint(sbg_grid grid, sbg_tape tape, sbg_state lam, double *grad, void *stream);
+
+/* Device memory held by the tape (checkpoints, recompute buffer, work state)
+ * and its number of checkpoints; either pointer may be NULL. */
+sbg_status sbg_tape_info(sbg_tape tape, int64_t *device_bytes, int64_t *n_checkpoints);
+void sbg_tape_destroy(sbg_tape tape);
 
 /* ---- errors -------------------------------------------------------------------- */
 const char *sbg_last_error(void);            /* thread-local; "" when none                      */

@@ -75,6 +75,11 @@ SIGNATURES = [
                                   c_void_p, c_void_p]),
     ("sbg_run_to_steady", c_int32, [c_void_p, c_void_p, ctypes.POINTER(Params), c_double, c_int64, c_int64,
                                     c_void_p, c_void_p, c_void_p]),
+    ("sbg_forward_record", c_int32, [c_void_p, c_void_p, ctypes.POINTER(Params), c_int64, c_int64, c_void_p,
+                                     ctypes.POINTER(c_void_p)]),
+    ("sbg_adjoint", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("sbg_tape_info", c_int32, [c_void_p, c_void_p, c_void_p]),
+    ("sbg_tape_destroy", None, [c_void_p]),
     ("sbg_last_error", ctypes.c_char_p, []),
     ("sbg_status_string", ctypes.c_char_p, [c_int32]),
     ("sbg_abi_version", c_int32, []),
