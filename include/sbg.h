@@ -257,6 +257,21 @@ sbg_status sbg_run_to_steady(sbg_grid grid, sbg_state state, const sbg_params *p
                              int64_t check_every, int64_t max_steps, int64_t *steps_done,
                              double *rel_residual, void *stream);
 
+/* Batched steady-state solve (no counterpart in the paper: this library's
+ * batching pattern) for a grid from sbg_build_batch and one FP32 or
+ * SBG_F32X2 state: every geometry not yet converged advances by one
+ * persistent, pipelined launch per step over a device work list of 512-voxel
+ * spans (never straddling geometries), replayed from a captured CUDA graph of
+ * check_every launches (rounded up to even); after each interval each active
+ * geometry's FP64 relative residual ||L_h u|| / ||L_h u^0|| (species 0) is
+ * computed and geometries below tol leave the work list.  Host outputs of
+ * length n_geoms: steps_done[g] (steps at which g stopped) and
+ * rel_residual[g].  Returns NOT_CONVERGED when some geometry is still above
+ * tol after max_steps, NONFINITE on a NaN/Inf.  Synchronises `stream`. */
+sbg_status sbg_batch_run_to_steady(sbg_grid grid, sbg_state state, const sbg_params *params, double tol,
+                                   int64_t check_every, int64_t max_steps, int64_t *steps_done,
+                                   double *rel_residual, void *stream);
+
 /* ---- adjoint (no counterpart in the paper: this library's differentiation) -------
  * The step is linear, u^{n+1} = M u^n, so the gradient of a loss L(u^N) runs
  * lambda^n = M^T lambda^{n+1} backwards from lambda^N = dL/du^N: the

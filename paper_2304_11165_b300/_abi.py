@@ -75,6 +75,8 @@ SIGNATURES = [
                                   c_void_p, c_void_p]),
     ("sbg_run_to_steady", c_int32, [c_void_p, c_void_p, ctypes.POINTER(Params), c_double, c_int64, c_int64,
                                     c_void_p, c_void_p, c_void_p]),
+    ("sbg_batch_run_to_steady", c_int32, [c_void_p, c_void_p, ctypes.POINTER(Params), c_double, c_int64, c_int64,
+                                          c_void_p, c_void_p, c_void_p]),
     ("sbg_forward_record", c_int32, [c_void_p, c_void_p, ctypes.POINTER(Params), c_int64, c_int64, c_void_p,
                                      ctypes.POINTER(c_void_p)]),
     ("sbg_adjoint", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -254,6 +254,20 @@ class State:
             check(rc)
         return steps.value, rel.value
 
+    def batch_run_to_steady(self, params: Params, tol: float, check_every: int = 128,
+                            max_steps: int = 10 ** 9, stream=None, raise_on_max=True):
+        """All geometries of a batched grid to steady state; returns (steps[g], rel[g])."""
+        n = self.grid.n_geoms
+        steps = np.zeros(n, np.int64)
+        rel = np.zeros(n)
+        rc = self._lib.sbg_batch_run_to_steady(self.grid.handle, self.handle, ctypes.byref(params), float(tol),
+                                               int(check_every), int(max_steps),
+                                               steps.ctypes.data_as(ctypes.c_void_p),
+                                               rel.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream))
+        if rc != _abi.SBG_OK and not (rc == _abi.SBG_ERR_NOT_CONVERGED and not raise_on_max):
+            check(rc)
+        return steps, rel
+
     def close(self):
         if getattr(self, "handle", None):
             self._lib.sbg_state_destroy(self.handle)

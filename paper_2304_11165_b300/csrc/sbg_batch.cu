@@ -1,0 +1,139 @@
+// Batched steady-state solve over many geometries (no counterpart in the
+// paper: the batching pattern of this library).
+//
+// sbg_build_batch concatenates the block lists of all geometries (blocks
+// sorted by geometry, each carrying its geometry id; neighbour tables never
+// cross geometries).  This driver advances every unconverged geometry with
+// ONE persistent pipelined launch per step over a device work list of
+// 512-voxel spans that never straddle geometries, replays a captured CUDA
+// graph of `check_every` such launches, and after each interval computes every
+// active geometry's FP64 residual.  A geometry whose relative residual is
+// below tol leaves the work list; its blocks are not touched again, and since
+// check_every is even its values stay in the current buffer.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "sbg_internal.cuh"
+
+namespace sbg {
+sbg_status launch_step_work(sbg_grid g, sbg_state st, const sbg_params *p, int src, const int64_t *items,
+                            int64_t nitems, cudaStream_t s);
+}
+
+using namespace sbg;
+
+extern "C" sbg_status sbg_batch_run_to_steady(sbg_grid g, sbg_state st, const sbg_params *p, double tol,
+                                              int64_t check_every, int64_t max_steps, int64_t *steps_done,
+                                              double *rel_residual, void *stream) {
+    if (!g || !st || !p || !steps_done || !rel_residual)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_batch_run_to_steady: null pointer");
+    if (st->grid != g) return fail(SBG_ERR_INVALID_ARG, "sbg_batch_run_to_steady: state of another grid");
+    if (check_every < 2 || max_steps < 0 || !(tol > 0.0))
+        return fail(SBG_ERR_INVALID_ARG, "sbg_batch_run_to_steady: check_every >= 2, max_steps >= 0, tol > 0");
+    if (st->dtype == SBG_F64) return fail(SBG_ERR_INVALID_ARG, "sbg_batch_run_to_steady: FP32 or SBG_F32X2 states");
+    sbg_status rc = validate_params(g, p, st->ns);
+    if (rc != SBG_OK) return rc;
+    check_every += check_every & 1;  // even: parity of the current buffer is kept
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = g->n_geoms;
+    const int G = 512 / g->b3();
+    std::vector<double> r0(n, 0.0), red(kNumRed);
+    std::vector<char> active(n, 0);
+    for (int i = 0; i < n; ++i) {
+        steps_done[i] = 0;
+        rel_residual[i] = 0.0;
+        if (g->geom_count[i] == 0) continue;
+        rc = reduce_species(g, st, p, i, 0, -1, red.data(), s);
+        if (rc != SBG_OK) return rc;
+        if (red[SBG_RED_NONFINITE] > 0) return fail(SBG_ERR_NONFINITE, "sbg_batch_run_to_steady: non-finite initial state");
+        r0[i] = red[SBG_RED_RESIDUAL];
+        if (r0[i] > 0.0) {
+            active[i] = 1;
+            rel_residual[i] = 1.0;
+        }
+    }
+    int64_t max_items = 0;
+    for (int i = 0; i < n; ++i) max_items += (g->geom_count[i] + G - 1) / G;
+    int64_t *items = nullptr;
+    SBG_CUDA(cudaMalloc(&items, sizeof(int64_t) * 2 * std::max<int64_t>(max_items, 1)));
+    std::vector<int64_t> h;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (cs) cudaStreamDestroy(cs);
+        cudaFree(items);
+    };
+    auto rebuild = [&]() -> sbg_status {
+        h.clear();
+        for (int i = 0; i < n; ++i) {
+            if (!active[i]) continue;
+            const int64_t b0 = g->geom_begin[i], cnt = g->geom_count[i];
+            for (int64_t q = 0; q < cnt; q += G) {
+                h.push_back(b0 + q);
+                h.push_back(std::min<int64_t>(G, cnt - q));
+            }
+        }
+        if (!h.empty())
+            SBG_CUDA(cudaMemcpyAsync(items, h.data(), sizeof(int64_t) * h.size(), cudaMemcpyHostToDevice, s));
+        SBG_CUDA(cudaStreamSynchronize(s));
+        if (exec) {
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+        const int64_t nitems = (int64_t)h.size() / 2;
+        if (nitems == 0) return SBG_OK;
+        // first call outside capture (no kernel: empty list) sets up launch attributes
+        sbg_status r = launch_step_work(g, st, p, st->cur, items, 0, s);
+        if (r != SBG_OK) return r;
+        if (!cs) SBG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        SBG_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        int src = st->cur;
+        for (int64_t k = 0; k < check_every && r == SBG_OK; ++k) {
+            r = launch_step_work(g, st, p, src, items, nitems, cs);
+            src = 1 - src;
+        }
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (r != SBG_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+        return SBG_OK;
+    };
+    rc = rebuild();
+    int64_t done = 0;
+    while (rc == SBG_OK && !h.empty() && done < max_steps) {
+        if (cudaGraphLaunch(exec, s) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "batch graph launch");
+            break;
+        }
+        done += check_every;
+        bool changed = false;
+        for (int i = 0; i < n && rc == SBG_OK; ++i) {
+            if (!active[i]) continue;
+            rc = reduce_species(g, st, p, i, 0, -1, red.data(), s);
+            if (rc != SBG_OK) break;
+            if (red[SBG_RED_NONFINITE] > 0) {
+                rc = fail(SBG_ERR_NONFINITE, "sbg_batch_run_to_steady: non-finite value in geometry " + std::to_string(i));
+                break;
+            }
+            steps_done[i] = done;
+            rel_residual[i] = red[SBG_RED_RESIDUAL] / r0[i];
+            if (rel_residual[i] < tol) {
+                active[i] = 0;
+                changed = true;
+            }
+        }
+        if (rc == SBG_OK && changed) rc = rebuild();
+    }
+    cleanup();
+    if (rc != SBG_OK) return rc;
+    for (int i = 0; i < n; ++i)
+        if (active[i]) return fail(SBG_ERR_NOT_CONVERGED, "sbg_batch_run_to_steady: max_steps reached");
+    return SBG_OK;
+}

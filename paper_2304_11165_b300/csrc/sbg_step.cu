@@ -380,3 +380,21 @@ extern "C" sbg_status sbg_state_set_kernel(sbg_state st, int32_t variant, int32_
     st->ctas_per_sm = ctas_per_sm;
     return SBG_OK;
 }
+
+namespace sbg {
+// One pipelined step from buffer `src` over an explicit device work list of
+// (first block, block count) spans; used by the batch solver.
+sbg_status launch_step_work(sbg_grid g, sbg_state st, const sbg_params *p, int src, const int64_t *items,
+                            int64_t nitems, cudaStream_t s) {
+    StepArgs a;
+    fill_args(g, st, p, src, a);
+    a.items = items;
+    a.nitems = nitems;
+    cudaError_t e = cudaSuccess;
+    if (!launch_step_pipe(a, st->dtype, st->ns, g->B, p->k_surf != 0.0,
+                          st->variant == SBG_KERNEL_PIPELINED_PREFETCH, st->ctas_per_sm, g->err, s, &e))
+        return fail(SBG_ERR_INVALID_ARG, "batched stepping needs an FP32 or SBG_F32X2 state");
+    if (e != cudaSuccess) return cuda_fail(e, "pipelined step kernel launch (work list)");
+    return SBG_OK;
+}
+}  // namespace sbg

@@ -25,6 +25,8 @@ struct StepArgs {
     const float *pad;        // 4 sentinels, then 4 zeros
     const int32_t *gdims;
     int64_t nb;
+    const int64_t *items;    // optional work list for the pipelined kernel: (first block, count)
+    int64_t nitems;          //   pairs, each within one geometry and at most 512 voxels
     int held_mask;           // bit f: face f is Dirichlet
     StepCoef<float> cf;
     StepCoef<double> cd;
@@ -68,20 +70,40 @@ __device__ __forceinline__ double fused_update(double u, double xm, double xp, d
     return __fma_rn(dt, __dadd_rn(lap, react), u);
 }
 
-// Compensated update of one voxel: value = hi + lo.  Differences of hi and
-// of lo are formed separately (the hi differences of neighbouring values are
-// exact when they are within a factor 2), the increment d is added to hi
-// with an error-free two-sum, and the pair is renormalised.
+// Error-free sum a + b = s + e (Knuth's two-sum, exact in FP32).
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// Compensated update of one voxel: value = hi + lo.  Per axis, the second
+// difference of hi, X_a = (hi_- - hi) + (hi_+ - hi), and of lo are formed
+// separately.  At a steady state the X_a are not small, only their sum over
+// the three axes vanishes, so c_a X_a are combined with exact products
+// (fma) and error-free two-sums, and every rounding error joins the lo part;
+// the FP32 rounding of that cross-axis sum would otherwise leave the
+// iteration's fixed point ~1e-9 (relative residual) away from the true steady
+// state.  The increment d is added to hi with an error-free two-sum and the
+// pair is renormalised, so increments far below one FP32 ulp of the state
+// accumulate in lo instead of being rounded away.
 __device__ __forceinline__ void fused_update_x2(float hc, float lc, const float nh[6], const float nl[6],
                                                 const float c[3], float dt, float rate, float &rh,
                                                 float &rl) {
-    float lap = 0.f;
+    float p[3], lo = 0.f;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        const float dhi = __fsub_rn(__fsub_rn(nh[2 * ax + 1], hc), __fsub_rn(hc, nh[2 * ax]));
-        const float dlo = __fsub_rn(__fsub_rn(nl[2 * ax + 1], lc), __fsub_rn(lc, nl[2 * ax]));
-        lap = __fmaf_rn(c[ax], __fadd_rn(dhi, dlo), lap);
+        const float x = __fadd_rn(__fsub_rn(nh[2 * ax], hc), __fsub_rn(nh[2 * ax + 1], hc));
+        const float xl = __fadd_rn(__fsub_rn(nl[2 * ax], lc), __fsub_rn(nl[2 * ax + 1], lc));
+        p[ax] = __fmul_rn(c[ax], x);
+        lo = __fadd_rn(lo, __fmaf_rn(c[ax], x, -p[ax]));  // exact rounding error of the product
+        lo = __fmaf_rn(c[ax], xl, lo);
     }
+    float e1, e2;
+    float sum = two_sum(p[0], p[1], e1);
+    sum = two_sum(sum, p[2], e2);
+    const float lap = __fadd_rn(sum, __fadd_rn(__fadd_rn(e1, e2), lo));
     const float react = __fmul_rn(-rate, __fadd_rn(hc, lc));
     const float d = __fmul_rn(dt, __fadd_rn(lap, react));
     const float s = __fadd_rn(hc, d);
@@ -92,8 +114,6 @@ __device__ __forceinline__ void fused_update_x2(float hc, float lc, const float 
     rl = __fsub_rn(l2, __fsub_rn(rh, s));
 }
 
-// Launches the bulk-copy pipelined kernel (FP32 and compensated-FP32
-// states); returns false when the combination is not handled by it.
 // `prefetch` selects the variant that prefetches halos one group ahead.
 bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, bool prefetch,
                       int ctas_per_sm, int *err_flag, cudaStream_t s, cudaError_t *launch_err);

@@ -63,10 +63,21 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     uint64_t *full = reinterpret_cast<uint64_t *>(halo + (size_t)NA * L::kHalo);
 
     const int tid = threadIdx.x;
-    const int64_t ngroups = (a.nb + G - 1) / G;
+    // work items: consecutive groups of the block list, or an explicit list
+    // of (first block, block count) spans (the batch solver's active set)
+    const int64_t ngroups = a.items ? a.nitems : (a.nb + G - 1) / G;
     const int64_t g0 = ngroups * blockIdx.x / gridDim.x;
     const int64_t g1 = ngroups * (blockIdx.x + 1) / gridDim.x;
     if (g0 >= g1) return;  // uniform over the CTA
+    auto span = [&](int64_t gi, int64_t &b0, int64_t &nblk) {
+        if (a.items) {
+            b0 = __ldg(a.items + 2 * gi);
+            nblk = __ldg(a.items + 2 * gi + 1);
+        } else {
+            b0 = gi * G;
+            nblk = (a.nb - b0 < G) ? (a.nb - b0) : G;
+        }
+    };
 
     const float *src[NA];
     float *dst[NA];
@@ -90,8 +101,8 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     __syncthreads();
 
     auto issue = [&](int64_t gi, int s) {
-        const int64_t b0 = gi * G;
-        const int64_t nblk = (a.nb - b0 < G) ? (a.nb - b0) : G;
+        int64_t b0, nblk;
+        span(gi, b0, nblk);
         const uint32_t bytes = (uint32_t)(nblk * B3 * sizeof(float));
         mbar_arrive_expect_tx(&full[s], bytes * NA);
 #pragma unroll
@@ -135,8 +146,11 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     };
     auto load_ids = [&](int64_t gi) {
         Ids r{-1, -1, -1, -1, -1};
-        const int64_t b = gi * G + j;
-        if (gi < g1 && b < a.nb) {
+        if (gi >= g1) return r;
+        int64_t b0, nblk;
+        span(gi, b0, nblk);
+        const int64_t b = b0 + j;
+        if (j < nblk) {
             const int32_t *f = a.face + b * 6;
             if (hxm) r.xm = __ldg(f + 0);
             if (hxp) r.xp = __ldg(f + 1);
@@ -161,9 +175,12 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
         }
         h.w = make_float4(0.f, 0.f, 0.f, 0.f);
         if (REACT && id.ws >= 0) h.w = __ldg(reinterpret_cast<const float4 *>(a.w + (int64_t)id.ws * B3 + l0));
-        const int64_t b = gi * G + j;
         h.bc = make_int4(0, 0, 0, 0);
-        if (a.held_mask && gi < g1 && b < a.nb) h.bc = __ldg(a.blocks + b);
+        if (a.held_mask && gi < g1) {
+            int64_t b0, nblk;
+            span(gi, b0, nblk);
+            if (j < nblk) h.bc = __ldg(a.blocks + b0 + j);
+        }
     };
 
     // One group: park this group's prefetched halo values in this thread's
@@ -192,8 +209,10 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     auto body = [&](int64_t gi, int it, Halo &cur, Halo &nxt, const Ids &id1, Ids &id2) -> bool {
         const int s = it % S;
         const uint32_t par = (uint32_t)((it / S) & 1);
-        const int64_t b = gi * G + j;
-        const bool valid = b < a.nb;
+        int64_t b0, nblk;
+        span(gi, b0, nblk);
+        const int64_t b = b0 + j;
+        const bool valid = j < nblk;
         if (PF) {
             if (valid) park(cur);
             id2 = load_ids(gi + 2);
@@ -324,7 +343,7 @@ static cudaError_t launch_pipe_pf(const StepArgs &a, int ctas_per_sm, int *err, 
         if (occ < 1) occ = 1;
     }
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-    const int64_t ngroups = (a.nb + G - 1) / G;
+    const int64_t ngroups = a.items ? a.nitems : (a.nb + G - 1) / G;
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ngroups) grid = ngroups;
     if (grid < 1) return cudaSuccess;

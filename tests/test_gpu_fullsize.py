@@ -1,0 +1,111 @@
+"""Parity at the workloads' full sizes, in the launch configuration the bench
+times (pipelined kernel, block edge 4).
+
+* 256^3 tortuosity solve: the compensated-FP32 steady state (relative
+  residual < 1e-8) against the FP64 oracle's CG steady state stored by
+  tests/golden/make_golden.py: D_eff to 1e-6 relative, the field at 4096
+  sampled voxels to 1e-5.
+* 512^3 two-species reactive run: after n steps every voxel depends only on
+  voxels at most n steps away, so the oracle recomputes sampled voxels exactly
+  on a (2n+1)^3 crop around each; plus the exact per-step balance of the total
+  mass, sum(A+B)^{n+1} = sum(A+B)^n - dt * decay_B * sum B^n.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import Physics, grf256, reactive512
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2304_11165_b300 import Grid, State, make_params  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "grf256_steady.json")
+
+
+@pytest.fixture(scope="module")
+def reactive():
+    return reactive512()
+
+
+def test_grf256_steady_state_matches_the_oracle_cg():
+    gold = json.load(open(GOLDEN))
+    phi, u0, phys = grf256()
+    g = Grid(phi, block=4)
+    st = State(g, 1, "f32x2").set_kernel("pipelined").set(u0)
+    p = make_params(phys)
+    steps, rel = st.run_to_steady(p, 1e-8, check_every=4096, max_steps=8_000_000)
+    assert rel < 1e-8
+    d_eff, tau, psi = st.effective_D(p)
+    assert psi == gold["psi"]
+    assert abs(d_eff - gold["D_eff"]) <= 1e-6 * gold["D_eff"], (d_eff, gold["D_eff"])
+    assert abs(tau - gold["tau"]) <= 1e-6 * gold["tau"]
+    field = st.get()
+    z, y, x = np.array(gold["samples_zyx"]).T
+    err = np.max(np.abs(field[z, y, x] - np.array(gold["samples_u"])))
+    assert err <= 1e-5, err
+
+
+def crop_reference(phi, u0, phys, centre, n):
+    """Oracle value of the voxel `centre` after n steps, from the crop of all
+    voxels within n steps of it (a closed box: crop faces that are box faces
+    keep the no-flux rule, the others are at least n voxels away)."""
+    z, y, x = centre
+    nz, ny, nx = phi.shape
+    lo = [max(0, c - n) for c in (z, y, x)]
+    hi = [min(s, c + n + 1) for c, s in zip((z, y, x), (nz, ny, nx))]
+    sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+    sub = np.ascontiguousarray(phi[sl])
+    pc = Physics(dims=tuple(reversed(sub.shape)), dt=phys.dt, nspecies=phys.nspecies, D=phys.D,
+                 decay=phys.decay, k_surf=phys.k_surf)
+    usub = np.ascontiguousarray(u0[(slice(None),) + sl])
+    out = oracle.Problem(sub, pc).run(usub, n)
+    return out[:, z - lo[0], y - lo[1], x - lo[2]]
+
+
+def test_reactive512_sampled_voxels_match_the_oracle(reactive):
+    phi, u0, phys = reactive
+    n = 40
+    g = Grid(phi, block=4)
+    st = State(g, 2, "f32").set_kernel("pipelined").set_all(u0)
+    st.step(make_params(phys), n)
+    A, B = st.get(0), st.get(1)
+    rng = np.random.default_rng(7)
+    act = phi > np.float32(oracle.FLT_EPSILON)
+    # half the samples where species A and B change (the x < 32 front), half anywhere
+    front = np.argwhere(act[:, :, 20:44]) + np.array([0, 0, 20])
+    anywhere = np.argwhere(act[::7, ::7, ::7]) * 7
+    picks = [tuple(front[i]) for i in rng.choice(len(front), 12, replace=False)] + \
+            [tuple(anywhere[i]) for i in rng.choice(len(anywhere), 12, replace=False)]
+    for c in picks:
+        ref = crop_reference(phi, u0, phys, c, n)
+        assert abs(A[c] - ref[0]) <= 1e-5 and abs(B[c] - ref[1]) <= 1e-5, (c, A[c], B[c], ref)
+
+
+def test_reactive512_total_mass_balance_per_step(reactive):
+    phi, u0, phys = reactive
+    g = Grid(phi, block=4)
+    st = State(g, 2, "f32").set_kernel("pipelined").set_all(u0)
+    p = make_params(phys)
+    red = st.reduce(p)
+    m_prev = red[0]["mass"] + red[1]["mass"]
+    b_prev = red[1]["mass"]
+    m0 = m_prev
+    worst = 0.0
+    for _ in range(60):
+        st.step(p, 1)
+        red = st.reduce(p)
+        m = red[0]["mass"] + red[1]["mass"]
+        expected = m_prev - phys.dt * phys.decay[1] * b_prev
+        worst = max(worst, abs(m - expected) / m0)
+        m_prev, b_prev = m, red[1]["mass"]
+        assert red[0]["min"] >= 0.0 and red[0]["max"] <= 1.0 + 1e-6
+    # FP32 state: the per-step balance holds to the rounding of the stored values
+    assert worst < 2e-7, worst

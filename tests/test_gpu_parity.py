@@ -182,7 +182,7 @@ def test_channel_steady_state_gives_exact_deff():
     g = Grid(phi, block=8)
     st = State(g, 1, "f32x2").set(u0)
     p = make_params(phys)
-    steps, rel = st.run_to_steady(p, 1e-10, check_every=500)
+    steps, rel = st.run_to_steady(p, 1e-10, check_every=500, max_steps=2_000_000)
     d_eff, tau, psi = st.effective_D(p)
     assert abs(psi - 25 / 144) < 1e-15
     assert abs(d_eff - psi) < 1e-6 * psi
