@@ -118,8 +118,9 @@ enum {
 /* ---- grid ------------------------------------------------------------------
  * Block activation and indexing (Sec. 2.3-2.4: chunks stored only if they
  * hold at least one inserted point; Appendix B Listing 5 for the insertion
- * test).  Builds, on `stream`: the compact list of active blocks in x-fastest
- * block order, an open-addressing device hash from block coordinates to block
+ * test).  Builds, on `stream`: the compact list of active blocks in tiled
+ * order (tiles of 32^3 voxels in x-fastest order, blocks x-fastest inside a
+ * tile, so that face neighbours are close in the list), an open-addressing device hash from block coordinates to block
  * id, the 26-neighbour table (id or -1), one occupancy bitmap per block and
  * the surface-weight slabs of blocks that meet the band 0 < phi < eps_b.
  * phi: dense FP32 [Nz][Ny][Nx], host or device (opts->phi_on_device).

@@ -6,9 +6,10 @@
 // inserts a point iff phi > lower bound + eps (Appendix B, Listing 5).  This
 // file builds the same information for B^3 blocks (B = 4 or 8) directly on
 // the device: one warp scans each box block of phi, an exclusive scan
-// compacts the active ones in x-fastest block order, an open-addressing hash
+// compacts the active ones in tiled block order, an open-addressing hash
 // maps block coordinates to ids, and the neighbour table is resolved once so
-// that the time step never probes the hash.
+// that the time step never probes the hash.  Blocks are listed tile by tile
+// (see BlockEnum) so that face neighbours are close in the list.
 #include <math.h>
 
 #include <algorithm>
@@ -132,14 +133,51 @@ static sbg_status exclusive_scan(const int32_t *in, int64_t n, bool as_flags, in
 }
 
 // ---------------------------------------------------------------------------
-// block activation: one warp per box block counts voxels with phi > eps
+// Block order.  Box blocks are enumerated tile by tile (tiles of T x T x T
+// blocks, T = 32 / B, i.e. 32^3 voxels; tiles and the blocks inside a tile in
+// x-fastest order), and the active ones are compacted in that order.  All six
+// face neighbours of a block are then close to it in the list, so a CTA that
+// walks a contiguous range of the list finds most halo values in L2 and meets
+// a neighbour block soon after reading its halo.
+struct BlockEnum {
+    int nbx, nby, nbz, T, ntx, nty, ntz;
+    __host__ __device__ int64_t count() const { return (int64_t)ntx * nty * ntz * T * T * T; }
+    // enumeration index -> block coordinates; false when the slot is padding
+    __host__ __device__ bool decode(int64_t k, int &bx, int &by, int &bz) const {
+        const int64_t t3 = (int64_t)T * T * T;
+        const int64_t tile = k / t3;
+        const int inner = (int)(k - tile * t3);
+        const int tx = (int)(tile % ntx), ty = (int)((tile / ntx) % nty), tz = (int)(tile / ((int64_t)ntx * nty));
+        bx = tx * T + inner % T;
+        by = ty * T + (inner / T) % T;
+        bz = tz * T + inner / (T * T);
+        return bx < nbx && by < nby && bz < nbz;
+    }
+};
+static BlockEnum make_enum(int64_t nx, int64_t ny, int64_t nz, int B) {
+    BlockEnum e;
+    e.nbx = (int)((nx + B - 1) / B);
+    e.nby = (int)((ny + B - 1) / B);
+    e.nbz = (int)((nz + B - 1) / B);
+    e.T = 32 / B;
+    e.ntx = (e.nbx + e.T - 1) / e.T;
+    e.nty = (e.nby + e.T - 1) / e.T;
+    e.ntz = (e.nbz + e.T - 1) / e.T;
+    return e;
+}
+
+// block activation: one warp per enumerated box block counts voxels with phi > eps
 template <int B>
-__global__ void k_block_count(const float *__restrict__ phi, int nx, int ny, int nz, int nbx,
-                              int nby, int64_t nbox, float eps, int32_t *count) {
+__global__ void k_block_count(const float *__restrict__ phi, int nx, int ny, int nz, BlockEnum en,
+                              int64_t nbox, float eps, int32_t *count) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= nbox) return;
-    const int bx = (int)(warp % nbx), by = (int)((warp / nbx) % nby), bz = (int)(warp / ((int64_t)nbx * nby));
+    int bx, by, bz;
+    if (!en.decode(warp, bx, by, bz)) {
+        if (lane == 0) count[warp] = 0;
+        return;
+    }
     int c = 0;
     for (int l = lane; l < B * B * B; l += 32) {
         int x = bx * B + l % B, y = by * B + (l / B) % B, z = bz * B + l / (B * B);
@@ -150,14 +188,12 @@ __global__ void k_block_count(const float *__restrict__ phi, int nx, int ny, int
     if (lane == 0) count[warp] = c;
 }
 
-__global__ void k_compact(const int32_t *count, const int32_t *pos, int64_t nbox, int nbx, int nby,
-                          int geom, int64_t offset, int4 *blocks) {
+__global__ void k_compact(const int32_t *count, const int32_t *pos, int64_t nbox, BlockEnum en, int geom,
+                          int64_t offset, int4 *blocks) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nbox || count[k] == 0) return;
     int4 b;
-    b.x = (int)(k % nbx);
-    b.y = (int)((k / nbx) % nby);
-    b.z = (int)(k / ((int64_t)nbx * nby));
+    en.decode(k, b.x, b.y, b.z);
     b.w = geom;
     blocks[offset + pos[k]] = b;
 }
@@ -391,13 +427,12 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
             TRYC(cudaMalloc(&dphi[i], sizeof(float) * nvox));
             TRYC(cudaMemcpyAsync(dphi[i], phis[i], sizeof(float) * nvox, cudaMemcpyHostToDevice, st));
         }
-        const int nbx = (int)((nx + B - 1) / B), nby = (int)((ny + B - 1) / B),
-                  nbz = (int)((nz + B - 1) / B);
-        const int64_t nbox = (int64_t)nbx * nby * nbz;
+        const BlockEnum en = make_enum(nx, ny, nz, B);
+        const int64_t nbox = en.count();
         TRYC(cudaMalloc(&dcount[i], sizeof(int32_t) * nbox));
         TRYC(cudaMalloc(&dpos[i], sizeof(int32_t) * nbox));
         k_block_count<B><<<(unsigned)((nbox * 32 + 255) / 256), 256, 0, st>>>(
-            dphi[i], (int)nx, (int)ny, (int)nz, nbx, nby, nbox, g->eps_mask, dcount[i]);
+            dphi[i], (int)nx, (int)ny, (int)nz, en, nbox, g->eps_mask, dcount[i]);
         TRY(cuda_ok(cudaGetLastError(), "k_block_count"));
         int64_t nbg = 0;
         TRY(exclusive_scan(dcount[i], nbox, true, dpos[i], &nbg, st));
@@ -442,11 +477,10 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
     // pass 2: compaction, bitmaps, band flags
     for (int i = 0; i < n; ++i) {
         const int64_t nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
-        const int nbx = (int)((nx + B - 1) / B), nby = (int)((ny + B - 1) / B),
-                  nbz = (int)((nz + B - 1) / B);
-        const int64_t nbox = (int64_t)nbx * nby * nbz;
-        k_compact<<<(unsigned)((nbox + 255) / 256), 256, 0, st>>>(dcount[i], dpos[i], nbox, nbx, nby,
-                                                                 i, g->geom_begin[i], g->blocks);
+        const BlockEnum en = make_enum(nx, ny, nz, B);
+        const int64_t nbox = en.count();
+        k_compact<<<(unsigned)((nbox + 255) / 256), 256, 0, st>>>(dcount[i], dpos[i], nbox, en, i,
+                                                                 g->geom_begin[i], g->blocks);
         if (g->geom_count[i] > 0)
             k_block_fill<B><<<(unsigned)((g->geom_count[i] * 32 + 255) / 256), 256, 0, st>>>(
                 dphi[i], (int)nx, (int)ny, (int)nz, g->blocks, g->geom_begin[i], g->geom_count[i],

@@ -6,7 +6,9 @@ times (pipelined kernel, block edge 4).
   1e-6 relative, the field at 4096 sampled voxels to 1e-5.  On this geometry
   the D_eff error follows the relative residual R as ~0.11 R (the slowest
   mode's flux cancels in the mean of inlet and outlet flux, the next one does
-  not), so the solve runs to R < 5e-9; R < 1e-8 gives 1.1e-6.
+  not; R < 1e-8 gives 1.1e-6) while the field error is ~3000 R (that mode's
+  amplitude), so the solve runs to R < 1e-10, near the compensated state's
+  floor of ~2e-11.
 * 512^3 two-species reactive run: after n steps every voxel depends only on
   voxels at most n steps away, so the oracle recomputes sampled voxels exactly
   on a (2n+1)^3 crop around each; plus the exact per-step balance of the total
@@ -43,8 +45,8 @@ def test_grf256_steady_state_matches_the_oracle_cg():
     g = Grid(phi, block=4)
     st = State(g, 1, "f32x2").set_kernel("pipelined").set(u0)
     p = make_params(phys)
-    steps, rel = st.run_to_steady(p, 5e-9, check_every=4096, max_steps=4_000_000)
-    assert rel < 5e-9
+    steps, rel = st.run_to_steady(p, 1e-10, check_every=8192, max_steps=4_000_000)
+    assert rel < 1e-10
     d_eff, tau, psi = st.effective_D(p)
     assert psi == gold["psi"]
     assert abs(d_eff - gold["D_eff"]) <= 1e-6 * gold["D_eff"], (d_eff, gold["D_eff"])

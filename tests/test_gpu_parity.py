@@ -74,7 +74,19 @@ def test_grid_tables_match_brute_force(case):
     act = np.zeros((nbz * block, nby * block, nbx * block), bool)
     act[:nz, :ny, :nx] = P.active > 0
     occ = act.reshape(nbz, block, nby, block, nbx, block).any(axis=(1, 3, 5))
-    expect = [(bx, by, bz) for bz in range(nbz) for by in range(nby) for bx in range(nbx) if occ[bz, by, bx]]
+    # tiled order: tiles of T^3 blocks (T = 32 / B, 32^3 voxels), tiles and blocks inside a tile x-fastest
+    T = 32 // block
+    ntx, nty, ntz = [(n + T - 1) // T for n in (nbx, nby, nbz)]
+    expect = []
+    for tz in range(ntz):
+        for ty in range(nty):
+            for tx in range(ntx):
+                for iz in range(T):
+                    for iy in range(T):
+                        for ix in range(T):
+                            bx, by, bz = tx * T + ix, ty * T + iy, tz * T + iz
+                            if bx < nbx and by < nby and bz < nbz and occ[bz, by, bx]:
+                                expect.append((bx, by, bz))
     assert [tuple(b[:3]) for b in blocks] == expect
     assert g.n_active == int(P.active.sum())
     index = {c: i for i, c in enumerate(expect)}
