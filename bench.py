@@ -1,12 +1,12 @@
 #!/usr/bin/env python3
 """Throughput of the sparse-block-grid reaction-diffusion step on one B300.
 
-Workload (default): the 256^3 tortuosity solve - a thresholded Gaussian
-random field (correlation length 8, porosity 0.35), c = 1 / c = 0 held on the
-x faces, D = 1, dt = 0.15, compensated-FP32 state (FP32 arithmetic, value =
-hi + lo) with FP64 reductions.  One bench step = one check interval of the
-steady-state solve: 128 forward-Euler steps plus the FP64 residual and flux
-reduction that decides convergence.
+Default workload (`--workload grf256`): the 256^3 tortuosity solve - a
+thresholded Gaussian random field (correlation length 8, porosity 0.35),
+c = 1 / c = 0 held on the x faces, D = 1, dt = 0.15, compensated-FP32 state
+(FP32 arithmetic, value = hi + lo) with FP64 reductions.  One bench step = one
+check interval of the steady-state solve: 128 forward-Euler steps plus the
+FP64 residual and flux reduction that decides convergence.
 
 Metric: active-voxel updates per second (GVox/s) = n_active * 128 * steps /
 time.  `value` is measured with CUDA events on the stream the library uses,
@@ -16,14 +16,23 @@ D_eff read back.  `roofline` reports the step kernel's algorithmic bytes
 (16 B per active voxel: hi and lo read and written) per launch over its
 average launch time, against the measured HBM copy bandwidth.
 
+Other workloads print one JSON line each:
+  --workload reactive512   two species, surface reaction A -> B, 2000 steps (512^3)
+  --workload gradient256   checkpointed adjoint of 1000 steps (256^3): adjoint / forward time,
+                           memory, FP64 central-difference checks (--fd)
+  --workload batch64       64 uneven geometries: one batched launch per step vs per-geometry
+                           launches (fixed steps; --converge: steady solves to 1e-6)
+
 `--impl reference` times the FP64 dense CPU oracle on the host cores on the
 same workload (a bounded number of steps per bench step).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -39,6 +48,8 @@ if ROOT not in sys.path:
 CHECK_EVERY = 128
 BYTES_PER_VOXEL = {"f32": 8, "f32x2": 16, "f64": 16}
 METRIC = "active-voxel updates/s per RD step (grf256 tortuosity solve)"
+KERNEL_SOURCES = ["paper_2304_11165_b300/csrc/sbg_step_pipe.cu", "paper_2304_11165_b300/csrc/sbg_step.cuh",
+                  "paper_2304_11165_b300/csrc/sbg_ptx.cuh"]
 
 
 def parse():
@@ -47,14 +58,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sbg", choices=["sbg", "reference"])
-    ap.add_argument("--n", type=int, default=256, help="box side")
+    ap.add_argument("--workload", default="grf256", choices=["grf256", "reactive512", "gradient256", "batch64"])
+    ap.add_argument("--n", type=int, default=None, help="box side (default: the workload's)")
     ap.add_argument("--block", type=int, default=4)
-    ap.add_argument("--dtype", default="f32x2", choices=["f32", "f32x2", "f64"])
+    ap.add_argument("--dtype", default="f32x2", choices=["f32", "f32x2"])
+    ap.add_argument("--variant", default="pipelined", choices=["plain", "pipelined", "prefetch"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--fd", action="store_true", help="gradient256: FP64 central differences")
+    ap.add_argument("--converge", action="store_true", help="batch64: steady solves to 1e-6")
+    ap.add_argument("--sides", default="64,96,128,192,256", help="batch64: box sides")
+    ap.add_argument("--count", type=int, default=64, help="batch64: number of geometries")
     return ap.parse_args()
 
 
+# ---------------------------------------------------------------------------
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -63,10 +81,26 @@ def load_peaks():
     return 6400.0, "fallback"
 
 
-def workload(n):
-    from workloads import grf256
-    phi, u0, phys = grf256(n=n)
-    return phi, u0, phys
+def kernel_sha():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    summary is missing or the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    sha = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
+    tb = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+    if not sha or not tb or sha.group(1) != kernel_sha():
+        return None
+    return int(tb.group(1))
 
 
 class ClockSampler:
@@ -117,7 +151,7 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(phi, u0, phys, n_active, seconds, nsteps_hint=None):
+def cpu_baseline(phi, u0, phys, n_active, seconds):
     """The FP64 dense oracle as it stands, on the host cores, on a bounded
     number of steps of the same workload."""
     import oracle
@@ -126,22 +160,32 @@ def cpu_baseline(phi, u0, phys, n_active, seconds, nsteps_hint=None):
     t0 = time.perf_counter()
     u = P.run(u, 1)
     one = time.perf_counter() - t0
-    nsteps = nsteps_hint or max(1, int(seconds / max(one, 1e-6)))
+    nsteps = max(1, int(seconds / max(one, 1e-6)))
     t0 = time.perf_counter()
     P.run(u, nsteps)
     dt = time.perf_counter() - t0
-    return {"value": n_active * nsteps / dt / 1e9, "unit": "GVox/s", "cores": oracle.num_threads(),
+    species = int(phys.nspecies)
+    return {"value": species * n_active * nsteps / dt / 1e9, "unit": "GVox/s", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": "%d FP64 dense steps of the full %s box (all %d voxels visited per step)"
-                      % (nsteps, "x".join(str(d) for d in phys.dims), int(np.prod(phys.dims)))}, dt
+                      % (nsteps, "x".join(str(d) for d in phys.dims), int(np.prod(phys.dims)))}
 
 
+def emit(line):
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    phi, u0, phys = workload(args.n)
+    if args.workload != "grf256":
+        emit({"impl": "reference", "unavailable": "the reference arm times the default workload only"})
+        return 0
+    from workloads import grf256
     import oracle
+    phi, u0, phys = grf256(n=args.n or 256)
     P = oracle.Problem(phi, phys)
     n_active = int(P.active.sum())
     u = P.shape_state(u0)
@@ -153,26 +197,25 @@ def run_reference(args):
         u = P.run(u, per_step)
     dt = time.perf_counter() - t0
     value = n_active * per_step * args.steps / dt / 1e9
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GVox/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "grf256 tortuosity solve (256^3 GRF, porosity 0.35)",
-                       "box": list(phys.dims), "steps_per_bench_step": per_step},
-            "cpu_baseline": {"value": value, "unit": "GVox/s", "cores": oracle.num_threads(),
-                             "kind": "oracle",
-                             "sample": "%d FP64 dense steps of the full box per bench step" % per_step},
-            "e2e": {"value": value, "unit": "GVox/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "GVox/s",
+          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+          "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": "grf256 tortuosity solve (256^3 GRF, porosity 0.35)",
+                     "box": list(phys.dims), "steps_per_bench_step": per_step},
+          "cpu_baseline": {"value": value, "unit": "GVox/s", "cores": oracle.num_threads(), "kind": "oracle",
+                           "sample": "%d FP64 dense steps of the full box per bench step" % per_step},
+          "e2e": {"value": value, "unit": "GVox/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
     return 0
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-
+# ---------------------------------------------------------------------------
+def run_grf256(args):
     import torch
+    from paper_2304_11165_b300 import Grid, State, make_params
+    import paper_2304_11165_b300._abi as abi
+    from workloads import grf256
+
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -182,29 +225,21 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    # CPU baseline first (before heavy GPU use; the oracle runs in this process's threads)
-    phi, u0, phys = workload(args.n)
-    from paper_2304_11165_b300 import Grid, State, make_params
-    import paper_2304_11165_b300._abi as abi
-
+    n = args.n or 256
+    phi, u0, phys = grf256(n=n)
     stream = torch.cuda.current_stream(dev)
     g = Grid(phi, block=args.block, stream=stream)
     n_active = g.n_active
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _ = cpu_baseline(phi, u0, phys, n_active, args.cpu_seconds)
+        cpu = cpu_baseline(phi, u0, phys, n_active, args.cpu_seconds)
 
-    st = State(g, 1, args.dtype)
+    st = State(g, 1, args.dtype).set_kernel(args.variant)
     p = make_params(phys)
-    u0_dev = torch.from_numpy(u0.astype(np.float32)).to(dev)
-    st.set(u0_dev, stream=stream)
-
-    def bench_step():
-        st.step(p, CHECK_EVERY, stream=stream)
-        return st.effective_D(p, stream=stream)
-
+    st.set(torch.from_numpy(u0.astype(np.float32)).to(dev), stream=stream)
     for _ in range(args.warmup):
-        bench_step()
+        st.step(p, CHECK_EVERY, stream=stream)
+        st.effective_D(p, stream=stream)
     torch.cuda.synchronize(dev)
 
     # device-resident timed region
@@ -232,12 +267,11 @@ def main():
         t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    updates = n_active * CHECK_EVERY * args.steps * world
-    value = updates / (total_ms / 1e3) / 1e9
+    value = n_active * CHECK_EVERY * args.steps * world / (total_ms / 1e3) / 1e9
 
     # end-to-end through the public API: dense field from pinned host memory every step
     u0_host = torch.from_numpy(u0.astype(np.float32)).pin_memory()
-    st2 = State(g, 1, args.dtype)
+    st2 = State(g, 1, args.dtype).set_kernel(args.variant)
     for _ in range(2):
         st2.set(u0_host, stream=stream)
         st2.step(p, CHECK_EVERY, stream=stream)
@@ -259,37 +293,289 @@ def main():
     algo_bytes = n_active * BYTES_PER_VOXEL[args.dtype]
     achieved = algo_bytes / (step_kernel_ms / 1e3) / 1e9
     d_eff, tau, psi = st.effective_D(p, stream=stream)
-    kernel_name = "k_step_x2" if args.dtype == "f32x2" else "k_step"
-    launches_per_step = CHECK_EVERY + 2
+    kernel_name = "k_step_pipe" if args.variant != "plain" else ("k_step_x2" if args.dtype == "f32x2" else "k_step")
+    traffic = None
+    if (n, args.block, args.dtype, args.variant) == (256, 4, "f32x2", "pipelined"):
+        traffic = profile_traffic("k_step_pipe_x2_grf256.md")
     line = {
         "metric": METRIC, "value": value, "unit": "GVox/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": "grf256 tortuosity solve: %d^3 GRF (correlation length 8, porosity 0.35), "
-                               "c=1/c=0 on the x faces, D=1, dt=0.15" % args.n,
-                   "block": args.block, "rd_steps_per_bench_step": CHECK_EVERY,
+                               "c=1/c=0 on the x faces, D=1, dt=0.15" % n,
+                   "block": args.block, "kernel": args.variant, "rd_steps_per_bench_step": CHECK_EVERY,
                    "n_active": n_active, "n_blocks": g.n_blocks, "porosity": psi,
-                   "state_bytes": st.grid.info["n_blocks"] * args.block ** 3 * BYTES_PER_VOXEL[args.dtype] * 2,
+                   "state_bytes": g.n_blocks * args.block ** 3 * BYTES_PER_VOXEL[args.dtype] * 2,
                    "l2": "working set (two state buffers) larger than the 126 MB L2; no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None,
-                     "algorithmic_bytes_per_launch": algo_bytes,
-                     "avg_launch_us": step_kernel_ms * 1e3},
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": step_kernel_ms * 1e3},
         "e2e": {"value": e2e_value, "unit": "GVox/s", "h2d_bytes_per_step": int(u0.size * 4),
                 "d2h_bytes_per_step": abi.NRED * 8},
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": (CHECK_EVERY + 2) * args.steps,
         "clocks": clocks,
         "result": {"D_eff_after_warmup_and_timed_steps": d_eff, "tau": tau},
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
-        print(json.dumps(line))
+        emit(line)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+def run_reactive512(args):
+    import torch
+    from paper_2304_11165_b300 import Grid, State, make_params
+    from workloads import reactive512
+    torch.cuda.set_device(0)
+    n = args.n or 512
+    phi, u0, phys = reactive512(n=n)
+    stream = torch.cuda.current_stream()
+    g = Grid(phi, block=args.block, stream=stream)
+    st = State(g, 2, "f32").set_kernel(args.variant).set_all(u0, stream=stream)
+    p = make_params(phys)
+    red0 = st.reduce(p)
+    per = 100
+    st.step(p, 3 * per, stream=stream)  # warm-up, then restart from the initial state
+    st.set_all(u0, stream=stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kernel_ms = 0.0
+    masses = []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(phys.steps // per):
+        a.record(stream)
+        st.step(p, per, stream=stream)
+        b.record(stream)
+        red = st.reduce(p)  # synchronises
+        kernel_ms += a.elapsed_time(b)
+        masses.append((red[0]["mass"], red[1]["mass"]))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    updates = 2 * g.n_active * phys.steps
+    peak, peak_kind = load_peaks()
+    band_slots = g.info["n_band_blocks"] * args.block ** 3
+    algo_bytes = g.n_active * 16 + band_slots * 4
+    per_launch_ms = kernel_ms / phys.steps
+    cpu = None if args.no_cpu_baseline else cpu_baseline(phi, u0, phys, g.n_active, args.cpu_seconds)
+    emit({"metric": "species-voxel updates/s (two-species reactive run)", "value": updates / (total_ms / 1e3) / 1e9,
+          "unit": "GVox/s", "n_gpus": 1, "steps": phys.steps, "ms_per_step": total_ms / phys.steps,
+          "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+          "config": {"workload": "reactive512: %d^3 Boolean sphere packing (median radius 12, sigma 0.3), "
+                                 "pore fraction %.3f, A->B surface reaction k=0.05, decay_B=0.001, %d steps"
+                                 % (n, phys.extra["pore_fraction"], phys.steps),
+                     "block": args.block, "kernel": args.variant, "n_active": g.n_active, "n_blocks": g.n_blocks,
+                     "band_blocks": g.info["n_band_blocks"]},
+          "roofline": {"bound": "hbm", "kernel": "k_step_pipe", "achieved": algo_bytes / (per_launch_ms / 1e3) / 1e9,
+                       "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                       "frac": algo_bytes / (per_launch_ms / 1e3) / 1e9 / peak,
+                       "traffic": profile_traffic("k_step_pipe_f32_reactive512.md"),
+                       "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": per_launch_ms * 1e3},
+          "result": {"mass_A0_B0": [red0[0]["mass"], red0[1]["mass"]], "mass_A_B_end": list(masses[-1]),
+                     "total_mass_change": (masses[-1][0] + masses[-1][1]) - (red0[0]["mass"] + red0[1]["mass"])},
+          "clocks": clocks, "cpu_baseline": cpu})
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_gradient256(args):
+    import dataclasses
+
+    import torch
+    from paper_2304_11165_b300 import Grid, State, make_params
+    from paper_2304_11165_b300.autograd import adjoint, forward_record
+    from workloads import gradient_setup
+    torch.cuda.set_device(0)
+    n = args.n or 256
+    phi, u0, phys, x_cut = gradient_setup(n=n)
+    nsteps, K = phys.steps, 64
+    stream = torch.cuda.current_stream()
+    torch.cuda.reset_peak_memory_stats()
+    g = Grid(phi, block=args.block)
+    p = make_params(phys)
+    active = State(g, 1, "f32").set(np.ones(phi.shape, np.float32)).get() != 0
+    slab = active.copy()
+    slab[:, :, :x_cut + 1] = False
+    lamN = np.where(slab, 1.0 / slab.sum(), 0.0)
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    st = State(g, 1, "f32").set_kernel(args.variant).set(u0)
+    _, fwd_ms = timed(lambda: st.step(p, nsteps))
+    st.set(u0)
+    tape, rec_ms = timed(lambda: forward_record(st, p, nsteps, K))
+    loss = float((st.get() * lamN).sum())
+    lam = State(g, 1, "f32").set(lamN)
+    grad, adj_ms = timed(lambda: adjoint(tape, lam))
+    lam0 = lam.get()
+    lam.set(lamN)
+    grad2, adj2_ms = timed(lambda: adjoint(tape, lam))  # second call: recompute buffer already allocated
+    info = tape.info()
+    mem = {"tape_bytes": info["device_bytes"], "grid_bytes": g.info["device_bytes"],
+           "state_bytes": 3 * g.n_blocks * args.block ** 3 * 4 * 2,
+           "torch_max_allocated": torch.cuda.max_memory_allocated()}
+    mem["total_bytes"] = mem["tape_bytes"] + mem["grid_bytes"] + mem["state_bytes"] + mem["torch_max_allocated"]
+    out = {"metric": "adjoint time / forward time (gradient of the outlet-slab mean, 1000 steps)",
+           "value": adj2_ms / fwd_ms, "unit": "ratio", "higher_is_better": False, "n_gpus": 1,
+           "dtype": "f32 state, f64 gradient sums", "data": "synthetic",
+           "config": {"workload": "gradient256: %d^3 GRF geometry, A0=1, A=0 held on x=%d, surface sink k=0.05, "
+                                  "%d steps, checkpoints every %d, loss = mean of A over pore voxels x > %d"
+                                  % (n, n - 1, nsteps, K, x_cut),
+                      "block": args.block, "n_active": g.n_active, "checkpoints": info["checkpoints"]},
+           "times_ms": {"forward": fwd_ms, "forward_recording_checkpoints": rec_ms, "adjoint_first_call": adj_ms,
+                        "adjoint": adj2_ms},
+           "gvox_forward": g.n_active * nsteps / (fwd_ms / 1e3) / 1e9,
+           "gvox_adjoint_incl_recompute": g.n_active * nsteps / (adj2_ms / 1e3) / 1e9,
+           "memory": mem, "loss": loss,
+           "gradient": {"dL_dD": grad[0], "dL_dk": grad[2], "repeat_equal": bool(np.array_equal(grad, grad2))}}
+    if args.fd:
+        def loss64(ph, u_init):
+            s = State(g, 1, "f64").set(u_init)
+            s.step(make_params(ph), nsteps)
+            return float((s.get() * lamN).sum())
+        fd = {}
+        for name, base in (("D", phys.D[0]), ("k", phys.k_surf)):
+            h = 1e-3 * base
+            if name == "D":
+                plus, minus = dataclasses.replace(phys, D=(base + h, 0.0)), dataclasses.replace(phys, D=(base - h, 0.0))
+            else:
+                plus, minus = dataclasses.replace(phys, k_surf=base + h), dataclasses.replace(phys, k_surf=base - h)
+            val = (loss64(plus, u0) - loss64(minus, u0)) / (2 * h)
+            gval = grad[0] if name == "D" else grad[2]
+            fd[name] = {"fd_fp64": val, "adjoint_fp32": gval, "rel_diff": abs(gval - val) / abs(val)}
+        rng = np.random.default_rng(5)
+        v = rng.standard_normal(phi.shape) * (lam0 != 0)
+        h = 1e-3
+        dirv = (loss64(phys, u0 + h * v) - loss64(phys, u0 - h * v)) / (2 * h)
+        ad = float((lam0 * v).sum())
+        fd["c0_direction"] = {"fd_fp64": dirv, "adjoint_fp32": ad, "rel_diff": abs(ad - dirv) / abs(dirv)}
+        out["finite_differences"] = fd
+    emit(out)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_batch64(args):
+    import torch
+    from paper_2304_11165_b300 import Grid, State, autotune, make_params
+    from workloads import batch_geometries
+    from workloads.configs import initial_with_faces
+    torch.cuda.set_device(0)
+    sides = tuple(int(s) for s in args.sides.split(","))
+    t0 = time.time()
+    geos = list(batch_geometries(count=args.count, sides=sides))
+    gen_s = time.time() - t0
+    phis = [phi for _, phi, _ in geos]
+    phys0 = geos[0][2]
+    p = make_params(phys0)
+    best, table = autotune.tune(phis, phys0, "f32x2")
+    B, variant, ctas = best["block"], best["variant"], best["ctas_per_sm"]
+    stream = torch.cuda.current_stream()
+
+    def init(state, gi, phys):
+        state.set(initial_with_faces(phys.dims, 0.0, phys), geom=gi, stream=stream)
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    nsteps = 1024
+    gb = Grid.batch(phis, block=B)
+    na, _, _ = gb.geometry_info()
+    sb = State(gb, 1, "f32x2").set_kernel(variant, ctas)
+    for gi, (_, _, ph) in enumerate(geos):
+        init(sb, gi, ph)
+    sb.step(p, 64)
+    _, batch_ms = timed(lambda: sb.step(p, nsteps))
+    seq = {}
+    for kv in ("plain", variant):
+        total = 0.0
+        for gi, (_, phi, ph) in enumerate(geos):
+            g1 = Grid(phi, block=B)
+            s1 = State(g1, 1, "f32x2").set_kernel(kv, ctas if kv == variant else 0)
+            init(s1, 0, ph)
+            s1.step(p, 64)
+            _, ms = timed(lambda: s1.step(p, nsteps))
+            total += ms
+            s1.close()
+            g1.close()
+        seq[kv] = total
+    upd = float(na.sum()) * nsteps
+    out = {"metric": "aggregate active-voxel updates/s, 64 uneven geometries (batched vs per-geometry launches)",
+           "value": upd / (batch_ms / 1e3) / 1e9, "unit": "GVox/s", "higher_is_better": True, "n_gpus": 1,
+           "dtype": "f32x2", "data": "synthetic",
+           "config": {"workload": "batch64: %d geometries, sides %s, spheres/GRF alternating, porosity U(0.2,0.6), "
+                                  "tortuosity physics" % (len(geos), list(sides)),
+                      "autotuned": best, "autotune_table": table, "n_active_total": int(na.sum()),
+                      "box_voxels_total": int(sum(phi.size for phi in phis)), "generation_s": gen_s},
+           "fixed_steps": {"steps": nsteps, "batched_ms": batch_ms,
+                           "sequential_plain_ms": seq["plain"], "sequential_same_kernel_ms": seq[variant],
+                           "gvox_batched": upd / (batch_ms / 1e3) / 1e9,
+                           "gvox_sequential_plain": upd / (seq["plain"] / 1e3) / 1e9,
+                           "gvox_sequential_same_kernel": upd / (seq[variant] / 1e3) / 1e9}}
+    if args.converge:
+        for gi, (_, _, ph) in enumerate(geos):
+            init(sb, gi, ph)
+        t = time.perf_counter()
+        steps_b, rel_b = sb.batch_run_to_steady(p, 1e-6, check_every=512, max_steps=3_000_000, raise_on_max=False)
+        torch.cuda.synchronize()
+        wall_b = time.perf_counter() - t
+        deff_b = [sb.effective_D(p, geom=gi)[0] for gi in range(len(geos))]
+        t = time.perf_counter()
+        steps_s, deff_s = [], []
+        for gi, (_, phi, ph) in enumerate(geos):
+            g1 = Grid(phi, block=B)
+            s1 = State(g1, 1, "f32x2").set_kernel("plain")
+            init(s1, 0, ph)
+            st_, _ = s1.run_to_steady(p, 1e-6, check_every=512, max_steps=3_000_000, raise_on_max=False)
+            steps_s.append(st_)
+            deff_s.append(s1.effective_D(p)[0])
+            s1.close()
+            g1.close()
+        torch.cuda.synchronize()
+        wall_s = time.perf_counter() - t
+        work_b = float(sum(int(na[i]) * int(steps_b[i]) for i in range(len(geos))))
+        work_s = float(sum(int(na[i]) * int(steps_s[i]) for i in range(len(geos))))
+        dd = [abs(a - b) / max(abs(b), 1e-30) for a, b in zip(deff_b, deff_s) if abs(b) > 1e-12]
+        out["converge"] = {"tol": 1e-6, "batched_wall_s": wall_b, "sequential_plain_wall_s": wall_s,
+                           "gvox_batched": work_b / wall_b / 1e9, "gvox_sequential_plain": work_s / wall_s / 1e9,
+                           "max_rel_residual_batched": float(np.max(rel_b)),
+                           "steps_min_max": [int(np.min(steps_b)), int(np.max(steps_b))],
+                           "max_rel_diff_deff_batched_vs_sequential": max(dd) if dd else 0.0}
+    emit(out)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload != "grf256" and int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    return {"grf256": run_grf256, "reactive512": run_reactive512, "gradient256": run_gradient256,
+            "batch64": run_batch64}[args.workload](args)
 
 
 if __name__ == "__main__":
