@@ -175,6 +175,24 @@ def emit(line):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, device=None):
+    """The largest x over all ranks (a timed region's duration), or x itself
+    without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, max_ms):
+    """Whole-job throughput of `world` independent replicas: the units all
+    ranks processed over the slowest rank's time, per second."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -260,14 +278,13 @@ def run_grf256(args):
         st.effective_D(p, stream=stream)
     end.record(stream)
     torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
     clocks = sampler.stop()
     total_ms = start.elapsed_time(end)
     step_kernel_ms = sum(a.elapsed_time(b) for a, b in ev) / (args.steps * CHECK_EVERY)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = n_active * CHECK_EVERY * args.steps * world / (total_ms / 1e3) / 1e9
+    total_ms = max_over_ranks(total_ms, dev)
+    value = replica_throughput(n_active * CHECK_EVERY * args.steps, world, total_ms) / 1e9
 
     # end-to-end through the public API: dense field from pinned host memory every step
     u0_host = torch.from_numpy(u0.astype(np.float32)).pin_memory()
@@ -286,8 +303,8 @@ def run_grf256(args):
         st2.effective_D(p, stream=stream)
     e_end.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = e_start.elapsed_time(e_end)
-    e2e_value = n_active * CHECK_EVERY * args.steps * world / (e2e_ms / 1e3) / 1e9
+    e2e_ms = max_over_ranks(e_start.elapsed_time(e_end), dev)
+    e2e_value = replica_throughput(n_active * CHECK_EVERY * args.steps, world, e2e_ms) / 1e9
 
     peak, peak_kind = load_peaks()
     algo_bytes = n_active * BYTES_PER_VOXEL[args.dtype]

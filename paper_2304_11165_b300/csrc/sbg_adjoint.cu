@@ -11,7 +11,7 @@
 //   lambda^n = M^T lambda^{n+1}:
 //   lambda_i^n = lambda_i (1 - dt sum c - dt rate_i) + dt sum_{free active nbr j} c_a lambda_j
 //                (+ dt k w_i lambda_B,i for species A).
-// The same kernel accumulates, in FP64, this step's contribution to
+// The same kernel accumulates (FP64 above the warp level) this step's contribution to
 //   dL/dD_s += sum_i lambda_{s,i}^{n+1} dt g_{s,i}(u^n),  g = sum_a [(u~+ - u) - (u - u~-)] / dx_a^2,
 //   dL/dk   += sum_i dt w_i u_{A,i}^n (lambda_{B,i}^{n+1} - lambda_{A,i}^{n+1}),
 // with u~ the no-flux mirror.  Per-CTA partial sums go to a buffer of the tape
@@ -19,7 +19,10 @@
 //
 // Checkpointing: sbg_forward_record keeps the state every K steps; sbg_adjoint
 // walks the segments backwards, recomputes the K states of a segment from its
-// checkpoint and runs K adjoint steps over them.
+// checkpoint (each step writes straight into the next recompute buffer, so no
+// state is copied) and runs K adjoint steps over them.  Each CTA adds its
+// partial sums to its own FP64 slot in every adjoint step (a fixed order: the
+// steps'), and one CTA sums the slots once at the end.
 #include <math.h>
 
 #include <cstring>
@@ -37,8 +40,7 @@ struct sbg_tape_s {
     size_t state_bytes = 0;          // one species-set of one state, bytes
     std::vector<void *> ckpt;        // states at n = 0, K, 2K, ...
     std::vector<void *> seg;         // recompute buffer: up to K states
-    sbg_state work = nullptr;        // stepping state
-    double *partials = nullptr;
+    double *partials = nullptr;      // per-CTA sums, accumulated over the adjoint steps
     double *acc = nullptr;           // dL/dD_0, dL/dD_1, dL/dk
     int64_t nctas = 0;
     int64_t bytes = 0;
@@ -47,6 +49,7 @@ struct sbg_tape_s {
 namespace sbg {
 
 sbg_status step_n(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, cudaStream_t s);
+sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, cudaStream_t s);
 
 template <typename T>
 struct AdjArgs {
@@ -66,8 +69,11 @@ struct AdjArgs {
     double *partials;
 };
 
+// Per-voxel gradient terms and their warp sums are formed in the state's
+// precision (one product per voxel, 32 terms per warp); warp partials are
+// converted to FP64 and everything above the warp is summed in FP64.
 template <typename T, int B, int BPC, int NS>
-__global__ void __launch_bounds__(BPC * B * B * B) k_adjoint(const AdjArgs<T> a) {
+__global__ void __launch_bounds__(BPC * B * B * B, (sizeof(T) == 8 ? 1 : 2)) k_adjoint(const AdjArgs<T> a) {
     constexpr int B3 = B * B * B;
     constexpr int NT = BPC * B3;
     __shared__ T tl[NS][NT];   // lambda^{n+1}
@@ -102,7 +108,7 @@ __global__ void __launch_bounds__(BPC * B * B * B) k_adjoint(const AdjArgs<T> a)
     }
     __syncthreads();
 
-    double gD[2] = {0.0, 0.0}, gk = 0.0;
+    T gD[2] = {T(0), T(0)}, gk = T(0);
     if (valid) {
         const int nx = a.gdims[bc.w * 4 + 0], ny = a.gdims[bc.w * 4 + 1], nz = a.gdims[bc.w * 4 + 2];
         const int gx = bc.x * B + x, gy = bc.y * B + y, gz = bc.z * B + z;
@@ -146,30 +152,30 @@ __global__ void __launch_bounds__(BPC * B * B * B) k_adjoint(const AdjArgs<T> a)
                     const T rate = a.decay[s] + (s == 0 ? a.k * w : T(0));
                     out = lam * (T(1) - a.dt * sum_c - a.dt * rate) + a.dt * offd;
                     if (s == 0 && NS == 2) out += a.dt * a.k * w * lc[NS - 1];
-                    gD[s] += (double)lam * (double)a.dt * (double)g;
+                    gD[s] += lam * a.dt * g;
                     if (s == 0 && a.k != T(0)) {
-                        const double lb = NS == 2 ? (double)lc[NS - 1] : 0.0;
-                        gk += (double)a.dt * (double)w * (double)uc * (lb - (double)lam);
+                        const T lb = NS == 2 ? lc[NS - 1] : T(0);
+                        gk += a.dt * w * uc * (lb - lam);
                     }
                 }
             }
             a.lam_out[s][b * B3 + l] = out;
         }
     }
-    // CTA partial sums (warp shuffle, then shared memory, fixed order)
-    double v[3] = {gD[0], gD[1], gk};
+    // CTA partial sums (warp shuffle, then FP64 in shared memory, fixed order)
+    T v[3] = {gD[0], gD[1], gk};
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
-        if (lane == 0) red[warp][q] = v[q];
+        if (lane == 0) red[warp][q] = (double)v[q];
     }
     __syncthreads();
     if (tid < 3) {
         double acc = 0.0;
         for (int wi = 0; wi < NT / 32; ++wi) acc += red[wi][tid];
-        a.partials[(int64_t)blockIdx.x * 3 + tid] = acc;
+        a.partials[(int64_t)blockIdx.x * 3 + tid] += acc;
     }
 }
 
@@ -185,7 +191,7 @@ __global__ void k_adj_accum(const double *partials, int64_t nctas, double *acc) 
             for (int q = 0; q < 3; ++q) sm[threadIdx.x][q] += sm[threadIdx.x + st][q];
         __syncthreads();
     }
-    if (threadIdx.x < 3) acc[threadIdx.x] += sm[0][threadIdx.x];
+    if (threadIdx.x < 3) acc[threadIdx.x] = sm[0][threadIdx.x];
 }
 
 template <typename T>
@@ -224,7 +230,6 @@ static sbg_status launch_adj_t(sbg_tape tp, const void *u, const void *const *li
     a.partials = tp->partials;
     const int64_t nctas = (g->nb + BPC - 1) / BPC;
     k_adjoint<T, B, BPC, NS><<<(unsigned)nctas, BPC * B * B * B, 0, s>>>(a);
-    k_adj_accum<<<1, 256, 0, s>>>(tp->partials, nctas, tp->acc);
     SBG_LAUNCH_CHECK("adjoint kernel launch");
     return SBG_OK;
 }
@@ -245,25 +250,35 @@ static sbg_status launch_adj(sbg_tape tp, const void *u, sbg_state lam, cudaStre
     return rc;
 }
 
-// state's current species arrays -> one packed buffer (species-major), and back
+// state's current species arrays -> one packed buffer (species-major)
 static sbg_status save_state(sbg_tape tp, sbg_state st, void *dst, cudaStream_t s) {
     const size_t per = tp->state_bytes / tp->ns;
     for (int sp = 0; sp < tp->ns; ++sp)
         SBG_CUDA(cudaMemcpyAsync((char *)dst + sp * per, st->val[st->cur][sp], per, cudaMemcpyDeviceToDevice, s));
     return SBG_OK;
 }
-static sbg_status load_state(sbg_tape tp, sbg_state st, const void *srcp, cudaStream_t s) {
+
+// One forward step from packed buffer `src` into packed buffer `dst`, through
+// a state object that owns no memory and points at the two buffers.
+static sbg_status step_packed(sbg_tape tp, const void *src, void *dst, cudaStream_t s) {
+    sbg_state_s view;
+    view.grid = tp->grid;
+    view.ns = tp->ns;
+    view.dtype = tp->dtype;
+    view.nslots = (int64_t)(tp->state_bytes / tp->ns / (tp->dtype == SBG_F64 ? 8 : 4));
     const size_t per = tp->state_bytes / tp->ns;
-    for (int sp = 0; sp < tp->ns; ++sp)
-        SBG_CUDA(cudaMemcpyAsync(st->val[st->cur][sp], (const char *)srcp + sp * per, per, cudaMemcpyDeviceToDevice, s));
-    return SBG_OK;
+    for (int sp = 0; sp < tp->ns; ++sp) {
+        view.val[0][sp] = (char *)src + sp * per;
+        view.val[1][sp] = (char *)dst + sp * per;
+    }
+    view.variant = SBG_KERNEL_AUTO;
+    return launch_step(tp->grid, &view, &tp->p, 0, s);
 }
 
 static void tape_free(sbg_tape tp) {
     if (!tp) return;
     for (void *p : tp->ckpt) cudaFree(p);
     for (void *p : tp->seg) cudaFree(p);
-    if (tp->work) sbg_state_destroy(tp->work);
     cudaFree(tp->partials);
     cudaFree(tp->acc);
     delete tp;
@@ -326,13 +341,11 @@ extern "C" sbg_status sbg_adjoint(sbg_grid g, sbg_tape tp, sbg_state lam, double
     if (lam->dtype != tp->dtype || lam->ns != tp->ns)
         return fail(SBG_ERR_INVALID_ARG, "sbg_adjoint: lambda state must match the recorded state's dtype and species");
     cudaStream_t s = (cudaStream_t)stream;
-    SBG_CUDA(cudaMemsetAsync(tp->acc, 0, sizeof(double) * 3, s));
+    SBG_CUDA(cudaMemsetAsync(tp->partials, 0, sizeof(double) * 3 * tp->nctas, s));
     sbg_status rc = SBG_OK;
-    if (!tp->work) rc = sbg_state_create(g, tp->ns, tp->dtype, &tp->work);
-    if (rc != SBG_OK) return rc;
-    tp->work->variant = SBG_KERNEL_AUTO;
     const int64_t K = tp->K;
-    while ((int64_t)tp->seg.size() < std::min<int64_t>(K, std::max<int64_t>(tp->nsteps, 1))) {
+    // recompute buffers for u^{n0+1} .. u^{n0+K-1} (u^{n0} is the checkpoint itself)
+    while ((int64_t)tp->seg.size() < std::min<int64_t>(K, std::max<int64_t>(tp->nsteps, 1)) - 1) {
         void *q = nullptr;
         cudaError_t e = cudaMalloc(&q, tp->state_bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (tape recompute buffer)");
@@ -344,13 +357,13 @@ extern "C" sbg_status sbg_adjoint(sbg_grid g, sbg_tape tp, sbg_state lam, double
         const int64_t n0 = c * K;
         const int64_t len = std::min<int64_t>(K, tp->nsteps - n0);
         if (len <= 0) continue;
-        // recompute u^{n0} .. u^{n0+len-1}
-        rc = load_state(tp, tp->work, tp->ckpt[c], s);
-        for (int64_t m = 0; m < len && rc == SBG_OK; ++m) {
-            rc = save_state(tp, tp->work, tp->seg[m], s);
-            if (rc == SBG_OK && m + 1 < len) rc = step_n(g, tp->work, &tp->p, 1, s);
-        }
-        for (int64_t m = len - 1; m >= 0 && rc == SBG_OK; --m) rc = launch_adj(tp, tp->seg[m], lam, s);
+        auto u_at = [&](int64_t m) -> void * { return m == 0 ? tp->ckpt[c] : tp->seg[m - 1]; };
+        for (int64_t m = 1; m < len && rc == SBG_OK; ++m) rc = step_packed(tp, u_at(m - 1), u_at(m), s);
+        for (int64_t m = len - 1; m >= 0 && rc == SBG_OK; --m) rc = launch_adj(tp, u_at(m), lam, s);
+    }
+    if (rc == SBG_OK) {
+        k_adj_accum<<<1, 256, 0, s>>>(tp->partials, tp->nctas, tp->acc);
+        SBG_LAUNCH_CHECK("adjoint sum kernel launch");
     }
     if (rc != SBG_OK) return rc;
     SBG_CUDA(cudaMemcpyAsync(g->red_host, tp->acc, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
@@ -363,7 +376,7 @@ extern "C" sbg_status sbg_adjoint(sbg_grid g, sbg_tape tp, sbg_state lam, double
 
 extern "C" sbg_status sbg_tape_info(sbg_tape tp, int64_t *device_bytes, int64_t *n_checkpoints) {
     if (!tp) return fail(SBG_ERR_INVALID_ARG, "sbg_tape_info: null tape");
-    if (device_bytes) *device_bytes = tp->bytes + (tp->work ? tp->work->bytes : 0);
+    if (device_bytes) *device_bytes = tp->bytes;
     if (n_checkpoints) *n_checkpoints = (int64_t)tp->ckpt.size();
     return SBG_OK;
 }
