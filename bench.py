@@ -46,7 +46,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 CHECK_EVERY = 128
-BYTES_PER_VOXEL = {"f32": 8, "f32x2": 16, "f64": 16}
+# per active voxel and step: read and write the state; f32r reads the correction d and the source r
+# and writes d
+BYTES_PER_VOXEL = {"f32": 8, "f32x2": 16, "f64": 16, "f32r": 12}
 METRIC = "active-voxel updates/s per RD step (grf256 tortuosity solve)"
 KERNEL_SOURCES = ["paper_2304_11165_b300/csrc/sbg_step_pipe.cu", "paper_2304_11165_b300/csrc/sbg_step.cuh",
                   "paper_2304_11165_b300/csrc/sbg_ptx.cuh"]
@@ -61,7 +63,7 @@ def parse():
     ap.add_argument("--workload", default="grf256", choices=["grf256", "reactive512", "gradient256", "batch64"])
     ap.add_argument("--n", type=int, default=None, help="box side (default: the workload's)")
     ap.add_argument("--block", type=int, default=4)
-    ap.add_argument("--dtype", default="f32x2", choices=["f32", "f32x2"])
+    ap.add_argument("--dtype", default="f32x2", choices=["f32", "f32x2", "f32r"])
     ap.add_argument("--variant", default="pipelined", choices=["plain", "pipelined", "prefetch"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -312,8 +314,8 @@ def run_grf256(args):
     d_eff, tau, psi = st.effective_D(p, stream=stream)
     kernel_name = "k_step_pipe" if args.variant != "plain" else ("k_step_x2" if args.dtype == "f32x2" else "k_step")
     traffic = None
-    if (n, args.block, args.dtype, args.variant) == (256, 4, "f32x2", "pipelined"):
-        traffic = profile_traffic("k_step_pipe_x2_grf256.md")
+    if (n, args.block, args.variant) == (256, 4, "pipelined"):
+        traffic = profile_traffic("k_step_pipe_%s_grf256.md" % args.dtype)
     line = {
         "metric": METRIC, "value": value, "unit": "GVox/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

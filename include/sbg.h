@@ -53,9 +53,17 @@ typedef enum {
 typedef enum {
     SBG_F32 = 0,   /* FP32 state and stencil                                                   */
     SBG_F64 = 1,   /* FP64 state and stencil                                                   */
-    SBG_F32X2 = 2  /* compensated FP32: value = hi + lo, two FP32 arrays, FP32 arithmetic with
+    SBG_F32X2 = 2, /* compensated FP32: value = hi + lo, two FP32 arrays, FP32 arithmetic with
                       error-free sums, so that forward Euler keeps increments far below one
                       FP32 ulp (needed for steady states to a 1e-8 relative residual)         */
+    SBG_F32R = 3   /* FP32 correction on a compensated base (one species): value = b + d with
+                      b = hi + lo (FP32 pair) and d an FP32 correction.  Each step advances d
+                      by forward Euler with the source r = L_h b (stored as FP32), which in
+                      exact arithmetic is the forward-Euler step of b + d; every reduction and
+                      every 128 steps the library recomputes r from b + d in double-float
+                      arithmetic and folds d into b.  The step moves 12 B per voxel in plain
+                      FP32 arithmetic; the rounding of d is relative to the change since the
+                      last fold, so steady states reach residuals like SBG_F32X2's         */
 } sbg_dtype;
 
 enum { SBG_FACE_NOFLUX = 0, SBG_FACE_DIRICHLET = 1 };
@@ -162,13 +170,16 @@ sbg_status sbg_state_create(sbg_grid grid, int32_t nspecies, sbg_dtype dtype, sb
  * dense_dtype (SBG_F32 or SBG_F64), host or device (on_device).  Values of
  * inactive voxels are ignored; a NaN input is stored as a canonical NaN so
  * that reductions report it.  For SBG_F32X2 states the value is split into
- * hi = fl32(v), lo = fl32(v - hi).  For a batch, `geom` selects the geometry
- * (0 otherwise).  Synchronises `stream` when dense is host memory. */
+ * hi = fl32(v), lo = fl32(v - hi); SBG_F32R states store that pair as the
+ * base with a zero correction (the source r is recomputed before the next
+ * step).  For a batch, `geom` selects the geometry (0 otherwise).
+ * Synchronises `stream` when dense is host memory. */
 sbg_status sbg_state_set(sbg_grid grid, sbg_state state, int32_t geom, int32_t species,
                          const void *dense, int32_t dense_dtype, int32_t on_device, void *stream);
 
 /* Gathers species `species` into a dense array (inactive voxels -> 0).  For
- * SBG_F32X2 states an SBG_F64 output receives hi + lo. */
+ * SBG_F32X2 states an SBG_F64 output receives hi + lo, for SBG_F32R states
+ * hi + lo + d. */
 sbg_status sbg_state_get(sbg_grid grid, sbg_state state, int32_t geom, int32_t species,
                          void *dense, int32_t dense_dtype, int32_t on_device, void *stream);
 
@@ -211,11 +222,16 @@ sbg_status sbg_step(sbg_grid grid, sbg_state state, const sbg_params *params, in
 double sbg_stability_limit(const sbg_params *params, const int64_t dims[3], double band_eps);
 
 /* ---- reductions -------------------------------------------------------------
- * FP64 reductions over the current state (warp shuffles, per-CTA partials in a
- * scratch buffer of the grid, then a fixed-order final pass: the result is
- * deterministic).  out: host double[nspecies * SBG_NRED] (layout above); for a
- * batch, `geom` selects the geometry (-1 = all geometries together).
- * Synchronises `stream`. */
+ * Reductions over the current state, accumulated in FP64 (FP64 states) or in
+ * double-float pairs per voxel and warp and FP64 above (FP32-based states;
+ * ~48-bit significand, B300 runs FP64 at a small fraction of its FP32 rate);
+ * per-CTA partials in a scratch buffer of the grid, then a fixed-order final
+ * pass: the result is deterministic.  out: host double[nspecies * SBG_NRED]
+ * (layout above); min and max are those of the stored FP32 values (hi parts
+ * for compensated states).  For a batch, `geom` selects the geometry (-1 =
+ * all geometries together).  For SBG_F32R states the same pass also stores
+ * the source r = L_h u and folds the correction into the base (the field is
+ * unchanged up to double-float rounding).  Synchronises `stream`. */
 sbg_status sbg_reduce(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom,
                       double *out, void *stream);
 
@@ -240,6 +256,8 @@ sbg_status sbg_reduce(sbg_grid grid, sbg_state state, const sbg_params *params, 
  * sbg_reduce's up to the order of the FP64 sums. */
 sbg_status sbg_reduce_noalloc(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom,
                               int32_t species, double *out_dev, void *stream);
+/* (For SBG_F32R states sbg_reduce_noalloc only reads the state: no source
+ * update, no fold.) */
 
 /* Effective diffusivity and diffusive tortuosity (Eq. 2: tau = D / D_eff with
  * the pore-space D_eff) from the x-face fluxes of species 0:
@@ -259,8 +277,8 @@ sbg_status sbg_run_to_steady(sbg_grid grid, sbg_state state, const sbg_params *p
                              double *rel_residual, void *stream);
 
 /* Batched steady-state solve (no counterpart in the paper: this library's
- * batching pattern) for a grid from sbg_build_batch and one FP32 or
- * SBG_F32X2 state: every geometry not yet converged advances by one
+ * batching pattern) for a grid from sbg_build_batch and one SBG_F32,
+ * SBG_F32X2 or SBG_F32R state: every geometry not yet converged advances by one
  * persistent, pipelined launch per step over a device work list of 512-voxel
  * spans (never straddling geometries), replayed from a captured CUDA graph of
  * check_every launches (rounded up to even); after each interval each active
@@ -289,14 +307,18 @@ sbg_status sbg_forward_record(sbg_grid grid, sbg_state state, const sbg_params *
                               int64_t checkpoint_every, void *stream, sbg_tape *out);
 
 /* Runs the adjoint over the recorded steps: segments are taken last to first,
- * the K states of a segment are recomputed from its checkpoint (a buffer of K
- * states, allocated on the first call), and K adjoint steps run over them.
- * lam: in: dL/du^N; out: dL/du^0 (0 on held and inactive voxels); same grid,
- * dtype and species as the recorded state.  grad (host, 3 doubles):
+ * the states of a segment are recomputed from its checkpoint into a buffer of
+ * K - 1 states (allocated on the first call; each recompute step writes the
+ * next buffer, nothing is copied), and K adjoint steps run over them.
+ * lam: in: dL/du^N (values on held voxels are ignored: set to 0); out:
+ * dL/du^0 (0 on held and inactive voxels); same grid, dtype and species as
+ * the recorded state.  grad (host, 3 doubles):
  *   grad[0] = dL/dD_0, grad[1] = dL/dD_1 (0 with one species),
  *   grad[2] = dL/dk_surf,
- * each accumulated over steps and voxels in FP64 (per-CTA partials added in a
- * fixed order).  Synchronises `stream`. */
+ * accumulated over steps and voxels: FP64 tapes in FP64; SBG_F32 tapes (run
+ * by the pipelined kernel) in double-float pairs per thread and warp and FP64
+ * per CTA; each CTA adds to its own slot and the slots are summed once in a
+ * fixed order.  Synchronises `stream`. */
 sbg_status sbg_adjoint(sbg_grid grid, sbg_tape tape, sbg_state lam, double *grad, void *stream);
 
 /* Device memory held by the tape (checkpoints, recompute buffer, work state)

@@ -20,7 +20,7 @@ SBG_ERR_NONFINITE = 5
 SBG_ERR_TIMEOUT = 6
 SBG_ERR_NOT_CONVERGED = 7
 
-SBG_F32, SBG_F64, SBG_F32X2 = 0, 1, 2
+SBG_F32, SBG_F64, SBG_F32X2, SBG_F32R = 0, 1, 2, 3
 SBG_FACE_NOFLUX, SBG_FACE_DIRICHLET = 0, 1
 SBG_KERNEL_AUTO, SBG_KERNEL_PLAIN, SBG_KERNEL_PIPELINED, SBG_KERNEL_PIPELINED_PREFETCH = 0, 1, 2, 3
 

@@ -11,7 +11,7 @@ import numpy as np
 from . import _abi
 from ._abi import NRED, Params, check, load
 
-_DTYPES = {"f32": _abi.SBG_F32, "f64": _abi.SBG_F64, "f32x2": _abi.SBG_F32X2}
+_DTYPES = {"f32": _abi.SBG_F32, "f64": _abi.SBG_F64, "f32x2": _abi.SBG_F32X2, "f32r": _abi.SBG_F32R}
 
 
 def _stream_handle(stream):

@@ -11,7 +11,7 @@
 //   lambda^n = M^T lambda^{n+1}:
 //   lambda_i^n = lambda_i (1 - dt sum c - dt rate_i) + dt sum_{free active nbr j} c_a lambda_j
 //                (+ dt k w_i lambda_B,i for species A).
-// The same kernel accumulates (FP64 above the warp level) this step's contribution to
+// The same kernel accumulates this step's contribution to
 //   dL/dD_s += sum_i lambda_{s,i}^{n+1} dt g_{s,i}(u^n),  g = sum_a [(u~+ - u) - (u - u~-)] / dx_a^2,
 //   dL/dk   += sum_i dt w_i u_{A,i}^n (lambda_{B,i}^{n+1} - lambda_{A,i}^{n+1}),
 // with u~ the no-flux mirror.  Per-CTA partial sums go to a buffer of the tape
@@ -234,20 +234,69 @@ static sbg_status launch_adj_t(sbg_tape tp, const void *u, const void *const *li
     return SBG_OK;
 }
 
+// One FP64 adjoint step with the one-thread-per-voxel kernel.
 static sbg_status launch_adj(sbg_tape tp, const void *u, sbg_state lam, cudaStream_t s) {
     sbg_grid g = tp->grid;
     const void *lin[2] = {lam->val[lam->cur][0], lam->val[lam->cur][1]};
     void *lout[2] = {lam->val[1 - lam->cur][0], lam->val[1 - lam->cur][1]};
     sbg_status rc;
-    if (tp->dtype == SBG_F64) {
-        if (g->B == 8) rc = tp->ns == 1 ? launch_adj_t<double, 8, 1>(tp, u, lin, lout, s) : launch_adj_t<double, 8, 2>(tp, u, lin, lout, s);
-        else rc = tp->ns == 1 ? launch_adj_t<double, 4, 1>(tp, u, lin, lout, s) : launch_adj_t<double, 4, 2>(tp, u, lin, lout, s);
-    } else {
-        if (g->B == 8) rc = tp->ns == 1 ? launch_adj_t<float, 8, 1>(tp, u, lin, lout, s) : launch_adj_t<float, 8, 2>(tp, u, lin, lout, s);
-        else rc = tp->ns == 1 ? launch_adj_t<float, 4, 1>(tp, u, lin, lout, s) : launch_adj_t<float, 4, 2>(tp, u, lin, lout, s);
-    }
+    if (g->B == 8) rc = tp->ns == 1 ? launch_adj_t<double, 8, 1>(tp, u, lin, lout, s) : launch_adj_t<double, 8, 2>(tp, u, lin, lout, s);
+    else rc = tp->ns == 1 ? launch_adj_t<double, 4, 1>(tp, u, lin, lout, s) : launch_adj_t<double, 4, 2>(tp, u, lin, lout, s);
     if (rc == SBG_OK) lam->cur = 1 - lam->cur;
     return rc;
+}
+
+// lambda := 0 on Dirichlet-held voxels (held values are not free parameters)
+template <int B>
+__global__ void k_zero_held(float *l0, float *l1, const int4 *blocks, const int32_t *gdims, int held_mask,
+                            int64_t nb) {
+    constexpr int B3 = B * B * B;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb * B3) return;
+    const int64_t b = i / B3;
+    const int l = (int)(i - b * B3);
+    const int4 bc = blocks[b];
+    const int gx = bc.x * B + l % B, gy = bc.y * B + (l / B) % B, gz = bc.z * B + l / (B * B);
+    if (!is_held(held_mask, gx, gy, gz, gdims[bc.w * 4], gdims[bc.w * 4 + 1], gdims[bc.w * 4 + 2])) return;
+    if (!is_sent(l0[i])) l0[i] = 0.f;
+    if (l1 && !is_sent(l1[i])) l1[i] = 0.f;
+}
+
+static sbg_status zero_held(sbg_tape tp, sbg_state lam, cudaStream_t s) {
+    sbg_grid g = tp->grid;
+    StepArgs a;
+    fill_step_args(g, &tp->p, a);
+    if (!a.held_mask || g->nb == 0) return SBG_OK;
+    float *l0 = (float *)lam->val[lam->cur][0];
+    float *l1 = tp->ns == 2 ? (float *)lam->val[lam->cur][1] : nullptr;
+    const int64_t n = g->nb * g->b3();
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (g->B == 8) k_zero_held<8><<<grid, 256, 0, s>>>(l0, l1, g->blocks, g->gdims, a.held_mask, g->nb);
+    else k_zero_held<4><<<grid, 256, 0, s>>>(l0, l1, g->blocks, g->gdims, a.held_mask, g->nb);
+    SBG_LAUNCH_CHECK("adjoint held-voxel kernel launch");
+    return SBG_OK;
+}
+
+// One FP32 adjoint step with the pipelined kernel.
+static sbg_status launch_adj_pipe(sbg_tape tp, const void *u, sbg_state lam, cudaStream_t s) {
+    sbg_grid g = tp->grid;
+    StepArgs a;
+    fill_step_args(g, &tp->p, a);
+    PipeIO io;
+    std::memset(&io, 0, sizeof(io));
+    const size_t per = (size_t)g->nb * g->b3();
+    for (int sp = 0; sp < tp->ns; ++sp) {
+        io.src[sp] = (const float *)lam->val[lam->cur][sp];
+        io.src[tp->ns + sp] = (const float *)u + sp * per;
+        io.dst[sp] = (float *)lam->val[1 - lam->cur][sp];
+    }
+    io.gsum = tp->partials;
+    for (int ax = 0; ax < 3; ++ax) io.inv2[ax] = (float)(1.0 / (tp->p.dx[ax] * tp->p.dx[ax]));
+    int grid = 0;
+    cudaError_t e = launch_adjoint_pipe(a, io, tp->ns, g->B, tp->p.k_surf != 0.0, (int)tp->nctas, g->err, s, &grid);
+    if (e != cudaSuccess) return cuda_fail(e, "pipelined adjoint kernel launch");
+    lam->cur = 1 - lam->cur;
+    return SBG_OK;
 }
 
 // state's current species arrays -> one packed buffer (species-major)
@@ -324,7 +373,8 @@ extern "C" sbg_status sbg_forward_record(sbg_grid g, sbg_state st, const sbg_par
         }
     }
     const int BPC = g->B == 8 ? 1 : 8;
-    tp->nctas = std::max<int64_t>(1, (g->nb + BPC - 1) / BPC);
+    // one partial-sum slot per CTA of either adjoint kernel
+    tp->nctas = std::max<int64_t>(2048, (g->nb + BPC - 1) / BPC);
     if (rc == SBG_OK) rc = alloc((void **)&tp->partials, sizeof(double) * 3 * tp->nctas);
     if (rc == SBG_OK) rc = alloc((void **)&tp->acc, sizeof(double) * 3);
     if (rc != SBG_OK) {
@@ -342,7 +392,8 @@ extern "C" sbg_status sbg_adjoint(sbg_grid g, sbg_tape tp, sbg_state lam, double
         return fail(SBG_ERR_INVALID_ARG, "sbg_adjoint: lambda state must match the recorded state's dtype and species");
     cudaStream_t s = (cudaStream_t)stream;
     SBG_CUDA(cudaMemsetAsync(tp->partials, 0, sizeof(double) * 3 * tp->nctas, s));
-    sbg_status rc = SBG_OK;
+    sbg_status rc = tp->dtype == SBG_F32 ? zero_held(tp, lam, s) : SBG_OK;
+    if (rc != SBG_OK) return rc;
     const int64_t K = tp->K;
     // recompute buffers for u^{n0+1} .. u^{n0+K-1} (u^{n0} is the checkpoint itself)
     while ((int64_t)tp->seg.size() < std::min<int64_t>(K, std::max<int64_t>(tp->nsteps, 1)) - 1) {
@@ -359,7 +410,8 @@ extern "C" sbg_status sbg_adjoint(sbg_grid g, sbg_tape tp, sbg_state lam, double
         if (len <= 0) continue;
         auto u_at = [&](int64_t m) -> void * { return m == 0 ? tp->ckpt[c] : tp->seg[m - 1]; };
         for (int64_t m = 1; m < len && rc == SBG_OK; ++m) rc = step_packed(tp, u_at(m - 1), u_at(m), s);
-        for (int64_t m = len - 1; m >= 0 && rc == SBG_OK; --m) rc = launch_adj(tp, u_at(m), lam, s);
+        for (int64_t m = len - 1; m >= 0 && rc == SBG_OK; --m)
+            rc = tp->dtype == SBG_F32 ? launch_adj_pipe(tp, u_at(m), lam, s) : launch_adj(tp, u_at(m), lam, s);
     }
     if (rc == SBG_OK) {
         k_adj_accum<<<1, 256, 0, s>>>(tp->partials, tp->nctas, tp->acc);
@@ -368,6 +420,8 @@ extern "C" sbg_status sbg_adjoint(sbg_grid g, sbg_tape tp, sbg_state lam, double
     if (rc != SBG_OK) return rc;
     SBG_CUDA(cudaMemcpyAsync(g->red_host, tp->acc, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
     SBG_CUDA(cudaStreamSynchronize(s));
+    rc = check_device_error(g, s);
+    if (rc != SBG_OK) return rc;
     grad[0] = g->red_host[0];
     grad[1] = g->red_host[1];
     grad[2] = g->red_host[2];

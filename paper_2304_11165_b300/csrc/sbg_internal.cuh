@@ -128,6 +128,11 @@ struct sbg_state_s {
     int graph_ctas = -1;
     int variant = SBG_KERNEL_AUTO;  // step kernel choice (sbg_state_set_kernel)
     int ctas_per_sm = 0;
+    // SBG_F32R (one species): val[b][0] holds the FP32 correction d; the base
+    // b = bh + bl and the source r = L_h b are single arrays updated in place
+    float *bh = nullptr, *bl = nullptr, *rsrc = nullptr;
+    bool r_valid = false;           // r matches the base of every geometry
+    int64_t since_refresh = 0;      // steps since r was recomputed and d folded
     size_t elem() const { return dtype == SBG_F64 ? 8 : 4; }
 };
 
@@ -139,4 +144,9 @@ sbg_status validate_params(sbg_grid g, const sbg_params *p, int ns);
 // implemented in sbg_reduce.cu
 sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species,
                           int which_buffer, double *out_host, cudaStream_t stream);
+// SBG_F32R: recompute r = L_h (b + d) over every geometry and fold d into b
+// (kernel launches only, no synchronisation)
+sbg_status refresh_source(sbg_grid g, sbg_state st, const sbg_params *p, cudaStream_t stream);
+// steps between refreshes of an SBG_F32R state inside sbg_step
+constexpr int64_t kRefreshSteps = 128;
 }  // namespace sbg

@@ -3,12 +3,18 @@
 // counts; effective diffusivity and tortuosity (Eq. 2); the steady-state
 // driver.
 //
-// Each thread accumulates in FP64, warps combine with __shfl_down_sync, each
-// CTA writes one partial record to the grid's scratch buffer, and a single
-// CTA adds the records in a fixed order, so the result is deterministic for a
-// given grid.  The residual is evaluated in FP64 from the stored values
-// (hi + lo for compensated states), so that a steady-state test at a 1e-8
-// relative residual measures the state, not FP32 rounding of the stencil.
+// FP32 and compensated states: each thread evaluates the residual and
+// accumulates its sums in double-float arithmetic (hi + lo FP32 pairs with
+// error-free two-sums and fma products, ~48-bit significand), warps combine
+// the pairs with __shfl_down_sync, and FP64 starts at the warp partials; B300
+// runs FP64 at a small fraction of its FP32 rate, so per-voxel FP64 would cost
+// several times the step itself.  FP64 states accumulate in FP64 throughout.
+// Each CTA writes one partial record to the grid's scratch buffer, and a
+// single CTA adds the records in a fixed order, so the result is
+// deterministic for a given grid.  The residual is evaluated from the stored
+// values (hi + lo for compensated states) to ~1e-14 relative, so that a
+// steady-state test at a 1e-10 relative residual measures the state, not FP32
+// rounding of the stencil.
 #include <math.h>
 
 #include <cstring>
@@ -33,6 +39,13 @@ struct RedArgs {
     double c[3];
     double D, decay, k, inv_dx, area, dv;
     double *partials;
+    // the same coefficients as double-float pairs, and the FP32 surface weights
+    float ch[3], cl[3], dech, decl, kh, kl;
+    const float *wf;
+    // SBG_F32R: base pair (val[s] is the correction d) and, when set, the
+    // source array the reduction writes (r = fl32(L_h u) on free voxels, 0 on held)
+    const float *bh, *bl;
+    float *rout;
 };
 
 template <typename T, bool X2>
@@ -195,21 +208,247 @@ __global__ void __launch_bounds__(256) k_reduce_final(const double *partials, in
     }
 }
 
-template <typename T, bool X2, int B>
-static void launch_reduce(const RedArgs &a, int nctas, cudaStream_t s) {
-    k_reduce<T, X2, B><<<nctas, kRedThreads, 0, s>>>(a);
+// ---------------------------------------------------------------------------
+// FP32 / compensated states: double-float per voxel and per warp.
+struct DF {
+    float h, l;
+};
+__device__ __forceinline__ float tsum(float a, float b, float &e) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    float e;
+    const float s = tsum(a.h, b.h, e);
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ DF df_mul(DF a, DF c) {
+    const float p = __fmul_rn(a.h, c.h);
+    float e = __fmaf_rn(a.h, c.h, -p);
+    e = __fmaf_rn(a.h, c.l, e);
+    e = __fmaf_rn(a.l, c.h, e);
+    const float h = __fadd_rn(p, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+__device__ __forceinline__ double df_to_d(DF a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ DF df_shfl_add(DF a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const DF b = {__shfl_down_sync(0xffffffffu, a.h, o), __shfl_down_sync(0xffffffffu, a.l, o)};
+        a = df_add(a, b);
+    }
+    return a;
 }
 
-// Reduces species `species` of buffer `which` (st->cur when < 0) into out_host[kNumRed].
-sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species,
-                          int which, double *out_host, cudaStream_t s) {
-    const int buf = which < 0 ? st->cur : which;
-    RedArgs a;
+// Value modes of the FP32-based reduction: the stored value, hi + lo, or
+// (SBG_F32R) base hi + lo plus the correction d.
+enum ValMode : int { kVF32 = 0, kVX2 = 1, kVR = 2 };
+
+// value at `slot` as an (unnormalised) double-float pair; false outside Omega
+template <int VM>
+__device__ __forceinline__ bool load_df(const RedArgs &a, int s, int64_t slot, float &h, float &l) {
+    const float v = ((const float *)a.val[s])[slot];
+    if (is_sent(v)) return false;
+    if (VM == kVF32) {
+        h = v;
+        l = 0.f;
+    } else if (VM == kVX2) {
+        h = v;
+        l = a.lo[s][slot];
+    } else {
+        float e;
+        h = tsum(a.bh[slot], v, e);
+        l = __fadd_rn(e, a.bl[slot]);
+    }
+    return true;
+}
+
+// neighbour (hi, lo) across face f; false when it is outside Omega (mirrored)
+template <int VM, int B>
+__device__ __forceinline__ bool nbr_f(const RedArgs &a, int s, int64_t b, int l, int x, int y, int z, int f,
+                                      float &nh, float &nl) {
+    constexpr int B3 = B * B * B;
+    int64_t nb = b;
+    int ln = l;
+    switch (f) {
+        case 0: if (x > 0) ln = l - 1; else { nb = a.face[b * 6 + 0]; ln = l + (B - 1); } break;
+        case 1: if (x < B - 1) ln = l + 1; else { nb = a.face[b * 6 + 1]; ln = l - (B - 1); } break;
+        case 2: if (y > 0) ln = l - B; else { nb = a.face[b * 6 + 2]; ln = l + (B - 1) * B; } break;
+        case 3: if (y < B - 1) ln = l + B; else { nb = a.face[b * 6 + 3]; ln = l - (B - 1) * B; } break;
+        case 4: if (z > 0) ln = l - B * B; else { nb = a.face[b * 6 + 4]; ln = l + (B - 1) * B * B; } break;
+        default: if (z < B - 1) ln = l + B * B; else { nb = a.face[b * 6 + 5]; ln = l - (B - 1) * B * B; } break;
+    }
+    if (nb < 0) return false;
+    return load_df<VM>(a, s, nb * B3 + ln, nh, nl);
+}
+
+template <int VM, int B>
+__global__ void __launch_bounds__(kRedThreads) k_reduce_f(const RedArgs a) {
+    constexpr int B3 = B * B * B;
+    DF mass = {0.f, 0.f}, res = {0.f, 0.f}, jin = {0.f, 0.f}, jout = {0.f, 0.f};
+    float mn = INFINITY, mx = -INFINITY;
+    int nact = 0, nonfin = 0;
+    const int s = a.species;
+    const DF c[3] = {{a.ch[0], a.cl[0]}, {a.ch[1], a.cl[1]}, {a.ch[2], a.cl[2]}};
+    const DF dec = {a.dech, a.decl}, kk = {a.kh, a.kl};
+    const int64_t total = a.b_count * B3;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = a.b_begin + t / B3;
+        const int l = (int)(t % B3);
+        const int64_t slot = b * B3 + l;
+        float h, lo;
+        if (!load_df<VM>(a, s, slot, h, lo)) continue;
+        ++nact;
+        if (!isfinite(h)) {
+            ++nonfin;
+            continue;
+        }
+        const DF u = {h, lo};
+        mass = df_add(mass, u);
+        mn = fminf(mn, h);
+        mx = fmaxf(mx, h);
+        const int x = l % B, y = (l / B) % B, z = l / (B * B);
+        const int4 bc = a.blocks[b];
+        const int nx = a.gdims[bc.w * 4 + 0], ny = a.gdims[bc.w * 4 + 1], nz = a.gdims[bc.w * 4 + 2];
+        const int gx = bc.x * B + x, gy = bc.y * B + y, gz = bc.z * B + z;
+        const bool held = ((a.held_mask & 1) && gx == 0) || ((a.held_mask & 2) && gx == nx - 1) ||
+                          ((a.held_mask & 4) && gy == 0) || ((a.held_mask & 8) && gy == ny - 1) ||
+                          ((a.held_mask & 16) && gz == 0) || ((a.held_mask & 32) && gz == nz - 1);
+        if (!held) {
+            // L_h u = sum_a c_a [(u~- - u) + (u~+ - u)] - rate u (+ transfer), double-float
+            DF lap = {0.f, 0.f};
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                DF d = {0.f, 0.f};
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    float nh, nl;
+                    if (nbr_f<VM, B>(a, s, b, l, x, y, z, 2 * ax + side, nh, nl)) {
+                        float e;
+                        const float dh = tsum(nh, -h, e);
+                        d = df_add(d, {dh, VM != kVF32 ? __fadd_rn(e, __fsub_rn(nl, lo)) : e});
+                    }
+                }
+                lap = df_add(lap, df_mul(d, c[ax]));
+            }
+            DF rate = dec;
+            float w = 0.f;
+            if (a.k != 0.0) {
+                const int ws = a.wslab[b];
+                w = ws >= 0 ? a.wf[(int64_t)ws * B3 + l] : 0.f;
+                if (s == 0) rate = df_add(rate, df_mul(kk, {w, 0.f}));
+            }
+            DF r = df_mul(rate, u);
+            r = df_add(lap, {-r.h, -r.l});
+            if (a.k != 0.0 && s == 1) {
+                // + k w u_A
+                DF ua = {0.f, 0.f};
+                load_df<VM>(a, 0, slot, ua.h, ua.l);
+                r = df_add(r, df_mul(df_mul(kk, {w, 0.f}), ua));
+            }
+            const float p = __fmul_rn(r.h, r.h);
+            res = df_add(res, {p, __fmaf_rn(r.h, r.h, -p) + 2.f * r.h * r.l});
+            if (VM == kVR && a.rout) a.rout[slot] = __fadd_rn(r.h, r.l);
+        } else if (VM == kVR && a.rout) {
+            a.rout[slot] = 0.f;
+        }
+        if (nx >= 2 && (gx == 0 || gx == nx - 2)) {
+            float nh, nl;
+            if (nbr_f<VM, B>(a, s, b, l, x, y, z, 1, nh, nl)) {
+                // u - u_{x+1}, double-float; scaled by D / dx * area below
+                float e;
+                const float dh = tsum(h, -nh, e);
+                const DF d = {dh, VM != kVF32 ? __fadd_rn(e, __fsub_rn(lo, nl)) : e};
+                if (gx == 0) jin = df_add(jin, d);
+                if (gx == nx - 2) jout = df_add(jout, d);
+            }
+        }
+    }
+    mass = df_shfl_add(mass);
+    res = df_shfl_add(res);
+    jin = df_shfl_add(jin);
+    jout = df_shfl_add(jout);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        nact += __shfl_down_sync(0xffffffffu, nact, o);
+        nonfin += __shfl_down_sync(0xffffffffu, nonfin, o);
+    }
+    __shared__ double sm[kRedThreads / 32][kNumRed];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        const double flux = a.D * a.inv_dx * a.area;
+        sm[warp][SBG_RED_MASS] = df_to_d(mass) * a.dv;
+        sm[warp][SBG_RED_JIN] = df_to_d(jin) * flux;
+        sm[warp][SBG_RED_JOUT] = df_to_d(jout) * flux;
+        sm[warp][SBG_RED_RESIDUAL] = df_to_d(res);
+        sm[warp][SBG_RED_MIN] = (double)mn;
+        sm[warp][SBG_RED_MAX] = (double)mx;
+        sm[warp][SBG_RED_NONFINITE] = (double)nonfin;
+        sm[warp][SBG_RED_NACTIVE] = (double)nact;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumRed) {
+        const int q = threadIdx.x;
+        double v = sm[0][q];
+        for (int wi = 1; wi < kRedThreads / 32; ++wi)
+            v = (q == SBG_RED_MIN) ? fmin(v, sm[wi][q]) : (q == SBG_RED_MAX) ? fmax(v, sm[wi][q]) : v + sm[wi][q];
+        a.partials[(int64_t)blockIdx.x * kNumRed + q] = v;
+    }
+}
+
+// coefficients as double-float pairs (host side)
+static void split_df(double x, float &h, float &l) {
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+static void fill_df(RedArgs &a, const float *wf) {
+    for (int ax = 0; ax < 3; ++ax) split_df(a.c[ax], a.ch[ax], a.cl[ax]);
+    split_df(a.decay, a.dech, a.decl);
+    split_df(a.k, a.kh, a.kl);
+    a.wf = wf;
+}
+
+// SBG_F32R: b := b + d (double-float, renormalised), d := 0, in place over a slot range
+__global__ void k_fold(float *__restrict__ d, float *__restrict__ bh, float *__restrict__ bl, int64_t begin,
+                       int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t slot = begin + i;
+    const float dv = d[slot];
+    if (is_sent(dv) || dv == 0.f) return;
+    float e;
+    const float h = tsum(bh[slot], dv, e);
+    const float l = __fadd_rn(e, bl[slot]);
+    const float h2 = __fadd_rn(h, l);
+    bh[slot] = h2;
+    bl[slot] = __fsub_rn(l, __fsub_rn(h2, h));
+    d[slot] = 0.f;
+}
+
+template <typename T, int VM, int B>
+static void launch_reduce(const RedArgs &a, int nctas, cudaStream_t s) {
+    if (sizeof(T) == 8) k_reduce<double, false, B><<<nctas, kRedThreads, 0, s>>>(a);
+    else k_reduce_f<VM, B><<<nctas, kRedThreads, 0, s>>>(a);
+}
+
+// Arguments of a reduction of species `species` of buffer `buf` over one
+// geometry (geom >= 0) or all blocks.
+static void fill_red_args(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species, int buf,
+                          double *partials, RedArgs &a) {
     std::memset(&a, 0, sizeof(a));
     for (int sp = 0; sp < st->ns; ++sp) {
         a.val[sp] = st->val[buf][sp];
         a.lo[sp] = st->lo[buf][sp];
     }
+    a.bh = st->bh;
+    a.bl = st->bl;
     a.blocks = g->blocks;
     a.face = g->face_nbr;
     a.wslab = g->wslab;
@@ -228,22 +467,81 @@ sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geo
     a.inv_dx = 1.0 / p->dx[0];
     a.area = p->dx[1] * p->dx[2];
     a.dv = p->dx[0] * p->dx[1] * p->dx[2];
-    a.partials = g->partials;
-    const int64_t work = a.b_count * g->b3();
-    int nctas = (int)std::min<int64_t>(kRedMaxCtas, (work + kRedThreads - 1) / kRedThreads);
-    if (nctas < 1) nctas = 1;
+    fill_df(a, g->w);
+    a.partials = partials;
+}
+
+static void dispatch_reduce(sbg_grid g, sbg_state st, const RedArgs &a, int nctas, cudaStream_t s) {
     if (st->dtype == SBG_F64) {
-        if (g->B == 8) launch_reduce<double, false, 8>(a, nctas, s);
-        else launch_reduce<double, false, 4>(a, nctas, s);
+        if (g->B == 8) launch_reduce<double, kVF32, 8>(a, nctas, s);
+        else launch_reduce<double, kVF32, 4>(a, nctas, s);
     } else if (st->dtype == SBG_F32) {
-        if (g->B == 8) launch_reduce<float, false, 8>(a, nctas, s);
-        else launch_reduce<float, false, 4>(a, nctas, s);
+        if (g->B == 8) launch_reduce<float, kVF32, 8>(a, nctas, s);
+        else launch_reduce<float, kVF32, 4>(a, nctas, s);
+    } else if (st->dtype == SBG_F32X2) {
+        if (g->B == 8) launch_reduce<float, kVX2, 8>(a, nctas, s);
+        else launch_reduce<float, kVX2, 4>(a, nctas, s);
     } else {
-        if (g->B == 8) launch_reduce<float, true, 8>(a, nctas, s);
-        else launch_reduce<float, true, 4>(a, nctas, s);
+        if (g->B == 8) launch_reduce<float, kVR, 8>(a, nctas, s);
+        else launch_reduce<float, kVR, 4>(a, nctas, s);
     }
+}
+
+static int reduce_ctas(const RedArgs &a, sbg_grid g) {
+    const int64_t work = a.b_count * g->b3();
+    const int nctas = (int)std::min<int64_t>(kRedMaxCtas, (work + kRedThreads - 1) / kRedThreads);
+    return nctas < 1 ? 1 : nctas;
+}
+
+// SBG_F32R: the reduction pass of `a` (with a.rout set) has written r over
+// its block range; fold d into b there.
+static sbg_status fold_range(sbg_grid g, sbg_state st, const RedArgs &a, cudaStream_t s) {
+    const int64_t n = a.b_count * g->b3();
+    if (n > 0)
+        k_fold<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((float *)st->val[st->cur][0], st->bh, st->bl,
+                                                           a.b_begin * g->b3(), n);
+    SBG_LAUNCH_CHECK("fold kernel launch");
+    return SBG_OK;
+}
+
+sbg_status refresh_source(sbg_grid g, sbg_state st, const sbg_params *p, cudaStream_t s) {
+    if (st->dtype != SBG_F32R) return SBG_OK;
+    if (g->nb > 0) {
+        RedArgs a;
+        fill_red_args(g, st, p, -1, 0, st->cur, g->partials, a);
+        a.rout = st->rsrc;
+        dispatch_reduce(g, st, a, reduce_ctas(a, g), s);
+        SBG_LAUNCH_CHECK("source refresh launch");
+        sbg_status rc = fold_range(g, st, a, s);
+        if (rc != SBG_OK) return rc;
+    }
+    st->r_valid = true;
+    st->since_refresh = 0;
+    return SBG_OK;
+}
+
+// Reduces species `species` of buffer `which` (st->cur when < 0) into
+// out_host[kNumRed].  SBG_F32R states: also refreshes r and folds d over the
+// reduced range.
+sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species,
+                          int which, double *out_host, cudaStream_t s) {
+    const int buf = which < 0 ? st->cur : which;
+    RedArgs a;
+    fill_red_args(g, st, p, geom, species, buf, g->partials, a);
+    const bool refresh = st->dtype == SBG_F32R && buf == st->cur;
+    if (refresh) a.rout = st->rsrc;
+    const int nctas = reduce_ctas(a, g);
+    dispatch_reduce(g, st, a, nctas, s);
     k_reduce_final<<<1, 256, 0, s>>>(g->partials, nctas, g->red_dev);
     SBG_LAUNCH_CHECK("reduction launch");
+    if (refresh) {
+        sbg_status rc = fold_range(g, st, a, s);
+        if (rc != SBG_OK) return rc;
+        if (geom < 0 || g->n_geoms == 1) {
+            st->r_valid = true;
+            st->since_refresh = 0;
+        }
+    }
     SBG_CUDA(cudaMemcpyAsync(g->red_host, g->red_dev, sizeof(double) * kNumRed, cudaMemcpyDeviceToHost, s));
     SBG_CUDA(cudaStreamSynchronize(s));
     std::memcpy(out_host, g->red_host, sizeof(double) * kNumRed);
@@ -410,43 +708,11 @@ extern "C" sbg_status sbg_reduce_noalloc(sbg_grid g, sbg_state st, const sbg_par
     if (rc != SBG_OK) return rc;
 
     RedArgs a;
-    std::memset(&a, 0, sizeof(a));
-    for (int sp = 0; sp < st->ns; ++sp) {
-        a.val[sp] = st->val[st->cur][sp];
-        a.lo[sp] = st->lo[st->cur][sp];
-    }
-    a.blocks = g->blocks;
-    a.face = g->face_nbr;
-    a.wslab = g->wslab;
-    a.w = g->w64;
-    a.gdims = g->gdims;
-    a.b_begin = b_begin;
-    a.b_count = b_count;
-    a.species = species;
-    a.ns = st->ns;
-    for (int f = 0; f < 6; ++f)
-        if (p->face_type[f] == SBG_FACE_DIRICHLET) a.held_mask |= 1 << f;
-    for (int ax = 0; ax < 3; ++ax) a.c[ax] = p->D[species] / (p->dx[ax] * p->dx[ax]);
-    a.D = p->D[species];
-    a.decay = p->decay[species];
-    a.k = p->k_surf;
-    a.inv_dx = 1.0 / p->dx[0];
-    a.area = p->dx[1] * p->dx[2];
-    a.dv = p->dx[0] * p->dx[1] * p->dx[2];
-    a.partials = scratch;
+    fill_red_args(g, st, p, geom, species, st->cur, scratch, a);  // a.rout stays null: read-only
     int nctas = (int)((work + kNoAllocSlotsPerCta - 1) / kNoAllocSlotsPerCta);
     if (nctas < 1) nctas = 1;
     cudaStream_t s = (cudaStream_t)stream;
-    if (st->dtype == SBG_F64) {
-        if (g->B == 8) launch_reduce<double, false, 8>(a, nctas, s);
-        else launch_reduce<double, false, 4>(a, nctas, s);
-    } else if (st->dtype == SBG_F32) {
-        if (g->B == 8) launch_reduce<float, false, 8>(a, nctas, s);
-        else launch_reduce<float, false, 4>(a, nctas, s);
-    } else {
-        if (g->B == 8) launch_reduce<float, true, 8>(a, nctas, s);
-        else launch_reduce<float, true, 4>(a, nctas, s);
-    }
+    dispatch_reduce(g, st, a, nctas, s);
     k_reduce_final<<<1, 256, 0, s>>>(scratch, nctas, out_dev);
     SBG_LAUNCH_CHECK("no-allocation reduction launch");
     return SBG_OK;

@@ -10,10 +10,12 @@
 
 namespace sbg {
 
+// corr (SBG_F32R states): the correction array, set to 0 (active) or the sentinel
 template <typename Tin, typename Tst, bool X2, int B>
 __global__ void k_scatter(const Tin *__restrict__ dense, int nx, int ny, int nz,
                           const int4 *__restrict__ blocks, const uint64_t *__restrict__ bitmap,
-                          int64_t begin, int64_t count, Tst *__restrict__ val, float *__restrict__ lo) {
+                          int64_t begin, int64_t count, Tst *__restrict__ val, float *__restrict__ lo,
+                          float *__restrict__ corr) {
     constexpr int B3 = B * B * B;
     constexpr int W = (B3 + 63) / 64;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -26,8 +28,10 @@ __global__ void k_scatter(const Tin *__restrict__ dense, int nx, int ny, int nz,
     if (!act) {
         val[slot] = sentinel<Tst>();
         if (X2) lo[slot] = 0.f;
+        if (corr) corr[slot] = sentinel_f32();
         return;
     }
+    if (corr) corr[slot] = 0.f;
     const int x = bc.x * B + l % B, y = bc.y * B + (l / B) % B, z = bc.z * B + l / (B * B);
     double v = (double)dense[((int64_t)z * ny + y) * nx + x];
     if (isnan(v)) v = __longlong_as_double(0x7fffffffffffffffll);  // canonical NaN, not the sentinel
@@ -46,7 +50,8 @@ __global__ void k_scatter(const Tin *__restrict__ dense, int nx, int ny, int nz,
 template <typename Tout, typename Tst, bool X2, int B>
 __global__ void k_gather(Tout *__restrict__ dense, int nx, int ny, int nz,
                          const int4 *__restrict__ blocks, int64_t begin, int64_t count,
-                         const Tst *__restrict__ val, const float *__restrict__ lo) {
+                         const Tst *__restrict__ val, const float *__restrict__ lo,
+                         const float *__restrict__ corr) {
     constexpr int B3 = B * B * B;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count * B3) return;
@@ -60,6 +65,7 @@ __global__ void k_gather(Tout *__restrict__ dense, int nx, int ny, int nz,
     if (is_sent(v)) return;  // dense output was zeroed
     double d = (double)v;
     if (X2) d += (double)lo[slot];
+    if (corr) d += (double)corr[slot];
     dense[((int64_t)z * ny + y) * nx + x] = (Tout)d;
 }
 
@@ -72,16 +78,23 @@ static sbg_status scatter_gather(sbg_grid g, sbg_state st, int geom, int species
     const unsigned grid = (unsigned)((count * B * B * B + 255) / 256);
     void *val = st->val[st->cur][species];
     float *lo = st->lo[st->cur][species];
+    float *corr = nullptr;
+    if (st->dtype == SBG_F32R) {  // the base pair takes the value, the correction is zeroed
+        corr = (float *)val;
+        val = st->bh;
+        lo = st->bl;
+        if (to_state) st->r_valid = false;
+    }
 #define SG_LAUNCH(TIN, TST, X2)                                                                   \
     do {                                                                                         \
         if (to_state)                                                                            \
             k_scatter<TIN, TST, X2, B><<<grid, 256, 0, s>>>((const TIN *)ddense, (int)nx, (int)ny, \
                                                           (int)nz, g->blocks, g->bitmap, begin,  \
-                                                          count, (TST *)val, lo);                \
+                                                          count, (TST *)val, lo, corr);          \
         else                                                                                     \
             k_gather<TIN, TST, X2, B><<<grid, 256, 0, s>>>((TIN *)ddense, (int)nx, (int)ny,       \
                                                          (int)nz, g->blocks, begin, count,       \
-                                                         (const TST *)val, lo);                  \
+                                                         (const TST *)val, lo, corr);            \
     } while (0)
     const bool in64 = dense_dtype == SBG_F64;
     if (st->dtype == SBG_F64) {
@@ -134,8 +147,10 @@ using namespace sbg;
 extern "C" sbg_status sbg_state_create(sbg_grid g, int32_t nspecies, sbg_dtype dtype, sbg_state *out) {
     if (!g || !out) return fail(SBG_ERR_INVALID_ARG, "sbg_state_create: null pointer");
     if (nspecies < 1 || nspecies > 2) return fail(SBG_ERR_INVALID_ARG, "sbg_state_create: nspecies must be 1 or 2");
-    if (dtype != SBG_F32 && dtype != SBG_F64 && dtype != SBG_F32X2)
+    if (dtype != SBG_F32 && dtype != SBG_F64 && dtype != SBG_F32X2 && dtype != SBG_F32R)
         return fail(SBG_ERR_INVALID_ARG, "sbg_state_create: bad dtype");
+    if (dtype == SBG_F32R && nspecies != 1)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_state_create: SBG_F32R states hold one species");
     *out = nullptr;
     sbg_state st = new sbg_state_s();
     st->grid = g;
@@ -144,7 +159,8 @@ extern "C" sbg_status sbg_state_create(sbg_grid g, int32_t nspecies, sbg_dtype d
     st->nslots = g->nb * (int64_t)g->b3();
     const size_t per = (size_t)st->nslots * st->elem();
     const size_t perlo = dtype == SBG_F32X2 ? (size_t)st->nslots * 4 : 0;
-    const size_t total = 2 * (size_t)nspecies * (per + perlo);
+    const size_t extra = dtype == SBG_F32R ? 3 * (size_t)st->nslots * 4 : 0;  // base hi, lo and source
+    const size_t total = 2 * (size_t)nspecies * (per + perlo) + extra;
     cudaError_t e = cudaMalloc(&st->base, total > 0 ? total : 16);
     if (e != cudaSuccess) {
         delete st;
@@ -161,6 +177,11 @@ extern "C" sbg_status sbg_state_create(sbg_grid g, int32_t nspecies, sbg_dtype d
                 p += perlo;
             }
         }
+    if (extra) {
+        st->bh = (float *)p;
+        st->bl = st->bh + st->nslots;
+        st->rsrc = st->bl + st->nslots;
+    }
     // every slot starts as the sentinel until sbg_state_set (0xff.. bytes: a NaN, not the sentinel,
     // so an unset state is reported as non-finite)
     e = cudaMemset(st->base, 0xff, total > 0 ? total : 16);
@@ -196,6 +217,11 @@ extern "C" sbg_status sbg_state_copy(sbg_state dst, sbg_state src, void *stream)
         if (src->dtype == SBG_F32X2)
             SBG_CUDA(cudaMemcpyAsync(dst->lo[dst->cur][sp], src->lo[src->cur][sp],
                                      (size_t)src->nslots * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    if (src->dtype == SBG_F32R) {  // base hi, lo and source are contiguous
+        SBG_CUDA(cudaMemcpyAsync(dst->bh, src->bh, 3 * (size_t)src->nslots * 4, cudaMemcpyDeviceToDevice, s));
+        dst->r_valid = src->r_valid;
+        dst->since_refresh = src->since_refresh;
     }
     return SBG_OK;
 }

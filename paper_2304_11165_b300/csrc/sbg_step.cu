@@ -14,6 +14,7 @@
 // results do not depend on the block size.
 #include <math.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "sbg_internal.cuh"
@@ -22,7 +23,10 @@
 namespace sbg {
 
 // Plain FP32 / FP64 state, NS species, optional reaction (REACT: k_surf != 0).
-template <typename T, int B, int BPC, int NS, bool REACT>
+// SRC: the correction d of an SBG_F32R state (one FP32 species), whose update
+// takes the stored source r = L_h b in place of the transfer term and the
+// surface loss k w in its rate.
+template <typename T, int B, int BPC, int NS, bool REACT, bool SRC = false>
 __global__ void __launch_bounds__(BPC * B * B * B, (sizeof(T) == 8 ? 1024 : 2048) / (BPC * B * B * B))
 k_step(const StepArgs a) {
     constexpr int B3 = B * B * B;
@@ -67,12 +71,23 @@ k_step(const StepArgs a) {
         const int ws = a.wslab[b];
         if (ws >= 0) w = sizeof(T) == 8 ? (T)a.w64[(int64_t)ws * B3 + l] : (T)a.w[(int64_t)ws * B3 + l];
     }
-    const T transfer = REACT ? k.k * w * uc[0] : T(0);
+    const T transfer = (REACT && !SRC) ? k.k * w * uc[0] : T(0);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const T u = uc[s];
         T res = u;
-        if (!is_sent(u) && !held) {
+        if (SRC && !is_sent(u) && !held) {
+            const T *t = tile[s] + j * B3;
+            const T xm = mirror(x > 0 ? t[l - 1] : hxm[s], u);
+            const T xp = mirror(x < B - 1 ? t[l + 1] : hxp[s], u);
+            const T ym = mirror(y > 0 ? t[l - B] : hym[s], u);
+            const T yp = mirror(y < B - 1 ? t[l + B] : hyp[s], u);
+            const T zm = mirror(z > 0 ? t[l - B * B] : hzm[s], u);
+            const T zp = mirror(z < B - 1 ? t[l + B * B] : hzp[s], u);
+            const float rate = REACT ? __fmaf_rn(a.cf.k, (float)w, a.cf.decay[0]) : a.cf.decay[0];
+            res = (T)fused_update((float)u, (float)xm, (float)xp, (float)ym, (float)yp, (float)zm, (float)zp,
+                                  a.cf.c[0], a.cf.dt, rate, a.src_term[b * B3 + l]);
+        } else if (!is_sent(u) && !held) {
             const T *t = tile[s] + j * B3;
             const T xm = mirror(x > 0 ? t[l - 1] : hxm[s], u);
             const T xp = mirror(x < B - 1 ? t[l + 1] : hxp[s], u);
@@ -165,14 +180,9 @@ k_step_x2(const StepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-static void fill_args(sbg_grid g, sbg_state st, const sbg_params *p, int src, StepArgs &a) {
+// Grid tables and coefficients of a step (no state arrays).
+void fill_step_args(sbg_grid g, const sbg_params *p, StepArgs &a) {
     std::memset(&a, 0, sizeof(a));
-    for (int s = 0; s < st->ns; ++s) {
-        a.in[s] = st->val[src][s];
-        a.out[s] = st->val[1 - src][s];
-        a.in_lo[s] = st->lo[src][s];
-        a.out_lo[s] = st->lo[1 - src][s];
-    }
     a.blocks = g->blocks;
     a.face = g->face_nbr;
     a.wslab = g->wslab;
@@ -199,12 +209,23 @@ static void fill_args(sbg_grid g, sbg_state st, const sbg_params *p, int src, St
     a.cf.k = (float)p->k_surf;
 }
 
-template <typename T, int B, int NS>
+static void fill_args(sbg_grid g, sbg_state st, const sbg_params *p, int src, StepArgs &a) {
+    fill_step_args(g, p, a);
+    for (int s = 0; s < st->ns; ++s) {
+        a.in[s] = st->val[src][s];
+        a.out[s] = st->val[1 - src][s];
+        a.in_lo[s] = st->lo[src][s];
+        a.out_lo[s] = st->lo[1 - src][s];
+    }
+    a.src_term = st->rsrc;
+}
+
+template <typename T, int B, int NS, bool SRC = false>
 static void launch_plain(const StepArgs &a, bool react, cudaStream_t s) {
     constexpr int BPC = (B == 8) ? 1 : 8;
     const unsigned grid = (unsigned)((a.nb + BPC - 1) / BPC);
-    if (react) k_step<T, B, BPC, NS, true><<<grid, BPC * B * B * B, 0, s>>>(a);
-    else k_step<T, B, BPC, NS, false><<<grid, BPC * B * B * B, 0, s>>>(a);
+    if (react) k_step<T, B, BPC, NS, true, SRC><<<grid, BPC * B * B * B, 0, s>>>(a);
+    else k_step<T, B, BPC, NS, false, SRC><<<grid, BPC * B * B * B, 0, s>>>(a);
 }
 
 template <int B>
@@ -229,11 +250,14 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
             return SBG_OK;
         }
         if (st->variant >= SBG_KERNEL_PIPELINED)
-            return fail(SBG_ERR_INVALID_ARG, "the pipelined kernel handles FP32 and SBG_F32X2 states only");
+            return fail(SBG_ERR_INVALID_ARG, "the pipelined kernel handles FP32-based states only");
     }
     if (st->dtype == SBG_F32X2) {
         if (g->B == 8) launch_x2<8>(a, react, s);
         else launch_x2<4>(a, react, s);
+    } else if (st->dtype == SBG_F32R) {
+        if (g->B == 8) launch_plain<float, 8, 1, true>(a, react, s);
+        else launch_plain<float, 4, 1, true>(a, react, s);
     } else if (st->dtype == SBG_F32) {
         if (g->B == 8) {
             if (st->ns == 1) launch_plain<float, 8, 1>(a, react, s);
@@ -332,7 +356,29 @@ static sbg_status ensure_graph(sbg_grid g, sbg_state st, const sbg_params *p) {
     return SBG_OK;
 }
 
+static sbg_status step_n_plain(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, cudaStream_t s);
+
+// SBG_F32R states: before every kRefreshSteps steps (and before the first
+// step after sbg_state_set) the source r is recomputed from b + d and d is
+// folded into b, so that d stays the change of the last <= kRefreshSteps steps.
 sbg_status step_n(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, cudaStream_t s) {
+    if (st->dtype != SBG_F32R) return step_n_plain(g, st, p, nsteps, s);
+    int64_t done = 0;
+    while (done < nsteps) {
+        if (!st->r_valid || st->since_refresh >= kRefreshSteps) {
+            sbg_status rc = refresh_source(g, st, p, s);
+            if (rc != SBG_OK) return rc;
+        }
+        const int64_t m = std::min<int64_t>(nsteps - done, kRefreshSteps - st->since_refresh);
+        sbg_status rc = step_n_plain(g, st, p, m, s);
+        if (rc != SBG_OK) return rc;
+        done += m;
+        st->since_refresh += m;
+    }
+    return SBG_OK;
+}
+
+static sbg_status step_n_plain(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, cudaStream_t s) {
     int64_t done = 0;
     if (nsteps >= kGraphSteps && g->nb > 0) {
         sbg_status rc = ensure_graph(g, st, p);

@@ -25,6 +25,7 @@ struct StepArgs {
     const float *pad;        // 4 sentinels, then 4 zeros
     const int32_t *gdims;
     int64_t nb;
+    const float *src_term;   // SBG_F32R: per-slot source r = L_h b of the correction step
     const int64_t *items;    // optional work list for the pipelined kernel: (first block, count)
     int64_t nitems;          //   pairs, each within one geometry and at most 512 voxels
     int held_mask;           // bit f: face f is Dirichlet
@@ -114,8 +115,34 @@ __device__ __forceinline__ void fused_update_x2(float hc, float lc, const float 
     rl = __fsub_rn(l2, __fsub_rn(rh, s));
 }
 
+// Grid tables and coefficients of a step (no state arrays); sbg_step.cu.
+void fill_step_args(sbg_grid g, const sbg_params *p, StepArgs &a);
+
+// Double-float accumulation (value = hi + lo): adds (h2, l2) to (h, l).
+__device__ __forceinline__ void df_add(float &h, float &l, float h2, float l2) {
+    float e;
+    const float s = two_sum(h, h2, e);
+    e = __fadd_rn(e, __fadd_rn(l, l2));
+    h = __fadd_rn(s, e);
+    l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// Arrays of one pipelined launch beyond StepArgs (set by the launchers).
+struct PipeIO {
+    const float *src[4];  // streamed arrays, in the kernel mode's order
+    float *dst[2];        // written arrays
+    double *gsum;         // adjoint: per-CTA sums of dL/dD_0, dL/dD_1, dL/dk, added to across launches
+    float inv2[3];        // adjoint: 1 / dx_a^2
+};
+
 // `prefetch` selects the variant that prefetches halos one group ahead.
 bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, bool prefetch,
                       int ctas_per_sm, int *err_flag, cudaStream_t s, cudaError_t *launch_err);
+
+// One adjoint step on FP32 arrays with the pipelined kernel: io.src = lambda^{n+1}
+// (NS arrays) then u^n (NS arrays), io.dst = lambda^n.  *grid_out receives the
+// number of CTAs (each adds to io.gsum[cta * 3 + q]); at most max_ctas are used.
+cudaError_t launch_adjoint_pipe(const StepArgs &a, const PipeIO &io, int ns, int B, bool react, int max_ctas,
+                                int *err_flag, cudaStream_t s, int *grid_out);
 
 }  // namespace sbg

@@ -1,4 +1,5 @@
-// Pipelined persistent step kernel for FP32 and compensated-FP32 states.
+// Pipelined persistent kernels for FP32 arrays: the forward step of FP32 and
+// compensated-FP32 states, and the adjoint step.
 //
 // Why: one thread per voxel with one 4-byte load each keeps only ~8 KB in
 // flight per SM, far below what HBM3e needs (~40 KB per SM at ~800 ns), and a
@@ -11,19 +12,28 @@
 //    bulk copies (cp.async.bulk, TMA engine) completing on per-stage
 //    mbarriers, S groups ahead of the compute; only that thread waits on the
 //    barrier, the others sleep in __syncthreads;
-//  - each thread updates four x-consecutive voxels: its row and the rows
-//    above/below/in front/behind come from shared memory as 16-byte loads at
-//    per-thread constant offsets from the stage tile or the halo buffer, so
-//    the update has no position-dependent selects of values;
+//  - each thread updates four x-consecutive voxels;
 //  - the one-voxel face halos come from the neighbouring blocks (mostly L2
-//    hits): each thread prefetches the halo values of its own row one group
-//    ahead into registers (face ids two groups ahead; two alternating
-//    register sets, no copies) and parks them in its own slots of a halo
-//    buffer when their group comes up;
+//    hits): each thread loads the halo values of its own row and parks them
+//    in its own slots of a halo buffer, so that every neighbour of its row is
+//    at a per-thread constant offset from either the stage's tile or the halo
+//    buffer (16-byte shared loads, no position-dependent selects of values);
+//    one halo buffer serves all stages because a thread reads back only the
+//    slots it wrote itself;
 //  - results leave as one 16-byte store per thread and array.
 // Every wait on an mbarrier is bounded: on time-out the CTA sets the grid's
 // error word (reported as SBG_ERR_TIMEOUT), waits (bounded) for its copies in
 // flight and exits.
+//
+// Modes (the arrays streamed per group, in order):
+//  kFwd  NS species u_s                        -> u_s'           (FP32 state)
+//  kX2   hi, lo                                -> hi', lo'       (compensated state)
+//  kAdj  lambda_s^{n+1} (NS), u_s^n (NS)       -> lambda_s^n     (adjoint step)
+//  kSrc  d, r (r without halo)                 -> d'             (SBG_F32R correction)
+// The per-voxel arithmetic is that of the plain kernels (sbg_step.cu), with
+// the rounding of every operation pinned, so both give bitwise equal states.
+#include <cstring>
+
 #include "sbg_ptx.cuh"
 #include "sbg_step.cuh"
 
@@ -32,17 +42,27 @@ namespace sbg {
 constexpr int kPipeThreads = 128;
 constexpr int kGroupVox = 512;
 
+enum PipeMode : int { kFwd = 0, kX2 = 1, kAdj = 2, kSrc = 3 };
+
+template <int MODE, int NS>
+struct PipeShape {
+    static constexpr int NA = MODE == kFwd ? NS : MODE == kAdj ? 2 * NS : 2;  // arrays streamed
+    static constexpr int NH = MODE == kSrc ? 1 : NA;                          // the first NH have halos
+    static constexpr int NO = MODE == kX2 ? 2 : MODE == kSrc ? 1 : NS;        // arrays written
+};
+
 __device__ __forceinline__ float f4get(const float4 &v, int i) {
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
 // Shared memory of one CTA: an S-stage ring of groups (NA arrays of 512
 // voxels each, written by the bulk copies) and one halo buffer with a B x B
-// face per block of the group and face direction, per array.  Each thread
-// writes the halo values of its own row into its own halo slots and reads
-// them back itself, so the halo buffer needs no extra barrier.  Every
-// neighbour of a thread's row is at a per-thread constant offset from either
-// the stage's tile or the halo buffer; the base is chosen once per group.
+// face per block of the group and face direction, per array (written by the
+// threads: each thread writes the halo values of its own row into its own
+// halo slots and reads them back itself, so they need no extra barrier; one
+// buffer serves every stage because a thread parks a group's halo values only
+// after it finished its previous group).  One more CTA per SM fits than with
+// a halo buffer per stage, which measured faster than the saved selects.
 template <int B>
 struct PipeLayout {
     static constexpr int B3 = B * B * B;
@@ -51,16 +71,18 @@ struct PipeLayout {
     __host__ __device__ static constexpr int face(int j, int f) { return (j * 6 + f) * B * B; }
 };
 
-template <bool X2, int B, int NS, bool REACT, int S, int MINB, bool PF>
-__global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs a, int *err) {
+template <int MODE, int B, int NS, bool REACT, int S, int MINB, bool PF>
+__global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs a, const PipeIO io, int *err) {
     using L = PipeLayout<B>;
     constexpr int B3 = L::B3;
     constexpr int G = L::G;
-    constexpr int NA = X2 ? 2 : NS;  // arrays streamed per group
+    constexpr int NA = PipeShape<MODE, NS>::NA;
+    constexpr int NH = PipeShape<MODE, NS>::NH;
+    constexpr int NO = PipeShape<MODE, NS>::NO;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *stages = reinterpret_cast<float *>(smem_raw);   // [S][NA][512]
-    float *halo = stages + (size_t)S * NA * kGroupVox;     // [NA][kHalo]
-    uint64_t *full = reinterpret_cast<uint64_t *>(halo + (size_t)NA * L::kHalo);
+    float *stages = reinterpret_cast<float *>(smem_raw);                // [S][NA][512]
+    float *halo = stages + (size_t)S * NA * kGroupVox;                  // [NH][kHalo]
+    uint64_t *full = reinterpret_cast<uint64_t *>(halo + (size_t)NH * L::kHalo);
 
     const int tid = threadIdx.x;
     // work items: consecutive groups of the block list, or an explicit list
@@ -79,21 +101,6 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
         }
     };
 
-    const float *src[NA];
-    float *dst[NA];
-    if (X2) {
-        src[0] = (const float *)a.in[0];
-        src[NA - 1] = a.in_lo[0];
-        dst[0] = (float *)a.out[0];
-        dst[NA - 1] = a.out_lo[0];
-    } else {
-#pragma unroll
-        for (int k = 0; k < NA; ++k) {
-            src[k] = (const float *)a.in[k];
-            dst[k] = (float *)a.out[k];
-        }
-    }
-
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
         fence_barrier_init();
@@ -107,7 +114,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
         mbar_arrive_expect_tx(&full[s], bytes * NA);
 #pragma unroll
         for (int k = 0; k < NA; ++k)
-            bulk_g2s(stages + ((size_t)s * NA + k) * kGroupVox, src[k] + b0 * B3, bytes, &full[s]);
+            bulk_g2s(stages + ((size_t)s * NA + k) * kGroupVox, io.src[k] + b0 * B3, bytes, &full[s]);
     };
     if (tid == 0)
         for (int s = 0; s < S && g0 + s < g1; ++s) issue(g0 + s, s);
@@ -124,7 +131,8 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     const int oy = hym ? l0 + (B - 1) * B : l0 - (B - 1) * B;
     const int oz = hzm ? l0 + (B - 1) * B * B : l0 - (B - 1) * B * B;
     const int fyy = hym ? 2 : 3, fzz = hzm ? 4 : 5;
-    // neighbour offsets: in the halo buffer when the neighbour is a halo value, else in the tile
+    // neighbour offsets: in the halo buffer when the neighbour is a halo
+    // value, else in the stage's tile
     const int sxm = hxm ? L::face(j, 0) + z * B + y : v0 - 1;
     const int sxp = hxp ? L::face(j, 1) + z * B + y : v0 + 4;
     const int sym = hym ? L::face(j, 2) + z * B + x0 : v0 - B;
@@ -139,8 +147,8 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
         int xm, xp, y, z, ws;
     };
     struct Halo {
-        float vxm[NA], vxp[NA];
-        float4 vy[NA], vz[NA];
+        float vxm[NH], vxp[NH];
+        float4 vy[NH], vz[NH];
         float4 w;
         int4 bc;
     };
@@ -164,13 +172,14 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     auto load_halo = [&](int64_t gi, const Ids &id, Halo &h) {
         const float SENT = sentinel_f32();
 #pragma unroll
-        for (int k = 0; k < NA; ++k) {
-            const float absent = (X2 && k == 1) ? 0.f : SENT;
-            h.vxm[k] = (id.xm >= 0) ? __ldg(src[k] + (int64_t)id.xm * B3 + oxm) : absent;
-            h.vxp[k] = (id.xp >= 0) ? __ldg(src[k] + (int64_t)id.xp * B3 + oxp) : absent;
-            h.vy[k] = (id.y >= 0) ? __ldg(reinterpret_cast<const float4 *>(src[k] + (int64_t)id.y * B3 + oy))
+        for (int k = 0; k < NH; ++k) {
+            const float absent = (MODE == kX2 && k == 1) ? 0.f : SENT;
+            const float *sk = io.src[k];
+            h.vxm[k] = (id.xm >= 0) ? __ldg(sk + (int64_t)id.xm * B3 + oxm) : absent;
+            h.vxp[k] = (id.xp >= 0) ? __ldg(sk + (int64_t)id.xp * B3 + oxp) : absent;
+            h.vy[k] = (id.y >= 0) ? __ldg(reinterpret_cast<const float4 *>(sk + (int64_t)id.y * B3 + oy))
                                   : make_float4(absent, absent, absent, absent);
-            h.vz[k] = (id.z >= 0) ? __ldg(reinterpret_cast<const float4 *>(src[k] + (int64_t)id.z * B3 + oz))
+            h.vz[k] = (id.z >= 0) ? __ldg(reinterpret_cast<const float4 *>(sk + (int64_t)id.z * B3 + oz))
                                   : make_float4(absent, absent, absent, absent);
         }
         h.w = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -182,15 +191,10 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
             if (j < nblk) h.bc = __ldg(a.blocks + b0 + j);
         }
     };
-
-    // One group: park this group's prefetched halo values in this thread's
-    // halo slots, prefetch the next group's halos (ids read a group earlier),
-    // wait for the stage, refill the previous stage, update.  The loop below
-    // is unrolled by two with the register sets swapped, so no prefetched
-    // value is copied (a copy would wait for the load every group).
+    // park this thread's halo values in its own slots of the halo buffer
     auto park = [&](const Halo &h) {
 #pragma unroll
-        for (int k = 0; k < NA; ++k) {
+        for (int k = 0; k < NH; ++k) {
             float *hb = halo + k * L::kHalo;
             if (hxm) hb[sxm] = h.vxm[k];
             if (hxp) hb[sxp] = h.vxp[k];
@@ -198,6 +202,9 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
             if (dz) *reinterpret_cast<float4 *>(hb + shz) = h.vz[k];
         }
     };
+
+    // adjoint: this thread's gradient sums, double-float (hi, lo) per quantity
+    float gh[3] = {0.f, 0.f, 0.f}, gl[3] = {0.f, 0.f, 0.f};
 
     // One group.  PF: park this group's halo values (prefetched during the
     // previous group), prefetch the next group's (ids read a group earlier).
@@ -238,25 +245,33 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
         if (!valid) return true;
         if (!PF) park(cur);
 
-        // Dirichlet-held voxels
+        // Dirichlet-held voxels of this row: a row test (y, z faces) and at
+        // most two x positions
         bool held[4] = {false, false, false, false};
         if (a.held_mask) {
+            const int m = a.held_mask;
             const int4 bc = cur.bc;
             const int nx = __ldg(a.gdims + bc.w * 4 + 0), ny = __ldg(a.gdims + bc.w * 4 + 1),
                       nz = __ldg(a.gdims + bc.w * 4 + 2);
-            const int gx = bc.x * B + x0, gy = bc.y * B + y, gz = bc.z * B + z;
+            const int gx0 = bc.x * B + x0, gy = bc.y * B + y, gz = bc.z * B + z;
+            const bool row = ((m & 4) && gy == 0) || ((m & 8) && gy == ny - 1) || ((m & 16) && gz == 0) ||
+                             ((m & 32) && gz == nz - 1);
+            const int i0 = (m & 1) ? -gx0 : -1;           // i with gx0 + i == 0
+            const int i1 = (m & 2) ? nx - 1 - gx0 : -1;   // i with gx0 + i == nx - 1
 #pragma unroll
-            for (int i = 0; i < 4; ++i) held[i] = is_held(a.held_mask, gx + i, gy, gz, nx, ny, nz);
+            for (int i = 0; i < 4; ++i) held[i] = row || i == i0 || i == i1;
         }
         const float4 w4 = cur.w;
 
-        float4 uc[NA], ym[NA], yp[NA], zm[NA], zp[NA];
-        float xm[NA], xp[NA];
+        float4 uc[NA], ym[NH], yp[NH], zm[NH], zp[NH];
+        float xm[NH], xp[NH];
 #pragma unroll
-        for (int k = 0; k < NA; ++k) {
+        for (int k = 0; k < NA; ++k)
+            uc[k] = *reinterpret_cast<const float4 *>(stages + ((size_t)s * NA + k) * kGroupVox + v0);
+#pragma unroll
+        for (int k = 0; k < NH; ++k) {
             const float *t = stages + ((size_t)s * NA + k) * kGroupVox;
             const float *h = halo + k * L::kHalo;
-            uc[k] = *reinterpret_cast<const float4 *>(t + v0);
             xm[k] = (hxm ? h : t)[sxm];
             xp[k] = (hxp ? h : t)[sxp];
             ym[k] = *reinterpret_cast<const float4 *>((hym ? h : t) + sym);
@@ -265,7 +280,8 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
             zp[k] = *reinterpret_cast<const float4 *>((hzp ? h : t) + szp);
         }
         const StepCoef<float> &kc = a.cf;
-        float res[NA][4];
+        float res[NO][4];
+        float q[3] = {0.f, 0.f, 0.f};  // adjoint: this group's gradient terms
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             // neighbours of voxel i in array 0 decide the no-flux mirror for every array
@@ -275,35 +291,73 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
 #pragma unroll
             for (int f = 0; f < 6; ++f) out[f] = is_sent(n0[f]);
             const float c0 = f4get(uc[0], i);
-            const bool upd = !is_sent(c0) && !held[i];
+            const bool act = !is_sent(c0);
+            const bool upd = act && !held[i];
 #pragma unroll
-            for (int k = 0; k < NA; ++k) res[k][i] = f4get(uc[k], i);
+            for (int k = 0; k < NO; ++k)
+                res[k][i] = (MODE == kAdj && act && held[i]) ? 0.f : f4get(uc[k], i);
             if (!upd) continue;
-            float nv[NA][6];
+            float nv[NH][6];
 #pragma unroll
-            for (int k = 0; k < NA; ++k) {
+            for (int k = 0; k < NH; ++k) {
                 const float c = f4get(uc[k], i);
                 const float raw[6] = {i == 0 ? xm[k] : f4get(uc[k], i - 1), i == 3 ? xp[k] : f4get(uc[k], i + 1),
                                       f4get(ym[k], i), f4get(yp[k], i), f4get(zm[k], i), f4get(zp[k], i)};
 #pragma unroll
                 for (int f = 0; f < 6; ++f) nv[k][f] = out[f] ? c : raw[f];
             }
-            if (X2) {
+            if (MODE == kX2) {
                 float rate = kc.decay[0];
                 if (REACT) rate = __fmaf_rn(kc.k, f4get(w4, i), rate);
-                fused_update_x2(c0, f4get(uc[NA - 1], i), nv[0], nv[NA - 1], kc.c[0], kc.dt, rate, res[0][i],
-                                res[NA - 1][i]);
-            } else {
+                fused_update_x2(c0, f4get(uc[1], i), nv[0], nv[1], kc.c[0], kc.dt, rate, res[0][i], res[1][i]);
+            } else if (MODE == kSrc) {
+                // correction d of an SBG_F32R state: the source r = L_h b replaces
+                // the base's part of the update
+                float rate = kc.decay[0];
+                if (REACT) rate = __fmaf_rn(kc.k, f4get(w4, i), rate);
+                res[0][i] = fused_update(c0, nv[0][0], nv[0][1], nv[0][2], nv[0][3], nv[0][4], nv[0][5], kc.c[0],
+                                         kc.dt, rate, f4get(uc[1], i));
+            } else if (MODE == kFwd) {
                 const float t = REACT ? __fmul_rn(__fmul_rn(kc.k, f4get(w4, i)), c0) : 0.f;
 #pragma unroll
-                for (int k = 0; k < NA; ++k)
+                for (int k = 0; k < NS; ++k)
                     res[k][i] = fused_update(f4get(uc[k], i), nv[k][0], nv[k][1], nv[k][2], nv[k][3], nv[k][4],
                                              nv[k][5], kc.c[k], kc.dt, kc.decay[k], k == 0 ? -t : t);
+            } else {
+                // lambda^n = M^T lambda^{n+1}: the forward stencil on lambda (held
+                // voxels hold lambda = 0), with the A -> B transfer transposed
+                const float kw = REACT ? __fmul_rn(kc.k, f4get(w4, i)) : 0.f;
+                const float lamB = NS == 2 ? f4get(uc[1], i) : 0.f;
+#pragma unroll
+                for (int sp = 0; sp < NS; ++sp) {
+                    const float rate = (sp == 0 && REACT) ? __fadd_rn(kc.decay[0], kw) : kc.decay[sp];
+                    const float t = (sp == 0 && NS == 2 && REACT) ? __fmul_rn(kw, lamB) : 0.f;
+                    res[sp][i] = fused_update(f4get(uc[sp], i), nv[sp][0], nv[sp][1], nv[sp][2], nv[sp][3],
+                                              nv[sp][4], nv[sp][5], kc.c[sp], kc.dt, rate, t);
+                    // dL/dD_s += lambda_s dt g_s(u^n), g = sum_a [(u~+ - u) + (u~- - u)] / dx_a^2
+                    const float u = f4get(uc[NS + sp], i);
+                    const float *nu = nv[NS + sp];
+                    float g = __fmul_rn(io.inv2[0], __fadd_rn(__fsub_rn(nu[0], u), __fsub_rn(nu[1], u)));
+                    g = __fmaf_rn(io.inv2[1], __fadd_rn(__fsub_rn(nu[2], u), __fsub_rn(nu[3], u)), g);
+                    g = __fmaf_rn(io.inv2[2], __fadd_rn(__fsub_rn(nu[4], u), __fsub_rn(nu[5], u)), g);
+                    q[sp] = __fmaf_rn(__fmul_rn(f4get(uc[sp], i), kc.dt), g, q[sp]);
+                }
+                if (REACT) {
+                    // dL/dk += dt w u_A (lambda_B - lambda_A)
+                    const float uA = f4get(uc[NS], i);
+                    const float dl = __fsub_rn(lamB, c0);
+                    q[2] = __fmaf_rn(__fmul_rn(__fmul_rn(kc.dt, f4get(w4, i)), uA), dl, q[2]);
+                }
             }
         }
+        if (MODE == kAdj) {
 #pragma unroll
-        for (int k = 0; k < NA; ++k)
-            *reinterpret_cast<float4 *>(dst[k] + b * B3 + l0) = make_float4(res[k][0], res[k][1], res[k][2], res[k][3]);
+            for (int qq = 0; qq < 3; ++qq) df_add(gh[qq], gl[qq], q[qq], 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < NO; ++k)
+            *reinterpret_cast<float4 *>(io.dst[k] + b * B3 + l0) =
+                make_float4(res[k][0], res[k][1], res[k][2], res[k][3]);
         return true;
     };
 
@@ -314,25 +368,65 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
         idA = load_ids(g0 + 1);
     }
     int it = 0;
+    bool ok = true;
     for (int64_t gi = g0; gi < g1; gi += 2, it += 2) {
-        if (!body(gi, it, hA, hB, idA, idB)) return;
+        if (!body(gi, it, hA, hB, idA, idB)) {
+            ok = false;
+            break;
+        }
         if (gi + 1 >= g1) break;
-        if (!body(gi + 1, it + 1, hB, hA, idB, idA)) return;
+        if (!body(gi + 1, it + 1, hB, hA, idB, idA)) {
+            ok = false;
+            break;
+        }
+    }
+    if (MODE == kAdj && ok) {
+        // CTA sums: double-float across the warp, FP64 across the warps; each
+        // CTA adds to its own slot, so the order of additions is fixed
+        __shared__ double red[kPipeThreads / 32][3];
+#pragma unroll
+        for (int qq = 0; qq < 3; ++qq) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float h2 = __shfl_down_sync(0xffffffffu, gh[qq], o);
+                const float l2 = __shfl_down_sync(0xffffffffu, gl[qq], o);
+                df_add(gh[qq], gl[qq], h2, l2);
+            }
+            if ((tid & 31) == 0) red[tid >> 5][qq] = (double)gh[qq] + (double)gl[qq];
+        }
+        __syncthreads();
+        if (tid < 3) {
+            double v = 0.0;
+            for (int w = 0; w < kPipeThreads / 32; ++w) v += red[w][tid];
+            io.gsum[(int64_t)blockIdx.x * 3 + tid] += v;
+        }
     }
 }
 
-template <bool X2, int B, int NS, bool REACT, bool PF>
-static cudaError_t launch_pipe_pf(const StepArgs &a, int ctas_per_sm, int *err, cudaStream_t s) {
-    constexpr int NA = X2 ? 2 : NS;
-    constexpr int S = NA == 1 ? 6 : 4;
-    constexpr size_t smem = ((size_t)S * NA * kGroupVox + (size_t)NA * PipeLayout<B>::kHalo) * sizeof(float) +
+template <int MODE, int NA>
+struct PipeStages {
+    static constexpr int S = NA == 1 ? 6 : NA == 2 ? 4 : 3;
+};
+
+template <int MODE, int B, int NS, bool REACT, bool PF>
+static cudaError_t launch_pipe_pf(const StepArgs &a, const PipeIO &io, int ctas_per_sm, int max_ctas, int *err,
+                                  cudaStream_t s, int *grid_out) {
+    constexpr int NA = PipeShape<MODE, NS>::NA;
+    constexpr int S = PipeStages<MODE, NA>::S;
+    constexpr int NH = PipeShape<MODE, NS>::NH;
+    constexpr size_t smem = ((size_t)S * NA * kGroupVox + (size_t)NH * PipeLayout<B>::kHalo) * sizeof(float) +
                             S * sizeof(uint64_t);
     constexpr int G = kGroupVox / (B * B * B);
     // Without prefetch: 64 registers per thread (8 CTAs of 128 threads per SM)
-    // with one array, 80 (6 CTAs) with two.  With prefetch the two register
-    // sets need up to 128 registers (4 CTAs per SM).
-    constexpr int MINB = PF ? 4 : (NA == 1 ? 8 : 6);
-    auto kern = k_step_pipe<X2, B, NS, REACT, S, MINB, PF>;
+    // with one array, 80 (6 CTAs) with two (96, 5 CTAs, for the adjoint with
+    // its gradient sums), 128 (4 CTAs) with four.  With
+    // prefetch the two register sets need up to 128 registers (4 CTAs per SM).
+    // No more CTAs than fit in the SM's 228 KB of shared memory (1 KB of it
+    // reserved per CTA) are asked for, so the registers go to those that fit.
+    constexpr int kBase = PF ? 4 : (NA == 1 ? 8 : NA == 2 ? (MODE == kAdj ? 5 : 6) : 4);
+    constexpr int kFit = (int)((228 * 1024) / (smem + 1024));
+    constexpr int MINB = kBase < kFit ? kBase : (kFit > 0 ? kFit : 1);
+    auto kern = k_step_pipe<MODE, B, NS, REACT, S, MINB, PF>;
     static int occ = -1, nsm = 0;
     if (occ < 0) {
         int dev = 0;
@@ -346,43 +440,74 @@ static cudaError_t launch_pipe_pf(const StepArgs &a, int ctas_per_sm, int *err, 
     const int64_t ngroups = a.items ? a.nitems : (a.nb + G - 1) / G;
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ngroups) grid = ngroups;
+    if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+    if (grid_out) *grid_out = (int)(grid > 0 ? grid : 0);
     if (grid < 1) return cudaSuccess;
-    kern<<<(unsigned)grid, kPipeThreads, smem, s>>>(a, err);
+    kern<<<(unsigned)grid, kPipeThreads, smem, s>>>(a, io, err);
     return cudaGetLastError();
 }
 
-// Halo prefetch on or off: chosen by the kernel variant of the state.
-static thread_local bool t_prefetch = false;
-template <bool X2, int B, int NS, bool REACT>
-static cudaError_t launch_pipe_t(const StepArgs &a, int ctas_per_sm, int *err, cudaStream_t s) {
-    return t_prefetch ? launch_pipe_pf<X2, B, NS, REACT, true>(a, ctas_per_sm, err, s)
-                      : launch_pipe_pf<X2, B, NS, REACT, false>(a, ctas_per_sm, err, s);
+template <int MODE, int B, int NS, bool REACT>
+static cudaError_t launch_pipe_t(const StepArgs &a, const PipeIO &io, bool prefetch, int ctas_per_sm, int *err,
+                                 cudaStream_t s) {
+    return prefetch ? launch_pipe_pf<MODE, B, NS, REACT, true>(a, io, ctas_per_sm, 0, err, s, nullptr)
+                    : launch_pipe_pf<MODE, B, NS, REACT, false>(a, io, ctas_per_sm, 0, err, s, nullptr);
+}
+
+template <int MODE, int NS>
+static cudaError_t launch_pipe_b(const StepArgs &a, const PipeIO &io, int B, bool react, bool prefetch,
+                                 int ctas_per_sm, int *err, cudaStream_t s) {
+    if (B == 8)
+        return react ? launch_pipe_t<MODE, 8, NS, true>(a, io, prefetch, ctas_per_sm, err, s)
+                     : launch_pipe_t<MODE, 8, NS, false>(a, io, prefetch, ctas_per_sm, err, s);
+    return react ? launch_pipe_t<MODE, 4, NS, true>(a, io, prefetch, ctas_per_sm, err, s)
+                 : launch_pipe_t<MODE, 4, NS, false>(a, io, prefetch, ctas_per_sm, err, s);
 }
 
 bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, bool prefetch,
                       int ctas_per_sm, int *err_flag, cudaStream_t s, cudaError_t *launch_err) {
+    PipeIO io;
+    std::memset(&io, 0, sizeof(io));
     cudaError_t e = cudaSuccess;
-    t_prefetch = prefetch;
     if (dtype == SBG_F32X2 && ns == 1) {
-        if (B == 8) e = react ? launch_pipe_t<true, 8, 1, true>(a, ctas_per_sm, err_flag, s)
-                              : launch_pipe_t<true, 8, 1, false>(a, ctas_per_sm, err_flag, s);
-        else e = react ? launch_pipe_t<true, 4, 1, true>(a, ctas_per_sm, err_flag, s)
-                       : launch_pipe_t<true, 4, 1, false>(a, ctas_per_sm, err_flag, s);
-    } else if (dtype == SBG_F32 && ns == 1) {
-        if (B == 8) e = react ? launch_pipe_t<false, 8, 1, true>(a, ctas_per_sm, err_flag, s)
-                              : launch_pipe_t<false, 8, 1, false>(a, ctas_per_sm, err_flag, s);
-        else e = react ? launch_pipe_t<false, 4, 1, true>(a, ctas_per_sm, err_flag, s)
-                       : launch_pipe_t<false, 4, 1, false>(a, ctas_per_sm, err_flag, s);
-    } else if (dtype == SBG_F32 && ns == 2) {
-        if (B == 8) e = react ? launch_pipe_t<false, 8, 2, true>(a, ctas_per_sm, err_flag, s)
-                              : launch_pipe_t<false, 8, 2, false>(a, ctas_per_sm, err_flag, s);
-        else e = react ? launch_pipe_t<false, 4, 2, true>(a, ctas_per_sm, err_flag, s)
-                       : launch_pipe_t<false, 4, 2, false>(a, ctas_per_sm, err_flag, s);
+        io.src[0] = (const float *)a.in[0];
+        io.src[1] = a.in_lo[0];
+        io.dst[0] = (float *)a.out[0];
+        io.dst[1] = a.out_lo[0];
+        e = launch_pipe_b<kX2, 1>(a, io, B, react, prefetch, ctas_per_sm, err_flag, s);
+    } else if (dtype == SBG_F32R && ns == 1) {
+        io.src[0] = (const float *)a.in[0];
+        io.src[1] = a.src_term;
+        io.dst[0] = (float *)a.out[0];
+        e = launch_pipe_b<kSrc, 1>(a, io, B, react, prefetch, ctas_per_sm, err_flag, s);
+    } else if (dtype == SBG_F32 && (ns == 1 || ns == 2)) {
+        for (int k = 0; k < ns; ++k) {
+            io.src[k] = (const float *)a.in[k];
+            io.dst[k] = (float *)a.out[k];
+        }
+        e = ns == 1 ? launch_pipe_b<kFwd, 1>(a, io, B, react, prefetch, ctas_per_sm, err_flag, s)
+                    : launch_pipe_b<kFwd, 2>(a, io, B, react, prefetch, ctas_per_sm, err_flag, s);
     } else {
         return false;
     }
     *launch_err = e;
     return true;
+}
+
+cudaError_t launch_adjoint_pipe(const StepArgs &a, const PipeIO &io, int ns, int B, bool react, int max_ctas,
+                                int *err_flag, cudaStream_t s, int *grid_out) {
+    if (ns == 1) {
+        if (B == 8)
+            return react ? launch_pipe_pf<kAdj, 8, 1, true, false>(a, io, 0, max_ctas, err_flag, s, grid_out)
+                         : launch_pipe_pf<kAdj, 8, 1, false, false>(a, io, 0, max_ctas, err_flag, s, grid_out);
+        return react ? launch_pipe_pf<kAdj, 4, 1, true, false>(a, io, 0, max_ctas, err_flag, s, grid_out)
+                     : launch_pipe_pf<kAdj, 4, 1, false, false>(a, io, 0, max_ctas, err_flag, s, grid_out);
+    }
+    if (B == 8)
+        return react ? launch_pipe_pf<kAdj, 8, 2, true, false>(a, io, 0, max_ctas, err_flag, s, grid_out)
+                     : launch_pipe_pf<kAdj, 8, 2, false, false>(a, io, 0, max_ctas, err_flag, s, grid_out);
+    return react ? launch_pipe_pf<kAdj, 4, 2, true, false>(a, io, 0, max_ctas, err_flag, s, grid_out)
+                 : launch_pipe_pf<kAdj, 4, 2, false, false>(a, io, 0, max_ctas, err_flag, s, grid_out);
 }
 
 }  // namespace sbg
