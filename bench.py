@@ -3,18 +3,20 @@
 
 Default workload (`--workload grf256`): the 256^3 tortuosity solve - a
 thresholded Gaussian random field (correlation length 8, porosity 0.35),
-c = 1 / c = 0 held on the x faces, D = 1, dt = 0.15, compensated-FP32 state
-(FP32 arithmetic, value = hi + lo) with FP64 reductions.  One bench step = one
-check interval of the steady-state solve: 128 forward-Euler steps plus the
-FP64 residual and flux reduction that decides convergence.
+c = 1 / c = 0 held on the x faces, D = 1, dt = 0.15, an SBG_F32R state (FP32
+correction d on a compensated base b = hi + lo: each step is FP32 forward
+Euler on d with the source r = L_h b; the check folds d into b) with
+double-float/FP64 reductions.  One bench step = one check interval of the
+steady-state solve: 128 forward-Euler steps plus the residual and flux
+reduction that decides convergence (which also refreshes r and folds d).
 
 Metric: active-voxel updates per second (GVox/s) = n_active * 128 * steps /
 time.  `value` is measured with CUDA events on the stream the library uses,
 inputs resident in HBM; `e2e` repeats the measurement through the public API
 with the dense initial field uploaded from pinned host memory every step and
 D_eff read back.  `roofline` reports the step kernel's algorithmic bytes
-(16 B per active voxel: hi and lo read and written) per launch over its
-average launch time, against the measured HBM copy bandwidth.
+(12 B per active voxel: d and r read, d written; 16 B for --dtype f32x2) per
+launch over its average launch time, against the measured HBM copy bandwidth.
 
 Other workloads print one JSON line each:
   --workload reactive512   two species, surface reaction A -> B, 2000 steps (512^3)
@@ -63,8 +65,8 @@ def parse():
     ap.add_argument("--workload", default="grf256", choices=["grf256", "reactive512", "gradient256", "batch64"])
     ap.add_argument("--n", type=int, default=None, help="box side (default: the workload's)")
     ap.add_argument("--block", type=int, default=4)
-    ap.add_argument("--dtype", default="f32x2", choices=["f32", "f32x2", "f32r"])
-    ap.add_argument("--variant", default="pipelined", choices=["plain", "pipelined", "prefetch"])
+    ap.add_argument("--dtype", default="f32r", choices=["f32", "f32x2", "f32r"])
+    ap.add_argument("--variant", default="pipelined", choices=["plain", "pipelined", "prefetch", "async"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fd", action="store_true", help="gradient256: FP64 central differences")
@@ -504,7 +506,7 @@ def run_batch64(args):
     phis = [phi for _, phi, _ in geos]
     phys0 = geos[0][2]
     p = make_params(phys0)
-    best, table = autotune.tune(phis, phys0, "f32x2")
+    best, table = autotune.tune(phis, phys0, args.dtype)
     B, variant, ctas = best["block"], best["variant"], best["ctas_per_sm"]
     stream = torch.cuda.current_stream()
 
@@ -523,7 +525,7 @@ def run_batch64(args):
     nsteps = 1024
     gb = Grid.batch(phis, block=B)
     na, _, _ = gb.geometry_info()
-    sb = State(gb, 1, "f32x2").set_kernel(variant, ctas)
+    sb = State(gb, 1, args.dtype).set_kernel(variant, ctas)
     for gi, (_, _, ph) in enumerate(geos):
         init(sb, gi, ph)
     sb.step(p, 64)
@@ -533,7 +535,7 @@ def run_batch64(args):
         total = 0.0
         for gi, (_, phi, ph) in enumerate(geos):
             g1 = Grid(phi, block=B)
-            s1 = State(g1, 1, "f32x2").set_kernel(kv, ctas if kv == variant else 0)
+            s1 = State(g1, 1, args.dtype).set_kernel(kv, ctas if kv == variant else 0)
             init(s1, 0, ph)
             s1.step(p, 64)
             _, ms = timed(lambda: s1.step(p, nsteps))
@@ -544,7 +546,7 @@ def run_batch64(args):
     upd = float(na.sum()) * nsteps
     out = {"metric": "aggregate active-voxel updates/s, 64 uneven geometries (batched vs per-geometry launches)",
            "value": upd / (batch_ms / 1e3) / 1e9, "unit": "GVox/s", "higher_is_better": True, "n_gpus": 1,
-           "dtype": "f32x2", "data": "synthetic",
+           "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": "batch64: %d geometries, sides %s, spheres/GRF alternating, porosity U(0.2,0.6), "
                                   "tortuosity physics" % (len(geos), list(sides)),
                       "autotuned": best, "autotune_table": table, "n_active_total": int(na.sum()),
@@ -566,7 +568,7 @@ def run_batch64(args):
         steps_s, deff_s = [], []
         for gi, (_, phi, ph) in enumerate(geos):
             g1 = Grid(phi, block=B)
-            s1 = State(g1, 1, "f32x2").set_kernel("plain")
+            s1 = State(g1, 1, args.dtype).set_kernel("plain")
             init(s1, 0, ph)
             st_, _ = s1.run_to_steady(p, 1e-6, check_every=512, max_steps=3_000_000, raise_on_max=False)
             steps_s.append(st_)

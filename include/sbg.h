@@ -190,10 +190,18 @@ sbg_status sbg_state_get(sbg_grid grid, sbg_state state, int32_t geom, int32_t s
  * SBG_KERNEL_PIPELINED (persistent CTAs streaming 512-voxel groups
  * through a bulk-copy ring; FP32 and SBG_F32X2 states only) or
  * SBG_KERNEL_PIPELINED_PREFETCH (the same, with face halos prefetched one
- * group ahead in registers: fewer CTAs per SM, less exposed latency).  ctas_per_sm:
+ * group ahead in registers: fewer CTAs per SM, less exposed latency) or
+ * SBG_KERNEL_PIPELINED_ASYNC (face halos copied one group ahead into shared
+ * memory with per-thread cp.async: no extra registers).  ctas_per_sm:
  * persistent CTAs per SM for the pipelined kernel (0 = as many as fit).
  * Results are bitwise identical across variants. */
-enum { SBG_KERNEL_AUTO = 0, SBG_KERNEL_PLAIN = 1, SBG_KERNEL_PIPELINED = 2, SBG_KERNEL_PIPELINED_PREFETCH = 3 };
+enum {
+    SBG_KERNEL_AUTO = 0,
+    SBG_KERNEL_PLAIN = 1,
+    SBG_KERNEL_PIPELINED = 2,
+    SBG_KERNEL_PIPELINED_PREFETCH = 3,
+    SBG_KERNEL_PIPELINED_ASYNC = 4
+};
 sbg_status sbg_state_set_kernel(sbg_state state, int32_t variant, int32_t ctas_per_sm);
 
 /* Copies all species of `src` into `dst` (same grid, dtype and species). */

@@ -217,7 +217,7 @@ class State:
     def set_kernel(self, variant: str = "auto", ctas_per_sm: int = 0):
         code = {"auto": _abi.SBG_KERNEL_AUTO, "plain": _abi.SBG_KERNEL_PLAIN,
                 "pipelined": _abi.SBG_KERNEL_PIPELINED,
-                "prefetch": _abi.SBG_KERNEL_PIPELINED_PREFETCH}[variant]
+                "prefetch": _abi.SBG_KERNEL_PIPELINED_PREFETCH, "async": _abi.SBG_KERNEL_PIPELINED_ASYNC}[variant]
         check(self._lib.sbg_state_set_kernel(self.handle, code, int(ctas_per_sm)))
         return self
 

@@ -392,7 +392,8 @@ extern "C" sbg_status sbg_adjoint(sbg_grid g, sbg_tape tp, sbg_state lam, double
         return fail(SBG_ERR_INVALID_ARG, "sbg_adjoint: lambda state must match the recorded state's dtype and species");
     cudaStream_t s = (cudaStream_t)stream;
     SBG_CUDA(cudaMemsetAsync(tp->partials, 0, sizeof(double) * 3 * tp->nctas, s));
-    sbg_status rc = tp->dtype == SBG_F32 ? zero_held(tp, lam, s) : SBG_OK;
+    sbg_status rc = prepare_held_bits(g, &tp->p, s);
+    if (rc == SBG_OK && tp->dtype == SBG_F32) rc = zero_held(tp, lam, s);
     if (rc != SBG_OK) return rc;
     const int64_t K = tp->K;
     // recompute buffers for u^{n0+1} .. u^{n0+K-1} (u^{n0} is the checkpoint itself)

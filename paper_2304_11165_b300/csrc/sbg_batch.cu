@@ -31,8 +31,10 @@ extern "C" sbg_status sbg_batch_run_to_steady(sbg_grid g, sbg_state st, const sb
     if (st->grid != g) return fail(SBG_ERR_INVALID_ARG, "sbg_batch_run_to_steady: state of another grid");
     if (check_every < 2 || max_steps < 0 || !(tol > 0.0))
         return fail(SBG_ERR_INVALID_ARG, "sbg_batch_run_to_steady: check_every >= 2, max_steps >= 0, tol > 0");
-    if (st->dtype == SBG_F64) return fail(SBG_ERR_INVALID_ARG, "sbg_batch_run_to_steady: FP32 or SBG_F32X2 states");
+    if (st->dtype == SBG_F64) return fail(SBG_ERR_INVALID_ARG, "sbg_batch_run_to_steady: FP32-based states");
     sbg_status rc = validate_params(g, p, st->ns);
+    if (rc != SBG_OK) return rc;
+    rc = prepare_held_bits(g, p, (cudaStream_t)stream);  // before the step graphs are captured
     if (rc != SBG_OK) return rc;
     check_every += check_every & 1;  // even: parity of the current buffer is kept
     cudaStream_t s = (cudaStream_t)stream;

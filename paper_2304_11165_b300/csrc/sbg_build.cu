@@ -373,6 +373,7 @@ static void grid_free(sbg_grid g) {
     cudaFreeHost(g->red_host);
     cudaFree(g->err);
     cudaFree(g->pad);
+    cudaFree(g->heldbits);
     cudaFreeHost(g->err_host);
     delete g;
 }

@@ -102,6 +102,8 @@ struct sbg_grid_s {
     double *red_dev = nullptr;     // [kNumRed]
     double *red_host = nullptr;    // pinned [kNumRed]
     float *pad = nullptr;          // 16-byte-aligned page: 4 sentinels then 4 zeros (absent halo neighbours)
+    uint64_t *heldbits = nullptr;  // [nb * words]: voxels held by the Dirichlet faces of heldbits_mask
+    int heldbits_mask = -1;        // face set heldbits was computed for (-1: none yet)
     int *err = nullptr;            // device error word written by bounded waits (0 = none)
     int *err_host = nullptr;       // pinned copy
     int64_t bytes = 0;
@@ -149,4 +151,7 @@ sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geo
 sbg_status refresh_source(sbg_grid g, sbg_state st, const sbg_params *p, cudaStream_t stream);
 // steps between refreshes of an SBG_F32R state inside sbg_step
 constexpr int64_t kRefreshSteps = 128;
+// implemented in sbg_step.cu: makes g->heldbits match the Dirichlet faces of
+// p (one small kernel when they changed); call before any stream capture
+sbg_status prepare_held_bits(sbg_grid g, const sbg_params *p, cudaStream_t s);
 }  // namespace sbg

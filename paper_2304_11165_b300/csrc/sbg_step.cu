@@ -180,6 +180,51 @@ k_step_x2(const StepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// held-voxel bits of each block for the Dirichlet face set `mask`: one
+// thread per 64-voxel word
+template <int B>
+__global__ void k_held_bits(const int4 *blocks, const int32_t *gdims, int mask, int64_t nb, uint64_t *out) {
+    constexpr int B3 = B * B * B;
+    constexpr int W = (B3 + 63) / 64;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb * W) return;
+    const int64_t b = i / W;
+    const int w = (int)(i - b * W);
+    const int4 bc = blocks[b];
+    const int nx = gdims[bc.w * 4], ny = gdims[bc.w * 4 + 1], nz = gdims[bc.w * 4 + 2];
+    uint64_t bits = 0;
+    for (int q = 0; q < 64 && w * 64 + q < B3; ++q) {
+        const int l = w * 64 + q;
+        if (is_held(mask, bc.x * B + l % B, bc.y * B + (l / B) % B, bc.z * B + l / (B * B), nx, ny, nz))
+            bits |= 1ull << q;
+    }
+    out[i] = bits;
+}
+
+static int held_mask_of(const sbg_params *p) {
+    int m = 0;
+    for (int f = 0; f < 6; ++f)
+        if (p->face_type[f] == SBG_FACE_DIRICHLET) m |= 1 << f;
+    return m;
+}
+
+sbg_status prepare_held_bits(sbg_grid g, const sbg_params *p, cudaStream_t s) {
+    const int mask = held_mask_of(p);
+    if (mask == 0 || g->nb == 0 || g->heldbits_mask == mask) return SBG_OK;
+    const int64_t n = g->nb * g->words();
+    if (!g->heldbits) {
+        cudaError_t e = cudaMalloc(&g->heldbits, sizeof(uint64_t) * n);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (held bits)");
+        g->bytes += (int64_t)(sizeof(uint64_t) * n);
+    }
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (g->B == 8) k_held_bits<8><<<grid, 256, 0, s>>>(g->blocks, g->gdims, mask, g->nb, g->heldbits);
+    else k_held_bits<4><<<grid, 256, 0, s>>>(g->blocks, g->gdims, mask, g->nb, g->heldbits);
+    SBG_LAUNCH_CHECK("held-bits kernel launch");
+    g->heldbits_mask = mask;
+    return SBG_OK;
+}
+
 // Grid tables and coefficients of a step (no state arrays).
 void fill_step_args(sbg_grid g, const sbg_params *p, StepArgs &a) {
     std::memset(&a, 0, sizeof(a));
@@ -191,9 +236,8 @@ void fill_step_args(sbg_grid g, const sbg_params *p, StepArgs &a) {
     a.pad = g->pad;
     a.gdims = g->gdims;
     a.nb = g->nb;
-    a.held_mask = 0;
-    for (int f = 0; f < 6; ++f)
-        if (p->face_type[f] == SBG_FACE_DIRICHLET) a.held_mask |= 1 << f;
+    a.held_mask = held_mask_of(p);
+    a.heldbits = (a.held_mask && g->heldbits_mask == a.held_mask) ? g->heldbits : nullptr;
     for (int s = 0; s < 2; ++s) {
         for (int ax = 0; ax < 3; ++ax) {
             double c = p->D[s] / (p->dx[ax] * p->dx[ax]);
@@ -242,9 +286,10 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
     StepArgs a;
     fill_args(g, st, p, src, a);
     const bool react = p->k_surf != 0.0;
+    if (a.held_mask && !a.heldbits) return fail(SBG_ERR_INVALID_ARG, "internal: held bits not prepared");
     if (st->variant != SBG_KERNEL_PLAIN) {
         cudaError_t e = cudaSuccess;
-        if (launch_step_pipe(a, st->dtype, st->ns, g->B, react, st->variant == SBG_KERNEL_PIPELINED_PREFETCH,
+        if (launch_step_pipe(a, st->dtype, st->ns, g->B, react, halo_variant_of(st->variant),
                              st->ctas_per_sm, g->err, s, &e)) {
             if (e != cudaSuccess) return cuda_fail(e, "pipelined step kernel launch");
             return SBG_OK;
@@ -362,6 +407,8 @@ static sbg_status step_n_plain(sbg_grid g, sbg_state st, const sbg_params *p, in
 // step after sbg_state_set) the source r is recomputed from b + d and d is
 // folded into b, so that d stays the change of the last <= kRefreshSteps steps.
 sbg_status step_n(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, cudaStream_t s) {
+    sbg_status prc = prepare_held_bits(g, p, s);
+    if (prc != SBG_OK) return prc;
     if (st->dtype != SBG_F32R) return step_n_plain(g, st, p, nsteps, s);
     int64_t done = 0;
     while (done < nsteps) {
@@ -418,7 +465,7 @@ extern "C" sbg_status sbg_step(sbg_grid g, sbg_state st, const sbg_params *p, in
 
 extern "C" sbg_status sbg_state_set_kernel(sbg_state st, int32_t variant, int32_t ctas_per_sm) {
     if (!st) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: null state");
-    if (variant < SBG_KERNEL_AUTO || variant > SBG_KERNEL_PIPELINED_PREFETCH || ctas_per_sm < 0 || ctas_per_sm > 64)
+    if (variant < SBG_KERNEL_AUTO || variant > SBG_KERNEL_PIPELINED_ASYNC || ctas_per_sm < 0 || ctas_per_sm > 64)
         return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: bad variant or ctas_per_sm");
     if (variant >= SBG_KERNEL_PIPELINED && st->dtype == SBG_F64)
         return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: no pipelined kernel for FP64 states");
@@ -434,11 +481,12 @@ sbg_status launch_step_work(sbg_grid g, sbg_state st, const sbg_params *p, int s
                             int64_t nitems, cudaStream_t s) {
     StepArgs a;
     fill_args(g, st, p, src, a);
+    if (a.held_mask && !a.heldbits) return fail(SBG_ERR_INVALID_ARG, "internal: held bits not prepared");
     a.items = items;
     a.nitems = nitems;
     cudaError_t e = cudaSuccess;
     if (!launch_step_pipe(a, st->dtype, st->ns, g->B, p->k_surf != 0.0,
-                          st->variant == SBG_KERNEL_PIPELINED_PREFETCH, st->ctas_per_sm, g->err, s, &e))
+                          halo_variant_of(st->variant), st->ctas_per_sm, g->err, s, &e))
         return fail(SBG_ERR_INVALID_ARG, "batched stepping needs an FP32 or SBG_F32X2 state");
     if (e != cudaSuccess) return cuda_fail(e, "pipelined step kernel launch (work list)");
     return SBG_OK;

@@ -24,6 +24,7 @@ struct StepArgs {
     const double *w64;
     const float *pad;        // 4 sentinels, then 4 zeros
     const int32_t *gdims;
+    const uint64_t *heldbits;  // per block, B^3 bits: voxel held by a Dirichlet face (null without)
     int64_t nb;
     const float *src_term;   // SBG_F32R: per-slot source r = L_h b of the correction step
     const int64_t *items;    // optional work list for the pipelined kernel: (first block, count)
@@ -50,15 +51,22 @@ __device__ __forceinline__ T mirror(T v, T c) { return is_sent(v) ? c : v; }
 // same value for the same neighbourhood whatever their data movement:
 //   u' = u + dt ( sum_a c_a [(u_{+a} - u) - (u - u_{-a})] - decay u + t )
 // with t = -k w u_A for species A and +k w u_A for species B.
-__device__ __forceinline__ float fused_update(float u, float xm, float xp, float ym, float yp, float zm,
-                                              float zp, const float c[3], float dt, float decay,
-                                              float t) {
-    const float dx = __fsub_rn(__fsub_rn(xp, u), __fsub_rn(u, xm));
+// The same update given the x second difference dx = (xp - u) - (u - xm)
+// (the pipelined kernel forms the x differences once per row and shares them
+// between neighbouring voxels).
+__device__ __forceinline__ float fused_update_dx(float u, float dx, float ym, float yp, float zm, float zp,
+                                                 const float c[3], float dt, float decay, float t) {
     const float dy = __fsub_rn(__fsub_rn(yp, u), __fsub_rn(u, ym));
     const float dz = __fsub_rn(__fsub_rn(zp, u), __fsub_rn(u, zm));
     const float lap = __fmaf_rn(c[2], dz, __fmaf_rn(c[1], dy, __fmul_rn(c[0], dx)));
     const float react = __fmaf_rn(-decay, u, t);
     return __fmaf_rn(dt, __fadd_rn(lap, react), u);
+}
+__device__ __forceinline__ float fused_update(float u, float xm, float xp, float ym, float yp, float zm,
+                                              float zp, const float c[3], float dt, float decay,
+                                              float t) {
+    const float dx = __fsub_rn(__fsub_rn(xp, u), __fsub_rn(u, xm));
+    return fused_update_dx(u, dx, ym, yp, zm, zp, c, dt, decay, t);
 }
 __device__ __forceinline__ double fused_update(double u, double xm, double xp, double ym, double yp,
                                                double zm, double zp, const double c[3], double dt,
@@ -135,9 +143,14 @@ struct PipeIO {
     float inv2[3];        // adjoint: 1 / dx_a^2
 };
 
-// `prefetch` selects the variant that prefetches halos one group ahead.
-bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, bool prefetch,
+// halo_variant: 0 halo loaded when its group comes up, 1 prefetched one group
+// ahead in registers, 2 copied one group ahead with cp.async (sbg_step_pipe.cu).
+bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, int halo_variant,
                       int ctas_per_sm, int *err_flag, cudaStream_t s, cudaError_t *launch_err);
+// the halo variant of a state's kernel choice
+inline int halo_variant_of(int variant) {
+    return variant == SBG_KERNEL_PIPELINED_PREFETCH ? 1 : variant == SBG_KERNEL_PIPELINED_ASYNC ? 2 : 0;
+}
 
 // One adjoint step on FP32 arrays with the pipelined kernel: io.src = lambda^{n+1}
 // (NS arrays) then u^n (NS arrays), io.dst = lambda^n.  *grid_out receives the

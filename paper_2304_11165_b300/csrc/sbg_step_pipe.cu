@@ -14,12 +14,16 @@
 //    barrier, the others sleep in __syncthreads;
 //  - each thread updates four x-consecutive voxels;
 //  - the one-voxel face halos come from the neighbouring blocks (mostly L2
-//    hits): each thread loads the halo values of its own row and parks them
-//    in its own slots of a halo buffer, so that every neighbour of its row is
-//    at a per-thread constant offset from either the stage's tile or the halo
+//    hits): each thread fetches the halo values of its own row into its own
+//    slots of a halo buffer, so that every neighbour of its row is at a
+//    per-thread constant offset from either the stage's tile or the halo
 //    buffer (16-byte shared loads, no position-dependent selects of values);
-//    one halo buffer serves all stages because a thread reads back only the
-//    slots it wrote itself;
+//    a thread reads back only the slots it wrote itself, so the halo needs no
+//    CTA barrier.  Halo variants (HV): 0 loads a group's halo into registers
+//    when the group comes up and parks it after the stage wait; 1 prefetches
+//    it one group ahead in registers; 2 copies it one group ahead with
+//    per-thread cp.async into the other half of a double halo buffer and
+//    waits for its own copies (cp.async.wait_group) before the stage barrier;
 //  - results leave as one 16-byte store per thread and array.
 // Every wait on an mbarrier is bounded: on time-out the CTA sets the grid's
 // error word (reported as SBG_ERR_TIMEOUT), waits (bounded) for its copies in
@@ -71,8 +75,25 @@ struct PipeLayout {
     __host__ __device__ static constexpr int face(int j, int f) { return (j * 6 + f) * B * B; }
 };
 
-template <int MODE, int B, int NS, bool REACT, int S, int MINB, bool PF>
+template <int MODE, int B, int NS, bool REACT, int HV>
+struct PipeSmem {
+    static constexpr int NA = PipeShape<MODE, NS>::NA;
+    static constexpr int NH = PipeShape<MODE, NS>::NH;
+    static constexpr int G = kGroupVox / (B * B * B);
+    static constexpr int kHaloBufs = HV == 2 ? 2 : 1;
+    // floats after the stage ring: halo buffer(s), then (HV 2) the row weights [2][512]
+    static constexpr int kHaloFloats = kHaloBufs * NH * PipeLayout<B>::kHalo;
+    static constexpr int kWFloats = (HV == 2 && REACT) ? 2 * kGroupVox : 0;
+    __host__ __device__ static constexpr size_t floats(int S) {
+        return (size_t)S * NA * kGroupVox + kHaloFloats + kWFloats;
+    }
+    __host__ __device__ static constexpr size_t bytes(int S) { return floats(S) * sizeof(float) + S * sizeof(uint64_t); }
+};
+
+template <int MODE, int B, int NS, bool REACT, int S, int MINB, int HV>
 __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs a, const PipeIO io, int *err) {
+    constexpr bool PF = HV == 1;
+    using SM = PipeSmem<MODE, B, NS, REACT, HV>;
     using L = PipeLayout<B>;
     constexpr int B3 = L::B3;
     constexpr int G = L::G;
@@ -81,23 +102,27 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     constexpr int NO = PipeShape<MODE, NS>::NO;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *stages = reinterpret_cast<float *>(smem_raw);                // [S][NA][512]
-    float *halo = stages + (size_t)S * NA * kGroupVox;                  // [NH][kHalo]
-    uint64_t *full = reinterpret_cast<uint64_t *>(halo + (size_t)NH * L::kHalo);
+    float *halo = stages + (size_t)S * NA * kGroupVox;                  // [bufs][NH][kHalo]
+    float *wbuf = halo + SM::kHaloFloats;                               // HV 2, REACT: [2][512]
+    uint64_t *full = reinterpret_cast<uint64_t *>(stages + SM::floats(S));
 
     const int tid = threadIdx.x;
     // work items: consecutive groups of the block list, or an explicit list
     // of (first block, block count) spans (the batch solver's active set)
-    const int64_t ngroups = a.items ? a.nitems : (a.nb + G - 1) / G;
-    const int64_t g0 = ngroups * blockIdx.x / gridDim.x;
-    const int64_t g1 = ngroups * (blockIdx.x + 1) / gridDim.x;
+    // (the launcher guarantees nb * B^3 < 2^31, so block ids, group indices
+    // and voxel slots fit 32-bit ints)
+    const int nb = (int)a.nb;
+    const int ngroups = a.items ? (int)a.nitems : (nb + G - 1) / G;
+    const int g0 = (int)((int64_t)ngroups * blockIdx.x / gridDim.x);
+    const int g1 = (int)((int64_t)ngroups * (blockIdx.x + 1) / gridDim.x);
     if (g0 >= g1) return;  // uniform over the CTA
-    auto span = [&](int64_t gi, int64_t &b0, int64_t &nblk) {
+    auto span = [&](int gi, int &b0, int &nblk) {
         if (a.items) {
-            b0 = __ldg(a.items + 2 * gi);
-            nblk = __ldg(a.items + 2 * gi + 1);
+            b0 = (int)__ldg(a.items + 2 * gi);
+            nblk = (int)__ldg(a.items + 2 * gi + 1);
         } else {
             b0 = gi * G;
-            nblk = (a.nb - b0 < G) ? (a.nb - b0) : G;
+            nblk = (nb - b0 < G) ? (nb - b0) : G;
         }
     };
 
@@ -107,8 +132,8 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     }
     __syncthreads();
 
-    auto issue = [&](int64_t gi, int s) {
-        int64_t b0, nblk;
+    auto issue = [&](int gi, int s) {
+        int b0, nblk;
         span(gi, b0, nblk);
         const uint32_t bytes = (uint32_t)(nblk * B3 * sizeof(float));
         mbar_arrive_expect_tx(&full[s], bytes * NA);
@@ -123,7 +148,8 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     const int v0 = 4 * tid;
     const int j = v0 / B3;
     const int l0 = v0 - j * B3;
-    const int x0 = l0 % B, y = (l0 / B) % B, z = l0 / (B * B);
+    const int x0 = (B == 4) ? 0 : l0 % B;  // a B = 4 row is the whole x extent of its block
+    const int y = (l0 / B) % B, z = l0 / (B * B);
     const bool hxm = (x0 == 0), hxp = (x0 + 3 == B - 1);  // which neighbours are halo values
     const bool hym = (y == 0), hyp = (y == B - 1), hzm = (z == 0), hzp = (z == B - 1);
     // where, in the neighbouring block, this thread's halo values are
@@ -142,65 +168,123 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     const int shy = hym ? sym : syp;
     const int shz = hzm ? szm : szp;
     const bool dy = hym || hyp, dz = hzm || hzp;
+    // one haloed array: the four halo base pointers of this thread, once
+    const float *hp[4] = {io.src[0] + oxm, io.src[0] + oxp, io.src[0] + oy, io.src[0] + oz};
 
     struct Ids {
         int xm, xp, y, z, ws;
+        uint32_t hb;  // held bits of this thread's four voxels (Dirichlet faces)
     };
     struct Halo {
         float vxm[NH], vxp[NH];
         float4 vy[NH], vz[NH];
         float4 w;
-        int4 bc;
+        int ixm, ixp;  // x neighbour inside the group: its offset in the stage tile, else -1
+        uint32_t hb;   // held bits of the row
     };
-    auto load_ids = [&](int64_t gi) {
-        Ids r{-1, -1, -1, -1, -1};
+    auto load_ids = [&](int gi) {
+        Ids r{-1, -1, -1, -1, -1, 0u};
         if (gi >= g1) return r;
-        int64_t b0, nblk;
+        int b0, nblk;
         span(gi, b0, nblk);
-        const int64_t b = b0 + j;
+        const int b = b0 + j;
         if (j < nblk) {
-            const int32_t *f = a.face + b * 6;
+            const int32_t *f = a.face + 6 * b;
             if (hxm) r.xm = __ldg(f + 0);
             if (hxp) r.xp = __ldg(f + 1);
             if (dy) r.y = __ldg(f + fyy);
             if (dz) r.z = __ldg(f + fzz);
             if (REACT) r.ws = __ldg(a.wslab + b);
+            if (a.held_mask) {
+                constexpr int W = (B3 + 63) / 64;
+                const uint64_t word = __ldg(reinterpret_cast<const unsigned long long *>(a.heldbits) + b * W + (l0 >> 6));
+                r.hb = (uint32_t)(word >> (l0 & 63)) & 0xFu;
+            }
         }
         return r;
     };
     // halo values of this thread's row, its surface weights and block coordinates
-    auto load_halo = [&](int64_t gi, const Ids &id, Halo &h) {
+    auto load_halo = [&](int gi, const Ids &id, Halo &h) {
+        // an x neighbour in the same group (the list is in tiled, x-fastest
+        // order, so most are) is read from the stage tile instead
+        int b0 = 0, nblk = 0;
+        if (gi < g1) span(gi, b0, nblk);
+        h.ixm = (hxm && (unsigned)(id.xm - b0) < (unsigned)nblk) ? (id.xm - b0) * B3 + oxm : -1;
+        h.ixp = (hxp && (unsigned)(id.xp - b0) < (unsigned)nblk) ? (id.xp - b0) * B3 + oxp : -1;
         const float SENT = sentinel_f32();
 #pragma unroll
         for (int k = 0; k < NH; ++k) {
             const float absent = (MODE == kX2 && k == 1) ? 0.f : SENT;
-            const float *sk = io.src[k];
-            h.vxm[k] = (id.xm >= 0) ? __ldg(sk + (int64_t)id.xm * B3 + oxm) : absent;
-            h.vxp[k] = (id.xp >= 0) ? __ldg(sk + (int64_t)id.xp * B3 + oxp) : absent;
-            h.vy[k] = (id.y >= 0) ? __ldg(reinterpret_cast<const float4 *>(sk + (int64_t)id.y * B3 + oy))
+            // this thread's halo addresses are fixed offsets from neighbour block
+            // starts: one wide multiply-add per load
+            const float *pxm = (NH == 1 ? hp[0] : io.src[k] + oxm), *pxp = (NH == 1 ? hp[1] : io.src[k] + oxp);
+            const float *py = (NH == 1 ? hp[2] : io.src[k] + oy), *pz = (NH == 1 ? hp[3] : io.src[k] + oz);
+            h.vxm[k] = (id.xm >= 0 && h.ixm < 0) ? __ldg(pxm + id.xm * B3) : absent;
+            h.vxp[k] = (id.xp >= 0 && h.ixp < 0) ? __ldg(pxp + id.xp * B3) : absent;
+            h.vy[k] = (id.y >= 0) ? __ldg(reinterpret_cast<const float4 *>(py + id.y * B3))
                                   : make_float4(absent, absent, absent, absent);
-            h.vz[k] = (id.z >= 0) ? __ldg(reinterpret_cast<const float4 *>(sk + (int64_t)id.z * B3 + oz))
+            h.vz[k] = (id.z >= 0) ? __ldg(reinterpret_cast<const float4 *>(pz + id.z * B3))
                                   : make_float4(absent, absent, absent, absent);
         }
         h.w = make_float4(0.f, 0.f, 0.f, 0.f);
         if (REACT && id.ws >= 0) h.w = __ldg(reinterpret_cast<const float4 *>(a.w + (int64_t)id.ws * B3 + l0));
-        h.bc = make_int4(0, 0, 0, 0);
-        if (a.held_mask && gi < g1) {
-            int64_t b0, nblk;
-            span(gi, b0, nblk);
-            if (j < nblk) h.bc = __ldg(a.blocks + b0 + j);
-        }
+        h.hb = id.hb;
     };
     // park this thread's halo values in its own slots of the halo buffer
     auto park = [&](const Halo &h) {
 #pragma unroll
         for (int k = 0; k < NH; ++k) {
             float *hb = halo + k * L::kHalo;
-            if (hxm) hb[sxm] = h.vxm[k];
-            if (hxp) hb[sxp] = h.vxp[k];
+            if (hxm && h.ixm < 0) hb[sxm] = h.vxm[k];
+            if (hxp && h.ixp < 0) hb[sxp] = h.vxp[k];
             if (dy) *reinterpret_cast<float4 *>(hb + shy) = h.vy[k];
             if (dz) *reinterpret_cast<float4 *>(hb + shz) = h.vz[k];
         }
+    };
+
+    // HV 2: cp.async copies of group gi's halo values (ids `id`), row weights
+    // and block coordinates into buffer `buf`, as one commit group per call
+    // (an empty group past the end, so every group has one)
+    uint32_t hbq0 = 0u, hbq1 = 0u;  // HV 2: held bits of the groups in the two halo buffers
+    auto issue_async = [&](int gi, const Ids &id, int buf) {
+        if (HV != 2) return;
+        if (buf) hbq1 = id.hb;
+        else hbq0 = id.hb;
+        if (gi < g1) {
+            int b0, nblk;
+            span(gi, b0, nblk);
+            if (j < nblk) {
+                const float SENT = sentinel_f32();
+#pragma unroll
+                for (int k = 0; k < NH; ++k) {
+                    const float absent = (MODE == kX2 && k == 1) ? 0.f : SENT;
+                    const float *sk = io.src[k];
+                    float *hb = halo + ((size_t)buf * NH + k) * L::kHalo;
+                    if (hxm) {
+                        if (id.xm >= 0) cp_async4(hb + sxm, sk + (int64_t)id.xm * B3 + oxm);
+                        else hb[sxm] = absent;
+                    }
+                    if (hxp) {
+                        if (id.xp >= 0) cp_async4(hb + sxp, sk + (int64_t)id.xp * B3 + oxp);
+                        else hb[sxp] = absent;
+                    }
+                    if (dy) {
+                        if (id.y >= 0) cp_async16(hb + shy, sk + (int64_t)id.y * B3 + oy);
+                        else *reinterpret_cast<float4 *>(hb + shy) = make_float4(absent, absent, absent, absent);
+                    }
+                    if (dz) {
+                        if (id.z >= 0) cp_async16(hb + shz, sk + (int64_t)id.z * B3 + oz);
+                        else *reinterpret_cast<float4 *>(hb + shz) = make_float4(absent, absent, absent, absent);
+                    }
+                }
+                if (REACT) {
+                    float *wb = wbuf + buf * kGroupVox + v0;
+                    if (id.ws >= 0) cp_async16(wb, a.w + (int64_t)id.ws * B3 + l0);
+                    else *reinterpret_cast<float4 *>(wb) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        }
+        cp_async_commit();
     };
 
     // adjoint: this thread's gradient sums, double-float (hi, lo) per quantity
@@ -213,14 +297,20 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     // the SM to hide their latency.  The loop below is unrolled by two with
     // the register sets swapped, so no prefetched value is copied (a copy
     // would wait for the load every group).
-    auto body = [&](int64_t gi, int it, Halo &cur, Halo &nxt, const Ids &id1, Ids &id2) -> bool {
+    auto body = [&](int gi, int it, Halo &cur, Halo &nxt, const Ids &id1, Ids &id2) -> bool {
         const int s = it % S;
         const uint32_t par = (uint32_t)((it / S) & 1);
-        int64_t b0, nblk;
+        int b0, nblk;
         span(gi, b0, nblk);
-        const int64_t b = b0 + j;
+        const int b = b0 + j;
         const bool valid = j < nblk;
-        if (PF) {
+        if (HV == 2) {
+            // the next group's halo into the other buffer (ids read a group
+            // earlier), ids two groups ahead, then this group's own copies
+            issue_async(gi + 1, id1, (it + 1) & 1);
+            id2 = load_ids(gi + 2);
+            cp_async_wait_group<1>();
+        } else if (PF) {
             if (valid) park(cur);
             id2 = load_ids(gi + 2);
             load_halo(gi + 1, id1, nxt);
@@ -232,6 +322,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
         bool ok = true;
         if (tid == 0) ok = mbar_wait_bounded(&full[s], par);
         if (__syncthreads_or(!ok)) {
+            if (HV == 2) cp_async_wait_all();
             if (tid == 0) {
                 atomicExch(err, (int)SBG_ERR_TIMEOUT);
                 for (int q = it; q < it + S && g0 + q < g1; ++q)
@@ -243,25 +334,16 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
         // every thread has finished the previous group: refill its stage
         if (tid == 0 && it >= 1 && gi - 1 + S < g1) issue(gi - 1 + S, (it - 1) % S);
         if (!valid) return true;
-        if (!PF) park(cur);
+        if (HV == 0) park(cur);
 
-        // Dirichlet-held voxels of this row: a row test (y, z faces) and at
-        // most two x positions
-        bool held[4] = {false, false, false, false};
-        if (a.held_mask) {
-            const int m = a.held_mask;
-            const int4 bc = cur.bc;
-            const int nx = __ldg(a.gdims + bc.w * 4 + 0), ny = __ldg(a.gdims + bc.w * 4 + 1),
-                      nz = __ldg(a.gdims + bc.w * 4 + 2);
-            const int gx0 = bc.x * B + x0, gy = bc.y * B + y, gz = bc.z * B + z;
-            const bool row = ((m & 4) && gy == 0) || ((m & 8) && gy == ny - 1) || ((m & 16) && gz == 0) ||
-                             ((m & 32) && gz == nz - 1);
-            const int i0 = (m & 1) ? -gx0 : -1;           // i with gx0 + i == 0
-            const int i1 = (m & 2) ? nx - 1 - gx0 : -1;   // i with gx0 + i == nx - 1
+        // Dirichlet-held voxels of this row (bits prepared per block for the
+        // current Dirichlet faces)
+        const uint32_t hbits = HV == 2 ? ((it & 1) ? hbq1 : hbq0) : cur.hb;
+        bool held[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) held[i] = row || i == i0 || i == i1;
-        }
-        const float4 w4 = cur.w;
+        for (int i = 0; i < 4; ++i) held[i] = (hbits >> i) & 1u;
+        const float4 w4 = (HV == 2 && REACT) ? *reinterpret_cast<const float4 *>(wbuf + (it & 1) * kGroupVox + v0)
+                                             : cur.w;
 
         float4 uc[NA], ym[NH], yp[NH], zm[NH], zp[NH];
         float xm[NH], xp[NH];
@@ -271,9 +353,10 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
 #pragma unroll
         for (int k = 0; k < NH; ++k) {
             const float *t = stages + ((size_t)s * NA + k) * kGroupVox;
-            const float *h = halo + k * L::kHalo;
-            xm[k] = (hxm ? h : t)[sxm];
-            xp[k] = (hxp ? h : t)[sxp];
+            const float *h = halo + ((size_t)(HV == 2 ? (it & 1) : 0) * NH + k) * L::kHalo;
+            const int ixm = HV == 2 ? -1 : cur.ixm, ixp = HV == 2 ? -1 : cur.ixp;
+            xm[k] = ixm >= 0 ? t[ixm] : (hxm ? h : t)[sxm];
+            xp[k] = ixp >= 0 ? t[ixp] : (hxp ? h : t)[sxp];
             ym[k] = *reinterpret_cast<const float4 *>((hym ? h : t) + sym);
             yp[k] = *reinterpret_cast<const float4 *>((hyp ? h : t) + syp);
             zm[k] = *reinterpret_cast<const float4 *>((hzm ? h : t) + szm);
@@ -282,6 +365,32 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
         const StepCoef<float> &kc = a.cf;
         float res[NO][4];
         float q[3] = {0.f, 0.f, 0.f};  // adjoint: this group's gradient terms
+        // With one haloed array every voxel of the row is computed (an inactive
+        // one from sentinels) and the result selected, so the row takes no
+        // divergent branches; with more arrays the four interleaved updates
+        // would not fit the register budget, and inactive or held voxels
+        // branch around the update instead.
+        constexpr bool kBranchFree = NH == 1;
+        // x differences along the row, shared by neighbouring voxels (all modes
+        // but the compensated one): with R = (xm, the row's four values, xp),
+        // Dx[k][j] = R[j+1] - R[j]; voxel i takes (x_{i+1} - u_i) = Dx[k][i+1]
+        // and (u_i - x_{i-1}) = Dx[k][i], each replaced by 0 when that
+        // neighbour is outside Omega: the values the per-voxel form computes
+        // from mirrored neighbours, so results stay bitwise the same.
+        bool actx[6];
+        float Dx[NH][5];
+        if (MODE != kX2) {
+            actx[0] = !is_sent(xm[0]);
+            actx[5] = !is_sent(xp[0]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) actx[i + 1] = !is_sent(f4get(uc[0], i));
+#pragma unroll
+            for (int k = 0; k < NH; ++k) {
+                const float R[6] = {xm[k], uc[k].x, uc[k].y, uc[k].z, uc[k].w, xp[k]};
+#pragma unroll
+                for (int jj = 0; jj < 5; ++jj) Dx[k][jj] = __fsub_rn(R[jj + 1], R[jj]);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             // neighbours of voxel i in array 0 decide the no-flux mirror for every array
@@ -289,40 +398,50 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
                                  f4get(ym[0], i), f4get(yp[0], i), f4get(zm[0], i), f4get(zp[0], i)};
             bool out[6];
 #pragma unroll
-            for (int f = 0; f < 6; ++f) out[f] = is_sent(n0[f]);
+            for (int f = (MODE == kX2 ? 0 : 2); f < 6; ++f) out[f] = is_sent(n0[f]);
             const float c0 = f4get(uc[0], i);
             const bool act = !is_sent(c0);
             const bool upd = act && !held[i];
+            if (!kBranchFree && !upd) {
 #pragma unroll
-            for (int k = 0; k < NO; ++k)
-                res[k][i] = (MODE == kAdj && act && held[i]) ? 0.f : f4get(uc[k], i);
-            if (!upd) continue;
-            float nv[NH][6];
+                for (int k = 0; k < NO; ++k) res[k][i] = (MODE == kAdj && act) ? 0.f : f4get(uc[k], i);
+                continue;
+            }
+            float nv[NH][6];  // mirrored neighbours (x entries only for the compensated mode)
+            float dxs[NH];    // x second differences (other modes)
 #pragma unroll
             for (int k = 0; k < NH; ++k) {
                 const float c = f4get(uc[k], i);
                 const float raw[6] = {i == 0 ? xm[k] : f4get(uc[k], i - 1), i == 3 ? xp[k] : f4get(uc[k], i + 1),
                                       f4get(ym[k], i), f4get(yp[k], i), f4get(zm[k], i), f4get(zp[k], i)};
 #pragma unroll
-                for (int f = 0; f < 6; ++f) nv[k][f] = out[f] ? c : raw[f];
+                for (int f = (MODE == kX2 ? 0 : 2); f < 6; ++f) nv[k][f] = out[f] ? c : raw[f];
+                if (MODE != kX2) {
+                    const float dp = actx[i + 2] ? Dx[k][i + 1] : 0.f;
+                    const float dm = actx[i] ? Dx[k][i] : 0.f;
+                    nv[k][0] = dm;  // kept for the adjoint's g(u): (x_{i-1} - u) = -dm
+                    nv[k][1] = dp;
+                    dxs[k] = __fsub_rn(dp, dm);
+                }
             }
+            float nr[NO];
             if (MODE == kX2) {
                 float rate = kc.decay[0];
                 if (REACT) rate = __fmaf_rn(kc.k, f4get(w4, i), rate);
-                fused_update_x2(c0, f4get(uc[1], i), nv[0], nv[1], kc.c[0], kc.dt, rate, res[0][i], res[1][i]);
+                fused_update_x2(c0, f4get(uc[1], i), nv[0], nv[1], kc.c[0], kc.dt, rate, nr[0], nr[NO - 1]);
             } else if (MODE == kSrc) {
                 // correction d of an SBG_F32R state: the source r = L_h b replaces
                 // the base's part of the update
                 float rate = kc.decay[0];
                 if (REACT) rate = __fmaf_rn(kc.k, f4get(w4, i), rate);
-                res[0][i] = fused_update(c0, nv[0][0], nv[0][1], nv[0][2], nv[0][3], nv[0][4], nv[0][5], kc.c[0],
-                                         kc.dt, rate, f4get(uc[1], i));
+                nr[0] = fused_update_dx(c0, dxs[0], nv[0][2], nv[0][3], nv[0][4], nv[0][5], kc.c[0], kc.dt, rate,
+                                        f4get(uc[1], i));
             } else if (MODE == kFwd) {
                 const float t = REACT ? __fmul_rn(__fmul_rn(kc.k, f4get(w4, i)), c0) : 0.f;
 #pragma unroll
                 for (int k = 0; k < NS; ++k)
-                    res[k][i] = fused_update(f4get(uc[k], i), nv[k][0], nv[k][1], nv[k][2], nv[k][3], nv[k][4],
-                                             nv[k][5], kc.c[k], kc.dt, kc.decay[k], k == 0 ? -t : t);
+                    nr[k] = fused_update_dx(f4get(uc[k], i), dxs[k], nv[k][2], nv[k][3], nv[k][4], nv[k][5],
+                                            kc.c[k], kc.dt, kc.decay[k], k == 0 ? -t : t);
             } else {
                 // lambda^n = M^T lambda^{n+1}: the forward stencil on lambda (held
                 // voxels hold lambda = 0), with the A -> B transfer transposed
@@ -332,23 +451,28 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
                 for (int sp = 0; sp < NS; ++sp) {
                     const float rate = (sp == 0 && REACT) ? __fadd_rn(kc.decay[0], kw) : kc.decay[sp];
                     const float t = (sp == 0 && NS == 2 && REACT) ? __fmul_rn(kw, lamB) : 0.f;
-                    res[sp][i] = fused_update(f4get(uc[sp], i), nv[sp][0], nv[sp][1], nv[sp][2], nv[sp][3],
-                                              nv[sp][4], nv[sp][5], kc.c[sp], kc.dt, rate, t);
+                    nr[sp] = fused_update_dx(f4get(uc[sp], i), dxs[sp], nv[sp][2], nv[sp][3], nv[sp][4],
+                                             nv[sp][5], kc.c[sp], kc.dt, rate, t);
                     // dL/dD_s += lambda_s dt g_s(u^n), g = sum_a [(u~+ - u) + (u~- - u)] / dx_a^2
                     const float u = f4get(uc[NS + sp], i);
                     const float *nu = nv[NS + sp];
-                    float g = __fmul_rn(io.inv2[0], __fadd_rn(__fsub_rn(nu[0], u), __fsub_rn(nu[1], u)));
+                    // x part: (x_{i-1} - u) + (x_{i+1} - u) = -dm + dp (nu[0] = dm, nu[1] = dp)
+                    float g = __fmul_rn(io.inv2[0], __fadd_rn(-nu[0], nu[1]));
                     g = __fmaf_rn(io.inv2[1], __fadd_rn(__fsub_rn(nu[2], u), __fsub_rn(nu[3], u)), g);
                     g = __fmaf_rn(io.inv2[2], __fadd_rn(__fsub_rn(nu[4], u), __fsub_rn(nu[5], u)), g);
-                    q[sp] = __fmaf_rn(__fmul_rn(f4get(uc[sp], i), kc.dt), g, q[sp]);
+                    const float term = __fmul_rn(__fmul_rn(f4get(uc[sp], i), kc.dt), g);
+                    q[sp] = __fadd_rn(q[sp], upd ? term : 0.f);
                 }
                 if (REACT) {
                     // dL/dk += dt w u_A (lambda_B - lambda_A)
                     const float uA = f4get(uc[NS], i);
-                    const float dl = __fsub_rn(lamB, c0);
-                    q[2] = __fmaf_rn(__fmul_rn(__fmul_rn(kc.dt, f4get(w4, i)), uA), dl, q[2]);
+                    const float term = __fmul_rn(__fmul_rn(__fmul_rn(kc.dt, f4get(w4, i)), uA), __fsub_rn(lamB, c0));
+                    q[2] = __fadd_rn(q[2], upd ? term : 0.f);
                 }
             }
+#pragma unroll
+            for (int k = 0; k < NO; ++k)
+                res[k][i] = upd ? nr[k] : ((MODE == kAdj && act) ? 0.f : f4get(uc[k], i));
         }
         if (MODE == kAdj) {
 #pragma unroll
@@ -366,10 +490,13 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     if (PF) {
         load_halo(g0, idA, hA);
         idA = load_ids(g0 + 1);
+    } else if (HV == 2) {
+        issue_async(g0, idA, 0);
+        idA = load_ids(g0 + 1);
     }
     int it = 0;
     bool ok = true;
-    for (int64_t gi = g0; gi < g1; gi += 2, it += 2) {
+    for (int gi = g0; gi < g1; gi += 2, it += 2) {
         if (!body(gi, it, hA, hB, idA, idB)) {
             ok = false;
             break;
@@ -380,6 +507,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
             break;
         }
     }
+    if (HV == 2) cp_async_wait_all();  // no copy may land after the CTA's shared memory is gone
     if (MODE == kAdj && ok) {
         // CTA sums: double-float across the warp, FP64 across the warps; each
         // CTA adds to its own slot, so the order of additions is fixed
@@ -408,25 +536,23 @@ struct PipeStages {
     static constexpr int S = NA == 1 ? 6 : NA == 2 ? 4 : 3;
 };
 
-template <int MODE, int B, int NS, bool REACT, bool PF>
-static cudaError_t launch_pipe_pf(const StepArgs &a, const PipeIO &io, int ctas_per_sm, int max_ctas, int *err,
+template <int MODE, int B, int NS, bool REACT, int HV>
+static cudaError_t launch_pipe_hv(const StepArgs &a, const PipeIO &io, int ctas_per_sm, int max_ctas, int *err,
                                   cudaStream_t s, int *grid_out) {
     constexpr int NA = PipeShape<MODE, NS>::NA;
     constexpr int S = PipeStages<MODE, NA>::S;
-    constexpr int NH = PipeShape<MODE, NS>::NH;
-    constexpr size_t smem = ((size_t)S * NA * kGroupVox + (size_t)NH * PipeLayout<B>::kHalo) * sizeof(float) +
-                            S * sizeof(uint64_t);
+    constexpr size_t smem = PipeSmem<MODE, B, NS, REACT, HV>::bytes(S);
     constexpr int G = kGroupVox / (B * B * B);
     // Without prefetch: 64 registers per thread (8 CTAs of 128 threads per SM)
     // with one array, 80 (6 CTAs) with two (96, 5 CTAs, for the adjoint with
-    // its gradient sums), 128 (4 CTAs) with four.  With
-    // prefetch the two register sets need up to 128 registers (4 CTAs per SM).
+    // its gradient sums), 128 (4 CTAs) with four.  With register prefetch
+    // (HV 1) the two register sets need up to 128 registers (4 CTAs per SM).
     // No more CTAs than fit in the SM's 228 KB of shared memory (1 KB of it
     // reserved per CTA) are asked for, so the registers go to those that fit.
-    constexpr int kBase = PF ? 4 : (NA == 1 ? 8 : NA == 2 ? (MODE == kAdj ? 5 : 6) : 4);
+    constexpr int kBase = HV == 1 ? 4 : (NA == 1 ? 8 : NA == 2 ? (MODE == kAdj ? 5 : 6) : 4);
     constexpr int kFit = (int)((228 * 1024) / (smem + 1024));
     constexpr int MINB = kBase < kFit ? kBase : (kFit > 0 ? kFit : 1);
-    auto kern = k_step_pipe<MODE, B, NS, REACT, S, MINB, PF>;
+    auto kern = k_step_pipe<MODE, B, NS, REACT, S, MINB, HV>;
     static int occ = -1, nsm = 0;
     if (occ < 0) {
         int dev = 0;
@@ -448,24 +574,27 @@ static cudaError_t launch_pipe_pf(const StepArgs &a, const PipeIO &io, int ctas_
 }
 
 template <int MODE, int B, int NS, bool REACT>
-static cudaError_t launch_pipe_t(const StepArgs &a, const PipeIO &io, bool prefetch, int ctas_per_sm, int *err,
+static cudaError_t launch_pipe_t(const StepArgs &a, const PipeIO &io, int hv, int ctas_per_sm, int *err,
                                  cudaStream_t s) {
-    return prefetch ? launch_pipe_pf<MODE, B, NS, REACT, true>(a, io, ctas_per_sm, 0, err, s, nullptr)
-                    : launch_pipe_pf<MODE, B, NS, REACT, false>(a, io, ctas_per_sm, 0, err, s, nullptr);
+    if (hv == 1) return launch_pipe_hv<MODE, B, NS, REACT, 1>(a, io, ctas_per_sm, 0, err, s, nullptr);
+    if (hv == 2) return launch_pipe_hv<MODE, B, NS, REACT, 2>(a, io, ctas_per_sm, 0, err, s, nullptr);
+    return launch_pipe_hv<MODE, B, NS, REACT, 0>(a, io, ctas_per_sm, 0, err, s, nullptr);
 }
 
 template <int MODE, int NS>
-static cudaError_t launch_pipe_b(const StepArgs &a, const PipeIO &io, int B, bool react, bool prefetch,
+static cudaError_t launch_pipe_b(const StepArgs &a, const PipeIO &io, int B, bool react, int hv,
                                  int ctas_per_sm, int *err, cudaStream_t s) {
     if (B == 8)
-        return react ? launch_pipe_t<MODE, 8, NS, true>(a, io, prefetch, ctas_per_sm, err, s)
-                     : launch_pipe_t<MODE, 8, NS, false>(a, io, prefetch, ctas_per_sm, err, s);
-    return react ? launch_pipe_t<MODE, 4, NS, true>(a, io, prefetch, ctas_per_sm, err, s)
-                 : launch_pipe_t<MODE, 4, NS, false>(a, io, prefetch, ctas_per_sm, err, s);
+        return react ? launch_pipe_t<MODE, 8, NS, true>(a, io, hv, ctas_per_sm, err, s)
+                     : launch_pipe_t<MODE, 8, NS, false>(a, io, hv, ctas_per_sm, err, s);
+    return react ? launch_pipe_t<MODE, 4, NS, true>(a, io, hv, ctas_per_sm, err, s)
+                 : launch_pipe_t<MODE, 4, NS, false>(a, io, hv, ctas_per_sm, err, s);
 }
 
-bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, bool prefetch,
+bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, int halo_variant,
                       int ctas_per_sm, int *err_flag, cudaStream_t s, cudaError_t *launch_err) {
+    const int hv = halo_variant;
+    if (a.nb * (int64_t)(B * B * B) >= (int64_t(1) << 31)) return false;  // 32-bit slot indices in the kernel
     PipeIO io;
     std::memset(&io, 0, sizeof(io));
     cudaError_t e = cudaSuccess;
@@ -474,19 +603,19 @@ bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool re
         io.src[1] = a.in_lo[0];
         io.dst[0] = (float *)a.out[0];
         io.dst[1] = a.out_lo[0];
-        e = launch_pipe_b<kX2, 1>(a, io, B, react, prefetch, ctas_per_sm, err_flag, s);
+        e = launch_pipe_b<kX2, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
     } else if (dtype == SBG_F32R && ns == 1) {
         io.src[0] = (const float *)a.in[0];
         io.src[1] = a.src_term;
         io.dst[0] = (float *)a.out[0];
-        e = launch_pipe_b<kSrc, 1>(a, io, B, react, prefetch, ctas_per_sm, err_flag, s);
+        e = launch_pipe_b<kSrc, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
     } else if (dtype == SBG_F32 && (ns == 1 || ns == 2)) {
         for (int k = 0; k < ns; ++k) {
             io.src[k] = (const float *)a.in[k];
             io.dst[k] = (float *)a.out[k];
         }
-        e = ns == 1 ? launch_pipe_b<kFwd, 1>(a, io, B, react, prefetch, ctas_per_sm, err_flag, s)
-                    : launch_pipe_b<kFwd, 2>(a, io, B, react, prefetch, ctas_per_sm, err_flag, s);
+        e = ns == 1 ? launch_pipe_b<kFwd, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s)
+                    : launch_pipe_b<kFwd, 2>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
     } else {
         return false;
     }
@@ -496,18 +625,19 @@ bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool re
 
 cudaError_t launch_adjoint_pipe(const StepArgs &a, const PipeIO &io, int ns, int B, bool react, int max_ctas,
                                 int *err_flag, cudaStream_t s, int *grid_out) {
+    if (a.nb * (int64_t)(B * B * B) >= (int64_t(1) << 31)) return cudaErrorInvalidValue;  // 32-bit slot indices
     if (ns == 1) {
         if (B == 8)
-            return react ? launch_pipe_pf<kAdj, 8, 1, true, false>(a, io, 0, max_ctas, err_flag, s, grid_out)
-                         : launch_pipe_pf<kAdj, 8, 1, false, false>(a, io, 0, max_ctas, err_flag, s, grid_out);
-        return react ? launch_pipe_pf<kAdj, 4, 1, true, false>(a, io, 0, max_ctas, err_flag, s, grid_out)
-                     : launch_pipe_pf<kAdj, 4, 1, false, false>(a, io, 0, max_ctas, err_flag, s, grid_out);
+            return react ? launch_pipe_hv<kAdj, 8, 1, true, 0>(a, io, 0, max_ctas, err_flag, s, grid_out)
+                         : launch_pipe_hv<kAdj, 8, 1, false, 0>(a, io, 0, max_ctas, err_flag, s, grid_out);
+        return react ? launch_pipe_hv<kAdj, 4, 1, true, 0>(a, io, 0, max_ctas, err_flag, s, grid_out)
+                     : launch_pipe_hv<kAdj, 4, 1, false, 0>(a, io, 0, max_ctas, err_flag, s, grid_out);
     }
     if (B == 8)
-        return react ? launch_pipe_pf<kAdj, 8, 2, true, false>(a, io, 0, max_ctas, err_flag, s, grid_out)
-                     : launch_pipe_pf<kAdj, 8, 2, false, false>(a, io, 0, max_ctas, err_flag, s, grid_out);
-    return react ? launch_pipe_pf<kAdj, 4, 2, true, false>(a, io, 0, max_ctas, err_flag, s, grid_out)
-                 : launch_pipe_pf<kAdj, 4, 2, false, false>(a, io, 0, max_ctas, err_flag, s, grid_out);
+        return react ? launch_pipe_hv<kAdj, 8, 2, true, 0>(a, io, 0, max_ctas, err_flag, s, grid_out)
+                     : launch_pipe_hv<kAdj, 8, 2, false, 0>(a, io, 0, max_ctas, err_flag, s, grid_out);
+    return react ? launch_pipe_hv<kAdj, 4, 2, true, 0>(a, io, 0, max_ctas, err_flag, s, grid_out)
+                 : launch_pipe_hv<kAdj, 4, 2, false, 0>(a, io, 0, max_ctas, err_flag, s, grid_out);
 }
 
 }  // namespace sbg

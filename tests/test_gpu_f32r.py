@@ -49,7 +49,8 @@ def test_f32r_is_bitwise_independent_of_block_size_and_kernel():
     phi, phys, u0 = blob_case((37, 29, 23), 0.3, 51)
     p = make_params(phys)
     outs = []
-    for block, variant in ((4, "plain"), (4, "pipelined"), (4, "prefetch"), (8, "pipelined"), (8, "plain")):
+    for block, variant in ((4, "plain"), (4, "pipelined"), (4, "prefetch"), (4, "async"), (8, "pipelined"),
+                           (8, "async"), (8, "plain")):
         g = Grid(phi, block=block)
         st = State(g, 1, "f32r").set_kernel(variant).set(u0)
         st.step(p, 200)
@@ -71,11 +72,17 @@ def test_f32r_step_counts_do_not_depend_on_call_pattern():
     np.testing.assert_array_equal(a, st.get())
 
 
-def test_f32r_reduction_matches_the_oracle_and_leaves_the_field():
-    phi, phys, u0 = blob_case((26, 21, 19), 0.4, 53)
+@pytest.mark.parametrize("k,res_tol", [(0.0, 1e-10), (0.4, 1e-7)])
+def test_f32r_reduction_matches_the_oracle_and_leaves_the_field(k, res_tol):
+    """The reduction of an SBG_F32R state against the oracle's reduction of the
+    same field (read back in FP64), and the field against the oracle's run.
+    The first 128 steps after a set carry the whole change in d, so the field
+    is FP32-accurate there; the reduction itself is double-float.  With a
+    surface reaction the residual uses the FP32 surface weights the step uses
+    (the oracle's are FP64), which bounds its agreement at ~1e-7."""
+    phi, phys, u0 = blob_case((26, 21, 19), k, 53)
     P = oracle.Problem(phi, phys)
     ref_u = P.run(u0[None], 90)
-    ref = P.reduce(ref_u)[0]
     g = Grid(phi, block=4)
     st = State(g, 1, "f32r").set(u0)
     p = make_params(phys)
@@ -85,9 +92,12 @@ def test_f32r_reduction_matches_the_oracle_and_leaves_the_field():
     after = st.get()
     # the fold changes the representation, not the field (double-float rounding)
     assert np.max(np.abs(after - before)) <= 1e-12
-    u = np.abs(ref_u[0]) * (P.active > 0)
-    assert abs(red["mass"] - ref["mass"]) <= 1e-9 * u.sum() * np.prod(phys.dx)
-    assert abs(red["residual"] - ref["residual"]) <= 1e-6 * ref["residual"]
+    assert rel_err(before, ref_u[0]) < 2e-7
+    ref = P.reduce(before[None])[0]
+    assert abs(red["mass"] - ref["mass"]) <= 1e-12 * abs(ref["mass"])
+    assert abs(red["residual"] - ref["residual"]) <= res_tol * ref["residual"]
+    for key in ("J_in", "J_out"):
+        assert abs(red[key] - ref[key]) <= 1e-10 * max(abs(ref[key]), 1.0)
     assert red["n_active"] == ref["n_active"]
 
 

@@ -1,14 +1,14 @@
 """Parity at the workloads' full sizes, in the launch configuration the bench
 times (pipelined kernel, block edge 4).
 
-* 256^3 tortuosity solve: the compensated-FP32 steady state against the FP64
-  oracle's CG steady state stored by tests/golden/make_golden.py: D_eff to
-  1e-6 relative, the field at 4096 sampled voxels to 1e-5.  On this geometry
-  the D_eff error follows the relative residual R as ~0.11 R (the slowest
-  mode's flux cancels in the mean of inlet and outlet flux, the next one does
-  not; R < 1e-8 gives 1.1e-6) while the field error is ~3000 R (that mode's
-  amplitude), so the solve runs to R < 1e-10, near the compensated state's
-  floor of ~2e-11.
+* 256^3 tortuosity solve (SBG_F32R state, as the bench runs it): the steady
+  state against the FP64 oracle's CG steady state stored by
+  tests/golden/make_golden.py: D_eff to 1e-6 relative, the field at 4096
+  sampled voxels to 1e-5.  On this geometry the D_eff error follows the
+  relative residual R as ~0.11 R (the slowest mode's flux cancels in the mean
+  of inlet and outlet flux, the next one does not; R < 1e-8 gives 1.1e-6)
+  while the field error is ~3000 R (that mode's amplitude), so the solve runs
+  to R < 1e-10.
 * 512^3 two-species reactive run: after n steps every voxel depends only on
   voxels at most n steps away, so the oracle recomputes sampled voxels exactly
   on a (2n+1)^3 crop around each; plus the exact per-step balance of the total
@@ -43,7 +43,7 @@ def test_grf256_steady_state_matches_the_oracle_cg():
     gold = json.load(open(GOLDEN))
     phi, u0, phys = grf256()
     g = Grid(phi, block=4)
-    st = State(g, 1, "f32x2").set_kernel("pipelined").set(u0)
+    st = State(g, 1, "f32r").set_kernel("pipelined").set(u0)
     p = make_params(phys)
     steps, rel = st.run_to_steady(p, 1e-10, check_every=8192, max_steps=4_000_000)
     assert rel < 1e-10

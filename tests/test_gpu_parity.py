@@ -246,13 +246,13 @@ def test_pipelined_kernel_is_bitwise_the_plain_kernel(block, dtype, ns, k):
     phi, phys, u0 = make_case((37, 29, 23), ns, k, (0, 1), 11)
     p = make_params(phys)
     outs = []
-    for variant in ("plain", "pipelined", "prefetch"):
+    for variant in ("plain", "pipelined", "prefetch", "async"):
         g = Grid(phi, block=block)
         st = State(g, ns, dtype).set_kernel(variant).set_all(u0)
         st.step(p, 77)
         outs.append(st.get_all())
-    np.testing.assert_array_equal(outs[0], outs[1])
-    np.testing.assert_array_equal(outs[0], outs[2])
+    for o in outs[1:]:
+        np.testing.assert_array_equal(outs[0], o)
     ref = oracle.Problem(phi, phys).run(u0, 77)
     assert rel_err(outs[1], ref) < 1e-5
 
@@ -265,5 +265,7 @@ def test_pipelined_kernel_with_few_ctas_walks_long_ranges():
     a = State(g, 1, "f32").set_kernel("plain").set_all(u0).step(p, 20).get_all()
     b = State(g, 1, "f32").set_kernel("pipelined", ctas_per_sm=1).set_all(u0).step(p, 20).get_all()
     c = State(g, 1, "f32").set_kernel("prefetch", ctas_per_sm=1).set_all(u0).step(p, 20).get_all()
+    d = State(g, 1, "f32").set_kernel("async", ctas_per_sm=1).set_all(u0).step(p, 20).get_all()
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(a, c)
+    np.testing.assert_array_equal(a, d)
