@@ -531,6 +531,358 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two rows per thread, for the modes with one haloed array (FP32 one species,
+// SBG_F32R correction).  Groups of 1024 voxels (sixteen 4^3 blocks or two 8^3
+// blocks); each thread updates two y-adjacent rows of four voxels, so the
+// per-group work (face ids, Dirichlet bits, the stage barrier, spans) is
+// shared by eight voxels, and the y neighbour between the two rows is already
+// in registers.  The per-voxel arithmetic is the same as above (bitwise).
+constexpr int kGroup2 = 1024;
+
+template <int B>
+struct Rows2Layout {
+    static constexpr int B3 = B * B * B;
+    static constexpr int G = kGroup2 / B3;       // blocks per group
+    static constexpr int TPB = B3 / 8;           // threads per block
+    static constexpr int kHalo = G * 6 * B * B;  // a B x B face per block and direction
+    __host__ __device__ static constexpr int face(int j, int f) { return (j * 6 + f) * B * B; }
+};
+
+// New values of one row of four voxels (u), given its mirrored-or-not
+// neighbours; hb: held bits of the row; src: the SBG_F32R source r.
+template <int MODE, bool REACT>
+__device__ __forceinline__ float4 row_update(const float4 u, float xm, float xp, const float4 ym, const float4 yp,
+                                             const float4 zm, const float4 zp, const float4 src, const float4 w4,
+                                             uint32_t hb, const StepCoef<float> &kc) {
+    bool actx[6];
+    actx[0] = !is_sent(xm);
+    actx[5] = !is_sent(xp);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) actx[i + 1] = !is_sent(f4get(u, i));
+    const float R[6] = {xm, u.x, u.y, u.z, u.w, xp};
+    float Dx[5];
+#pragma unroll
+    for (int jj = 0; jj < 5; ++jj) Dx[jj] = __fsub_rn(R[jj + 1], R[jj]);
+    float res[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float c = f4get(u, i);
+        const float yv[4] = {f4get(ym, i), f4get(yp, i), f4get(zm, i), f4get(zp, i)};
+        float nv[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) nv[f] = is_sent(yv[f]) ? c : yv[f];
+        const float dp = actx[i + 2] ? Dx[i + 1] : 0.f;
+        const float dm = actx[i] ? Dx[i] : 0.f;
+        const float dxs = __fsub_rn(dp, dm);
+        float nr;
+        if (MODE == kSrc) {
+            float rate = kc.decay[0];
+            if (REACT) rate = __fmaf_rn(kc.k, f4get(w4, i), rate);
+            nr = fused_update_dx(c, dxs, nv[0], nv[1], nv[2], nv[3], kc.c[0], kc.dt, rate, f4get(src, i));
+        } else {
+            const float t = REACT ? __fmul_rn(__fmul_rn(kc.k, f4get(w4, i)), c) : 0.f;
+            nr = fused_update_dx(c, dxs, nv[0], nv[1], nv[2], nv[3], kc.c[0], kc.dt, kc.decay[0], -t);
+        }
+        const bool upd = actx[i + 1] && !((hb >> i) & 1u);
+        res[i] = upd ? nr : c;
+    }
+    return make_float4(res[0], res[1], res[2], res[3]);
+}
+
+// AH: halo values copied one group ahead with per-thread cp.async into the
+// other half of a double halo buffer (no registers held across the group).
+template <int MODE, int B, bool REACT, int S, int MINB, bool AH>
+__global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArgs a, const PipeIO io, int *err) {
+    using L = Rows2Layout<B>;
+    constexpr int B3 = L::B3;
+    constexpr int G = L::G;
+    constexpr int TPB = L::TPB;
+    constexpr int NA = MODE == kSrc ? 2 : 1;  // streamed arrays; only the first has halos
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *stages = reinterpret_cast<float *>(smem_raw);  // [S][NA][1024]
+    float *halo = stages + (size_t)S * NA * kGroup2;      // [AH ? 2 : 1][kHalo]
+    float *wbuf = halo + (AH ? 2 : 1) * L::kHalo;         // AH and REACT: [2][1024] row weights
+    uint64_t *full = reinterpret_cast<uint64_t *>(wbuf + ((AH && REACT) ? 2 * kGroup2 : 0));
+
+    const int tid = threadIdx.x;
+    // (the launcher guarantees nb * B^3 < 2^31: 32-bit block ids and slots)
+    const int nb = (int)a.nb;
+    const int ngroups = (nb + G - 1) / G;
+    const int g0 = (int)((int64_t)ngroups * blockIdx.x / gridDim.x);
+    const int g1 = (int)((int64_t)ngroups * (blockIdx.x + 1) / gridDim.x);
+    if (g0 >= g1) return;  // uniform over the CTA
+    auto span = [&](int gi, int &b0, int &nblk) {
+        b0 = gi * G;
+        nblk = (nb - b0 < G) ? (nb - b0) : G;
+    };
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    auto issue = [&](int gi, int s) {
+        int b0, nblk;
+        span(gi, b0, nblk);
+        const uint32_t bytes = (uint32_t)(nblk * B3 * sizeof(float));
+        mbar_arrive_expect_tx(&full[s], bytes * NA);
+#pragma unroll
+        for (int k = 0; k < NA; ++k)
+            bulk_g2s(stages + ((size_t)s * NA + k) * kGroup2, io.src[k] + b0 * B3, bytes, &full[s]);
+    };
+    if (tid == 0)
+        for (int s = 0; s < S && g0 + s < g1; ++s) issue(g0 + s, s);
+
+    // this thread's rows: a = (y0, z) and b = (y0 + 1, z), x0 .. x0 + 3, of block j
+    const int j = tid / TPB, r = tid % TPB;
+    const int x0 = (B == 4) ? 0 : (r & 1) * 4;
+    const int rr = (B == 4) ? r : (r >> 1);
+    const int y0 = (rr % (B / 2)) * 2, z = rr / (B / 2);
+    const int la = (z * B + y0) * B + x0;  // row a in its block; row b is la + B
+    const int va = j * B3 + la;            // row a in the group tile
+    const bool hxm = (x0 == 0), hxp = (x0 + 3 == B - 1);
+    const bool hym = (y0 == 0), hyp = (y0 + 1 == B - 1), hzm = (z == 0), hzp = (z == B - 1);
+    // offsets of this thread's halo values in the neighbour blocks (row a; row b at + B)
+    const int oxm = la + (B - 1), oxp = la + 3 - (B - 1);
+    const int oym = la + (B - 1) * B;           // row a's y- neighbour row (y = B - 1)
+    const int oyp = la + B - (B - 1) * B;       // row b's y+ neighbour row (y = 0)
+    const int ozm = la + (B - 1) * B * B, ozp = la - (B - 1) * B * B;
+    // halo slots: x faces indexed z*B + y, y faces z*B + x, z faces y*B + x
+    const int sxm = L::face(j, 0) + z * B + y0, sxp = L::face(j, 1) + z * B + y0;
+    const int sym = L::face(j, 2) + z * B + x0, syp = L::face(j, 3) + z * B + x0;
+    const int szm = L::face(j, 4) + y0 * B + x0, szp = L::face(j, 5) + y0 * B + x0;
+    const float *s0 = io.src[0];
+
+    struct Ids {
+        int xm, xp, ym, yp, zm, zp, ws;
+        uint32_t hb;  // held bits: row a in bits 0-3, row b in bits 4-7
+    };
+    struct Halo {
+        float vxm[2], vxp[2];
+        float4 vym, vyp, vzm[2], vzp[2];
+        float4 w[2];
+        int ixm, ixp;  // x neighbour inside the group: row a's offset in the stage tile, else -1
+        uint32_t hb;
+    };
+    auto load_ids = [&](int gi) {
+        Ids q{-1, -1, -1, -1, -1, -1, -1, 0u};
+        if (gi >= g1) return q;
+        int b0, nblk;
+        span(gi, b0, nblk);
+        const int b = b0 + j;
+        if (j < nblk) {
+            const int32_t *f = a.face + 6 * b;
+            if (hxm) q.xm = __ldg(f + 0);
+            if (hxp) q.xp = __ldg(f + 1);
+            if (hym) q.ym = __ldg(f + 2);
+            if (hyp) q.yp = __ldg(f + 3);
+            if (hzm) q.zm = __ldg(f + 4);
+            if (hzp) q.zp = __ldg(f + 5);
+            if (REACT) q.ws = __ldg(a.wslab + b);
+            if (a.held_mask) {
+                constexpr int W = (B3 + 63) / 64;
+                const uint64_t word =
+                    __ldg(reinterpret_cast<const unsigned long long *>(a.heldbits) + b * W + (la >> 6));
+                q.hb = ((uint32_t)(word >> (la & 63)) & 0xFu) | (((uint32_t)(word >> ((la + B) & 63)) & 0xFu) << 4);
+            }
+        }
+        return q;
+    };
+    auto load_halo = [&](int gi, const Ids &id, Halo &h) {
+        int b0 = 0, nblk = 0;
+        if (gi < g1) span(gi, b0, nblk);
+        h.ixm = (hxm && (unsigned)(id.xm - b0) < (unsigned)nblk) ? (id.xm - b0) * B3 + oxm : -1;
+        h.ixp = (hxp && (unsigned)(id.xp - b0) < (unsigned)nblk) ? (id.xp - b0) * B3 + oxp : -1;
+        const float SENT = sentinel_f32();
+        const float4 SENT4 = make_float4(SENT, SENT, SENT, SENT);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            h.vxm[q] = (id.xm >= 0 && h.ixm < 0) ? __ldg(s0 + id.xm * B3 + oxm + q * B) : SENT;
+            h.vxp[q] = (id.xp >= 0 && h.ixp < 0) ? __ldg(s0 + id.xp * B3 + oxp + q * B) : SENT;
+            h.vzm[q] = (id.zm >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.zm * B3 + ozm + q * B)) : SENT4;
+            h.vzp[q] = (id.zp >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.zp * B3 + ozp + q * B)) : SENT4;
+            h.w[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (REACT && id.ws >= 0) h.w[q] = __ldg(reinterpret_cast<const float4 *>(a.w + id.ws * B3 + la + q * B));
+        }
+        h.vym = (id.ym >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.ym * B3 + oym)) : SENT4;
+        h.vyp = (id.yp >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.yp * B3 + oyp)) : SENT4;
+        h.hb = id.hb;
+    };
+    auto park = [&](const Halo &h) {
+        if (hxm && h.ixm < 0) {
+            halo[sxm] = h.vxm[0];
+            halo[sxm + 1] = h.vxm[1];
+        }
+        if (hxp && h.ixp < 0) {
+            halo[sxp] = h.vxp[0];
+            halo[sxp + 1] = h.vxp[1];
+        }
+        if (hym) *reinterpret_cast<float4 *>(halo + sym) = h.vym;
+        if (hyp) *reinterpret_cast<float4 *>(halo + syp) = h.vyp;
+        if (hzm) {
+            *reinterpret_cast<float4 *>(halo + szm) = h.vzm[0];
+            *reinterpret_cast<float4 *>(halo + szm + B) = h.vzm[1];
+        }
+        if (hzp) {
+            *reinterpret_cast<float4 *>(halo + szp) = h.vzp[0];
+            *reinterpret_cast<float4 *>(halo + szp + B) = h.vzp[1];
+        }
+    };
+
+    // AH: per halo buffer, the row's x offsets inside the group and held bits
+    int aixm0 = -1, aixm1 = -1, aixp0 = -1, aixp1 = -1;
+    uint32_t ahb0 = 0u, ahb1 = 0u;
+    auto issue_async = [&](int gi, const Ids &id, int buf) {
+        if (!AH) return;
+        int ixm = -1, ixp = -1;
+        if (gi < g1) {
+            int b0, nblk;
+            span(gi, b0, nblk);
+            if (j < nblk) {
+                ixm = (hxm && (unsigned)(id.xm - b0) < (unsigned)nblk) ? (id.xm - b0) * B3 + oxm : -1;
+                ixp = (hxp && (unsigned)(id.xp - b0) < (unsigned)nblk) ? (id.xp - b0) * B3 + oxp : -1;
+                const float SENT = sentinel_f32();
+                const float4 SENT4 = make_float4(SENT, SENT, SENT, SENT);
+                float *hb = halo + buf * L::kHalo;
+                if (hxm && ixm < 0) {
+                    if (id.xm >= 0) {
+                        cp_async4(hb + sxm, s0 + id.xm * B3 + oxm);
+                        cp_async4(hb + sxm + 1, s0 + id.xm * B3 + oxm + B);
+                    } else {
+                        hb[sxm] = SENT;
+                        hb[sxm + 1] = SENT;
+                    }
+                }
+                if (hxp && ixp < 0) {
+                    if (id.xp >= 0) {
+                        cp_async4(hb + sxp, s0 + id.xp * B3 + oxp);
+                        cp_async4(hb + sxp + 1, s0 + id.xp * B3 + oxp + B);
+                    } else {
+                        hb[sxp] = SENT;
+                        hb[sxp + 1] = SENT;
+                    }
+                }
+                if (hym) {
+                    if (id.ym >= 0) cp_async16(hb + sym, s0 + id.ym * B3 + oym);
+                    else *reinterpret_cast<float4 *>(hb + sym) = SENT4;
+                }
+                if (hyp) {
+                    if (id.yp >= 0) cp_async16(hb + syp, s0 + id.yp * B3 + oyp);
+                    else *reinterpret_cast<float4 *>(hb + syp) = SENT4;
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    if (hzm) {
+                        if (id.zm >= 0) cp_async16(hb + szm + q * B, s0 + id.zm * B3 + ozm + q * B);
+                        else *reinterpret_cast<float4 *>(hb + szm + q * B) = SENT4;
+                    }
+                    if (hzp) {
+                        if (id.zp >= 0) cp_async16(hb + szp + q * B, s0 + id.zp * B3 + ozp + q * B);
+                        else *reinterpret_cast<float4 *>(hb + szp + q * B) = SENT4;
+                    }
+                    if (REACT) {
+                        float *wb = wbuf + buf * kGroup2 + va + q * B;
+                        if (id.ws >= 0) cp_async16(wb, a.w + id.ws * B3 + la + q * B);
+                        else *reinterpret_cast<float4 *>(wb) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+        }
+        if (buf) {
+            aixm1 = ixm;
+            aixp1 = ixp;
+            ahb1 = id.hb;
+        } else {
+            aixm0 = ixm;
+            aixp0 = ixp;
+            ahb0 = id.hb;
+        }
+        cp_async_commit();
+    };
+
+    // AH: id1 holds the ids of group gi + 1 and id2 receives those of gi + 2;
+    // otherwise id1 holds this group's ids and id2 receives the next group's.
+    auto body = [&](int gi, int it, Halo &cur, const Ids &id1, Ids &id2) -> bool {
+        const int s = it % S;
+        const uint32_t par = (uint32_t)((it / S) & 1);
+        int b0, nblk;
+        span(gi, b0, nblk);
+        const int b = b0 + j;
+        const bool valid = j < nblk;
+        if (AH) {
+            issue_async(gi + 1, id1, (it + 1) & 1);
+            id2 = load_ids(gi + 2);
+            cp_async_wait_group<1>();  // this group's halo copies (issued a group ago) have landed
+        } else {
+            load_halo(gi, id1, cur);
+            id2 = load_ids(gi + 1);
+        }
+        bool ok = true;
+        if (tid == 0) ok = mbar_wait_bounded(&full[s], par);
+        if (__syncthreads_or(!ok)) {
+            if (AH) cp_async_wait_all();
+            if (tid == 0) {
+                atomicExch(err, (int)SBG_ERR_TIMEOUT);
+                for (int q = it; q < it + S && g0 + q < g1; ++q)
+                    mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), 1ll << 28);
+            }
+            return false;
+        }
+        mbar_try_wait(&full[s], par);  // completed: gives this thread the acquire of the copied data
+        if (tid == 0 && it >= 1 && gi - 1 + S < g1) issue(gi - 1 + S, (it - 1) % S);
+        if (!valid) return true;
+        if (!AH) park(cur);
+        const int buf = AH ? (it & 1) : 0;
+        const float *hbase = halo + buf * L::kHalo;
+        const int ixm = AH ? (buf ? aixm1 : aixm0) : cur.ixm;
+        const int ixp = AH ? (buf ? aixp1 : aixp0) : cur.ixp;
+        const uint32_t hbits = AH ? (buf ? ahb1 : ahb0) : cur.hb;
+        float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0;
+        if (REACT) {
+            w0 = AH ? *reinterpret_cast<const float4 *>(wbuf + buf * kGroup2 + va) : cur.w[0];
+            w1 = AH ? *reinterpret_cast<const float4 *>(wbuf + buf * kGroup2 + va + B) : cur.w[1];
+        }
+
+        const float *t = stages + (size_t)s * NA * kGroup2;
+        const float4 ua = *reinterpret_cast<const float4 *>(t + va);
+        const float4 ub = *reinterpret_cast<const float4 *>(t + va + B);
+        const float xma = hxm ? (ixm >= 0 ? t[ixm] : hbase[sxm]) : t[va - 1];
+        const float xmb = hxm ? (ixm >= 0 ? t[ixm + B] : hbase[sxm + 1]) : t[va + B - 1];
+        const float xpa = hxp ? (ixp >= 0 ? t[ixp] : hbase[sxp]) : t[va + 4];
+        const float xpb = hxp ? (ixp >= 0 ? t[ixp + B] : hbase[sxp + 1]) : t[va + B + 4];
+        const float4 yma = *reinterpret_cast<const float4 *>(hym ? hbase + sym : t + va - B);
+        const float4 ypb = *reinterpret_cast<const float4 *>(hyp ? hbase + syp : t + va + 2 * B);
+        const float4 zma = *reinterpret_cast<const float4 *>(hzm ? hbase + szm : t + va - B * B);
+        const float4 zmb = *reinterpret_cast<const float4 *>(hzm ? hbase + szm + B : t + va + B - B * B);
+        const float4 zpa = *reinterpret_cast<const float4 *>(hzp ? hbase + szp : t + va + B * B);
+        const float4 zpb = *reinterpret_cast<const float4 *>(hzp ? hbase + szp + B : t + va + B + B * B);
+        float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+        if (MODE == kSrc) {
+            ra = *reinterpret_cast<const float4 *>(t + kGroup2 + va);
+            rb = *reinterpret_cast<const float4 *>(t + kGroup2 + va + B);
+        }
+        const float4 na = row_update<MODE, REACT>(ua, xma, xpa, yma, ub, zma, zpa, ra, w0, hbits, a.cf);
+        const float4 nbv = row_update<MODE, REACT>(ub, xmb, xpb, ua, ypb, zmb, zpb, rb, w1, hbits >> 4, a.cf);
+        *reinterpret_cast<float4 *>(io.dst[0] + b * B3 + la) = na;
+        *reinterpret_cast<float4 *>(io.dst[0] + b * B3 + la + B) = nbv;
+        return true;
+    };
+
+    Ids idA = load_ids(g0), idB;
+    Halo hc;
+    if (AH) {
+        issue_async(g0, idA, 0);
+        idA = load_ids(g0 + 1);
+    }
+    int it = 0;
+    for (int gi = g0; gi < g1; gi += 2, it += 2) {
+        if (!body(gi, it, hc, idA, idB)) break;
+        if (gi + 1 >= g1) break;
+        if (!body(gi + 1, it + 1, hc, idB, idA)) break;
+    }
+    if (AH) cp_async_wait_all();  // no copy may land after the CTA's shared memory is gone
+}
+
 template <int MODE, int NA>
 struct PipeStages {
     static constexpr int S = NA == 1 ? 6 : NA == 2 ? 4 : 3;
@@ -573,6 +925,51 @@ static cudaError_t launch_pipe_hv(const StepArgs &a, const PipeIO &io, int ctas_
     return cudaGetLastError();
 }
 
+template <int MODE, int B, bool REACT, bool AH>
+static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_per_sm, int *err, cudaStream_t s) {
+    constexpr int NA = MODE == kSrc ? 2 : 1;
+    constexpr int S = 4;
+    constexpr size_t smem = ((size_t)S * NA * kGroup2 + (AH ? 2 : 1) * Rows2Layout<B>::kHalo +
+                             ((AH && REACT) ? 2 * kGroup2 : 0)) * sizeof(float) + S * sizeof(uint64_t);
+    constexpr int kFit = (int)((228 * 1024) / (smem + 1024));
+    constexpr int MINB = 5 < kFit ? 5 : kFit;  // 102 registers per thread
+    auto kern = k_step_rows2<MODE, B, REACT, S, MINB, AH>;
+    static int occ = -1, nsm = 0;
+    if (occ < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPipeThreads, smem);
+        if (occ < 1) occ = 1;
+    }
+    const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
+    constexpr int G = kGroup2 / (B * B * B);
+    const int64_t ngroups = (a.nb + G - 1) / G;
+    int64_t grid = (int64_t)nsm * per_sm;
+    if (grid > ngroups) grid = ngroups;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, kPipeThreads, smem, s>>>(a, io, err);
+    return cudaGetLastError();
+}
+
+template <int MODE, bool AH>
+static cudaError_t launch_rows2_a(const StepArgs &a, const PipeIO &io, int B, bool react, int ctas_per_sm, int *err,
+                                  cudaStream_t s) {
+    if (B == 8)
+        return react ? launch_rows2<MODE, 8, true, AH>(a, io, ctas_per_sm, err, s)
+                     : launch_rows2<MODE, 8, false, AH>(a, io, ctas_per_sm, err, s);
+    return react ? launch_rows2<MODE, 4, true, AH>(a, io, ctas_per_sm, err, s)
+                 : launch_rows2<MODE, 4, false, AH>(a, io, ctas_per_sm, err, s);
+}
+// halo variant 0: loads when the group comes up; 2: cp.async one group ahead
+template <int MODE>
+static cudaError_t launch_rows2_b(const StepArgs &a, const PipeIO &io, int B, bool react, int hv, int ctas_per_sm,
+                                  int *err, cudaStream_t s) {
+    return hv == 2 ? launch_rows2_a<MODE, true>(a, io, B, react, ctas_per_sm, err, s)
+                   : launch_rows2_a<MODE, false>(a, io, B, react, ctas_per_sm, err, s);
+}
+
 template <int MODE, int B, int NS, bool REACT>
 static cudaError_t launch_pipe_t(const StepArgs &a, const PipeIO &io, int hv, int ctas_per_sm, int *err,
                                  cudaStream_t s) {
@@ -608,14 +1005,18 @@ bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool re
         io.src[0] = (const float *)a.in[0];
         io.src[1] = a.src_term;
         io.dst[0] = (float *)a.out[0];
-        e = launch_pipe_b<kSrc, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
+        e = (hv != 1 && !a.items) ? launch_rows2_b<kSrc>(a, io, B, react, hv, ctas_per_sm, err_flag, s)
+                                  : launch_pipe_b<kSrc, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
     } else if (dtype == SBG_F32 && (ns == 1 || ns == 2)) {
         for (int k = 0; k < ns; ++k) {
             io.src[k] = (const float *)a.in[k];
             io.dst[k] = (float *)a.out[k];
         }
-        e = ns == 1 ? launch_pipe_b<kFwd, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s)
-                    : launch_pipe_b<kFwd, 2>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
+        if (ns == 1)
+            e = (hv != 1 && !a.items) ? launch_rows2_b<kFwd>(a, io, B, react, hv, ctas_per_sm, err_flag, s)
+                                      : launch_pipe_b<kFwd, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
+        else
+            e = launch_pipe_b<kFwd, 2>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
     } else {
         return false;
     }
