@@ -63,6 +63,13 @@ def _load():
         lib.oracle_adjoint_step.argtypes = [P, P, P, P, I, P, P, P, P, D, P, P, D, P]
         lib.oracle_adjoint_run.argtypes = [P, P, P, P, I, P, P, D, P, P, D, I64, P, P, P, P]
         lib.oracle_adjoint_run.restype = I
+        lib.oracle_eps_sigmoid.argtypes = [P, I64, D, D, D, D, P]
+        lib.oracle_step_inhom.argtypes = [P, P, P, P, P, P, P, D, D, D]
+        lib.oracle_run_inhom.argtypes = [P, P, P, P, P, P, D, D, D, I64]
+        lib.oracle_run_inhom.restype = I
+        lib.oracle_reduce_inhom.argtypes = [P, P, P, P, P, P, D, D, P]
+        lib.oracle_steady_cg_inhom.argtypes = [P, P, P, P, P, D, P, D, I64, P]
+        lib.oracle_steady_cg_inhom.restype = D
         _lib = lib
     return _lib
 
@@ -79,15 +86,27 @@ def num_threads() -> int:
     return int(_load().oracle_num_threads())
 
 
+def eps_sigmoid(phi, d_min, d_max, g1, g2):
+    """Eq. 6 per voxel: d_min + d_max / (1 + exp(-(g1 + g2 phi))), FP64."""
+    phi = np.ascontiguousarray(phi, dtype=np.float32)
+    eps = np.empty(phi.shape, dtype=np.float64)
+    _load().oracle_eps_sigmoid(_p(phi), int(phi.size), float(d_min), float(d_max), float(g1), float(g2),
+                               _p(eps))
+    return eps
+
+
 @dataclass
 class Problem:
     """A dense problem: phi plus the physics of one run.
 
     ``phys`` is any object with the fields of ``workloads.Physics``.
     Derived arrays (active, fixed, w) are computed here by the oracle.
+    ``eps`` (optional, one species): a per-voxel diffusivity factor, the
+    diffusivity being D * eps with face means (inhomogeneous diffusion, Eq. 6).
     """
     phi: np.ndarray
     phys: object
+    eps: np.ndarray = None
 
     def __post_init__(self):
         lib = _load()
@@ -109,6 +128,9 @@ class Problem:
         self.w = np.zeros(self.phi.shape, dtype=np.float64)
         lib.oracle_surface_weight(_p(self.phi), _p(self.active), self.n, float(self.phys.band_eps),
                                   _p(self.w))
+        if self.eps is not None:
+            assert self.ns == 1 and self.k == 0.0, "inhomogeneous diffusion: one species, no surface reaction"
+            self.eps = _f64(self.eps).reshape(self.phi.shape).copy()
 
     # -- state helpers --------------------------------------------------------
     def shape_state(self, u):
@@ -124,6 +146,12 @@ class Problem:
     def step(self, u, dt=None, src=None):
         u = self.shape_state(u)
         out = np.empty_like(u)
+        if self.eps is not None:
+            assert src is None
+            _load().oracle_step_inhom(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.eps), _p(u),
+                                      _p(out), _p(self.dx), float(self.phys.dt if dt is None else dt),
+                                      float(self.D[0]), float(self.decay[0]))
+            return out
         src = None if src is None else _f64(src).reshape(u.shape)
         _load().oracle_step(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.w), self.ns,
                             _p(u), _p(out), _p(self.dx), float(self.phys.dt if dt is None else dt),
@@ -132,6 +160,13 @@ class Problem:
 
     def run(self, u, nsteps, dt=None):
         u = self.shape_state(u)
+        if self.eps is not None:
+            rc = _load().oracle_run_inhom(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.eps), _p(u),
+                                          _p(self.dx), float(self.phys.dt if dt is None else dt),
+                                          float(self.D[0]), float(self.decay[0]), int(nsteps))
+            if rc != 0:
+                raise MemoryError("oracle_run_inhom: allocation failed")
+            return u
         rc = _load().oracle_run(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.w), self.ns,
                                 _p(u), _p(self.dx), float(self.phys.dt if dt is None else dt),
                                 _p(self.D), _p(self.decay), self.k, int(nsteps))
@@ -150,6 +185,10 @@ class Problem:
         """Per species: dict(mass, J_in, J_out, residual, n_active)."""
         u = self.shape_state(u)
         out = np.zeros(self.ns * 5)
+        if self.eps is not None:
+            _load().oracle_reduce_inhom(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.eps), _p(u),
+                                        _p(self.dx), float(self.D[0]), float(self.decay[0]), _p(out))
+            return [dict(zip(("mass", "J_in", "J_out", "residual", "n_active"), out[:5]))]
         _load().oracle_reduce(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.w), self.ns,
                               _p(u), _p(self.dx), _p(self.D), _p(self.decay), self.k, _p(out))
         keys = ("mass", "J_in", "J_out", "residual", "n_active")
@@ -170,6 +209,11 @@ class Problem:
         """FP64 CG steady state of species 0; returns (u, relres, iterations)."""
         u = self.shape_state(u0)[0].copy()
         iters = ctypes.c_int64()
+        if self.eps is not None:
+            rel = _load().oracle_steady_cg_inhom(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.eps),
+                                                 _p(self.dx), float(self.D[0]), _p(u), float(tol), int(maxit),
+                                                 ctypes.byref(iters))
+            return u, float(rel), int(iters.value)
         rel = _load().oracle_steady_cg(_p(self.dims), _p(self.active), _p(self.fixed), _p(self.dx),
                                        float(self.D[0]), _p(u), float(tol), int(maxit),
                                        ctypes.byref(iters))

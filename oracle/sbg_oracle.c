@@ -323,7 +323,7 @@ void oracle_effective_D(const int64_t dims[3], const double dx[3], double J_in, 
  * u holds the start (with the held values) and receives the solution.
  * Returns the final relative residual ||b - A x|| / ||b||.                  */
 static void cg_apply(const int64_t dims[3], const uint8_t *active, const uint8_t *fixed,
-                     const double dx[3], double D, const double *v, double *Av)
+                     const double *eps, const double dx[3], double D, const double *v, double *Av)
 {
     const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
 #pragma omp parallel for schedule(static)
@@ -340,7 +340,7 @@ static void cg_apply(const int64_t dims[3], const uint8_t *active, const uint8_t
                         if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz) continue;
                         int64_t j = IDX(xx, yy, zz);
                         if (!active[j]) continue;
-                        double c = D / (dx[a] * dx[a]);
+                        double c = D / (dx[a] * dx[a]) * (eps ? 0.5 * (eps[i] + eps[j]) : 1.0);
                         /* held neighbours enter as value 0 (their values are in b) */
                         acc += c * (v[i] - (fixed[j] ? 0.0 : v[j]));
                     }
@@ -360,9 +360,9 @@ static double cg_dot(const int64_t dims[3], const double *a, const double *b, do
     return sum_slices(part, nz);
 }
 
-double oracle_steady_cg(const int64_t dims[3], const uint8_t *active, const uint8_t *fixed,
-                        const double dx[3], double D, double *u, double tol, int64_t maxit,
-                        int64_t *iters)
+static double steady_cg(const int64_t dims[3], const uint8_t *active, const uint8_t *fixed,
+                        const double *eps, const double dx[3], double D, double *u, double tol,
+                        int64_t maxit, int64_t *iters)
 {
     const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
     const int64_t n = nx * ny * nz;
@@ -393,7 +393,7 @@ double oracle_steady_cg(const int64_t dims[3], const uint8_t *active, const uint
                         if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz) continue;
                         int64_t j = IDX(xx, yy, zz);
                         if (!active[j]) continue;
-                        double c = D / (dx[a] * dx[a]);
+                        double c = D / (dx[a] * dx[a]) * (eps ? 0.5 * (eps[i] + eps[j]) : 1.0);
                         diag += c;
                         if (fixed[j]) bi += c * u[j];
                     }
@@ -401,14 +401,14 @@ double oracle_steady_cg(const int64_t dims[3], const uint8_t *active, const uint
                 dinv[i] = diag > 0.0 ? 1.0 / diag : 0.0;
             }
     double bnorm = sqrt(cg_dot(dims, b, b, part));
-    cg_apply(dims, active, fixed, dx, D, x, Ap);
+    cg_apply(dims, active, fixed, eps, dx, D, x, Ap);
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] - Ap[i];
     if (bnorm == 0.0) { rel = sqrt(cg_dot(dims, r, r, part)); goto store; }
     for (int64_t i = 0; i < n; ++i) { zv[i] = dinv[i] * r[i]; p[i] = zv[i]; }
     double rz = cg_dot(dims, r, zv, part);
     rel = sqrt(cg_dot(dims, r, r, part)) / bnorm;
     while (rel >= tol && *iters < maxit) {
-        cg_apply(dims, active, fixed, dx, D, p, Ap);
+        cg_apply(dims, active, fixed, eps, dx, D, p, Ap);
         double pAp = cg_dot(dims, p, Ap, part);
         if (!(pAp > 0.0)) break;
         double alpha = rz / pAp;
@@ -430,6 +430,134 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+double oracle_steady_cg(const int64_t dims[3], const uint8_t *active, const uint8_t *fixed,
+                        const double dx[3], double D, double *u, double tol, int64_t maxit,
+                        int64_t *iters)
+{
+    return steady_cg(dims, active, fixed, NULL, dx, D, u, tol, maxit, iters);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Inhomogeneous diffusion (Eq. 6 and the functor of Appendix B Listing 6;
+ * the paper's fertilizer application, Sec. 3.4): one species whose
+ * diffusivity is D * eps_i per voxel.  The flux between a voxel and a face
+ * neighbour uses the arithmetic mean of their diffusivities, and a neighbour
+ * outside Omega takes the centre's value and the centre's eps (no flux):
+ *   u'_i = u_i + dt ( sum_a 1/dx_a^2 [ D_{+a} (u~_{i+a} - u_i) - D_{-a} (u_i - u~_{i-a}) ] - decay u_i ),
+ *   D_{+-a} = D (eps_i + eps~_{i+-a}) / 2.                                   */
+
+/* Eq. 6: eps = d_min + d_max / (1 + exp(-(g1 + g2 phi))), per voxel.        */
+void oracle_eps_sigmoid(const float *phi, int64_t n, double d_min, double d_max, double g1,
+                        double g2, double *eps)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) eps[i] = d_min + d_max / (1.0 + exp(-(g1 + g2 * (double)phi[i])));
+}
+
+static double rhs_inhom_at(const double *u, const double *eps, const uint8_t *active, int64_t nx,
+                           int64_t ny, int64_t nz, int64_t x, int64_t y, int64_t z,
+                           const double dx[3], double D, double decay)
+{
+    const int64_t i = IDX(x, y, z);
+    const double uc = u[i], ec = eps[i];
+    double lap = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double up = nbr_value(u, active, nx, ny, nz, x, y, z, a, +1, uc);
+        const double um = nbr_value(u, active, nx, ny, nz, x, y, z, a, -1, uc);
+        const double ep = nbr_value(eps, active, nx, ny, nz, x, y, z, a, +1, ec);
+        const double em = nbr_value(eps, active, nx, ny, nz, x, y, z, a, -1, ec);
+        const double dp = D * (ec + ep) / 2.0, dm = D * (ec + em) / 2.0;
+        lap += (dp * (up - uc) - dm * (uc - um)) / (dx[a] * dx[a]);
+    }
+    return lap - decay * uc;
+}
+
+void oracle_step_inhom(const int64_t dims[3], const uint8_t *active, const uint8_t *fixed,
+                       const double *eps, const double *u, double *u_next, const double dx[3],
+                       double dt, double D, double decay)
+{
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                const int64_t i = IDX(x, y, z);
+                if (!active[i]) { u_next[i] = 0.0; continue; }
+                if (fixed[i]) { u_next[i] = u[i]; continue; }
+                u_next[i] = u[i] + dt * rhs_inhom_at(u, eps, active, nx, ny, nz, x, y, z, dx, D, decay);
+            }
+}
+
+int oracle_run_inhom(const int64_t dims[3], const uint8_t *active, const uint8_t *fixed,
+                     const double *eps, double *u, const double dx[3], double dt, double D,
+                     double decay, int64_t nsteps)
+{
+    const int64_t n = dims[0] * dims[1] * dims[2];
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!tmp) return -1;
+    double *a = u, *b = tmp;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        oracle_step_inhom(dims, active, fixed, eps, a, b, dx, dt, D, decay);
+        double *c = a; a = b; b = c;
+    }
+    if (a != u) memcpy(u, a, sizeof(double) * (size_t)n);
+    free(tmp);
+    return 0;
+}
+
+/* Reductions of the inhomogeneous case, out[5] as oracle_reduce; the x-face
+ * flux uses the face diffusivity D (eps_p + eps_{p+1}) / 2.                  */
+void oracle_reduce_inhom(const int64_t dims[3], const uint8_t *active, const uint8_t *fixed,
+                         const double *eps, const double *u, const double dx[3], double D,
+                         double decay, double *out)
+{
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    const double dv = dx[0] * dx[1] * dx[2];
+    const double area = dx[1] * dx[2];
+    double *part = (double *)calloc((size_t)(5 * nz), sizeof(double));
+    if (!part) return;
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < nz; ++z) {
+        ksum m = {0, 0}, jin = {0, 0}, jout = {0, 0}, r2 = {0, 0}, cnt = {0, 0};
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                const int64_t i = IDX(x, y, z);
+                if (!active[i]) continue;
+                kadd(&cnt, 1.0);
+                kadd(&m, u[i] * dv);
+                if (!fixed[i]) {
+                    const double r = rhs_inhom_at(u, eps, active, nx, ny, nz, x, y, z, dx, D, decay);
+                    kadd(&r2, r * r);
+                }
+                if (nx >= 2 && (x == 0 || x == nx - 2) && active[i + 1]) {
+                    const double j = D * (eps[i] + eps[i + 1]) / 2.0 * (u[i] - u[i + 1]) / dx[0] * area;
+                    if (x == 0) kadd(&jin, j);
+                    if (x == nx - 2) kadd(&jout, j);
+                }
+            }
+        part[0 * nz + z] = m.s;
+        part[1 * nz + z] = jin.s;
+        part[2 * nz + z] = jout.s;
+        part[3 * nz + z] = r2.s;
+        part[4 * nz + z] = cnt.s;
+    }
+    out[0] = sum_slices(part + 0 * nz, nz);
+    out[1] = sum_slices(part + 1 * nz, nz);
+    out[2] = sum_slices(part + 2 * nz, nz);
+    out[3] = sqrt(sum_slices(part + 3 * nz, nz));
+    out[4] = sum_slices(part + 4 * nz, nz);
+    free(part);
+}
+
+/* Steady state of the inhomogeneous case by CG (face coefficients
+ * D (eps_i + eps_j) / 2 dx_a^-2: still a symmetric graph Laplacian).       */
+double oracle_steady_cg_inhom(const int64_t dims[3], const uint8_t *active, const uint8_t *fixed,
+                              const double *eps, const double dx[3], double D, double *u,
+                              double tol, int64_t maxit, int64_t *iters)
+{
+    return steady_cg(dims, active, fixed, eps, dx, D, u, tol, maxit, iters);
+}
+
 /* Adjoint of one step.  The forward step is linear, u^{n+1} = M u^n, with
  * (free voxel i, species s)
  *   M_ii = 1 - dt sum_{active nbr j} c_a - dt decay_s - [s=0] dt k w_i,
