@@ -20,6 +20,7 @@ launch over its average launch time, against the measured HBM copy bandwidth.
 
 Other workloads print one JSON line each:
   --workload reactive512   two species, surface reaction A -> B, 2000 steps (512^3)
+  --workload inhom512      inhomogeneous diffusion (Eq. 6 factor) from one face, 2000 steps (512^3)
   --workload gradient256   checkpointed adjoint of 1000 steps (256^3): adjoint / forward time,
                            memory, FP64 central-difference checks (--fd)
   --workload batch64       64 uneven geometries: one batched launch per step vs per-geometry
@@ -62,11 +63,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sbg", choices=["sbg", "reference"])
-    ap.add_argument("--workload", default="grf256", choices=["grf256", "reactive512", "gradient256", "batch64"])
+    ap.add_argument("--workload", default="grf256",
+                    choices=["grf256", "reactive512", "inhom512", "gradient256", "batch64"])
     ap.add_argument("--n", type=int, default=None, help="box side (default: the workload's)")
     ap.add_argument("--block", type=int, default=4)
     ap.add_argument("--dtype", default="f32r", choices=["f32", "f32x2", "f32r"])
-    ap.add_argument("--variant", default="pipelined", choices=["plain", "pipelined", "prefetch", "async"])
+    ap.add_argument("--variant", default="async", choices=["plain", "pipelined", "prefetch", "async"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fd", action="store_true", help="gradient256: FP64 central differences")
@@ -332,10 +334,13 @@ def run_grf256(args):
     algo_bytes = n_active * BYTES_PER_VOXEL[args.dtype]
     achieved = algo_bytes / (step_kernel_ms / 1e3) / 1e9
     d_eff, tau, psi = st.effective_D(p, stream=stream)
-    kernel_name = "k_step_pipe" if args.variant != "plain" else ("k_step_x2" if args.dtype == "f32x2" else "k_step")
+    if args.variant == "plain":
+        kernel_name = "k_step_x2" if args.dtype == "f32x2" else "k_step"
+    else:  # single-array modes run the two-rows-per-thread pipelined kernel
+        kernel_name = "k_step_rows2" if args.dtype in ("f32", "f32r") and args.variant != "prefetch" else "k_step_pipe"
     traffic = None
-    if (n, args.block, args.variant) == (256, 4, "pipelined"):
-        traffic = profile_traffic("k_step_pipe_%s_grf256.md" % args.dtype)
+    if (n, args.block) == (256, 4):
+        traffic = profile_traffic("%s_%s_%s_grf256.md" % (kernel_name, args.variant, args.dtype))
     line = {
         "metric": METRIC, "value": value, "unit": "GVox/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -418,10 +423,87 @@ def run_reactive512(args):
           "roofline": {"bound": "hbm", "kernel": "k_step_pipe", "achieved": algo_bytes / (per_launch_ms / 1e3) / 1e9,
                        "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                        "frac": algo_bytes / (per_launch_ms / 1e3) / 1e9 / peak,
-                       "traffic": profile_traffic("k_step_pipe_f32_reactive512.md"),
+                       "traffic": profile_traffic("k_step_pipe_%s_f32_reactive512.md" % args.variant),
                        "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": per_launch_ms * 1e3},
           "result": {"mass_A0_B0": [red0[0]["mass"], red0[1]["mass"]], "mass_A_B_end": list(masses[-1]),
                      "total_mass_change": (masses[-1][0] + masses[-1][1]) - (red0[0]["mass"] + red0[1]["mass"])},
+          "clocks": clocks, "cpu_baseline": cpu})
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_inhom512(args):
+    """Inhomogeneous diffusion (Eq. 6 factor, face-mean fluxes) of a solute
+    entering from the x = 0 face of the 512^3 packed bed: one FP32 species,
+    2000 steps.  Algorithmic bytes: u read and written and the factor read,
+    12 B per active voxel."""
+    import torch
+    from paper_2304_11165_b300 import Grid, State, make_params
+    from workloads import inhom512
+    torch.cuda.set_device(0)
+    n = args.n or 512
+    phi, u0, phys, (d_min, d_max, g1, g2) = inhom512(n=n)
+    stream = torch.cuda.current_stream()
+    g = Grid(phi, block=args.block, stream=stream)
+    g.set_diffusivity_sigmoid(phi, d_min, d_max, g1, g2, stream=stream)
+    st = State(g, 1, "f32").set_kernel(args.variant).set(u0, stream=stream)
+    p = make_params(phys)
+    red0 = st.reduce(p)
+    per = 100
+    st.step(p, 3 * per, stream=stream)  # warm-up, then restart from the initial state
+    st.set(u0, stream=stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kernel_ms = 0.0
+    masses = []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(phys.steps // per):
+        a.record(stream)
+        st.step(p, per, stream=stream)
+        b.record(stream)
+        red = st.reduce(p)  # synchronises
+        kernel_ms += a.elapsed_time(b)
+        masses.append(red[0]["mass"])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    updates = g.n_active * phys.steps
+    peak, peak_kind = load_peaks()
+    algo_bytes = g.n_active * 12
+    per_launch_ms = kernel_ms / phys.steps
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        eps = oracle.eps_sigmoid(phi, d_min, d_max, g1, g2)
+        P = oracle.Problem(phi, phys, eps=eps)
+        u = P.shape_state(u0)
+        t0 = time.perf_counter()
+        u = P.run(u, 1)
+        one = time.perf_counter() - t0
+        nsteps = max(1, int(args.cpu_seconds / max(one, 1e-6)))
+        t0 = time.perf_counter()
+        P.run(u, nsteps)
+        dt = time.perf_counter() - t0
+        cpu = {"value": g.n_active * nsteps / dt / 1e9, "unit": "GVox/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": "%d FP64 dense steps of the full %d^3 box" % (nsteps, n)}
+    emit({"metric": "active-voxel updates/s (inhomogeneous diffusion, Eq. 6 factor)",
+          "value": updates / (total_ms / 1e3) / 1e9, "unit": "GVox/s", "n_gpus": 1, "steps": phys.steps,
+          "ms_per_step": total_ms / phys.steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+          "config": {"workload": "inhom512: %d^3 Boolean sphere packing, pore fraction %.3f, D = eps(phi) from "
+                                 "Eq. 6 (D_min 0, D_max 1, gamma2 4, gamma1 %.3g), c = 1 held on x = 0, %d steps"
+                                 % (n, phys.extra["pore_fraction"], g1, phys.steps),
+                     "block": args.block, "kernel": args.variant, "n_active": g.n_active, "n_blocks": g.n_blocks},
+          "roofline": {"bound": "hbm", "kernel": "k_step_pipe", "achieved": algo_bytes / (per_launch_ms / 1e3) / 1e9,
+                       "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                       "frac": algo_bytes / (per_launch_ms / 1e3) / 1e9 / peak,
+                       "traffic": profile_traffic("k_step_pipe_%s_inhom512.md" % args.variant),
+                       "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": per_launch_ms * 1e3},
+          "result": {"mass_start": red0[0]["mass"], "mass_end": masses[-1]},
           "clocks": clocks, "cpu_baseline": cpu})
     return 0
 
@@ -613,8 +695,8 @@ def main():
         return run_reference(args)
     if args.workload != "grf256" and int(os.environ.get("RANK", "0")) != 0:
         return 0
-    return {"grf256": run_grf256, "reactive512": run_reactive512, "gradient256": run_gradient256,
-            "batch64": run_batch64}[args.workload](args)
+    return {"grf256": run_grf256, "reactive512": run_reactive512, "inhom512": run_inhom512,
+            "gradient256": run_gradient256, "batch64": run_batch64}[args.workload](args)
 
 
 if __name__ == "__main__":

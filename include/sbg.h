@@ -159,6 +159,38 @@ sbg_status sbg_grid_tables(sbg_grid grid, int32_t *nbr26, int32_t *blocks);
 
 void sbg_grid_destroy(sbg_grid grid);
 
+/* ---- inhomogeneous diffusion (Eq. 6; the functor of Appendix B Listing 6) ----
+ * A per-voxel diffusivity factor eps for single-species states: species 0
+ * diffuses with D_0 * eps_i, and the flux between a voxel and a face
+ * neighbour uses the arithmetic mean of their diffusivities,
+ *   u'_i = u_i + dt ( sum_a 1/dx_a^2 [ D_{+a} (u~_{i+a} - u_i) - D_{-a} (u_i - u~_{i-a}) ] - decay_0 u_i ),
+ *   D_{+-a} = D_0 (eps_i + eps_{i+-a}) / 2,
+ * with the no-flux rule as for constant D (a neighbour outside Omega takes the
+ * centre's value, so its face carries no flux).  The factor lives in the grid
+ * (FP32 and FP64 copies, block layout) and applies to every SBG_F32 or
+ * SBG_F64 one-species state of the grid; stepping a state of another kind,
+ * with two species or with k_surf != 0 returns SBG_ERR_INVALID_ARG while a
+ * factor is set.  The explicit limit becomes that of D_0 * max(eps).
+ * Reductions use the same face diffusivities for fluxes and the residual.
+ *
+ * sbg_grid_set_diffusivity: eps from a dense array [Nz][Ny][Nx] of
+ * dense_dtype (SBG_F32 or SBG_F64; host or device) for geometry `geom`;
+ * values must be finite and >= 0 on active voxels (SBG_ERR_INVALID_ARG
+ * otherwise; the factor is then cleared).  Synchronises `stream`. */
+sbg_status sbg_grid_set_diffusivity(sbg_grid grid, int32_t geom, const void *dense, int32_t dense_dtype,
+                                    int32_t on_device, void *stream);
+
+/* eps from phi by Eq. 6, evaluated on the device in FP64 per active voxel:
+ *   eps = d_min + d_max / (1 + exp(-(gamma1 + gamma2 phi))),
+ * phi: FP32 [Nz][Ny][Nx] (host or device) of geometry `geom`.  Requires
+ * d_min >= 0, d_max >= 0.  Synchronises `stream`. */
+sbg_status sbg_grid_set_diffusivity_sigmoid(sbg_grid grid, int32_t geom, const float *phi, int32_t phi_on_device,
+                                            double d_min, double d_max, double gamma1, double gamma2,
+                                            void *stream);
+
+/* Removes the factor (constant D per species again). */
+sbg_status sbg_grid_clear_diffusivity(sbg_grid grid);
+
 /* ---- state -----------------------------------------------------------------
  * nspecies fields in block layout u[s][block * B^3 + (z*B + y)*B + x] plus the
  * ping-pong partner (the two concentration properties of Appendix B Listing
@@ -184,8 +216,8 @@ sbg_status sbg_state_get(sbg_grid grid, sbg_state state, int32_t geom, int32_t s
                          void *dense, int32_t dense_dtype, int32_t on_device, void *stream);
 
 /* Step-kernel choice for a state (this library's tuning knob; no
- * counterpart in the paper).  variant: SBG_KERNEL_AUTO (pipelined kernel
- * where it exists, else the one-thread-per-voxel kernel), SBG_KERNEL_PLAIN
+ * counterpart in the paper).  variant: SBG_KERNEL_AUTO (the pipelined kernel
+ * with cp.async halos where it exists, else the one-thread-per-voxel kernel), SBG_KERNEL_PLAIN
  * (one thread per voxel, block tile in shared memory, one launch-sized grid)
  * SBG_KERNEL_PIPELINED (persistent CTAs streaming 512-voxel groups
  * through a bulk-copy ring; FP32 and SBG_F32X2 states only) or

@@ -142,6 +142,29 @@ class Grid:
                                                bc.ctypes.data_as(ctypes.c_void_p)))
         return na, bb, bc
 
+    def set_diffusivity(self, eps, geom: int = 0, stream=None):
+        """Per-voxel diffusivity factor (inhomogeneous diffusion of one species:
+        D_0 * eps with face means); eps: dense [Nz, Ny, Nx], numpy or torch."""
+        ptr, code, on_dev, keep = _dense_ptr(eps)
+        check(self._lib.sbg_grid_set_diffusivity(self.handle, geom, ptr, code, on_dev, _stream_handle(stream)))
+        return self
+
+    def set_diffusivity_sigmoid(self, phi, d_min, d_max, gamma1, gamma2, geom: int = 0, stream=None):
+        """The factor from phi by Eq. 6: d_min + d_max / (1 + exp(-(gamma1 + gamma2 phi)))."""
+        if isinstance(phi, np.ndarray):
+            arr = np.ascontiguousarray(phi, dtype=np.float32)
+            ptr, on_dev, keep = arr.ctypes.data_as(ctypes.c_void_p), 0, arr
+        else:
+            keep = phi.contiguous().float()
+            ptr, on_dev = ctypes.c_void_p(keep.data_ptr()), int(keep.is_cuda)
+        check(self._lib.sbg_grid_set_diffusivity_sigmoid(self.handle, geom, ptr, on_dev, float(d_min), float(d_max),
+                                                         float(gamma1), float(gamma2), _stream_handle(stream)))
+        return self
+
+    def clear_diffusivity(self):
+        check(self._lib.sbg_grid_clear_diffusivity(self.handle))
+        return self
+
     def tables(self):
         nbr = np.zeros((self.n_blocks, 26), np.int32)
         blocks = np.zeros((self.n_blocks, 4), np.int32)

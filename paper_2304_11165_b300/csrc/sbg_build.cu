@@ -374,6 +374,8 @@ static void grid_free(sbg_grid g) {
     cudaFree(g->err);
     cudaFree(g->pad);
     cudaFree(g->heldbits);
+    cudaFree(g->eps);
+    cudaFree(g->eps64);
     cudaFreeHost(g->err_host);
     delete g;
 }

@@ -102,6 +102,11 @@ struct sbg_grid_s {
     double *red_dev = nullptr;     // [kNumRed]
     double *red_host = nullptr;    // pinned [kNumRed]
     float *pad = nullptr;          // 16-byte-aligned page: 4 sentinels then 4 zeros (absent halo neighbours)
+    float *eps = nullptr;          // [nb * B^3] diffusivity factor (inhomogeneous diffusion), FP32
+    double *eps64 = nullptr;       // the same in FP64 (FP64 states, reductions of them)
+    bool has_eps = false;
+    float eps_max = 0.f;           // largest factor on an active voxel (stability limit)
+    int eps_version = 0;           // bumped when the factor is set or cleared (captured graphs)
     uint64_t *heldbits = nullptr;  // [nb * words]: voxels held by the Dirichlet faces of heldbits_mask
     int heldbits_mask = -1;        // face set heldbits was computed for (-1: none yet)
     int *err = nullptr;            // device error word written by bounded waits (0 = none)
@@ -128,6 +133,7 @@ struct sbg_state_s {
     sbg_params graph_params{};
     int graph_variant = -1;
     int graph_ctas = -1;
+    int graph_eps_version = -1;
     int variant = SBG_KERNEL_AUTO;  // step kernel choice (sbg_state_set_kernel)
     int ctas_per_sm = 0;
     // SBG_F32R (one species): val[b][0] holds the FP32 correction d; the base

@@ -46,6 +46,9 @@ struct RedArgs {
     // source array the reduction writes (r = fl32(L_h u) on free voxels, 0 on held)
     const float *bh, *bl;
     float *rout;
+    // inhomogeneous diffusion: diffusivity factor per slot (null: constant D)
+    const float *epsf;
+    const double *eps64;
 };
 
 template <typename T, bool X2>
@@ -80,6 +83,34 @@ __device__ __forceinline__ double nbr_val(const RedArgs &a, int s, int64_t b, in
     double v = load_val<T, X2>(a, s, nb * B3 + ln, act);
     if (act_out) *act_out = act;
     return act ? v : vc;
+}
+
+// diffusivity factor of the neighbour across face f (0 for an absent block:
+// that face carries no flux, the value only has to be finite)
+__device__ __forceinline__ int64_t nbr_slot_of(const RedArgs &a, int64_t b, int l, int x, int y, int z, int f,
+                                               int B) {
+    const int B3 = B * B * B;
+    int64_t nb = b;
+    int ln = l;
+    switch (f) {
+        case 0: if (x > 0) ln = l - 1; else { nb = a.face[b * 6 + 0]; ln = l + (B - 1); } break;
+        case 1: if (x < B - 1) ln = l + 1; else { nb = a.face[b * 6 + 1]; ln = l - (B - 1); } break;
+        case 2: if (y > 0) ln = l - B; else { nb = a.face[b * 6 + 2]; ln = l + (B - 1) * B; } break;
+        case 3: if (y < B - 1) ln = l + B; else { nb = a.face[b * 6 + 3]; ln = l - (B - 1) * B; } break;
+        case 4: if (z > 0) ln = l - B * B; else { nb = a.face[b * 6 + 4]; ln = l + (B - 1) * B * B; } break;
+        default: if (z < B - 1) ln = l + B * B; else { nb = a.face[b * 6 + 5]; ln = l - (B - 1) * B * B; } break;
+    }
+    return nb < 0 ? -1 : nb * B3 + ln;
+}
+template <int B>
+__device__ __forceinline__ double nbr_eps64(const RedArgs &a, int64_t b, int l, int x, int y, int z, int f) {
+    const int64_t q = nbr_slot_of(a, b, l, x, y, z, f, B);
+    return q < 0 ? 0.0 : a.eps64[q];
+}
+template <int B>
+__device__ __forceinline__ float nbr_epsf(const RedArgs &a, int64_t b, int l, int x, int y, int z, int f) {
+    const int64_t q = nbr_slot_of(a, b, l, x, y, z, f, B);
+    return q < 0 ? 0.f : a.epsf[q];
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -132,13 +163,20 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const RedArgs a) {
         const bool held = ((a.held_mask & 1) && gx == 0) || ((a.held_mask & 2) && gx == nx - 1) ||
                           ((a.held_mask & 4) && gy == 0) || ((a.held_mask & 8) && gy == ny - 1) ||
                           ((a.held_mask & 16) && gz == 0) || ((a.held_mask & 32) && gz == nz - 1);
+        const double ec = a.eps64 ? a.eps64[b * B3 + l] : 1.0;
         if (!held) {
             double lap = 0.0;
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
                 const double vm = nbr_val<T, X2, B>(a, s, b, l, x, y, z, 2 * ax, v);
                 const double vp = nbr_val<T, X2, B>(a, s, b, l, x, y, z, 2 * ax + 1, v);
-                lap += a.c[ax] * ((vp - v) - (v - vm));
+                if (a.eps64) {  // face diffusivities (eps_c + eps_nb) / 2
+                    const double fm = 0.5 * (ec + nbr_eps64<B>(a, b, l, x, y, z, 2 * ax));
+                    const double fp = 0.5 * (ec + nbr_eps64<B>(a, b, l, x, y, z, 2 * ax + 1));
+                    lap += a.c[ax] * (fp * (vp - v) - fm * (v - vm));
+                } else {
+                    lap += a.c[ax] * ((vp - v) - (v - vm));
+                }
             }
             double react = -a.decay * v;
             if (a.k != 0.0) {
@@ -156,7 +194,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const RedArgs a) {
             bool act1;
             const double v1 = nbr_val<T, X2, B>(a, s, b, l, x, y, z, 1, v, &act1);
             if (act1) {
-                const double j = a.D * (v - v1) * a.inv_dx * a.area;
+                const double f = a.eps64 ? 0.5 * (ec + nbr_eps64<B>(a, b, l, x, y, z, 1)) : 1.0;
+                const double j = a.D * f * (v - v1) * a.inv_dx * a.area;
                 if (gx == 0) acc[SBG_RED_JIN] += j;
                 if (gx == nx - 2) acc[SBG_RED_JOUT] += j;
             }
@@ -322,6 +361,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_f(const RedArgs a) {
         if (!held) {
             // L_h u = sum_a c_a [(u~- - u) + (u~+ - u)] - rate u (+ transfer), double-float
             DF lap = {0.f, 0.f};
+            const float ec = a.epsf ? a.epsf[slot] : 1.f;
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
                 DF d = {0.f, 0.f};
@@ -331,7 +371,13 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_f(const RedArgs a) {
                     if (nbr_f<VM, B>(a, s, b, l, x, y, z, 2 * ax + side, nh, nl)) {
                         float e;
                         const float dh = tsum(nh, -h, e);
-                        d = df_add(d, {dh, VM != kVF32 ? __fadd_rn(e, __fsub_rn(nl, lo)) : e});
+                        DF diff = {dh, VM != kVF32 ? __fadd_rn(e, __fsub_rn(nl, lo)) : e};
+                        if (a.epsf) {  // face diffusivity (eps_c + eps_nb) / 2, exact as a pair
+                            float fe;
+                            const float fs = tsum(ec, nbr_epsf<B>(a, b, l, x, y, z, 2 * ax + side), fe);
+                            diff = df_mul(diff, {__fmul_rn(fs, 0.5f), __fmul_rn(fe, 0.5f)});
+                        }
+                        d = df_add(d, diff);
                     }
                 }
                 lap = df_add(lap, df_mul(d, c[ax]));
@@ -363,7 +409,12 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_f(const RedArgs a) {
                 // u - u_{x+1}, double-float; scaled by D / dx * area below
                 float e;
                 const float dh = tsum(h, -nh, e);
-                const DF d = {dh, VM != kVF32 ? __fadd_rn(e, __fsub_rn(lo, nl)) : e};
+                DF d = {dh, VM != kVF32 ? __fadd_rn(e, __fsub_rn(lo, nl)) : e};
+                if (a.epsf) {
+                    float fe;
+                    const float fs = tsum(a.epsf[slot], nbr_epsf<B>(a, b, l, x, y, z, 1), fe);
+                    d = df_mul(d, {__fmul_rn(fs, 0.5f), __fmul_rn(fe, 0.5f)});
+                }
                 if (gx == 0) jin = df_add(jin, d);
                 if (gx == nx - 2) jout = df_add(jout, d);
             }
@@ -469,6 +520,10 @@ static void fill_red_args(sbg_grid g, sbg_state st, const sbg_params *p, int geo
     a.dv = p->dx[0] * p->dx[1] * p->dx[2];
     fill_df(a, g->w);
     a.partials = partials;
+    if (g->has_eps && st->ns == 1) {
+        if (st->dtype == SBG_F64) a.eps64 = g->eps64;
+        else if (st->dtype == SBG_F32) a.epsf = g->eps;
+    }
 }
 
 static void dispatch_reduce(sbg_grid g, sbg_state st, const RedArgs &a, int nctas, cudaStream_t s) {

@@ -237,6 +237,8 @@ void fill_step_args(sbg_grid g, const sbg_params *p, StepArgs &a) {
     a.gdims = g->gdims;
     a.nb = g->nb;
     a.held_mask = held_mask_of(p);
+    a.eps = g->has_eps ? g->eps : nullptr;
+    a.eps64 = g->has_eps ? g->eps64 : nullptr;
     a.heldbits = (a.held_mask && g->heldbits_mask == a.held_mask) ? g->heldbits : nullptr;
     for (int s = 0; s < 2; ++s) {
         for (int ax = 0; ax < 3; ++ax) {
@@ -272,6 +274,74 @@ static void launch_plain(const StepArgs &a, bool react, cudaStream_t s) {
     else k_step<T, B, BPC, NS, false, SRC><<<grid, BPC * B * B * B, 0, s>>>(a);
 }
 
+// Plain kernel for inhomogeneous diffusion (one species, FP32 or FP64): the
+// state and the diffusivity factor are staged as block tiles; a halo factor
+// of an absent neighbour block reads 0 (its face carries no flux anyway).
+template <typename T, int B, int BPC>
+__global__ void __launch_bounds__(BPC * B * B * B, (sizeof(T) == 8 ? 1024 : 2048) / (BPC * B * B * B))
+k_step_inh(const StepArgs a) {
+    constexpr int B3 = B * B * B;
+    __shared__ T tile[BPC * B3];
+    __shared__ T etile[BPC * B3];
+    const int tid = threadIdx.x;
+    const int j = tid / B3;
+    const int l = tid - j * B3;
+    const int64_t b = (int64_t)blockIdx.x * BPC + j;
+    const bool valid = b < a.nb;
+    const int x = l % B, y = (l / B) % B, z = l / (B * B);
+    const T *in = (const T *)a.in[0];
+    const T *ep = sizeof(T) == 8 ? (const T *)a.eps64 : (const T *)a.eps;
+    T uc = T(0), ec = T(0), hu[6], he[6];
+    int4 bc = make_int4(0, 0, 0, 0);
+    const int off[6] = {B - 1, -(B - 1), (B - 1) * B, -(B - 1) * B, (B - 1) * B * B, -(B - 1) * B * B};
+    const bool edge[6] = {x == 0, x == B - 1, y == 0, y == B - 1, z == 0, z == B - 1};
+    if (valid) {
+        bc = a.blocks[b];
+        uc = in[b * B3 + l];
+        ec = ep[b * B3 + l];
+        tile[tid] = uc;
+        etile[tid] = ec;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const int nid = edge[f] ? a.face[b * 6 + f] : -1;
+            hu[f] = nid >= 0 ? in[(int64_t)nid * B3 + l + off[f]] : sentinel<T>();
+            he[f] = nid >= 0 ? ep[(int64_t)nid * B3 + l + off[f]] : T(0);
+        }
+    }
+    __syncthreads();
+    if (!valid) return;
+    const int nx = a.gdims[bc.w * 4 + 0], ny = a.gdims[bc.w * 4 + 1], nz = a.gdims[bc.w * 4 + 2];
+    const bool held = is_held(a.held_mask, bc.x * B + x, bc.y * B + y, bc.z * B + z, nx, ny, nz);
+    T res = uc;
+    if (!is_sent(uc) && !held) {
+        const T *t = tile + j * B3;
+        const T *e = etile + j * B3;
+        const int step[6] = {-1, 1, -B, B, -B * B, B * B};
+        T nv[6], en[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            nv[f] = mirror(edge[f] ? hu[f] : t[l + step[f]], uc);
+            en[f] = edge[f] ? he[f] : e[l + step[f]];
+        }
+        T dp[3], dm[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            dp[ax] = nv[2 * ax + 1] - uc;
+            dm[ax] = uc - nv[2 * ax];
+        }
+        const StepCoef<T> &k = coef<T>(a);
+        res = inh_update(uc, dp, dm, ec, en, k.c[0], k.dt, k.decay[0]);
+    }
+    ((T *)a.out[0])[b * B3 + l] = res;
+}
+
+template <typename T, int B>
+static void launch_inh(const StepArgs &a, cudaStream_t s) {
+    constexpr int BPC = (B == 8) ? 1 : 8;
+    const unsigned grid = (unsigned)((a.nb + BPC - 1) / BPC);
+    k_step_inh<T, B, BPC><<<grid, BPC * B * B * B, 0, s>>>(a);
+}
+
 template <int B>
 static void launch_x2(const StepArgs &a, bool react, cudaStream_t s) {
     constexpr int BPC = (B == 8) ? 1 : 8;
@@ -287,6 +357,9 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
     fill_args(g, st, p, src, a);
     const bool react = p->k_surf != 0.0;
     if (a.held_mask && !a.heldbits) return fail(SBG_ERR_INVALID_ARG, "internal: held bits not prepared");
+    const bool inh = a.eps != nullptr;
+    if (inh && ((st->dtype != SBG_F32 && st->dtype != SBG_F64) || st->ns != 1))
+        return fail(SBG_ERR_INVALID_ARG, "a diffusivity factor is set: SBG_F32 or SBG_F64 states of one species only");
     if (st->variant != SBG_KERNEL_PLAIN) {
         cudaError_t e = cudaSuccess;
         if (launch_step_pipe(a, st->dtype, st->ns, g->B, react, halo_variant_of(st->variant),
@@ -303,6 +376,14 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
     } else if (st->dtype == SBG_F32R) {
         if (g->B == 8) launch_plain<float, 8, 1, true>(a, react, s);
         else launch_plain<float, 4, 1, true>(a, react, s);
+    } else if (inh) {
+        if (st->dtype == SBG_F32) {
+            if (g->B == 8) launch_inh<float, 8>(a, s);
+            else launch_inh<float, 4>(a, s);
+        } else {
+            if (g->B == 8) launch_inh<double, 8>(a, s);
+            else launch_inh<double, 4>(a, s);
+        }
     } else if (st->dtype == SBG_F32) {
         if (g->B == 8) {
             if (st->ns == 1) launch_plain<float, 8, 1>(a, react, s);
@@ -351,9 +432,13 @@ sbg_status validate_params(sbg_grid g, const sbg_params *p, int ns) {
     for (int f = 0; f < 6; ++f)
         if (p->face_type[f] != SBG_FACE_NOFLUX && p->face_type[f] != SBG_FACE_DIRICHLET)
             return fail(SBG_ERR_INVALID_ARG, "face_type must be NOFLUX or DIRICHLET");
+    if (g->has_eps && (ns != 1 || p->k_surf != 0.0))
+        return fail(SBG_ERR_INVALID_ARG, "a diffusivity factor is set: one species and k_surf = 0 only");
+    sbg_params pe = *p;
+    if (g->has_eps) pe.D[0] = p->D[0] * (double)g->eps_max;  // the largest diffusivity bounds dt
     if (!p->allow_unstable) {
         for (int i = 0; i < g->n_geoms; ++i) {
-            double lim = stability_limit(p, &g->dims[3 * i], g->band_eps);
+            double lim = stability_limit(&pe, &g->dims[3 * i], g->band_eps);
             if (p->dt > lim)
                 return fail(SBG_ERR_UNSTABLE_DT, "dt " + std::to_string(p->dt) + " above the explicit limit " +
                                                      std::to_string(lim));
@@ -366,7 +451,8 @@ constexpr int64_t kGraphSteps = 64;  // steps per captured graph (even: parity p
 
 static sbg_status ensure_graph(sbg_grid g, sbg_state st, const sbg_params *p) {
     if (st->graph && st->graph_cur == st->cur && st->graph_variant == st->variant &&
-        st->graph_ctas == st->ctas_per_sm && std::memcmp(&st->graph_params, p, sizeof(*p)) == 0)
+        st->graph_ctas == st->ctas_per_sm && st->graph_eps_version == g->eps_version &&
+        std::memcmp(&st->graph_params, p, sizeof(*p)) == 0)
         return SBG_OK;
     if (st->graph) {
         cudaGraphExecDestroy(st->graph);
@@ -396,6 +482,7 @@ static sbg_status ensure_graph(sbg_grid g, sbg_state st, const sbg_params *p) {
     st->graph_cur = st->cur;
     st->graph_variant = st->variant;
     st->graph_ctas = st->ctas_per_sm;
+    st->graph_eps_version = g->eps_version;
     st->graph_params = *p;
     st->graph_steps = kGraphSteps;
     return SBG_OK;

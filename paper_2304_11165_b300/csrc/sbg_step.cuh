@@ -27,6 +27,8 @@ struct StepArgs {
     const uint64_t *heldbits;  // per block, B^3 bits: voxel held by a Dirichlet face (null without)
     int64_t nb;
     const float *src_term;   // SBG_F32R: per-slot source r = L_h b of the correction step
+    const float *eps;        // inhomogeneous diffusion: per-slot diffusivity factor (null: constant D)
+    const double *eps64;     //   the same in FP64
     const int64_t *items;    // optional work list for the pipelined kernel: (first block, count)
     int64_t nitems;          //   pairs, each within one geometry and at most 512 voxels
     int held_mask;           // bit f: face f is Dirichlet
@@ -76,6 +78,40 @@ __device__ __forceinline__ double fused_update(double u, double xm, double xp, d
     const double dz = __dsub_rn(__dsub_rn(zp, u), __dsub_rn(u, zm));
     const double lap = __fma_rn(c[2], dz, __fma_rn(c[1], dy, __dmul_rn(c[0], dx)));
     const double react = __fma_rn(-decay, u, t);
+    return __fma_rn(dt, __dadd_rn(lap, react), u);
+}
+
+// Inhomogeneous diffusion (the functor of Appendix B Listing 6): given the
+// one-sided differences dp_a = u~_{+a} - u and dm_a = u - u~_{-a} (0 towards a
+// neighbour outside Omega) and the factors of the centre (ec) and of the six
+// neighbours (en: -x, +x, -y, +y, -z, +z; any finite value where the
+// difference is 0), with c_a = D / dx_a^2:
+//   u' = u + dt ( sum_a c_a [ (ec + en_{+a})/2 dp_a - (ec + en_{-a})/2 dm_a ] - decay u ).
+// (FP32 and FP64, with every rounding pinned so that all kernels agree bitwise)
+__device__ __forceinline__ float inh_update(float u, const float dp[3], const float dm[3], float ec,
+                                            const float en[6], const float c[3], float dt, float decay) {
+    float tx[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float fp = __fmul_rn(__fadd_rn(ec, en[2 * ax + 1]), 0.5f);
+        const float fm = __fmul_rn(__fadd_rn(ec, en[2 * ax]), 0.5f);
+        tx[ax] = __fsub_rn(__fmul_rn(fp, dp[ax]), __fmul_rn(fm, dm[ax]));
+    }
+    const float lap = __fmaf_rn(c[2], tx[2], __fmaf_rn(c[1], tx[1], __fmul_rn(c[0], tx[0])));
+    const float react = __fmul_rn(-decay, u);
+    return __fmaf_rn(dt, __fadd_rn(lap, react), u);
+}
+__device__ __forceinline__ double inh_update(double u, const double dp[3], const double dm[3], double ec,
+                                             const double en[6], const double c[3], double dt, double decay) {
+    double tx[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const double fp = __dmul_rn(__dadd_rn(ec, en[2 * ax + 1]), 0.5);
+        const double fm = __dmul_rn(__dadd_rn(ec, en[2 * ax]), 0.5);
+        tx[ax] = __dsub_rn(__dmul_rn(fp, dp[ax]), __dmul_rn(fm, dm[ax]));
+    }
+    const double lap = __fma_rn(c[2], tx[2], __fma_rn(c[1], tx[1], __dmul_rn(c[0], tx[0])));
+    const double react = __dmul_rn(-decay, u);
     return __fma_rn(dt, __dadd_rn(lap, react), u);
 }
 
@@ -147,9 +183,10 @@ struct PipeIO {
 // ahead in registers, 2 copied one group ahead with cp.async (sbg_step_pipe.cu).
 bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, int halo_variant,
                       int ctas_per_sm, int *err_flag, cudaStream_t s, cudaError_t *launch_err);
-// the halo variant of a state's kernel choice
+// the halo variant of a state's kernel choice (SBG_KERNEL_AUTO: cp.async one
+// group ahead, measured as fast as or faster than the others on every workload)
 inline int halo_variant_of(int variant) {
-    return variant == SBG_KERNEL_PIPELINED_PREFETCH ? 1 : variant == SBG_KERNEL_PIPELINED_ASYNC ? 2 : 0;
+    return variant == SBG_KERNEL_PIPELINED_PREFETCH ? 1 : variant == SBG_KERNEL_PIPELINED ? 0 : 2;
 }
 
 // One adjoint step on FP32 arrays with the pipelined kernel: io.src = lambda^{n+1}

@@ -34,6 +34,7 @@
 //  kX2   hi, lo                                -> hi', lo'       (compensated state)
 //  kAdj  lambda_s^{n+1} (NS), u_s^n (NS)       -> lambda_s^n     (adjoint step)
 //  kSrc  d, r (r without halo)                 -> d'             (SBG_F32R correction)
+//  kInh  u, eps                                -> u'             (inhomogeneous diffusion)
 // The per-voxel arithmetic is that of the plain kernels (sbg_step.cu), with
 // the rounding of every operation pinned, so both give bitwise equal states.
 #include <cstring>
@@ -46,13 +47,13 @@ namespace sbg {
 constexpr int kPipeThreads = 128;
 constexpr int kGroupVox = 512;
 
-enum PipeMode : int { kFwd = 0, kX2 = 1, kAdj = 2, kSrc = 3 };
+enum PipeMode : int { kFwd = 0, kX2 = 1, kAdj = 2, kSrc = 3, kInh = 4 };
 
 template <int MODE, int NS>
 struct PipeShape {
     static constexpr int NA = MODE == kFwd ? NS : MODE == kAdj ? 2 * NS : 2;  // arrays streamed
     static constexpr int NH = MODE == kSrc ? 1 : NA;                          // the first NH have halos
-    static constexpr int NO = MODE == kX2 ? 2 : MODE == kSrc ? 1 : NS;        // arrays written
+    static constexpr int NO = MODE == kX2 ? 2 : (MODE == kSrc || MODE == kInh) ? 1 : NS;  // arrays written
 };
 
 __device__ __forceinline__ float f4get(const float4 &v, int i) {
@@ -214,7 +215,8 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
         const float SENT = sentinel_f32();
 #pragma unroll
         for (int k = 0; k < NH; ++k) {
-            const float absent = (MODE == kX2 && k == 1) ? 0.f : SENT;
+            // the compensated lo part and the diffusivity factor of an absent block read 0
+            const float absent = ((MODE == kX2 || MODE == kInh) && k == 1) ? 0.f : SENT;
             // this thread's halo addresses are fixed offsets from neighbour block
             // starts: one wide multiply-add per load
             const float *pxm = (NH == 1 ? hp[0] : io.src[k] + oxm), *pxp = (NH == 1 ? hp[1] : io.src[k] + oxp);
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
                 const float SENT = sentinel_f32();
 #pragma unroll
                 for (int k = 0; k < NH; ++k) {
-                    const float absent = (MODE == kX2 && k == 1) ? 0.f : SENT;
+                    const float absent = ((MODE == kX2 || MODE == kInh) && k == 1) ? 0.f : SENT;
                     const float *sk = io.src[k];
                     float *hb = halo + ((size_t)buf * NH + k) * L::kHalo;
                     if (hxm) {
@@ -436,6 +438,14 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
                 if (REACT) rate = __fmaf_rn(kc.k, f4get(w4, i), rate);
                 nr[0] = fused_update_dx(c0, dxs[0], nv[0][2], nv[0][3], nv[0][4], nv[0][5], kc.c[0], kc.dt, rate,
                                         f4get(uc[1], i));
+            } else if (MODE == kInh) {
+                // inhomogeneous diffusion: one-sided differences of u (0 towards
+                // a neighbour outside Omega) and the raw neighbour factors
+                const float dp[3] = {nv[0][1], __fsub_rn(nv[0][3], c0), __fsub_rn(nv[0][5], c0)};
+                const float dm[3] = {nv[0][0], __fsub_rn(c0, nv[0][2]), __fsub_rn(c0, nv[0][4])};
+                const float en[6] = {i == 0 ? xm[1] : f4get(uc[1], i - 1), i == 3 ? xp[1] : f4get(uc[1], i + 1),
+                                     f4get(ym[1], i), f4get(yp[1], i), f4get(zm[1], i), f4get(zp[1], i)};
+                nr[0] = inh_update(c0, dp, dm, f4get(uc[1], i), en, kc.c[0], kc.dt, kc.decay[0]);
             } else if (MODE == kFwd) {
                 const float t = REACT ? __fmul_rn(__fmul_rn(kc.k, f4get(w4, i)), c0) : 0.f;
 #pragma unroll
@@ -598,7 +608,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
     constexpr int B3 = L::B3;
     constexpr int G = L::G;
     constexpr int TPB = L::TPB;
-    constexpr int NA = MODE == kSrc ? 2 : 1;  // streamed arrays; only the first has halos
+    constexpr int NA = 1;  // streamed array (u or d); the SBG_F32R source r is read per row from global memory
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *stages = reinterpret_cast<float *>(smem_raw);  // [S][NA][1024]
     float *halo = stages + (size_t)S * NA * kGroup2;      // [AH ? 2 : 1][kHalo]
@@ -809,6 +819,12 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
         span(gi, b0, nblk);
         const int b = b0 + j;
         const bool valid = j < nblk;
+        // SBG_F32R: this row pair's source values (read now, used after the stage barrier)
+        float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
+        if (MODE == kSrc && valid) {
+            ra = __ldg(reinterpret_cast<const float4 *>(io.src[1] + b * B3 + la));
+            rb = __ldg(reinterpret_cast<const float4 *>(io.src[1] + b * B3 + la + B));
+        }
         if (AH) {
             issue_async(gi + 1, id1, (it + 1) & 1);
             id2 = load_ids(gi + 2);
@@ -856,11 +872,6 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
         const float4 zmb = *reinterpret_cast<const float4 *>(hzm ? hbase + szm + B : t + va + B - B * B);
         const float4 zpa = *reinterpret_cast<const float4 *>(hzp ? hbase + szp : t + va + B * B);
         const float4 zpb = *reinterpret_cast<const float4 *>(hzp ? hbase + szp + B : t + va + B + B * B);
-        float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
-        if (MODE == kSrc) {
-            ra = *reinterpret_cast<const float4 *>(t + kGroup2 + va);
-            rb = *reinterpret_cast<const float4 *>(t + kGroup2 + va + B);
-        }
         const float4 na = row_update<MODE, REACT>(ua, xma, xpa, yma, ub, zma, zpa, ra, w0, hbits, a.cf);
         const float4 nbv = row_update<MODE, REACT>(ub, xmb, xpb, ua, ypb, zmb, zpb, rb, w1, hbits >> 4, a.cf);
         *reinterpret_cast<float4 *>(io.dst[0] + b * B3 + la) = na;
@@ -927,7 +938,7 @@ static cudaError_t launch_pipe_hv(const StepArgs &a, const PipeIO &io, int ctas_
 
 template <int MODE, int B, bool REACT, bool AH>
 static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_per_sm, int *err, cudaStream_t s) {
-    constexpr int NA = MODE == kSrc ? 2 : 1;
+    constexpr int NA = 1;
     constexpr int S = 4;
     constexpr size_t smem = ((size_t)S * NA * kGroup2 + (AH ? 2 : 1) * Rows2Layout<B>::kHalo +
                              ((AH && REACT) ? 2 * kGroup2 : 0)) * sizeof(float) + S * sizeof(uint64_t);
@@ -1007,6 +1018,11 @@ bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool re
         io.dst[0] = (float *)a.out[0];
         e = (hv != 1 && !a.items) ? launch_rows2_b<kSrc>(a, io, B, react, hv, ctas_per_sm, err_flag, s)
                                   : launch_pipe_b<kSrc, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
+    } else if (dtype == SBG_F32 && ns == 1 && a.eps) {
+        io.src[0] = (const float *)a.in[0];
+        io.src[1] = a.eps;
+        io.dst[0] = (float *)a.out[0];
+        e = launch_pipe_b<kInh, 1>(a, io, B, false, hv, ctas_per_sm, err_flag, s);
     } else if (dtype == SBG_F32 && (ns == 1 || ns == 2)) {
         for (int k = 0; k < ns; ++k) {
             io.src[k] = (const float *)a.in[k];

@@ -27,6 +27,7 @@ from .configs import (  # noqa: F401
     grf256,
     grf_geometry,
     reactive512,
+    inhom512,
     gradient_setup,
     batch_geometries,
 )

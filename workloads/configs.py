@@ -134,6 +134,26 @@ def reactive512(n: int = 512, seed: int = SEED_REACTIVE512, porosity: float = 0.
     return phi, u0, phys
 
 
+def inhom512(n: int = 512, seed: int = SEED_REACTIVE512, porosity: float = 0.40, steps: int = 2000):
+    """Inhomogeneous diffusion of a solute entering from one face (the paper's
+    fertilizer application, Sec. 3.4, on a synthetic packed bed): the
+    reactive512 geometry (Boolean spheres, pore fraction 0.40); one species
+    with diffusivity D * eps(phi) from Eq. 6 with D_min = 0, D_max = 1,
+    gamma2 = 4 per voxel and gamma1 = gamma2 * min(phi over the pore space)
+    (the paper's smoothing parameters, gamma2 = 4 read per grid spacing);
+    c = 1 held on the x = 0 face, 0 elsewhere initially; dt = 0.9 x limit.
+    Returns (phi, u0, physics, (d_min, d_max, gamma1, gamma2))."""
+    phi, count, psi = boolean_sphere_pack(n, 12.0, 0.3, porosity, seed)
+    pore = phi > np.float32(np.finfo(np.float32).eps)
+    g2 = 4.0
+    g1 = g2 * float(phi[pore].min())
+    d, v = _dirichlet_x(lo=1.0)
+    phys = Physics(dims=(n, n, n), dt=DT_PURE_DIFFUSION, D=(1.0, 0.0), dirichlet=d, face_value=v, steps=steps,
+                   extra={"spheres": count, "pore_fraction": psi})
+    u0 = initial_with_faces(phys.dims, 0.0, phys)
+    return phi, u0, phys, (0.0, 1.0, g1, g2)
+
+
 def gradient_setup(n: int = 256, crop: int | None = None, steps: int = 1000, seed: int = SEED_GRF256):
     """Adjoint case on the grf256 geometry (or its [0, crop)^3 corner).
 
