@@ -64,6 +64,7 @@ def _load():
         lib.oracle_adjoint_run.argtypes = [P, P, P, P, I, P, P, D, P, P, D, I64, P, P, P, P]
         lib.oracle_adjoint_run.restype = I
         lib.oracle_eps_sigmoid.argtypes = [P, I64, D, D, D, D, P]
+        lib.oracle_box_sum.argtypes = [P, P, P, P, P, P]
         lib.oracle_step_inhom.argtypes = [P, P, P, P, P, P, P, D, D, D]
         lib.oracle_run_inhom.argtypes = [P, P, P, P, P, P, D, D, D, I64]
         lib.oracle_run_inhom.restype = I
@@ -246,6 +247,25 @@ class Problem:
             raise MemoryError("oracle_adjoint_run: cannot store the state history")
         return lam0, grad, uN
 
+    def box_sum(self, u, lo, hi, species=0):
+        """(sum of u over the active voxels with lo <= (x, y, z) < hi, their count)."""
+        u = self.shape_state(u)
+        out = np.zeros(2)
+        _load().oracle_box_sum(_p(self.dims), _p(self.active), _p(np.ascontiguousarray(u[species])),
+                               _p(np.asarray(lo, dtype=np.int64)), _p(np.asarray(hi, dtype=np.int64)), _p(out))
+        return float(out[0]), int(out[1])
+
+    def frap_curve(self, u0, lo, hi, steps_per_sample, n_samples, species=0):
+        """Simulated FRAP (Sec. 3.3): the box sum of ``u0`` and after every
+        ``steps_per_sample`` steps, ``n_samples + 1`` values, and the box's
+        active-voxel count."""
+        u = self.shape_state(u0)
+        sums = [self.box_sum(u, lo, hi, species)[0]]
+        for _ in range(int(n_samples)):
+            u = self.run(u, steps_per_sample)
+            sums.append(self.box_sum(u, lo, hi, species)[0])
+        return np.array(sums), self.box_sum(u, lo, hi, species)[1]
+
     # -- the gradient workload's loss -------------------------------------------
     def slab_mask(self, x_cut):
         m = np.zeros(self.phi.shape, dtype=bool)
@@ -264,3 +284,27 @@ class Problem:
         lam = np.zeros((self.ns,) + self.phi.shape)
         lam[0][m] = 1.0 / m.sum()
         return lam
+
+
+def frap_fit(t, f, t_ref, f_ref, s_lo=1e-3, s_hi=1.0):
+    """Least-squares time-scale fit of a reference FRAP curve to a measured
+    one (Sec. 3.3: the bulk-box curve fitted to the porous one): the s in
+    [s_lo, s_hi] minimising sum_i (f_i - g(s t_i))^2, g the piecewise-linear
+    interpolant of (t_ref, f_ref).  A dense scan, then scipy's bounded Brent
+    search between the neighbours of the best scan point.  Returns (s, rss)."""
+    from scipy.optimize import minimize_scalar
+
+    t, f = _f64(t), _f64(f)
+    t_ref, f_ref = _f64(t_ref), _f64(f_ref)
+
+    def rss(s):
+        return float(np.sum((f - np.interp(s * t, t_ref, f_ref)) ** 2))
+
+    grid = np.linspace(s_lo, s_hi, 20001)
+    vals = np.array([rss(s) for s in grid])
+    k = int(np.argmin(vals))
+    a, b = grid[max(k - 1, 0)], grid[min(k + 1, grid.size - 1)]
+    r = minimize_scalar(rss, bounds=(a, b), method="bounded", options={"xatol": 1e-13 * s_hi})
+    if r.fun <= vals[k]:
+        return float(r.x), float(r.fun)
+    return float(grid[k]), float(vals[k])

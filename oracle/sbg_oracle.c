@@ -437,6 +437,27 @@ double oracle_steady_cg(const int64_t dims[3], const uint8_t *active, const uint
     return steady_cg(dims, active, fixed, NULL, dx, D, u, tol, maxit, iters);
 }
 
+/* Sum of u over the active voxels of the box lo <= (x, y, z) < hi, and their
+ * count: the mass of the bleached region of a simulated FRAP experiment
+ * (Sec. 3.3, the normalised mass in the initially bleached box).  out[2].   */
+void oracle_box_sum(const int64_t dims[3], const uint8_t *active, const double *u, const int64_t lo[3],
+                    const int64_t hi[3], double *out)
+{
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    ksum m = {0, 0};
+    double cnt = 0.0;
+    for (int64_t z = lo[2] < 0 ? 0 : lo[2]; z < (hi[2] > nz ? nz : hi[2]); ++z)
+        for (int64_t y = lo[1] < 0 ? 0 : lo[1]; y < (hi[1] > ny ? ny : hi[1]); ++y)
+            for (int64_t x = lo[0] < 0 ? 0 : lo[0]; x < (hi[0] > nx ? nx : hi[0]); ++x) {
+                const int64_t i = IDX(x, y, z);
+                if (!active[i]) continue;
+                kadd(&m, u[i]);
+                cnt += 1.0;
+            }
+    out[0] = m.s;
+    out[1] = cnt;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Inhomogeneous diffusion (Eq. 6 and the functor of Appendix B Listing 6;
  * the paper's fertilizer application, Sec. 3.4): one species whose

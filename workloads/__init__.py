@@ -28,6 +28,9 @@ from .configs import (  # noqa: F401
     grf_geometry,
     reactive512,
     inhom512,
+    frap256,
+    centred_box,
+    frap_initial,
     gradient_setup,
     batch_geometries,
 )

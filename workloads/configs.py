@@ -154,6 +154,35 @@ def inhom512(n: int = 512, seed: int = SEED_REACTIVE512, porosity: float = 0.40,
     return phi, u0, phys, (0.0, 1.0, g1, g2)
 
 
+def centred_box(dims, side):
+    """(lo, hi) of the cube of edge ``side`` centred in a box of ``dims`` (x, y, z)."""
+    lo = tuple(max((int(n) - int(side)) // 2, 0) for n in dims)
+    hi = tuple(min(l + int(side), int(n)) for l, n in zip(lo, dims))
+    return lo, hi
+
+
+def frap_initial(shape_zyx, lo, hi) -> np.ndarray:
+    """Bleached initial state: 1 everywhere except 0 in lo <= (x, y, z) < hi."""
+    u0 = np.ones(shape_zyx)
+    u0[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = 0.0
+    return u0
+
+
+def frap256(n: int = 256, seed: int = SEED_GRF256, porosity: float = 0.35, side: int = 64,
+            steps_per_sample: int = 64, samples: int = 64):
+    """Simulated FRAP (Sec. 3.3) in the grf256 geometry: closed box (no-flux
+    on every face), D = 1, dt = 0.15, the centred cube of edge ``side``
+    bleached (u = 0 there, 1 elsewhere), the box mass recorded every
+    ``steps_per_sample`` steps for ``samples`` samples; the bulk reference is
+    the same box with every voxel in the pore space.
+    Returns (phi, u0, physics, lo, hi)."""
+    phi = grf_geometry(n, seed, porosity)
+    phys = Physics(dims=(n, n, n), dt=DT_PURE_DIFFUSION, D=(1.0, 0.0), steps=steps_per_sample * samples,
+                   extra={"steps_per_sample": steps_per_sample, "samples": samples, "side": side})
+    lo, hi = centred_box(phys.dims, side)
+    return phi, frap_initial(phi.shape, lo, hi), phys, lo, hi
+
+
 def gradient_setup(n: int = 256, crop: int | None = None, steps: int = 1000, seed: int = SEED_GRF256):
     """Adjoint case on the grf256 geometry (or its [0, crop)^3 corner).
 
