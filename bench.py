@@ -21,6 +21,7 @@ launch over its average launch time, against the measured HBM copy bandwidth.
 Other workloads print one JSON line each:
   --workload reactive512   two species, surface reaction A -> B, 2000 steps (512^3)
   --workload inhom512      inhomogeneous diffusion (Eq. 6 factor) from one face, 2000 steps (512^3)
+  --workload frap256       simulated FRAP (bleached cube, pore and bulk recovery, D_eff fit) (256^3)
   --workload gradient256   checkpointed adjoint of 1000 steps (256^3): adjoint / forward time,
                            memory, FP64 central-difference checks (--fd)
   --workload batch64       64 uneven geometries: one batched launch per step vs per-geometry
@@ -64,7 +65,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sbg", choices=["sbg", "reference"])
     ap.add_argument("--workload", default="grf256",
-                    choices=["grf256", "reactive512", "inhom512", "gradient256", "batch64"])
+                    choices=["grf256", "reactive512", "inhom512", "frap256", "gradient256", "batch64"])
     ap.add_argument("--n", type=int, default=None, help="box side (default: the workload's)")
     ap.add_argument("--block", type=int, default=4)
     ap.add_argument("--dtype", default="f32r", choices=["f32", "f32x2", "f32r"])
@@ -509,6 +510,80 @@ def run_inhom512(args):
 
 
 # ---------------------------------------------------------------------------
+def run_frap256(args):
+    """Simulated FRAP (Sec. 3.3) in the grf256 geometry: the recovery of a
+    bleached centred cube of edge 64 in the closed pore space and in the bulk
+    box, 16384 steps each with the box mass recorded on the device every 128
+    steps, then the least-squares time-scale fit for D_eff and tau.  One
+    bench line for the whole estimate; the step kernel's algorithmic bytes
+    are 12 B per active voxel (SBG_F32R: d and r read, d written), and its
+    average launch time is taken over both curves (the 258 box sums between
+    the steps included)."""
+    import torch
+    from paper_2304_11165_b300 import Grid, State, make_params
+    from paper_2304_11165_b300.api import frap_fit
+    from paper_2304_11165_b300.frap import recovery
+    from workloads import frap256
+    torch.cuda.set_device(0)
+    n = args.n or 256
+    phi, u0, phys, lo, hi = frap256(n=n)
+    sps, ns = phys.extra["steps_per_sample"], phys.extra["samples"]
+    stream = torch.cuda.current_stream()
+    p = make_params(phys)
+    grids = [Grid(phi, block=args.block, stream=stream),
+             Grid(np.full(phi.shape, 1.0e3, np.float32), block=args.block, stream=stream)]
+    states = [State(g, 1, args.dtype).set_kernel(args.variant) for g in grids]
+    for st in states:  # warm-up (graph capture, clocks), then restart from the bleached state
+        st.set(u0, stream=stream)
+        st.step(p, 3 * sps, stream=stream)
+        st.set(u0, stream=stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t0 = time.perf_counter()
+    ev[0].record(stream)
+    t, F = recovery(states[0], p, lo, hi, sps, ns, phys.dt, stream=stream)
+    ev[1].record(stream)
+    _, Fb = recovery(states[1], p, lo, hi, sps, ns, phys.dt, stream=stream)
+    ev[2].record(stream)
+    s, rss = frap_fit(t, F, t, Fb, 1e-3, 1.0)
+    wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])]
+    steps = sps * ns
+    n_act = [g.n_active for g in grids]
+    updates = sum(n_act) * steps
+    peak, peak_kind = load_peaks()
+    bpv = BYTES_PER_VOXEL[args.dtype]
+    algo_bytes = [na * bpv for na in n_act]
+    achieved = sum(algo_bytes) * steps / (sum(ms) / 1e3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(phi, u0, phys, n_act[0], args.cpu_seconds)
+    emit({"metric": "active-voxel updates/s (simulated FRAP: pore and bulk recovery runs and fit)",
+          "value": updates / wall / 1e9, "unit": "GVox/s", "n_gpus": 1, "steps": 2 * steps,
+          "ms_per_step": wall * 1e3 / (2 * steps), "higher_is_better": True, "dtype": args.dtype,
+          "data": "synthetic",
+          "config": {"workload": "frap256: %d^3 GRF (correlation length 8, porosity 0.35), closed box, D = 1, "
+                                 "dt = 0.15, bleached centred cube of edge %d, %d steps per curve, box mass "
+                                 "every %d steps; bulk reference of the same box"
+                                 % (n, phys.extra["side"], steps, sps),
+                     "block": args.block, "kernel": args.variant, "n_active": n_act,
+                     "timing": "host clock around both curves and the fit (each curve synchronises once)"},
+          "roofline": {"bound": "hbm", "kernel": "k_step_rows2" if args.variant != "prefetch" else "k_step_pipe",
+                       "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "algorithmic_bytes_per_launch": algo_bytes,
+                       "avg_launch_us": [m * 1e3 / steps for m in ms]},
+          "result": {"D_eff": s * phys.D[0], "tau_frap": 1.0 / s, "rss": rss,
+                     "F_end": [float(F[-1]), float(Fb[-1])], "curve_ms": ms},
+          "clocks": clocks, "cpu_baseline": cpu})
+    return 0
+
+
+# ---------------------------------------------------------------------------
 def run_gradient256(args):
     import dataclasses
 
@@ -696,7 +771,7 @@ def main():
     if args.workload != "grf256" and int(os.environ.get("RANK", "0")) != 0:
         return 0
     return {"grf256": run_grf256, "reactive512": run_reactive512, "inhom512": run_inhom512,
-            "gradient256": run_gradient256, "batch64": run_batch64}[args.workload](args)
+            "frap256": run_frap256, "gradient256": run_gradient256, "batch64": run_batch64}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -299,6 +299,42 @@ sbg_status sbg_reduce_noalloc(sbg_grid grid, sbg_state state, const sbg_params *
 /* (For SBG_F32R states sbg_reduce_noalloc only reads the state: no source
  * update, no fold.) */
 
+/* Sum of species `species` over the active voxels of geometry `geom` with
+ * lo <= (x, y, z) < hi (voxel coordinates; the box may extend past the
+ * grid), and their number: out (host, 2 doubles) = {sum u, count}.  The mass
+ * of the bleached region of a simulated FRAP experiment (Sec. 3.3).
+ * Double-float per voxel and warp (FP32-based states) or FP64, then FP64 per
+ * CTA and a fixed-order final sum.  Synchronises `stream`. */
+sbg_status sbg_reduce_box(sbg_grid grid, sbg_state state, int32_t geom, int32_t species, const int64_t lo[3],
+                          const int64_t hi[3], double *out, void *stream);
+
+/* Simulated FRAP (Sec. 3.3): advances `state` by n_samples * steps_per_sample
+ * steps of `params` (exactly as sbg_step) and records the sum of species
+ * `species` over the active voxels of the box lo <= (x, y, z) < hi of
+ * geometry `geom` before the first step and after every steps_per_sample
+ * steps.  sums (host, n_samples + 1 doubles) receives the box sums in order;
+ * count (host, may be NULL) the number of active voxels in the box.  The
+ * sums stay on the device until one copy at the end (no synchronisation
+ * between samples); an even steps_per_sample keeps the cached step graph.
+ * Synchronises `stream`.  Errors: SBG_ERR_INVALID_ARG (bad geometry, species
+ * or counts), those of sbg_step. */
+sbg_status sbg_frap_curve(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom, int32_t species,
+                          const int64_t lo[3], const int64_t hi[3], int64_t steps_per_sample, int32_t n_samples,
+                          double *sums, int64_t *count, void *stream);
+
+/* Least-squares fit of a reference FRAP curve to a measured one over a time
+ * scale (Sec. 3.3: the bulk-box curve fitted to the porous one): the scale s
+ * in [s_lo, s_hi] that minimises sum_i (f[i] - g(s t[i]))^2, g the
+ * piecewise-linear interpolant of (t_ref, f_ref).  A bulk curve at D_ref
+ * evaluated at s t is the bulk curve at s D_ref evaluated at t, so
+ * D_eff = s D_ref.  Host arrays: t, f (n >= 1, t >= 0), t_ref strictly
+ * increasing with t_ref[0] <= s_lo min t and t_ref[m-1] >= s_hi max t
+ * (m >= 2).  A scan of 4001 points, then golden-section search in the best
+ * scan interval.  scale (host) gets s; rss (host, may be NULL) the residual
+ * sum of squares.  Pure host code; no device work. */
+sbg_status sbg_frap_fit(const double *t, const double *f, int64_t n, const double *t_ref, const double *f_ref,
+                        int64_t m, double s_lo, double s_hi, double *scale, double *rss);
+
 /* Effective diffusivity and diffusive tortuosity (Eq. 2: tau = D / D_eff with
  * the pore-space D_eff) from the x-face fluxes of species 0:
  *   D_eff = J L / (dC A), J = (J_in + J_out) / 2, L = (Nx - 1) dx,

@@ -260,6 +260,30 @@ class State:
         keys = ("mass", "J_in", "J_out", "residual", "min", "max", "nonfinite", "n_active")
         return [dict(zip(keys, out[s * NRED:(s + 1) * NRED])) for s in range(self.nspecies)]
 
+    def box_sum(self, lo, hi, species: int = 0, geom: int = 0, stream=None):
+        """(sum of u over the active voxels with lo <= (x, y, z) < hi, their count)."""
+        lo_a = np.asarray(lo, dtype=np.int64)
+        hi_a = np.asarray(hi, dtype=np.int64)
+        out = np.zeros(2)
+        check(self._lib.sbg_reduce_box(self.grid.handle, self.handle, geom, species,
+                                       lo_a.ctypes.data_as(ctypes.c_void_p), hi_a.ctypes.data_as(ctypes.c_void_p),
+                                       out.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)))
+        return float(out[0]), int(out[1])
+
+    def frap_curve(self, params: Params, lo, hi, steps_per_sample: int, n_samples: int, species: int = 0,
+                   geom: int = 0, stream=None):
+        """Box sums before the first step and after every ``steps_per_sample``
+        steps (``n_samples + 1`` values) and the box's active-voxel count."""
+        lo_a = np.asarray(lo, dtype=np.int64)
+        hi_a = np.asarray(hi, dtype=np.int64)
+        sums = np.zeros(int(n_samples) + 1)
+        count = ctypes.c_int64(0)
+        check(self._lib.sbg_frap_curve(self.grid.handle, self.handle, ctypes.byref(params), geom, species,
+                                       lo_a.ctypes.data_as(ctypes.c_void_p), hi_a.ctypes.data_as(ctypes.c_void_p),
+                                       int(steps_per_sample), int(n_samples), sums.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.byref(count), _stream_handle(stream)))
+        return sums, int(count.value)
+
     def effective_D(self, params: Params, geom: int = 0, stream=None):
         d, t, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         check(self._lib.sbg_effective_D(self.grid.handle, self.handle, ctypes.byref(params), geom,
@@ -301,3 +325,21 @@ class State:
             self.close()
         except Exception:
             pass
+
+
+def frap_fit(t, f, t_ref, f_ref, s_lo: float = 1e-3, s_hi: float = 1.0):
+    """(scale s, residual sum of squares) of the least-squares fit of the
+    reference curve g = interp(t_ref, f_ref) to (t, f) over g(s t)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    t_ref = np.ascontiguousarray(t_ref, dtype=np.float64)
+    f_ref = np.ascontiguousarray(f_ref, dtype=np.float64)
+    if t.shape != f.shape or t_ref.shape != f_ref.shape:
+        raise ValueError("frap_fit: times and values differ in length")
+    scale = ctypes.c_double(0.0)
+    rss = ctypes.c_double(0.0)
+    v = ctypes.c_void_p
+    check(load().sbg_frap_fit(t.ctypes.data_as(v), f.ctypes.data_as(v), t.size, t_ref.ctypes.data_as(v),
+                              f_ref.ctypes.data_as(v), t_ref.size, float(s_lo), float(s_hi), ctypes.byref(scale),
+                              ctypes.byref(rss)))
+    return scale.value, rss.value

@@ -152,6 +152,13 @@ sbg_status validate_params(sbg_grid g, const sbg_params *p, int ns);
 // implemented in sbg_reduce.cu
 sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species,
                           int which_buffer, double *out_host, cudaStream_t stream);
+// sum of one species over the active voxels of a box and their count into
+// dst[0..1] (device); kernel launches only
+sbg_status launch_box_sum(sbg_grid g, sbg_state st, int geom, int species, const int64_t lo[3], const int64_t hi[3],
+                          double *dst, cudaStream_t s);
+sbg_status check_box_args(sbg_grid g, sbg_state st, int geom, int species, const char *who);
+// implemented in sbg_step.cu: nsteps steps (graphs, SBG_F32R refreshes); no synchronisation
+sbg_status step_n(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, cudaStream_t s);
 // SBG_F32R: recompute r = L_h (b + d) over every geometry and fold d into b
 // (kernel launches only, no synchronisation)
 sbg_status refresh_source(sbg_grid g, sbg_state st, const sbg_params *p, cudaStream_t stream);

@@ -625,9 +625,123 @@ static sbg_status check_common(sbg_grid g, sbg_state st, const sbg_params *p, in
     return SBG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Sum of u over the active voxels of a box of one geometry (the bleached
+// region of a simulated FRAP experiment, Sec. 3.3): double-float per thread
+// and warp for FP32-based states, FP64 for FP64 states; per-CTA records in the
+// grid's scratch, one fixed-order final pass.
+template <typename T, int VM, int B>
+__global__ void __launch_bounds__(kRedThreads) k_box_sum(const RedArgs a, int4 lo, int4 hi) {
+    constexpr int B3 = B * B * B;
+    DF m = {0.f, 0.f};
+    double md = 0.0;
+    int cnt = 0;
+    const int64_t total = a.b_count * B3;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = a.b_begin + t / B3;
+        const int l = (int)(t % B3);
+        const int4 bc = a.blocks[b];
+        const int x = bc.x * B + l % B, y = bc.y * B + (l / B) % B, z = bc.z * B + l / (B * B);
+        if (x < lo.x || y < lo.y || z < lo.z || x >= hi.x || y >= hi.y || z >= hi.z) continue;
+        const int64_t slot = b * B3 + l;
+        if (sizeof(T) == 8) {
+            const double v = ((const double *)a.val[a.species])[slot];
+            if (is_sent(v)) continue;
+            md += v;
+        } else {
+            float h, lw;
+            if (!load_df<VM>(a, a.species, slot, h, lw)) continue;
+            m = df_add(m, {h, lw});
+        }
+        ++cnt;
+    }
+    __shared__ double sm[kRedThreads / 32][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double v = sizeof(T) == 8 ? warp_sum(md) : df_to_d(df_shfl_add(m));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if (lane == 0) {
+        sm[warp][0] = v;
+        sm[warp][1] = (double)cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double acc = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) acc += sm[w][threadIdx.x];
+        a.partials[(int64_t)blockIdx.x * 2 + threadIdx.x] = acc;
+    }
+}
+
+__global__ void k_box_final(const double *partials, int nctas, double *out) {
+    if (threadIdx.x >= 2) return;
+    double acc = 0.0;
+    for (int c = 0; c < nctas; ++c) acc += partials[(int64_t)c * 2 + threadIdx.x];
+    out[threadIdx.x] = acc;
+}
+
+sbg_status launch_box_sum(sbg_grid g, sbg_state st, int geom, int species, const int64_t lo[3], const int64_t hi[3],
+                          double *dst, cudaStream_t s) {
+    RedArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int sp = 0; sp < st->ns; ++sp) {
+        a.val[sp] = st->val[st->cur][sp];
+        a.lo[sp] = st->lo[st->cur][sp];
+    }
+    a.bh = st->bh;
+    a.bl = st->bl;
+    a.blocks = g->blocks;
+    a.b_begin = g->geom_begin[geom];
+    a.b_count = g->geom_count[geom];
+    a.species = species;
+    a.partials = g->partials;
+    auto clampi = [](int64_t v) { return (int)(v < -1 ? -1 : v > ((int64_t)1 << 30) ? ((int64_t)1 << 30) : v); };
+    const int4 l4 = make_int4(clampi(lo[0]), clampi(lo[1]), clampi(lo[2]), 0);
+    const int4 h4 = make_int4(clampi(hi[0]), clampi(hi[1]), clampi(hi[2]), 0);
+    const int64_t work = a.b_count * g->b3();
+    int nctas = (int)std::min<int64_t>(kRedMaxCtas, (work + kRedThreads - 1) / kRedThreads);
+    if (nctas < 1) nctas = 1;
+#define BOX_LAUNCH(T, VM)                                                                   \
+    do {                                                                                    \
+        if (g->B == 8) k_box_sum<T, VM, 8><<<nctas, kRedThreads, 0, s>>>(a, l4, h4);          \
+        else k_box_sum<T, VM, 4><<<nctas, kRedThreads, 0, s>>>(a, l4, h4);                   \
+    } while (0)
+    if (st->dtype == SBG_F64) BOX_LAUNCH(double, kVF32);
+    else if (st->dtype == SBG_F32) BOX_LAUNCH(float, kVF32);
+    else if (st->dtype == SBG_F32X2) BOX_LAUNCH(float, kVX2);
+    else BOX_LAUNCH(float, kVR);
+#undef BOX_LAUNCH
+    k_box_final<<<1, 32, 0, s>>>(g->partials, nctas, dst);
+    SBG_LAUNCH_CHECK("box sum launch");
+    return SBG_OK;
+}
+
+sbg_status check_box_args(sbg_grid g, sbg_state st, int geom, int species, const char *who) {
+    if (!g || !st) return fail(SBG_ERR_INVALID_ARG, std::string(who) + ": null pointer");
+    if (st->grid != g) return fail(SBG_ERR_INVALID_ARG, std::string(who) + ": state of another grid");
+    if (geom < 0 || geom >= g->n_geoms) return fail(SBG_ERR_INVALID_ARG, std::string(who) + ": bad geometry");
+    if (species < 0 || species >= st->ns) return fail(SBG_ERR_INVALID_ARG, std::string(who) + ": bad species");
+    return SBG_OK;
+}
+
 }  // namespace sbg
 
 using namespace sbg;
+
+extern "C" sbg_status sbg_reduce_box(sbg_grid g, sbg_state st, int32_t geom, int32_t species, const int64_t lo[3],
+                                     const int64_t hi[3], double *out, void *stream) {
+    sbg_status rc = check_box_args(g, st, geom, species, "sbg_reduce_box");
+    if (rc != SBG_OK) return rc;
+    if (!lo || !hi || !out) return fail(SBG_ERR_INVALID_ARG, "sbg_reduce_box: null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = launch_box_sum(g, st, geom, species, lo, hi, g->red_dev, s);
+    if (rc != SBG_OK) return rc;
+    SBG_CUDA(cudaMemcpyAsync(g->red_host, g->red_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SBG_CUDA(cudaStreamSynchronize(s));
+    out[0] = g->red_host[0];
+    out[1] = g->red_host[1];
+    return SBG_OK;
+}
 
 extern "C" sbg_status sbg_reduce(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom,
                                  double *out, void *stream) {

@@ -169,7 +169,7 @@ def frap_initial(shape_zyx, lo, hi) -> np.ndarray:
 
 
 def frap256(n: int = 256, seed: int = SEED_GRF256, porosity: float = 0.35, side: int = 64,
-            steps_per_sample: int = 64, samples: int = 64):
+            steps_per_sample: int = 128, samples: int = 128):
     """Simulated FRAP (Sec. 3.3) in the grf256 geometry: closed box (no-flux
     on every face), D = 1, dt = 0.15, the centred cube of edge ``side``
     bleached (u = 0 there, 1 elsewhere), the box mass recorded every
