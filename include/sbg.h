@@ -215,6 +215,32 @@ sbg_status sbg_state_set(sbg_grid grid, sbg_state state, int32_t geom, int32_t s
 sbg_status sbg_state_get(sbg_grid grid, sbg_state state, int32_t geom, int32_t species,
                          void *dense, int32_t dense_dtype, int32_t on_device, void *stream);
 
+/* External space-time source (the reaction term f(x, t) of Eq. 1 in the
+ * separable form f_s(x, t_n) = a_n S_s(x); the manufactured source of the
+ * verification in Sec. 3.1 and its appendix is S(r) exp(-B t)).
+ * sbg_state_set_source copies the spatial part S of species `species` for
+ * geometry `geom` from a dense [Nz][Ny][Nx] array (SBG_F32 or SBG_F64, host
+ * or device) into a per-slot array of the state's precision (allocated on
+ * first use, 0 on inactive voxels); SBG_F32 and SBG_F64 states only.
+ * Synchronises `stream`.  Errors: SBG_ERR_INVALID_ARG (bad geometry,
+ * species, dtypes, a non-finite value on an active voxel). */
+sbg_status sbg_state_set_source(sbg_grid grid, sbg_state state, int32_t geom, int32_t species,
+                                const void *dense, int32_t dense_dtype, int32_t on_device, void *stream);
+
+/* Frees the source arrays of every species. */
+sbg_status sbg_state_clear_source(sbg_state state);
+
+/* nsteps forward-Euler steps with the source: step n (0-based) computes
+ *   u' = u + dt ( L_h u - decay u -+ k w u_A + a_n S_s ),
+ * a_n = factors[n] (host array of nsteps finite values; a species without a
+ * source adds nothing), the source term rounded as fma(a_n, S_s, transfer).
+ * One launch of the one-thread-per-voxel kernel per step (a_n is a kernel
+ * argument, so no graph is replayed).  Constant D only (no diffusivity
+ * factor).  Asynchronous on `stream`.  Errors: those of sbg_step, and
+ * SBG_ERR_INVALID_ARG for other state types or a non-finite factor. */
+sbg_status sbg_step_source(sbg_grid grid, sbg_state state, const sbg_params *params, int64_t nsteps,
+                           const double *factors, void *stream);
+
 /* Step-kernel choice for a state (this library's tuning knob; no
  * counterpart in the paper).  variant: SBG_KERNEL_AUTO (the pipelined kernel
  * with cp.async halos where it exists, else the one-thread-per-voxel kernel), SBG_KERNEL_PLAIN

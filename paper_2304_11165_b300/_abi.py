@@ -64,6 +64,9 @@ SIGNATURES = [
     ("sbg_grid_set_diffusivity_sigmoid", c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_double, c_double,
                                                    c_double, c_double, c_void_p]),
     ("sbg_grid_clear_diffusivity", c_int32, [c_void_p]),
+    ("sbg_state_set_source", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p]),
+    ("sbg_state_clear_source", c_int32, [c_void_p]),
+    ("sbg_step_source", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     ("sbg_reduce_box", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("sbg_frap_curve", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_int64,
                                  c_int32, c_void_p, c_void_p, c_void_p]),

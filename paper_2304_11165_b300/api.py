@@ -253,6 +253,24 @@ class State:
                                  _stream_handle(stream)))
         return self
 
+    def set_source(self, dense, species: int = 0, geom: int = 0, stream=None):
+        """Spatial part S_s(x) of an external source a_n S_s(x) (dense [Nz, Ny, Nx])."""
+        ptr, code, on_dev, keep = _dense_ptr(dense)
+        check(self._lib.sbg_state_set_source(self.grid.handle, self.handle, geom, species, ptr, code, on_dev,
+                                             _stream_handle(stream)))
+        return self
+
+    def clear_source(self):
+        check(self._lib.sbg_state_clear_source(self.handle))
+        return self
+
+    def step_source(self, params: Params, factors, stream=None):
+        """len(factors) steps; step n adds dt * factors[n] * S_s(x)."""
+        f = np.ascontiguousarray(factors, dtype=np.float64)
+        check(self._lib.sbg_step_source(self.grid.handle, self.handle, ctypes.byref(params), int(f.size),
+                                        f.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)))
+        return self
+
     def reduce(self, params: Params, geom: int = 0, stream=None):
         out = np.zeros(self.nspecies * NRED)
         check(self._lib.sbg_reduce(self.grid.handle, self.handle, ctypes.byref(params), geom,

@@ -141,6 +141,9 @@ struct sbg_state_s {
     float *bh = nullptr, *bl = nullptr, *rsrc = nullptr;
     bool r_valid = false;           // r matches the base of every geometry
     int64_t since_refresh = 0;      // steps since r was recomputed and d folded
+    // external space-time source a_n S_s(x) (sbg_step_source): S_s per slot in
+    // the state's precision, 0 on inactive voxels; null: species without one
+    void *ext[2] = {nullptr, nullptr};
     size_t elem() const { return dtype == SBG_F64 ? 8 : 4; }
 };
 
@@ -157,6 +160,9 @@ sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geo
 sbg_status launch_box_sum(sbg_grid g, sbg_state st, int geom, int species, const int64_t lo[3], const int64_t hi[3],
                           double *dst, cudaStream_t s);
 sbg_status check_box_args(sbg_grid g, sbg_state st, int geom, int species, const char *who);
+// implemented in sbg_step.cu: one step from buffer src with the external
+// source scaled by `scale` (plain kernel; no state bookkeeping)
+sbg_status launch_step_ext(sbg_grid g, sbg_state st, const sbg_params *p, int src, double scale, cudaStream_t s);
 // implemented in sbg_step.cu: nsteps steps (graphs, SBG_F32R refreshes); no synchronisation
 sbg_status step_n(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, cudaStream_t s);
 // SBG_F32R: recompute r = L_h (b + d) over every geometry and fold d into b

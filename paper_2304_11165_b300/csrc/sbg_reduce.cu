@@ -673,11 +673,26 @@ __global__ void __launch_bounds__(kRedThreads) k_box_sum(const RedArgs a, int4 l
     }
 }
 
-__global__ void k_box_final(const double *partials, int nctas, double *out) {
-    if (threadIdx.x >= 2) return;
-    double acc = 0.0;
-    for (int c = 0; c < nctas; ++c) acc += partials[(int64_t)c * 2 + threadIdx.x];
-    out[threadIdx.x] = acc;
+// 256 threads: strided partial sums, then a fixed tree (deterministic for a
+// given CTA count)
+__global__ void __launch_bounds__(256) k_box_final(const double *partials, int nctas, double *out) {
+    __shared__ double sm[2][256];
+    double a0 = 0.0, a1 = 0.0;
+    for (int c = threadIdx.x; c < nctas; c += 256) {
+        a0 += partials[(int64_t)c * 2];
+        a1 += partials[(int64_t)c * 2 + 1];
+    }
+    sm[0][threadIdx.x] = a0;
+    sm[1][threadIdx.x] = a1;
+    __syncthreads();
+    for (int stride = 128; stride > 0; stride >>= 1) {
+        if ((int)threadIdx.x < stride) {
+            sm[0][threadIdx.x] += sm[0][threadIdx.x + stride];
+            sm[1][threadIdx.x] += sm[1][threadIdx.x + stride];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 2) out[threadIdx.x] = sm[threadIdx.x][0];
 }
 
 sbg_status launch_box_sum(sbg_grid g, sbg_state st, int geom, int species, const int64_t lo[3], const int64_t hi[3],
@@ -711,7 +726,7 @@ sbg_status launch_box_sum(sbg_grid g, sbg_state st, int geom, int species, const
     else if (st->dtype == SBG_F32X2) BOX_LAUNCH(float, kVX2);
     else BOX_LAUNCH(float, kVR);
 #undef BOX_LAUNCH
-    k_box_final<<<1, 32, 0, s>>>(g->partials, nctas, dst);
+    k_box_final<<<1, 256, 0, s>>>(g->partials, nctas, dst);
     SBG_LAUNCH_CHECK("box sum launch");
     return SBG_OK;
 }

@@ -229,6 +229,8 @@ extern "C" sbg_status sbg_state_copy(sbg_state dst, sbg_state src, void *stream)
 extern "C" void sbg_state_destroy(sbg_state st) {
     if (!st) return;
     if (st->graph) cudaGraphExecDestroy(st->graph);
+    cudaFree(st->ext[0]);
+    cudaFree(st->ext[1]);
     cudaFree(st->base);
     delete st;
 }

@@ -26,7 +26,9 @@ namespace sbg {
 // SRC: the correction d of an SBG_F32R state (one FP32 species), whose update
 // takes the stored source r = L_h b in place of the transfer term and the
 // surface loss k w in its rate.
-template <typename T, int B, int BPC, int NS, bool REACT, bool SRC = false>
+// EXT: an external space-time source a_n S_s(x) joins the transfer term
+// (rounded as fma(a_n, S_s, t)).
+template <typename T, int B, int BPC, int NS, bool REACT, bool SRC = false, bool EXT = false>
 __global__ void __launch_bounds__(BPC * B * B * B, (sizeof(T) == 8 ? 1024 : 2048) / (BPC * B * B * B))
 k_step(const StepArgs a) {
     constexpr int B3 = B * B * B;
@@ -95,8 +97,9 @@ k_step(const StepArgs a) {
             const T yp = mirror(y < B - 1 ? t[l + B] : hyp[s], u);
             const T zm = mirror(z > 0 ? t[l - B * B] : hzm[s], u);
             const T zp = mirror(z < B - 1 ? t[l + B * B] : hzp[s], u);
-            res = fused_update(u, xm, xp, ym, yp, zm, zp, k.c[s], k.dt, k.decay[s],
-                               s == 0 ? -transfer : transfer);
+            T tt = s == 0 ? -transfer : transfer;
+            if (EXT && a.ext[s]) tt = fma_pinned((T)a.ext_scale, ((const T *)a.ext[s])[b * B3 + l], tt);
+            res = fused_update(u, xm, xp, ym, yp, zm, zp, k.c[s], k.dt, k.decay[s], tt);
         }
         ((T *)a.out[s])[b * B3 + l] = res;
     }
@@ -266,12 +269,12 @@ static void fill_args(sbg_grid g, sbg_state st, const sbg_params *p, int src, St
     a.src_term = st->rsrc;
 }
 
-template <typename T, int B, int NS, bool SRC = false>
+template <typename T, int B, int NS, bool SRC = false, bool EXT = false>
 static void launch_plain(const StepArgs &a, bool react, cudaStream_t s) {
     constexpr int BPC = (B == 8) ? 1 : 8;
     const unsigned grid = (unsigned)((a.nb + BPC - 1) / BPC);
-    if (react) k_step<T, B, BPC, NS, true, SRC><<<grid, BPC * B * B * B, 0, s>>>(a);
-    else k_step<T, B, BPC, NS, false, SRC><<<grid, BPC * B * B * B, 0, s>>>(a);
+    if (react) k_step<T, B, BPC, NS, true, SRC, EXT><<<grid, BPC * B * B * B, 0, s>>>(a);
+    else k_step<T, B, BPC, NS, false, SRC, EXT><<<grid, BPC * B * B * B, 0, s>>>(a);
 }
 
 // Plain kernel for inhomogeneous diffusion (one species, FP32 or FP64): the
@@ -402,6 +405,41 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
         }
     }
     SBG_LAUNCH_CHECK("step kernel launch");
+    return SBG_OK;
+}
+
+// One step with the external source of the state scaled by `scale` (plain
+// kernel, SBG_F32 / SBG_F64 states, constant D).
+sbg_status launch_step_ext(sbg_grid g, sbg_state st, const sbg_params *p, int src, double scale, cudaStream_t s) {
+    if (g->nb == 0) return SBG_OK;
+    StepArgs a;
+    fill_args(g, st, p, src, a);
+    if (a.held_mask && !a.heldbits) return fail(SBG_ERR_INVALID_ARG, "internal: held bits not prepared");
+    if (a.eps) return fail(SBG_ERR_INVALID_ARG, "an external source with a diffusivity factor is not supported");
+    a.ext[0] = st->ext[0];
+    a.ext[1] = st->ext[1];
+    a.ext_scale = scale;
+    const bool react = p->k_surf != 0.0;
+    if (st->dtype == SBG_F32) {
+        if (g->B == 8) {
+            if (st->ns == 1) launch_plain<float, 8, 1, false, true>(a, react, s);
+            else launch_plain<float, 8, 2, false, true>(a, react, s);
+        } else {
+            if (st->ns == 1) launch_plain<float, 4, 1, false, true>(a, react, s);
+            else launch_plain<float, 4, 2, false, true>(a, react, s);
+        }
+    } else if (st->dtype == SBG_F64) {
+        if (g->B == 8) {
+            if (st->ns == 1) launch_plain<double, 8, 1, false, true>(a, react, s);
+            else launch_plain<double, 8, 2, false, true>(a, react, s);
+        } else {
+            if (st->ns == 1) launch_plain<double, 4, 1, false, true>(a, react, s);
+            else launch_plain<double, 4, 2, false, true>(a, react, s);
+        }
+    } else {
+        return fail(SBG_ERR_INVALID_ARG, "an external source needs an SBG_F32 or SBG_F64 state");
+    }
+    SBG_LAUNCH_CHECK("step kernel launch (external source)");
     return SBG_OK;
 }
 

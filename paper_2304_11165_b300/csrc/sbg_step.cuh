@@ -31,6 +31,8 @@ struct StepArgs {
     const double *eps64;     //   the same in FP64
     const int64_t *items;    // optional work list for the pipelined kernel: (first block, count)
     int64_t nitems;          //   pairs, each within one geometry and at most 512 voxels
+    const void *ext[2];      // external source S_s per slot (state precision; null: none)
+    double ext_scale;        //   its time factor a_n for this step: the term a_n S_s(x)
     int held_mask;           // bit f: face f is Dirichlet
     StepCoef<float> cf;
     StepCoef<double> cd;
@@ -80,6 +82,9 @@ __device__ __forceinline__ double fused_update(double u, double xm, double xp, d
     const double react = __fma_rn(-decay, u, t);
     return __fma_rn(dt, __dadd_rn(lap, react), u);
 }
+
+__device__ __forceinline__ float fma_pinned(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_pinned(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Inhomogeneous diffusion (the functor of Appendix B Listing 6): given the
 // one-sided differences dp_a = u~_{+a} - u and dm_a = u - u~_{-a} (0 towards a

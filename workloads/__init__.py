@@ -31,6 +31,7 @@ from .configs import (  # noqa: F401
     frap256,
     centred_box,
     frap_initial,
+    mms_disk,
     gradient_setup,
     batch_geometries,
 )

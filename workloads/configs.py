@@ -183,6 +183,27 @@ def frap256(n: int = 256, seed: int = SEED_GRF256, porosity: float = 0.35, side:
     return phi, frap_initial(phi.shape, lo, hi), phys, lo, hi
 
 
+def mms_disk(n: int, B: float = 20.0, t_final: float = 0.025, dt_over_h2: float = 0.125):
+    """The verification case of Sec. 3.1: diffusion (D = 1) inside the unit
+    disk, no flux on r = 1, on an n x n grid of cell centres covering
+    [-2, 2]^2 (nz = 1), phi = 1 - r (exact SDF), u0 = r^3/3 - r^4/4, and the
+    manufactured source of the appendix, S(r) exp(-B t) with
+    S = B r^4 / 4 - B r^3 / 3 + 4 r^2 - 3 r; dt = t_final / ceil(t_final /
+    (dt_over_h2 h^2)).  Returns (phi [1, n, n], u0, S, r, physics, nsteps)."""
+    h = 4.0 / n
+    c = -2.0 + (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    r = np.sqrt(X ** 2 + Y ** 2)
+    phi = (1.0 - r).astype(np.float32)[None]
+    nsteps = int(np.ceil(t_final / (dt_over_h2 * h * h)))
+    dt = t_final / nsteps
+    phys = Physics(dims=(n, n, 1), dt=dt, D=(1.0, 0.0), dx=(h, h, 1.0), steps=nsteps,
+                   extra={"B": B, "t_final": t_final, "h": h})
+    u0 = (r ** 3 / 3 - r ** 4 / 4)[None]
+    S = (B / 4 * r ** 4 - B / 3 * r ** 3 + 4 * r ** 2 - 3 * r)[None]
+    return phi, u0, S, r, phys, nsteps
+
+
 def gradient_setup(n: int = 256, crop: int | None = None, steps: int = 1000, seed: int = SEED_GRF256):
     """Adjoint case on the grf256 geometry (or its [0, crop)^3 corner).
 
