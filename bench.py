@@ -22,6 +22,7 @@ Other workloads print one JSON line each:
   --workload reactive512   two species, surface reaction A -> B, 2000 steps (512^3)
   --workload inhom512      inhomogeneous diffusion (Eq. 6 factor) from one face, 2000 steps (512^3)
   --workload frap256       simulated FRAP (bleached cube, pore and bulk recovery, D_eff fit) (256^3)
+  --workload mms           the unit-disk manufactured solution of Sec. 3.1, 32^2..1024^2, errors and orders
   --workload gradient256   checkpointed adjoint of 1000 steps (256^3): adjoint / forward time,
                            memory, FP64 central-difference checks (--fd)
   --workload batch64       64 uneven geometries: one batched launch per step vs per-geometry
@@ -65,7 +66,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sbg", choices=["sbg", "reference"])
     ap.add_argument("--workload", default="grf256",
-                    choices=["grf256", "reactive512", "inhom512", "frap256", "gradient256", "batch64"])
+                    choices=["grf256", "reactive512", "inhom512", "frap256", "mms", "gradient256", "batch64"])
     ap.add_argument("--n", type=int, default=None, help="box side (default: the workload's)")
     ap.add_argument("--block", type=int, default=4)
     ap.add_argument("--dtype", default="f32r", choices=["f32", "f32x2", "f32r"])
@@ -584,6 +585,62 @@ def run_frap256(args):
 
 
 # ---------------------------------------------------------------------------
+def run_mms(args):
+    """The verification case of Sec. 3.1 (unit disk, no flux on r = 1, the
+    appendix's manufactured source S(r) exp(-B t), dt = h^2/8, t = 0.025) on
+    grids of 32^2 to 1024^2 in FP32 and FP64 through the external-source
+    step: L2 and Linf errors against the exact solution and the observed
+    orders.  `value` is the FP32 L2 order between the two finest grids (the
+    paper reports about 1.5 for its FP32 runs)."""
+    import math
+    import torch
+    from paper_2304_11165_b300 import Grid, State, make_params
+    from workloads import mms_disk
+    torch.cuda.set_device(0)
+    sizes = [32, 64, 128, 256, 512, 1024]
+    table = {}
+    total_ms = 0.0
+    total_updates = 0
+    for dtype in ("f32", "f64"):
+        rows = []
+        for n in sizes:
+            phi, u0, S, r, phys, nsteps = mms_disk(n)
+            B, t_end = phys.extra["B"], phys.extra["t_final"]
+            fac = np.array([math.exp(-B * k * phys.dt) for k in range(nsteps)])
+            g = Grid(phi, block=args.block)
+            st = State(g, 1, dtype).set(u0).set_source(S)
+            p = make_params(phys)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st.step_source(p, fac)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3
+            u = st.get()[0]
+            exact = (r ** 3 / 3 - r ** 4 / 4) * math.exp(-B * t_end)
+            act = phi[0] > np.finfo(np.float32).eps
+            e = u[act] - exact[act]
+            rows.append({"n": n, "steps": nsteps, "l2": float(math.sqrt(np.mean(e ** 2))),
+                         "linf": float(np.max(np.abs(e))), "ms": ms})
+            total_ms += ms
+            total_updates += int(act.sum()) * nsteps
+            st.close()
+            g.close()
+        for i in range(1, len(rows)):
+            rows[i]["order_l2"] = math.log(rows[i - 1]["l2"] / rows[i]["l2"], 2.0)
+            rows[i]["order_linf"] = math.log(rows[i - 1]["linf"] / rows[i]["linf"], 2.0)
+        table[dtype] = rows
+    emit({"metric": "L2 error order, unit-disk manufactured solution (Sec. 3.1)",
+          "value": table["f32"][-1]["order_l2"], "unit": "order", "n_gpus": 1,
+          "steps": sum(r["steps"] for r in table["f32"]), "higher_is_better": True, "dtype": "f32",
+          "data": "synthetic",
+          "config": {"workload": "mms_disk: unit disk in [-2, 2]^2, n^2 cell centres, n = 32..1024, D = 1, "
+                                 "dt = h^2/8, t = 0.025, B = 20, exact SDF", "block": args.block,
+                     "kernel": "plain (one launch per step: the source factor is a kernel argument)"},
+          "result": table, "throughput_gvox_s": total_updates / (total_ms / 1e3) / 1e9})
+    return 0
+
+
+# ---------------------------------------------------------------------------
 def run_gradient256(args):
     import dataclasses
 
@@ -771,7 +828,7 @@ def main():
     if args.workload != "grf256" and int(os.environ.get("RANK", "0")) != 0:
         return 0
     return {"grf256": run_grf256, "reactive512": run_reactive512, "inhom512": run_inhom512,
-            "frap256": run_frap256, "gradient256": run_gradient256, "batch64": run_batch64}[args.workload](args)
+            "frap256": run_frap256, "mms": run_mms, "gradient256": run_gradient256, "batch64": run_batch64}[args.workload](args)
 
 
 if __name__ == "__main__":

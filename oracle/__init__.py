@@ -65,6 +65,9 @@ def _load():
         lib.oracle_adjoint_run.restype = I
         lib.oracle_eps_sigmoid.argtypes = [P, I64, D, D, D, D, P]
         lib.oracle_box_sum.argtypes = [P, P, P, P, P, P]
+        lib.oracle_sussman.argtypes = [P, P, P, D, I64, P]
+        lib.oracle_sussman.restype = I
+        lib.oracle_upwind_grad.argtypes = [P, P, P, P]
         lib.oracle_step_inhom.argtypes = [P, P, P, P, P, P, P, D, D, D]
         lib.oracle_run_inhom.argtypes = [P, P, P, P, P, P, D, D, D, I64]
         lib.oracle_run_inhom.restype = I
@@ -308,3 +311,26 @@ def frap_fit(t, f, t_ref, f_ref, s_lo=1e-3, s_hi=1.0):
     if r.fun <= vals[k]:
         return float(r.x), float(r.fun)
     return float(grid[k]), float(vals[k])
+
+
+def sussman(phi0, dx=(1.0, 1.0, 1.0), cfl=0.3, iters=100):
+    """Sussman redistancing (Sec. 2.1): ``iters`` forward-Euler iterations of
+    the redistancing PDE with the smoothed sign and first-order Godunov
+    differences; dalpha = cfl * min(dx).  phi0: dense [Nz, Ny, Nx]."""
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    nz, ny, nx = phi0.shape
+    out = np.empty_like(phi0)
+    rc = _load().oracle_sussman(_p(np.array([nx, ny, nz], dtype=np.int64)), _p(_f64(dx)), _p(phi0), float(cfl),
+                                int(iters), _p(out))
+    if rc != 0:
+        raise MemoryError("oracle_sussman: allocation failed")
+    return out
+
+
+def upwind_grad(phi, dx=(1.0, 1.0, 1.0)):
+    """The Godunov |grad phi| per voxel for the sign of phi there."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    nz, ny, nx = phi.shape
+    out = np.empty_like(phi)
+    _load().oracle_upwind_grad(_p(np.array([nx, ny, nz], dtype=np.int64)), _p(_f64(dx)), _p(phi), _p(out))
+    return out

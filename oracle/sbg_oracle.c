@@ -677,3 +677,90 @@ int oracle_adjoint_run(const int64_t dims[3], const uint8_t *active, const uint8
     free(hist); free(la); free(lb);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sussman redistancing (Sec. 2.1, the redistancing PDE with the smoothed
+ * sign of Peng et al.): phi is driven to the steady state of
+ *   d phi / d alpha = sigma(phi) (1 - |grad phi|),
+ *   sigma(phi) = phi / sqrt(phi^2 + |grad phi|^2 h^2),
+ * by forward Euler in the artificial time alpha with first-order upwind
+ * (Godunov) differences, the scheme the paper uses for its results.
+ * Readings: |grad phi| is the Godunov magnitude for the sign of phi at the
+ * voxel, and the same magnitude enters sigma; h = min(dx); a neighbour beyond
+ * the box takes the voxel's own value (zero gradient); a voxel with phi = 0
+ * does not move; every voxel is updated from the previous iterate (Jacobi).
+ *   D-_a = (phi_i - phi_{i-a}) / dx_a,  D+_a = (phi_{i+a} - phi_i) / dx_a,
+ *   phi > 0: G^2 = sum_a max(max(D-_a, 0)^2, min(D+_a, 0)^2),
+ *   phi < 0: G^2 = sum_a max(min(D-_a, 0)^2, max(D+_a, 0)^2),
+ *   phi' = phi + dalpha sigma (1 - G).                                       */
+static double godunov_mag(const double *p, int64_t nx, int64_t ny, int64_t nz, int64_t x, int64_t y,
+                          int64_t z, const double dx[3])
+{
+    const double c = p[IDX(x, y, z)];
+    const int64_t lo[3] = {x > 0 ? x - 1 : x, y > 0 ? y - 1 : y, z > 0 ? z - 1 : z};
+    const int64_t hi[3] = {x < nx - 1 ? x + 1 : x, y < ny - 1 ? y + 1 : y, z < nz - 1 ? z + 1 : z};
+    const double vm[3] = {p[IDX(lo[0], y, z)], p[IDX(x, lo[1], z)], p[IDX(x, y, lo[2])]};
+    const double vp[3] = {p[IDX(hi[0], y, z)], p[IDX(x, hi[1], z)], p[IDX(x, y, hi[2])]};
+    double g2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double dm = (c - vm[a]) / dx[a];
+        const double dp = (vp[a] - c) / dx[a];
+        double s1, s2;
+        if (c > 0.0) {
+            s1 = dm > 0.0 ? dm : 0.0;
+            s2 = dp < 0.0 ? dp : 0.0;
+        } else {
+            s1 = dm < 0.0 ? dm : 0.0;
+            s2 = dp > 0.0 ? dp : 0.0;
+        }
+        const double q1 = s1 * s1, q2 = s2 * s2;
+        g2 += q1 > q2 ? q1 : q2;
+    }
+    return sqrt(g2);
+}
+
+/* `iters` iterations from phi0 into out (both dense [Nz][Ny][Nx]); dalpha =
+ * cfl * min(dx).  Returns 0, or -1 when the work array cannot be allocated. */
+int oracle_sussman(const int64_t dims[3], const double dx[3], const double *phi0, double cfl, int64_t iters,
+                   double *out)
+{
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    const int64_t n = nx * ny * nz;
+    double h = dx[0];
+    if (dx[1] < h) h = dx[1];
+    if (dx[2] < h) h = dx[2];
+    const double dalpha = cfl * h;
+    double *a = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!a) return -1;
+    memcpy(a, phi0, sizeof(double) * (size_t)n);
+    for (int64_t it = 0; it < iters; ++it) {
+#pragma omp parallel for schedule(static)
+        for (int64_t z = 0; z < nz; ++z)
+            for (int64_t y = 0; y < ny; ++y)
+                for (int64_t x = 0; x < nx; ++x) {
+                    const double c = a[IDX(x, y, z)];
+                    if (c == 0.0) {
+                        out[IDX(x, y, z)] = c;
+                        continue;
+                    }
+                    const double g = godunov_mag(a, nx, ny, nz, x, y, z, dx);
+                    const double sigma = c / sqrt(c * c + g * g * h * h);
+                    out[IDX(x, y, z)] = c + dalpha * sigma * (1.0 - g);
+                }
+        memcpy(a, out, sizeof(double) * (size_t)n);
+    }
+    memcpy(out, a, sizeof(double) * (size_t)n);
+    free(a);
+    return 0;
+}
+
+/* The Godunov magnitude |grad phi| per voxel (the quantity the steady state
+ * drives to 1), for the pins. */
+void oracle_upwind_grad(const int64_t dims[3], const double dx[3], const double *phi, double *out)
+{
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) out[IDX(x, y, z)] = godunov_mag(phi, nx, ny, nz, x, y, z, dx);
+}
