@@ -23,6 +23,7 @@ Other workloads print one JSON line each:
   --workload inhom512      inhomogeneous diffusion (Eq. 6 factor) from one face, 2000 steps (512^3)
   --workload frap256       simulated FRAP (bleached cube, pore and bulk recovery, D_eff fit) (256^3)
   --workload mms           the unit-disk manufactured solution of Sec. 3.1, 32^2..1024^2, errors and orders
+  --workload redist512     Sussman redistancing of a 512^3 indicator on the device (200 iterations)
   --workload gradient256   checkpointed adjoint of 1000 steps (256^3): adjoint / forward time,
                            memory, FP64 central-difference checks (--fd)
   --workload batch64       64 uneven geometries: one batched launch per step vs per-geometry
@@ -66,7 +67,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sbg", choices=["sbg", "reference"])
     ap.add_argument("--workload", default="grf256",
-                    choices=["grf256", "reactive512", "inhom512", "frap256", "mms", "gradient256", "batch64"])
+                    choices=["grf256", "reactive512", "inhom512", "frap256", "mms", "redist512", "gradient256",
+                             "batch64"])
     ap.add_argument("--n", type=int, default=None, help="box side (default: the workload's)")
     ap.add_argument("--block", type=int, default=4)
     ap.add_argument("--dtype", default="f32r", choices=["f32", "f32x2", "f32r"])
@@ -590,7 +592,7 @@ def run_mms(args):
     appendix's manufactured source S(r) exp(-B t), dt = h^2/8, t = 0.025) on
     grids of 32^2 to 1024^2 in FP32 and FP64 through the external-source
     step: L2 and Linf errors against the exact solution and the observed
-    orders.  `value` is the FP32 L2 order between the two finest grids (the
+    orders.  `value` is the least-squares FP32 L2 order over all grids (the
     paper reports about 1.5 for its FP32 runs)."""
     import math
     import torch
@@ -629,14 +631,77 @@ def run_mms(args):
             rows[i]["order_l2"] = math.log(rows[i - 1]["l2"] / rows[i]["l2"], 2.0)
             rows[i]["order_linf"] = math.log(rows[i - 1]["linf"] / rows[i]["linf"], 2.0)
         table[dtype] = rows
+    # least-squares slope of log2(L2 error) against log2(1/h) over all grids
+    ln = np.log2(np.array(sizes, dtype=float))
+    le = np.log2(np.array([r["l2"] for r in table["f32"]]))
+    order = float(-np.polyfit(ln, le, 1)[0])
     emit({"metric": "L2 error order, unit-disk manufactured solution (Sec. 3.1)",
-          "value": table["f32"][-1]["order_l2"], "unit": "order", "n_gpus": 1,
+          "value": order, "unit": "order", "n_gpus": 1,
           "steps": sum(r["steps"] for r in table["f32"]), "higher_is_better": True, "dtype": "f32",
           "data": "synthetic",
           "config": {"workload": "mms_disk: unit disk in [-2, 2]^2, n^2 cell centres, n = 32..1024, D = 1, "
                                  "dt = h^2/8, t = 0.025, B = 20, exact SDF", "block": args.block,
                      "kernel": "plain (one launch per step: the source factor is a kernel argument)"},
           "result": table, "throughput_gvox_s": total_updates / (total_ms / 1e3) / 1e9})
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_redist512(args):
+    """Sussman redistancing on the device of the binary indicator (+1 pore,
+    -1 solid) of a 512^3 GRF pore space (correlation length 8, porosity
+    0.35), FP32, 200 iterations at cfl 0.3 with the band test every 16.
+    Metric: voxel updates per second.  Algorithmic bytes per iteration: the
+    field read once and written once, 8 B per voxel (the neighbours come from
+    L1/L2)."""
+    import torch
+    from paper_2304_11165_b300 import redistance
+    from workloads import gaussian_random_field, threshold_to_porosity
+    from workloads.configs import SEED_GRF256
+    torch.cuda.set_device(0)
+    n = args.n or 512
+    iters = 200
+    pore = threshold_to_porosity(gaussian_random_field((n, n, n), 8.0, SEED_GRF256), 0.35)
+    ind_host = np.where(pore, 1.0, -1.0).astype(np.float32)
+    ind = torch.from_numpy(ind_host).cuda()
+    stream = torch.cuda.current_stream()
+    redistance(ind, max_iter=3 * 16, stream=stream)  # warm-up
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    phi, it, res = redistance(ind, max_iter=iters, check_every=16, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = a.elapsed_time(b)
+    nvox = n ** 3
+    per_iter_ms = ms / it
+    algo_bytes = 8 * nvox
+    peak, peak_kind = load_peaks()
+    achieved = algo_bytes / (per_iter_ms / 1e3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.sussman(ind_host, iters=1)
+        dt = time.perf_counter() - t0
+        cpu = {"value": nvox / dt / 1e9, "unit": "GVox/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "one FP64 dense iteration of the full %d^3 field" % n}
+    emit({"metric": "voxel updates/s (Sussman redistancing, FP32, dense on the device)",
+          "value": nvox * it / (ms / 1e3) / 1e9, "unit": "GVox/s", "n_gpus": 1, "steps": it,
+          "ms_per_step": per_iter_ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+          "config": {"workload": "redist512: indicator (+1 pore / -1 solid) of a %d^3 GRF (correlation length 8, "
+                                 "porosity 0.35), cfl 0.3, %d iterations, band test every 16" % (n, iters),
+                     "l2": "the 0.5 GB field pair exceeds the 126 MB L2"},
+          "roofline": {"bound": "hbm", "kernel": "k_sussman", "achieved": achieved, "peak": peak,
+                       "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                       "traffic": profile_traffic("k_sussman_redist512.md"),
+                       "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": per_iter_ms * 1e3},
+          "result": {"iterations": it, "last_residual": res,
+                     "phi_range": [float(phi.min().item()), float(phi.max().item())]},
+          "clocks": clocks, "cpu_baseline": cpu})
     return 0
 
 
@@ -828,7 +893,8 @@ def main():
     if args.workload != "grf256" and int(os.environ.get("RANK", "0")) != 0:
         return 0
     return {"grf256": run_grf256, "reactive512": run_reactive512, "inhom512": run_inhom512,
-            "frap256": run_frap256, "mms": run_mms, "gradient256": run_gradient256, "batch64": run_batch64}[args.workload](args)
+            "frap256": run_frap256, "mms": run_mms, "redist512": run_redist512,
+            "gradient256": run_gradient256, "batch64": run_batch64}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -428,6 +428,36 @@ sbg_status sbg_adjoint(sbg_grid grid, sbg_tape tape, sbg_state lam, double *grad
 sbg_status sbg_tape_info(sbg_tape tape, int64_t *device_bytes, int64_t *n_checkpoints);
 void sbg_tape_destroy(sbg_tape tape);
 
+/* ---- level set: Sussman redistancing --------------------------------------------- */
+
+typedef struct {
+    double cfl;               /* dalpha = cfl * min(dx); cfl * min(dx) * sum_a 1/dx_a <= 1      */
+    int64_t max_iter;         /* iterations at most                                            */
+    double tol;               /* stop at a test where max |sigma (1 - G)| over voxels with
+                                 |phi| < band * min(dx) is below tol (<= 0: run max_iter)       */
+    double band;              /* half-width of that test's band, in units of min(dx); > 0       */
+    int32_t check_every;      /* iterations between tests (the last iteration always tests)     */
+} sbg_redist_opts;
+
+/* Sussman redistancing (Sec. 2.1): drives phi towards the signed distance to
+ * its zero level set as the steady state of
+ *   d phi / d alpha = sigma(phi) (1 - |grad phi|),
+ *   sigma(phi) = phi / sqrt(phi^2 + |grad phi|^2 h^2),  h = min(dx),
+ * by forward Euler in alpha with first-order upwind (Godunov) differences for
+ * the sign of phi at each voxel, every voxel from the previous iterate, a
+ * neighbour beyond the box taking the voxel's own value.  phi = 0 stays 0
+ * and no voxel changes sign.  phi_in / phi_out: dense [Nz][Ny][Nx] of dtype
+ * (SBG_F32 or SBG_F64; the arithmetic is in that precision), both host
+ * (on_device 0; distinct arrays) or both device (on_device 1; may be the same
+ * array).  iters_out, residual_out (host, may be NULL): iterations run and
+ * the last tested max |sigma (1 - G)| (NaN when none ran).  The field lives
+ * dense on the device with one ping-pong copy; one stencil pass per
+ * iteration.  Synchronises `stream`.  Errors: SBG_ERR_INVALID_ARG (dims
+ * outside [1, 2^20], dx <= 0, bad options or cfl), SBG_ERR_CUDA. */
+sbg_status sbg_redistance(const int64_t dims[3], const double dx[3], const void *phi_in, void *phi_out,
+                          int32_t dtype, int32_t on_device, const sbg_redist_opts *opts, int64_t *iters_out,
+                          double *residual_out, void *stream);
+
 /* ---- errors -------------------------------------------------------------------- */
 const char *sbg_last_error(void);            /* thread-local; "" when none                      */
 const char *sbg_status_string(sbg_status s);

@@ -9,4 +9,4 @@ tortuosity.  All compute runs in the hand-written CUDA kernels of
 ``libsbg.so`` behind the C ABI of ``include/sbg.h``.
 """
 from ._abi import SbgError, load  # noqa: F401
-from .api import Grid, State, make_params, stability_limit  # noqa: F401
+from .api import Grid, State, make_params, redistance, stability_limit  # noqa: F401

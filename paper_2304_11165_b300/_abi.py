@@ -39,6 +39,11 @@ class BuildOpts(ctypes.Structure):
                 ("band_eps", c_float)]
 
 
+class RedistOpts(ctypes.Structure):
+    _fields_ = [("cfl", c_double), ("max_iter", c_int64), ("tol", c_double), ("band", c_double),
+                ("check_every", c_int32)]
+
+
 class Params(ctypes.Structure):
     _fields_ = [("dx", c_double * 3), ("dt", c_double), ("nspecies", c_int32),
                 ("face_type", c_int32 * 6), ("D", c_double * 2), ("decay", c_double * 2),
@@ -67,6 +72,8 @@ SIGNATURES = [
     ("sbg_state_set_source", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p]),
     ("sbg_state_clear_source", c_int32, [c_void_p]),
     ("sbg_step_source", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+    ("sbg_redistance", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
+                                 c_void_p, c_void_p]),
     ("sbg_reduce_box", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("sbg_frap_curve", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_int64,
                                  c_int32, c_void_p, c_void_p, c_void_p]),

@@ -361,3 +361,39 @@ def frap_fit(t, f, t_ref, f_ref, s_lo: float = 1e-3, s_hi: float = 1.0):
                               f_ref.ctypes.data_as(v), t_ref.size, float(s_lo), float(s_hi), ctypes.byref(scale),
                               ctypes.byref(rss)))
     return scale.value, rss.value
+
+
+def redistance(phi0, dx=(1.0, 1.0, 1.0), cfl: float = 0.3, max_iter: int = 200, tol: float = 0.0,
+               band: float = 2.0, check_every: int = 16, stream=None):
+    """Sussman redistancing of a dense [Nz, Ny, Nx] level set on the device
+    (``sbg_redistance``).  A float32/float64 numpy array gives a numpy array
+    back, a CUDA tensor a CUDA tensor of the same dtype.  Returns
+    (phi, iterations, last tested residual)."""
+    try:
+        import torch
+        is_tensor = isinstance(phi0, torch.Tensor)
+    except ImportError:
+        is_tensor = False
+    if is_tensor:
+        src = phi0.contiguous()
+        if src.dtype not in (torch.float32, torch.float64) or not src.is_cuda:
+            raise TypeError("redistance: CUDA float32/float64 tensors only")
+        out = torch.empty_like(src)
+        code = _abi.SBG_F64 if src.dtype == torch.float64 else _abi.SBG_F32
+        pin, pout, on_dev = ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(out.data_ptr()), 1
+    else:
+        src = np.ascontiguousarray(phi0)
+        if src.dtype not in (np.float32, np.float64):
+            src = src.astype(np.float64)
+        out = np.empty_like(src)
+        code = _abi.SBG_F64 if src.dtype == np.float64 else _abi.SBG_F32
+        pin, pout, on_dev = src.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p), 0
+    nz, ny, nx = src.shape
+    dims = (ctypes.c_int64 * 3)(nx, ny, nz)
+    dxa = (ctypes.c_double * 3)(*[float(d) for d in dx])
+    opts = _abi.RedistOpts(float(cfl), int(max_iter), float(tol), float(band), int(check_every))
+    iters = ctypes.c_int64(0)
+    res = ctypes.c_double(0.0)
+    check(load().sbg_redistance(dims, dxa, pin, pout, code, on_dev, ctypes.byref(opts), ctypes.byref(iters),
+                                ctypes.byref(res), _stream_handle(stream)))
+    return out, iters.value, res.value
