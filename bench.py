@@ -91,14 +91,14 @@ def load_peaks():
     return 6400.0, "fallback"
 
 
-def kernel_sha():
+def kernel_sha(sources=None):
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in sources or KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, p), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profile_traffic(name):
+def profile_traffic(name, sources=None):
     """DRAM bytes per launch from a committed ncu summary, or None when the
     summary is missing or the kernel sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", name)
@@ -108,7 +108,7 @@ def profile_traffic(name):
         return None
     sha = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
     tb = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
-    if not sha or not tb or sha.group(1) != kernel_sha():
+    if not sha or not tb or sha.group(1) != kernel_sha(sources):
         return None
     return int(tb.group(1))
 
@@ -697,7 +697,8 @@ def run_redist512(args):
                      "l2": "the 0.5 GB field pair exceeds the 126 MB L2"},
           "roofline": {"bound": "hbm", "kernel": "k_sussman", "achieved": achieved, "peak": peak,
                        "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                       "traffic": profile_traffic("k_sussman_redist512.md"),
+                       "traffic": profile_traffic("k_sussman_redist512.md",
+                                                  ["paper_2304_11165_b300/csrc/sbg_redistance.cu"]),
                        "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": per_iter_ms * 1e3},
           "result": {"iterations": it, "last_residual": res,
                      "phi_range": [float(phi.min().item()), float(phi.max().item())]},
