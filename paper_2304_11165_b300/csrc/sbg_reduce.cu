@@ -454,6 +454,209 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_f(const RedArgs a) {
     }
 }
 
+// The same reduction for the common case (no surface reaction, constant D),
+// one thread per x-row of four voxels: the row and its four y/z neighbour
+// rows are loaded and combined into double-float values once (not once per
+// voxel and face), x neighbours come from the row itself, and the per-voxel
+// arithmetic is that of k_reduce_f in the same order, so r and every
+// per-voxel term are bitwise the same.
+template <int VM>
+__device__ __forceinline__ void load_row_df(const RedArgs &a, int s, int64_t slot, float h[4], float l[4],
+                                            bool act[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>((const float *)a.val[s] + slot);
+    const float vv[4] = {v.x, v.y, v.z, v.w};
+    float4 lo4 = make_float4(0.f, 0.f, 0.f, 0.f), bh4 = lo4, bl4 = lo4;
+    if (VM == kVX2) lo4 = *reinterpret_cast<const float4 *>(a.lo[s] + slot);
+    if (VM == kVR) {
+        bh4 = *reinterpret_cast<const float4 *>(a.bh + slot);
+        bl4 = *reinterpret_cast<const float4 *>(a.bl + slot);
+    }
+    const float lv[4] = {lo4.x, lo4.y, lo4.z, lo4.w};
+    const float bhv[4] = {bh4.x, bh4.y, bh4.z, bh4.w}, blv[4] = {bl4.x, bl4.y, bl4.z, bl4.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        act[i] = !is_sent(vv[i]);
+        if (VM == kVF32) {
+            h[i] = vv[i];
+            l[i] = 0.f;
+        } else if (VM == kVX2) {
+            h[i] = vv[i];
+            l[i] = lv[i];
+        } else {
+            float e;
+            h[i] = tsum(bhv[i], vv[i], e);
+            l[i] = __fadd_rn(e, blv[i]);
+        }
+    }
+}
+
+template <int VM, int B>
+__global__ void __launch_bounds__(kRedThreads, 4) k_reduce_rows(const RedArgs a) {
+    constexpr int B3 = B * B * B;
+    constexpr int RX = B / 4;              // rows of four along x per block row
+    constexpr int RPB = B * B * RX;        // threads per block
+    constexpr int BPC = kRedThreads / RPB; // blocks per CTA pass
+    DF mass = {0.f, 0.f}, res = {0.f, 0.f}, jin = {0.f, 0.f}, jout = {0.f, 0.f};
+    float mn = INFINITY, mx = -INFINITY;
+    int nact = 0, nonfin = 0;
+    const int s = a.species;
+    const DF dec = {a.dech, a.decl};
+    const int j = threadIdx.x / RPB, rr = threadIdx.x % RPB;
+    const int x0 = (rr % RX) * 4, y = (rr / RX) % B, z = rr / (RX * B);
+    const int lrow = (z * B + y) * B + x0;
+    const int rowbase = lrow - x0;  // x = 0 of this row
+    for (int64_t bb = (int64_t)blockIdx.x * BPC; bb < a.b_count; bb += (int64_t)gridDim.x * BPC) {
+        if (bb + j >= a.b_count) continue;
+        const int64_t b = a.b_begin + bb + j;
+        float ch[4], cl[4];
+        bool ca[4];
+        load_row_df<VM>(a, s, b * B3 + lrow, ch, cl, ca);
+        if (!(ca[0] || ca[1] || ca[2] || ca[3])) continue;
+        const int32_t *fn = a.face + b * 6;
+        const int4 bc = a.blocks[b];
+        const int nx = a.gdims[bc.w * 4 + 0], ny = a.gdims[bc.w * 4 + 1], nz = a.gdims[bc.w * 4 + 2];
+        const int gy = bc.y * B + y, gz = bc.z * B + z;
+        const bool held_yz = ((a.held_mask & 4) && gy == 0) || ((a.held_mask & 8) && gy == ny - 1) ||
+                             ((a.held_mask & 16) && gz == 0) || ((a.held_mask & 32) && gz == nz - 1);
+        // the Laplacian, built one axis and one side at a time: d_a = (0 + diff_-) + diff_+,
+        // lap = sum_a d_a c_a; the x-face differences u - u_{x+1} of the inlet and outlet
+        // planes go to the fluxes on the way
+        DF lap[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) lap[i] = {0.f, 0.f};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            DF d[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) d[i] = {0.f, 0.f};
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const bool minus = side == 0;
+                float vh[4], vl[4];
+                bool va[4];
+                if (ax == 0) {
+                    // x: the row itself, shifted, and one value beyond it
+                    float eh = 0.f, el = 0.f;
+                    bool ea = false;
+                    if (minus) {
+                        if (x0 > 0) ea = load_df<VM>(a, s, b * B3 + lrow - 1, eh, el);
+                        else if (fn[0] >= 0) ea = load_df<VM>(a, s, (int64_t)fn[0] * B3 + rowbase + (B - 1), eh, el);
+                    } else {
+                        if (x0 + 4 < B) ea = load_df<VM>(a, s, b * B3 + lrow + 4, eh, el);
+                        else if (fn[1] >= 0) ea = load_df<VM>(a, s, (int64_t)fn[1] * B3 + rowbase, eh, el);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int k = minus ? i - 1 : i + 1;
+                        const bool edge = minus ? i == 0 : i == 3;
+                        vh[i] = edge ? eh : ch[k < 0 ? 0 : (k > 3 ? 3 : k)];
+                        vl[i] = edge ? el : cl[k < 0 ? 0 : (k > 3 ? 3 : k)];
+                        va[i] = edge ? ea : ca[k < 0 ? 0 : (k > 3 ? 3 : k)];
+                    }
+                } else {
+                    const bool ydir = ax == 1;
+                    const int coord = ydir ? y : z;
+                    const int stride = ydir ? B : B * B;
+                    int64_t nbk = b;
+                    int lr = lrow + (minus ? -stride : stride);
+                    if (minus ? coord == 0 : coord == B - 1) {
+                        nbk = fn[ydir ? (minus ? 2 : 3) : (minus ? 4 : 5)];
+                        lr = lrow + (minus ? (B - 1) * stride : -(B - 1) * stride);
+                    }
+                    if (nbk >= 0) {
+                        load_row_df<VM>(a, s, nbk * B3 + lr, vh, vl, va);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            vh[i] = 0.f;
+                            vl[i] = 0.f;
+                            va[i] = false;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (ca[i] && va[i]) {
+                        float e;
+                        const float dh = tsum(vh[i], -ch[i], e);
+                        const DF diff = {dh, VM != kVF32 ? __fadd_rn(e, __fsub_rn(vl[i], cl[i])) : e};
+                        d[i] = df_add(d[i], diff);
+                        const int gx = bc.x * B + x0 + i;
+                        if (ax == 0 && !minus && nx >= 2 && (gx == 0 || gx == nx - 2) && isfinite(ch[i])) {
+                            float e2;  // u - u_{x+1}
+                            const float fh = tsum(ch[i], -vh[i], e2);
+                            const DF f = {fh, VM != kVF32 ? __fadd_rn(e2, __fsub_rn(cl[i], vl[i])) : e2};
+                            if (gx == 0) jin = df_add(jin, f);
+                            if (gx == nx - 2) jout = df_add(jout, f);
+                        }
+                    }
+                }
+            }
+            const DF cax = {a.ch[ax], a.cl[ax]};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) lap[i] = df_add(lap[i], df_mul(d[i], cax));
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (!ca[i]) continue;
+            ++nact;
+            const float h = ch[i], lo = cl[i];
+            if (!isfinite(h)) {
+                ++nonfin;
+                continue;
+            }
+            const DF u = {h, lo};
+            mass = df_add(mass, u);
+            mn = fminf(mn, h);
+            mx = fmaxf(mx, h);
+            const int gx = bc.x * B + x0 + i;
+            const bool held = held_yz || ((a.held_mask & 1) && gx == 0) || ((a.held_mask & 2) && gx == nx - 1);
+            const int64_t slot = b * B3 + lrow + i;
+            if (!held) {
+                DF r = df_mul(dec, u);
+                r = df_add(lap[i], {-r.h, -r.l});
+                const float p = __fmul_rn(r.h, r.h);
+                res = df_add(res, {p, __fmaf_rn(r.h, r.h, -p) + 2.f * r.h * r.l});
+                if (VM == kVR && a.rout) a.rout[slot] = __fadd_rn(r.h, r.l);
+            } else if (VM == kVR && a.rout) {
+                a.rout[slot] = 0.f;
+            }
+        }
+    }
+    mass = df_shfl_add(mass);
+    res = df_shfl_add(res);
+    jin = df_shfl_add(jin);
+    jout = df_shfl_add(jout);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        nact += __shfl_down_sync(0xffffffffu, nact, o);
+        nonfin += __shfl_down_sync(0xffffffffu, nonfin, o);
+    }
+    __shared__ double sm[kRedThreads / 32][kNumRed];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        const double flux = a.D * a.inv_dx * a.area;
+        sm[warp][SBG_RED_MASS] = df_to_d(mass) * a.dv;
+        sm[warp][SBG_RED_JIN] = df_to_d(jin) * flux;
+        sm[warp][SBG_RED_JOUT] = df_to_d(jout) * flux;
+        sm[warp][SBG_RED_RESIDUAL] = df_to_d(res);
+        sm[warp][SBG_RED_MIN] = (double)mn;
+        sm[warp][SBG_RED_MAX] = (double)mx;
+        sm[warp][SBG_RED_NONFINITE] = (double)nonfin;
+        sm[warp][SBG_RED_NACTIVE] = (double)nact;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumRed) {
+        const int q = threadIdx.x;
+        double v = sm[0][q];
+        for (int wi = 1; wi < kRedThreads / 32; ++wi)
+            v = (q == SBG_RED_MIN) ? fmin(v, sm[wi][q]) : (q == SBG_RED_MAX) ? fmax(v, sm[wi][q]) : v + sm[wi][q];
+        a.partials[(int64_t)blockIdx.x * kNumRed + q] = v;
+    }
+}
+
 // coefficients as double-float pairs (host side)
 static void split_df(double x, float &h, float &l) {
     h = (float)x;
@@ -486,6 +689,7 @@ __global__ void k_fold(float *__restrict__ d, float *__restrict__ bh, float *__r
 template <typename T, int VM, int B>
 static void launch_reduce(const RedArgs &a, int nctas, cudaStream_t s) {
     if (sizeof(T) == 8) k_reduce<double, false, B><<<nctas, kRedThreads, 0, s>>>(a);
+    else if (a.k == 0.0 && !a.epsf) k_reduce_rows<VM, B><<<nctas, kRedThreads, 0, s>>>(a);
     else k_reduce_f<VM, B><<<nctas, kRedThreads, 0, s>>>(a);
 }
 
