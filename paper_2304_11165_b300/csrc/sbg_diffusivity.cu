@@ -71,13 +71,24 @@ static sbg_status set_eps(sbg_grid g, int geom, const void *dense, int dense_dty
     const size_t ebytes = dense_dtype == SBG_F64 ? 8 : 4;
     const size_t bytes = (size_t)(nx * ny * nz) * ebytes;
     void *d = const_cast<void *>(dense);
-    if (!on_device) {
-        SBG_CUDA(cudaMallocAsync(&d, bytes, s));
-        SBG_CUDA(cudaMemcpyAsync(d, dense, bytes, cudaMemcpyHostToDevice, s));
-    }
     unsigned int *stat = nullptr;
-    SBG_CUDA(cudaMallocAsync((void **)&stat, 2 * sizeof(unsigned int), s));
-    SBG_CUDA(cudaMemsetAsync(stat, 0, 2 * sizeof(unsigned int), s));
+    {
+        // on failure, free what this call allocated before returning
+        cudaError_t e = cudaSuccess;
+        if (!on_device) {
+            e = cudaMallocAsync(&d, bytes, s);
+            if (e != cudaSuccess) d = nullptr;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d, dense, bytes, cudaMemcpyHostToDevice, s);
+        }
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&stat, 2 * sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(stat, 0, 2 * sizeof(unsigned int), s);
+        if (e != cudaSuccess) {
+            if (!on_device && d) cudaFreeAsync(d, s);
+            if (stat) cudaFreeAsync(stat, s);
+            cudaStreamSynchronize(s);
+            return cuda_fail(e, "staging buffers");
+        }
+    }
     if (count > 0) {
         const unsigned grid = (unsigned)((count * g->b3() + 255) / 256);
 #define EPS_LAUNCH(TIN, MODE_, B_)                                                                          \

@@ -69,13 +69,24 @@ extern "C" sbg_status sbg_state_set_source(sbg_grid g, sbg_state st, int32_t geo
     const int64_t begin = g->geom_begin[geom], count = g->geom_count[geom];
     const size_t bytes = (size_t)(nx * ny * nz) * (dense_dtype == SBG_F64 ? 8 : 4);
     void *d = const_cast<void *>(dense);
-    if (!on_device) {
-        SBG_CUDA(cudaMallocAsync(&d, bytes, s));
-        SBG_CUDA(cudaMemcpyAsync(d, dense, bytes, cudaMemcpyHostToDevice, s));
-    }
     unsigned int *bad = nullptr;
-    SBG_CUDA(cudaMallocAsync((void **)&bad, sizeof(unsigned int), s));
-    SBG_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned int), s));
+    {
+        // on failure, free what this call allocated before returning
+        cudaError_t e = cudaSuccess;
+        if (!on_device) {
+            e = cudaMallocAsync(&d, bytes, s);
+            if (e != cudaSuccess) d = nullptr;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d, dense, bytes, cudaMemcpyHostToDevice, s);
+        }
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&bad, sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) {
+            if (!on_device && d) cudaFreeAsync(d, s);
+            if (bad) cudaFreeAsync(bad, s);
+            cudaStreamSynchronize(s);
+            return cuda_fail(e, "staging buffers");
+        }
+    }
     if (count > 0) {
         const unsigned grid = (unsigned)((count * g->b3() + 255) / 256);
 #define SRC_LAUNCH(TIN, TST)                                                                                 \
