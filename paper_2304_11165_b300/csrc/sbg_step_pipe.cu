@@ -643,24 +643,30 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
     if (tid == 0)
         for (int s = 0; s < S && g0 + s < g1; ++s) issue(g0 + s, s);
 
-    // this thread's rows: a = (y0, z) and b = (y0 + 1, z), x0 .. x0 + 3, of block j
+    // this thread's rows: a = (y, z0) and b = (y, z0 + B/2), x0 .. x0 + 3, of block j.  With
+    // z0 < B/2 the eight threads of a quarter-warp hold eight consecutive rows, so each
+    // 16-byte row load from the stage tile touches every shared-memory bank once.
+    constexpr int ZB = (B / 2) * B * B;  // row b = row a + ZB in the block
+    constexpr int HB = (B / 2) * B;      // row b's slot = row a's + HB in the x and y halo faces
     const int j = tid / TPB, r = tid % TPB;
     const int x0 = (B == 4) ? 0 : (r & 1) * 4;
     const int rr = (B == 4) ? r : (r >> 1);
-    const int y0 = (rr % (B / 2)) * 2, z = rr / (B / 2);
-    const int la = (z * B + y0) * B + x0;  // row a in its block; row b is la + B
+    const int y = rr % B, z0 = rr / B;
+    const int la = (z0 * B + y) * B + x0;  // row a in its block
     const int va = j * B3 + la;            // row a in the group tile
     const bool hxm = (x0 == 0), hxp = (x0 + 3 == B - 1);
-    const bool hym = (y0 == 0), hyp = (y0 + 1 == B - 1), hzm = (z == 0), hzp = (z == B - 1);
-    // offsets of this thread's halo values in the neighbour blocks (row a; row b at + B)
+    const bool hym = (y == 0), hyp = (y == B - 1);             // both rows
+    const bool hzm = (z0 == 0), hzp = (z0 + B / 2 == B - 1);  // row a below, row b above
+    // offsets of this thread's halo values in the neighbour blocks (row a; row b at + ZB)
     const int oxm = la + (B - 1), oxp = la + 3 - (B - 1);
-    const int oym = la + (B - 1) * B;           // row a's y- neighbour row (y = B - 1)
-    const int oyp = la + B - (B - 1) * B;       // row b's y+ neighbour row (y = 0)
-    const int ozm = la + (B - 1) * B * B, ozp = la - (B - 1) * B * B;
+    const int oym = la + (B - 1) * B;           // y- neighbour row (y = B - 1)
+    const int oyp = la - (B - 1) * B;           // y+ neighbour row (y = 0)
+    const int ozm = la + (B - 1) * B * B;       // row a's z- neighbour row (z = B - 1)
+    const int ozp = la + ZB - (B - 1) * B * B;  // row b's z+ neighbour row (z = 0)
     // halo slots: x faces indexed z*B + y, y faces z*B + x, z faces y*B + x
-    const int sxm = L::face(j, 0) + z * B + y0, sxp = L::face(j, 1) + z * B + y0;
-    const int sym = L::face(j, 2) + z * B + x0, syp = L::face(j, 3) + z * B + x0;
-    const int szm = L::face(j, 4) + y0 * B + x0, szp = L::face(j, 5) + y0 * B + x0;
+    const int sxm = L::face(j, 0) + z0 * B + y, sxp = L::face(j, 1) + z0 * B + y;
+    const int sym = L::face(j, 2) + z0 * B + x0, syp = L::face(j, 3) + z0 * B + x0;
+    const int szm = L::face(j, 4) + y * B + x0, szp = L::face(j, 5) + y * B + x0;
     const float *s0 = io.src[0];
 
     struct Ids {
@@ -669,7 +675,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
     };
     struct Halo {
         float vxm[2], vxp[2];
-        float4 vym, vyp, vzm[2], vzp[2];
+        float4 vym[2], vyp[2], vzm, vzp;
         float4 w[2];
         int ixm, ixp;  // x neighbour inside the group: row a's offset in the stage tile, else -1
         uint32_t hb;
@@ -691,9 +697,10 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
             if (REACT) q.ws = __ldg(a.wslab + b);
             if (a.held_mask) {
                 constexpr int W = (B3 + 63) / 64;
-                const uint64_t word =
-                    __ldg(reinterpret_cast<const unsigned long long *>(a.heldbits) + b * W + (la >> 6));
-                q.hb = ((uint32_t)(word >> (la & 63)) & 0xFu) | (((uint32_t)(word >> ((la + B) & 63)) & 0xFu) << 4);
+                const unsigned long long *hw = reinterpret_cast<const unsigned long long *>(a.heldbits) + b * W;
+                const uint64_t wa = __ldg(hw + (la >> 6));
+                const uint64_t wb = (B == 4) ? wa : __ldg(hw + ((la + ZB) >> 6));
+                q.hb = ((uint32_t)(wa >> (la & 63)) & 0xFu) | (((uint32_t)(wb >> ((la + ZB) & 63)) & 0xFu) << 4);
             }
         }
         return q;
@@ -707,36 +714,36 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
         const float4 SENT4 = make_float4(SENT, SENT, SENT, SENT);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            h.vxm[q] = (id.xm >= 0 && h.ixm < 0) ? __ldg(s0 + id.xm * B3 + oxm + q * B) : SENT;
-            h.vxp[q] = (id.xp >= 0 && h.ixp < 0) ? __ldg(s0 + id.xp * B3 + oxp + q * B) : SENT;
-            h.vzm[q] = (id.zm >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.zm * B3 + ozm + q * B)) : SENT4;
-            h.vzp[q] = (id.zp >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.zp * B3 + ozp + q * B)) : SENT4;
+            h.vxm[q] = (id.xm >= 0 && h.ixm < 0) ? __ldg(s0 + id.xm * B3 + oxm + q * ZB) : SENT;
+            h.vxp[q] = (id.xp >= 0 && h.ixp < 0) ? __ldg(s0 + id.xp * B3 + oxp + q * ZB) : SENT;
+            h.vym[q] = (id.ym >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.ym * B3 + oym + q * ZB)) : SENT4;
+            h.vyp[q] = (id.yp >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.yp * B3 + oyp + q * ZB)) : SENT4;
             h.w[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (REACT && id.ws >= 0) h.w[q] = __ldg(reinterpret_cast<const float4 *>(a.w + id.ws * B3 + la + q * B));
+            if (REACT && id.ws >= 0) h.w[q] = __ldg(reinterpret_cast<const float4 *>(a.w + id.ws * B3 + la + q * ZB));
         }
-        h.vym = (id.ym >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.ym * B3 + oym)) : SENT4;
-        h.vyp = (id.yp >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.yp * B3 + oyp)) : SENT4;
+        h.vzm = (id.zm >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.zm * B3 + ozm)) : SENT4;
+        h.vzp = (id.zp >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.zp * B3 + ozp)) : SENT4;
         h.hb = id.hb;
     };
     auto park = [&](const Halo &h) {
         if (hxm && h.ixm < 0) {
             halo[sxm] = h.vxm[0];
-            halo[sxm + 1] = h.vxm[1];
+            halo[sxm + HB] = h.vxm[1];
         }
         if (hxp && h.ixp < 0) {
             halo[sxp] = h.vxp[0];
-            halo[sxp + 1] = h.vxp[1];
+            halo[sxp + HB] = h.vxp[1];
         }
-        if (hym) *reinterpret_cast<float4 *>(halo + sym) = h.vym;
-        if (hyp) *reinterpret_cast<float4 *>(halo + syp) = h.vyp;
-        if (hzm) {
-            *reinterpret_cast<float4 *>(halo + szm) = h.vzm[0];
-            *reinterpret_cast<float4 *>(halo + szm + B) = h.vzm[1];
+        if (hym) {
+            *reinterpret_cast<float4 *>(halo + sym) = h.vym[0];
+            *reinterpret_cast<float4 *>(halo + sym + HB) = h.vym[1];
         }
-        if (hzp) {
-            *reinterpret_cast<float4 *>(halo + szp) = h.vzp[0];
-            *reinterpret_cast<float4 *>(halo + szp + B) = h.vzp[1];
+        if (hyp) {
+            *reinterpret_cast<float4 *>(halo + syp) = h.vyp[0];
+            *reinterpret_cast<float4 *>(halo + syp + HB) = h.vyp[1];
         }
+        if (hzm) *reinterpret_cast<float4 *>(halo + szm) = h.vzm;
+        if (hzp) *reinterpret_cast<float4 *>(halo + szp) = h.vzp;
     };
 
     // AH: per halo buffer, the row's x offsets inside the group and held bits
@@ -757,42 +764,42 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
                 if (hxm && ixm < 0) {
                     if (id.xm >= 0) {
                         cp_async4(hb + sxm, s0 + id.xm * B3 + oxm);
-                        cp_async4(hb + sxm + 1, s0 + id.xm * B3 + oxm + B);
+                        cp_async4(hb + sxm + HB, s0 + id.xm * B3 + oxm + ZB);
                     } else {
                         hb[sxm] = SENT;
-                        hb[sxm + 1] = SENT;
+                        hb[sxm + HB] = SENT;
                     }
                 }
                 if (hxp && ixp < 0) {
                     if (id.xp >= 0) {
                         cp_async4(hb + sxp, s0 + id.xp * B3 + oxp);
-                        cp_async4(hb + sxp + 1, s0 + id.xp * B3 + oxp + B);
+                        cp_async4(hb + sxp + HB, s0 + id.xp * B3 + oxp + ZB);
                     } else {
                         hb[sxp] = SENT;
-                        hb[sxp + 1] = SENT;
+                        hb[sxp + HB] = SENT;
                     }
                 }
-                if (hym) {
-                    if (id.ym >= 0) cp_async16(hb + sym, s0 + id.ym * B3 + oym);
-                    else *reinterpret_cast<float4 *>(hb + sym) = SENT4;
+                if (hzm) {
+                    if (id.zm >= 0) cp_async16(hb + szm, s0 + id.zm * B3 + ozm);
+                    else *reinterpret_cast<float4 *>(hb + szm) = SENT4;
                 }
-                if (hyp) {
-                    if (id.yp >= 0) cp_async16(hb + syp, s0 + id.yp * B3 + oyp);
-                    else *reinterpret_cast<float4 *>(hb + syp) = SENT4;
+                if (hzp) {
+                    if (id.zp >= 0) cp_async16(hb + szp, s0 + id.zp * B3 + ozp);
+                    else *reinterpret_cast<float4 *>(hb + szp) = SENT4;
                 }
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
-                    if (hzm) {
-                        if (id.zm >= 0) cp_async16(hb + szm + q * B, s0 + id.zm * B3 + ozm + q * B);
-                        else *reinterpret_cast<float4 *>(hb + szm + q * B) = SENT4;
+                    if (hym) {
+                        if (id.ym >= 0) cp_async16(hb + sym + q * HB, s0 + id.ym * B3 + oym + q * ZB);
+                        else *reinterpret_cast<float4 *>(hb + sym + q * HB) = SENT4;
                     }
-                    if (hzp) {
-                        if (id.zp >= 0) cp_async16(hb + szp + q * B, s0 + id.zp * B3 + ozp + q * B);
-                        else *reinterpret_cast<float4 *>(hb + szp + q * B) = SENT4;
+                    if (hyp) {
+                        if (id.yp >= 0) cp_async16(hb + syp + q * HB, s0 + id.yp * B3 + oyp + q * ZB);
+                        else *reinterpret_cast<float4 *>(hb + syp + q * HB) = SENT4;
                     }
                     if (REACT) {
-                        float *wb = wbuf + buf * kGroup2 + va + q * B;
-                        if (id.ws >= 0) cp_async16(wb, a.w + id.ws * B3 + la + q * B);
+                        float *wb = wbuf + buf * kGroup2 + va + q * ZB;
+                        if (id.ws >= 0) cp_async16(wb, a.w + id.ws * B3 + la + q * ZB);
                         else *reinterpret_cast<float4 *>(wb) = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
@@ -823,7 +830,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
         float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra;
         if (MODE == kSrc && valid) {
             ra = __ldg(reinterpret_cast<const float4 *>(io.src[1] + b * B3 + la));
-            rb = __ldg(reinterpret_cast<const float4 *>(io.src[1] + b * B3 + la + B));
+            rb = __ldg(reinterpret_cast<const float4 *>(io.src[1] + b * B3 + la + ZB));
         }
         if (AH) {
             issue_async(gi + 1, id1, (it + 1) & 1);
@@ -856,26 +863,28 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
         float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0;
         if (REACT) {
             w0 = AH ? *reinterpret_cast<const float4 *>(wbuf + buf * kGroup2 + va) : cur.w[0];
-            w1 = AH ? *reinterpret_cast<const float4 *>(wbuf + buf * kGroup2 + va + B) : cur.w[1];
+            w1 = AH ? *reinterpret_cast<const float4 *>(wbuf + buf * kGroup2 + va + ZB) : cur.w[1];
         }
 
         const float *t = stages + (size_t)s * NA * kGroup2;
         const float4 ua = *reinterpret_cast<const float4 *>(t + va);
-        const float4 ub = *reinterpret_cast<const float4 *>(t + va + B);
+        const float4 ub = *reinterpret_cast<const float4 *>(t + va + ZB);
         const float xma = hxm ? (ixm >= 0 ? t[ixm] : hbase[sxm]) : t[va - 1];
-        const float xmb = hxm ? (ixm >= 0 ? t[ixm + B] : hbase[sxm + 1]) : t[va + B - 1];
+        const float xmb = hxm ? (ixm >= 0 ? t[ixm + ZB] : hbase[sxm + HB]) : t[va + ZB - 1];
         const float xpa = hxp ? (ixp >= 0 ? t[ixp] : hbase[sxp]) : t[va + 4];
-        const float xpb = hxp ? (ixp >= 0 ? t[ixp + B] : hbase[sxp + 1]) : t[va + B + 4];
+        const float xpb = hxp ? (ixp >= 0 ? t[ixp + ZB] : hbase[sxp + HB]) : t[va + ZB + 4];
         const float4 yma = *reinterpret_cast<const float4 *>(hym ? hbase + sym : t + va - B);
-        const float4 ypb = *reinterpret_cast<const float4 *>(hyp ? hbase + syp : t + va + 2 * B);
+        const float4 ymb = *reinterpret_cast<const float4 *>(hym ? hbase + sym + HB : t + va + ZB - B);
+        const float4 ypa = *reinterpret_cast<const float4 *>(hyp ? hbase + syp : t + va + B);
+        const float4 ypb = *reinterpret_cast<const float4 *>(hyp ? hbase + syp + HB : t + va + ZB + B);
         const float4 zma = *reinterpret_cast<const float4 *>(hzm ? hbase + szm : t + va - B * B);
-        const float4 zmb = *reinterpret_cast<const float4 *>(hzm ? hbase + szm + B : t + va + B - B * B);
-        const float4 zpa = *reinterpret_cast<const float4 *>(hzp ? hbase + szp : t + va + B * B);
-        const float4 zpb = *reinterpret_cast<const float4 *>(hzp ? hbase + szp + B : t + va + B + B * B);
-        const float4 na = row_update<MODE, REACT>(ua, xma, xpa, yma, ub, zma, zpa, ra, w0, hbits, a.cf);
-        const float4 nbv = row_update<MODE, REACT>(ub, xmb, xpb, ua, ypb, zmb, zpb, rb, w1, hbits >> 4, a.cf);
+        const float4 zpa = *reinterpret_cast<const float4 *>(t + va + B * B);
+        const float4 zmb = *reinterpret_cast<const float4 *>(t + va + ZB - B * B);
+        const float4 zpb = *reinterpret_cast<const float4 *>(hzp ? hbase + szp : t + va + ZB + B * B);
+        const float4 na = row_update<MODE, REACT>(ua, xma, xpa, yma, ypa, zma, zpa, ra, w0, hbits, a.cf);
+        const float4 nbv = row_update<MODE, REACT>(ub, xmb, xpb, ymb, ypb, zmb, zpb, rb, w1, hbits >> 4, a.cf);
         *reinterpret_cast<float4 *>(io.dst[0] + b * B3 + la) = na;
-        *reinterpret_cast<float4 *>(io.dst[0] + b * B3 + la + B) = nbv;
+        *reinterpret_cast<float4 *>(io.dst[0] + b * B3 + la + ZB) = nbv;
         return true;
     };
 
@@ -939,11 +948,18 @@ static cudaError_t launch_pipe_hv(const StepArgs &a, const PipeIO &io, int ctas_
 template <int MODE, int B, bool REACT, bool AH>
 static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_per_sm, int *err, cudaStream_t s) {
     constexpr int NA = 1;
-    constexpr int S = 4;
+    // Two ring stages (one group copied ahead while one computes) leave room for 9-10
+    // CTAs per SM; the row loads are conflict-free, so resident warps are what hides the
+    // latency: 9 CTAs (56 registers) for the SBG_F32R correction, 10 (51) for the rest,
+    // fewer where the shared memory does not fit them (measured on grf256: 33.5 -> 28.4 us
+    // and 29.6 -> 23.8 us against four stages and 5-6 CTAs).  Without cp.async halos the
+    // halo values wait in registers across the group, so that variant keeps 7.
+    constexpr int S = 2;
     constexpr size_t smem = ((size_t)S * NA * kGroup2 + (AH ? 2 : 1) * Rows2Layout<B>::kHalo +
                              ((AH && REACT) ? 2 * kGroup2 : 0)) * sizeof(float) + S * sizeof(uint64_t);
     constexpr int kFit = (int)((228 * 1024) / (smem + 1024));
-    constexpr int MINB = 5 < kFit ? 5 : kFit;  // 102 registers per thread
+    constexpr int kWant = !AH ? 7 : MODE == kSrc ? 9 : 10;
+    constexpr int MINB = kWant < kFit ? kWant : kFit;
     auto kern = k_step_rows2<MODE, B, REACT, S, MINB, AH>;
     static int occ = -1, nsm = 0;
     if (occ < 0) {
