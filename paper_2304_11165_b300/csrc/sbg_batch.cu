@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "sbg_internal.cuh"
+#include "sbg_step.cuh"
 
 namespace sbg {
 sbg_status launch_step_work(sbg_grid g, sbg_state st, const sbg_params *p, int src, const int64_t *items,
@@ -39,7 +40,8 @@ extern "C" sbg_status sbg_batch_run_to_steady(sbg_grid g, sbg_state st, const sb
     check_every += check_every & 1;  // even: parity of the current buffer is kept
     cudaStream_t s = (cudaStream_t)stream;
     const int n = g->n_geoms;
-    const int G = 512 / g->b3();
+    // work-list spans as large as the step kernel of this state takes
+    const int G = step_work_group_voxels(st->dtype, st->ns, g->has_eps, halo_variant_of(st->variant)) / g->b3();
     std::vector<double> r0(n, 0.0), red(kNumRed);
     std::vector<char> active(n, 0);
     for (int i = 0; i < n; ++i) {

@@ -186,6 +186,9 @@ struct PipeIO {
 
 // halo_variant: 0 halo loaded when its group comes up, 1 prefetched one group
 // ahead in registers, 2 copied one group ahead with cp.async (sbg_step_pipe.cu).
+// voxels per work-list span the pipelined step kernel takes for this state
+// (1024 for the two-row kernel's modes, else 512)
+int step_work_group_voxels(sbg_dtype dtype, int ns, bool eps, int halo_variant);
 bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, int halo_variant,
                       int ctas_per_sm, int *err_flag, cudaStream_t s, cudaError_t *launch_err);
 // the halo variant of a state's kernel choice (SBG_KERNEL_AUTO: cp.async one

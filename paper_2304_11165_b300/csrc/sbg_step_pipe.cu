@@ -618,13 +618,20 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
     const int tid = threadIdx.x;
     // (the launcher guarantees nb * B^3 < 2^31: 32-bit block ids and slots)
     const int nb = (int)a.nb;
-    const int ngroups = (nb + G - 1) / G;
+    // groups: consecutive G-block spans of the block list, or an explicit list of
+    // (first block, block count <= G) spans (the batch solver's active set)
+    const int ngroups = a.items ? (int)a.nitems : (nb + G - 1) / G;
     const int g0 = (int)((int64_t)ngroups * blockIdx.x / gridDim.x);
     const int g1 = (int)((int64_t)ngroups * (blockIdx.x + 1) / gridDim.x);
     if (g0 >= g1) return;  // uniform over the CTA
     auto span = [&](int gi, int &b0, int &nblk) {
-        b0 = gi * G;
-        nblk = (nb - b0 < G) ? (nb - b0) : G;
+        if (a.items) {
+            b0 = (int)__ldg(a.items + 2 * gi);
+            nblk = (int)__ldg(a.items + 2 * gi + 1);
+        } else {
+            b0 = gi * G;
+            nblk = (nb - b0 < G) ? (nb - b0) : G;
+        }
     };
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
@@ -972,7 +979,7 @@ static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_pe
     }
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
     constexpr int G = kGroup2 / (B * B * B);
-    const int64_t ngroups = (a.nb + G - 1) / G;
+    const int64_t ngroups = a.items ? a.nitems : (a.nb + G - 1) / G;
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ngroups) grid = ngroups;
     if (grid < 1) return cudaSuccess;
@@ -1015,6 +1022,16 @@ static cudaError_t launch_pipe_b(const StepArgs &a, const PipeIO &io, int B, boo
                  : launch_pipe_t<MODE, 4, NS, false>(a, io, hv, ctas_per_sm, err, s);
 }
 
+// The single-array modes (FP32 one species, SBG_F32R) run the two-row kernel
+// unless register-prefetched halos are asked for; its groups (and work-list
+// spans) hold up to 1024 voxels, the one-row kernel's 512.
+static bool rows2_path(sbg_dtype dtype, int ns, bool eps, int hv) {
+    return hv != 1 && ns == 1 && !eps && (dtype == SBG_F32 || dtype == SBG_F32R);
+}
+int step_work_group_voxels(sbg_dtype dtype, int ns, bool eps, int halo_variant) {
+    return rows2_path(dtype, ns, eps, halo_variant) ? kGroup2 : kGroupVox;
+}
+
 bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, int halo_variant,
                       int ctas_per_sm, int *err_flag, cudaStream_t s, cudaError_t *launch_err) {
     const int hv = halo_variant;
@@ -1032,8 +1049,9 @@ bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool re
         io.src[0] = (const float *)a.in[0];
         io.src[1] = a.src_term;
         io.dst[0] = (float *)a.out[0];
-        e = (hv != 1 && !a.items) ? launch_rows2_b<kSrc>(a, io, B, react, hv, ctas_per_sm, err_flag, s)
-                                  : launch_pipe_b<kSrc, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
+        e = rows2_path(dtype, ns, a.eps != nullptr, hv)
+                ? launch_rows2_b<kSrc>(a, io, B, react, hv, ctas_per_sm, err_flag, s)
+                : launch_pipe_b<kSrc, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
     } else if (dtype == SBG_F32 && ns == 1 && a.eps) {
         io.src[0] = (const float *)a.in[0];
         io.src[1] = a.eps;
@@ -1045,8 +1063,9 @@ bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool re
             io.dst[k] = (float *)a.out[k];
         }
         if (ns == 1)
-            e = (hv != 1 && !a.items) ? launch_rows2_b<kFwd>(a, io, B, react, hv, ctas_per_sm, err_flag, s)
-                                      : launch_pipe_b<kFwd, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
+            e = rows2_path(dtype, ns, false, hv)
+                    ? launch_rows2_b<kFwd>(a, io, B, react, hv, ctas_per_sm, err_flag, s)
+                    : launch_pipe_b<kFwd, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
         else
             e = launch_pipe_b<kFwd, 2>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
     } else {
