@@ -7,7 +7,7 @@
 // FP32 voxel update before the SM, not HBM, is the limit.  So:
 //  - persistent CTAs (several per SM) each walk a contiguous range of
 //    "groups" of the block list (a group = 512 voxels: one 8^3 block or eight
-//    4^3 blocks, contiguous in memory);
+//    4^3 blocks, contiguous in memory; 1024 for the two-row kernel below);
 //  - one thread streams groups into an S-stage shared-memory ring with 1-D
 //    bulk copies (cp.async.bulk, TMA engine) completing on per-stage
 //    mbarriers, S groups ahead of the compute; only that thread waits on the
@@ -544,10 +544,11 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
 // ---------------------------------------------------------------------------
 // Two rows per thread, for the modes with one haloed array (FP32 one species,
 // SBG_F32R correction).  Groups of 1024 voxels (sixteen 4^3 blocks or two 8^3
-// blocks); each thread updates two y-adjacent rows of four voxels, so the
-// per-group work (face ids, Dirichlet bits, the stage barrier, spans) is
-// shared by eight voxels, and the y neighbour between the two rows is already
-// in registers.  The per-voxel arithmetic is the same as above (bitwise).
+// blocks); each thread updates the rows (y, z0) and (y, z0 + B/2) of four
+// voxels, so the per-group work (face ids, Dirichlet bits, the stage barrier,
+// spans) is shared by eight voxels, and a quarter-warp's row loads cover
+// consecutive rows (no shared-memory bank conflicts).  The per-voxel
+// arithmetic is the same as above (bitwise).
 constexpr int kGroup2 = 1024;
 
 template <int B>
