@@ -1,5 +1,5 @@
 """Parity at the workloads' full sizes, in the launch configuration the bench
-times (pipelined kernel, block edge 4).
+times (pipelined kernel with cp.async halos, block edge 4).
 
 * 256^3 tortuosity solve (SBG_F32R state, as the bench runs it): the steady
   state against the FP64 oracle's CG steady state stored by
@@ -13,6 +13,14 @@ times (pipelined kernel, block edge 4).
   voxels at most n steps away, so the oracle recomputes sampled voxels exactly
   on a (2n+1)^3 crop around each; plus the exact per-step balance of the total
   mass, sum(A+B)^{n+1} = sum(A+B)^n - dt * decay_B * sum B^n.
+* 512^3 inhomogeneous diffusion (Eq. 6 factor from phi, c = 1 held on x = 0):
+  sampled voxels against the oracle on crops, as above, with the held face
+  kept where a crop touches it.
+* 256^3 simulated FRAP (closed box): the total mass is conserved, the bleached
+  box recovers and its mass equals the oracle's box sum of the GPU field.
+* 512^3 Sussman redistancing of a GRF indicator: every voxel keeps its sign,
+  and sampled voxels match the oracle run on crops (an iteration also reaches
+  one voxel further).
 """
 import json
 import os
@@ -21,7 +29,7 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import Physics, grf256, reactive512
+from workloads import Physics, frap256, grf256, inhom512, reactive512
 
 pytestmark = pytest.mark.gpu
 
@@ -29,7 +37,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
-from paper_2304_11165_b300 import Grid, State, make_params  # noqa: E402
+from paper_2304_11165_b300 import Grid, State, make_params, redistance  # noqa: E402
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "grf256_steady.json")
 
@@ -43,7 +51,7 @@ def test_grf256_steady_state_matches_the_oracle_cg():
     gold = json.load(open(GOLDEN))
     phi, u0, phys = grf256()
     g = Grid(phi, block=4)
-    st = State(g, 1, "f32r").set_kernel("pipelined").set(u0)
+    st = State(g, 1, "f32r").set_kernel("async").set(u0)
     p = make_params(phys)
     steps, rel = st.run_to_steady(p, 1e-10, check_every=8192, max_steps=4_000_000)
     assert rel < 1e-10
@@ -78,7 +86,7 @@ def test_reactive512_sampled_voxels_match_the_oracle(reactive):
     phi, u0, phys = reactive
     n = 40
     g = Grid(phi, block=4)
-    st = State(g, 2, "f32").set_kernel("pipelined").set_all(u0)
+    st = State(g, 2, "f32").set_kernel("async").set_all(u0)
     st.step(make_params(phys), n)
     A, B = st.get(0), st.get(1)
     rng = np.random.default_rng(7)
@@ -96,7 +104,7 @@ def test_reactive512_sampled_voxels_match_the_oracle(reactive):
 def test_reactive512_total_mass_balance_per_step(reactive):
     phi, u0, phys = reactive
     g = Grid(phi, block=4)
-    st = State(g, 2, "f32").set_kernel("pipelined").set_all(u0)
+    st = State(g, 2, "f32").set_kernel("async").set_all(u0)
     p = make_params(phys)
     red = st.reduce(p)
     m_prev = red[0]["mass"] + red[1]["mass"]
@@ -113,3 +121,68 @@ def test_reactive512_total_mass_balance_per_step(reactive):
         assert red[0]["min"] >= 0.0 and red[0]["max"] <= 1.0 + 1e-6
     # FP32 state: the per-step balance holds to the rounding of the stored values
     assert worst < 2e-7, worst
+
+
+def crop_slices(shape, centre, n):
+    lo = [max(0, c - n) for c in centre]
+    hi = [min(s_, c + n + 1) for c, s_ in zip(centre, shape)]
+    return lo, tuple(slice(a, b) for a, b in zip(lo, hi))
+
+
+def test_inhom512_sampled_voxels_match_the_oracle():
+    phi, u0, phys, (d_min, d_max, g1, g2) = inhom512()
+    n = 30
+    g = Grid(phi, block=4)
+    g.set_diffusivity_sigmoid(phi, d_min, d_max, g1, g2)
+    st = State(g, 1, "f32").set_kernel("async").set(u0)
+    st.step(make_params(phys), n)
+    u = st.get()
+    rng = np.random.default_rng(8)
+    act = phi > np.float32(oracle.FLT_EPSILON)
+    front = np.argwhere(act[:, :, 0:24])                 # where the solute enters
+    anywhere = np.argwhere(act[::9, ::9, ::9]) * 9
+    picks = [tuple(front[i]) for i in rng.choice(len(front), 10, replace=False)] + \
+            [tuple(anywhere[i]) for i in rng.choice(len(anywhere), 10, replace=False)]
+    for c in picks:
+        lo, sl = crop_slices(phi.shape, c, n)
+        sub = np.ascontiguousarray(phi[sl])
+        held = lo[2] == 0  # the crop touches the held x = 0 face
+        pc = Physics(dims=tuple(reversed(sub.shape)), dt=phys.dt, D=phys.D,
+                     dirichlet=(held, False, False, False, False, False), face_value=(1.0, 0, 0, 0, 0, 0))
+        eps = oracle.eps_sigmoid(sub, d_min, d_max, g1, g2)
+        ref = oracle.Problem(sub, pc, eps=eps).run(np.ascontiguousarray(u0[sl])[None], n)[0]
+        r = ref[c[0] - lo[0], c[1] - lo[1], c[2] - lo[2]]
+        assert abs(u[c] - r) <= 1e-5, (c, u[c], r)
+
+
+def test_frap256_conserves_mass_and_recovers():
+    phi, u0, phys, lo, hi = frap256()
+    g = Grid(phi, block=4)
+    st = State(g, 1, "f32r").set_kernel("async").set(u0)
+    p = make_params(phys)
+    total0, nact = st.box_sum((0, 0, 0), phi.shape[::-1])
+    sums, count = st.frap_curve(p, lo, hi, 128, 16)
+    total1, _ = st.box_sum((0, 0, 0), phi.shape[::-1])
+    assert abs(total1 - total0) <= 1e-6 * total0
+    # u stays in [0, 1] (maximum principle), so the box mass stays below its count
+    assert sums[0] == 0.0 and np.all(np.diff(sums) > -1e-6 * count) and 0.0 < sums[-1] < count
+    field = st.get()
+    ref, nref = oracle.Problem(phi, phys).box_sum(field[None], lo, hi)
+    assert nref == count and abs(sums[-1] - ref) <= 1e-9 * max(ref, 1.0)
+
+
+def test_redist512_keeps_signs_and_matches_the_oracle_on_crops():
+    from workloads import gaussian_random_field, threshold_to_porosity
+    from workloads.configs import SEED_GRF256
+    n_it = 24
+    pore = threshold_to_porosity(gaussian_random_field((512, 512, 512), 8.0, SEED_GRF256), 0.35)
+    ind = np.where(pore, 1.0, -1.0).astype(np.float32)
+    out, it, _ = redistance(torch.from_numpy(ind).cuda(), max_iter=n_it)
+    out = out.cpu().numpy()
+    assert it == n_it and np.array_equal(np.sign(out), ind)
+    rng = np.random.default_rng(9)
+    for c in [tuple(rng.integers(0, 512, 3)) for _ in range(8)] + [(0, 0, 0), (511, 511, 511)]:
+        lo, sl = crop_slices(ind.shape, c, n_it + 1)
+        ref = oracle.sussman(np.ascontiguousarray(ind[sl]).astype(np.float64), cfl=0.3, iters=n_it)
+        r = ref[c[0] - lo[0], c[1] - lo[1], c[2] - lo[2]]
+        assert abs(out[c] - r) <= 2e-5 * max(1.0, abs(r)), (c, out[c], r)
