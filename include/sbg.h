@@ -453,7 +453,8 @@ typedef struct {
  * the last tested max |sigma (1 - G)| (NaN when none ran).  The field lives
  * dense on the device with one ping-pong copy; one stencil pass per
  * iteration.  Synchronises `stream`.  Errors: SBG_ERR_INVALID_ARG (dims
- * outside [1, 2^20], dx <= 0, bad options or cfl), SBG_ERR_CUDA. */
+ * outside [1, 2^20], Ny > 524280, Nz > 1048560, dx <= 0, bad options or
+ * cfl), SBG_ERR_CUDA. */
 sbg_status sbg_redistance(const int64_t dims[3], const double dx[3], const void *phi_in, void *phi_out,
                           int32_t dtype, int32_t on_device, const sbg_redist_opts *opts, int64_t *iters_out,
                           double *residual_out, void *stream);

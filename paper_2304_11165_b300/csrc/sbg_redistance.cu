@@ -207,6 +207,8 @@ extern "C" sbg_status sbg_redistance(const int64_t dims[3], const double dx[3], 
     if (courant > 1.0)
         return fail(SBG_ERR_INVALID_ARG, "sbg_redistance: cfl * min(dx) * sum(1/dx) = " + std::to_string(courant) +
                                              " above 1 (the upwind scheme is not monotone)");
+    if ((dims[1] + kRdY - 1) / kRdY > 65535 || (dims[2] + kRdZ - 1) / kRdZ > 65535)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_redistance: Ny above 524280 or Nz above 1048560");
     if (!on_device && phi_in == phi_out)
         return fail(SBG_ERR_INVALID_ARG, "sbg_redistance: host input and output must differ");
     if (iters_out) *iters_out = 0;
