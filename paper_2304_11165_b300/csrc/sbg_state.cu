@@ -47,6 +47,55 @@ __global__ void k_scatter(const Tin *__restrict__ dense, int nx, int ny, int nz,
     }
 }
 
+// The same for FP32 input and an FP32-based state, one thread per x-row of
+// four slots: one 16-byte load of the dense row (when the row lies inside the
+// box and the dense array allows it) and 16-byte stores.  X2: also the low
+// part (0 for FP32 input) and, with corr, the SBG_F32R correction.
+template <bool X2, int B>
+__global__ void k_scatter_rows(const float *__restrict__ dense, int nx, int ny, int nz,
+                               const int4 *__restrict__ blocks, const uint64_t *__restrict__ bitmap, int64_t begin,
+                               int64_t count, bool vec_ok, float *__restrict__ val, float *__restrict__ lo,
+                               float *__restrict__ corr) {
+    constexpr int B3 = B * B * B;
+    constexpr int W = (B3 + 63) / 64;
+    constexpr int RPB = B3 / 4;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count * RPB) return;
+    const int64_t b = begin + t / RPB;
+    const int l0 = (int)(t % RPB) * 4;
+    const uint32_t bits = (uint32_t)(bitmap[b * W + l0 / 64] >> (l0 % 64)) & 0xFu;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (bits) {
+        const int4 bc = blocks[b];
+        const int x = bc.x * B + l0 % B, y = bc.y * B + (l0 / B) % B, z = bc.z * B + l0 / (B * B);
+        const int64_t di = ((int64_t)z * ny + y) * nx + x;
+        if (vec_ok && x + 3 < nx) {
+            const float4 q = *reinterpret_cast<const float4 *>(dense + di);
+            v[0] = q.x;
+            v[1] = q.y;
+            v[2] = q.z;
+            v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if ((bits >> i) & 1u) v[i] = dense[di + i];  // active voxels lie inside the box
+        }
+    }
+    const float SENT = sentinel_f32();
+    float o[4], cr[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool act = (bits >> i) & 1u;
+        const float h = isnan(v[i]) ? __uint_as_float(0x7fffffffu) : v[i];  // canonical NaN, not the sentinel
+        o[i] = act ? h : SENT;
+        cr[i] = act ? 0.f : SENT;
+    }
+    const int64_t slot = b * B3 + l0;
+    *reinterpret_cast<float4 *>(val + slot) = make_float4(o[0], o[1], o[2], o[3]);
+    if (X2) *reinterpret_cast<float4 *>(lo + slot) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (corr) *reinterpret_cast<float4 *>(corr + slot) = make_float4(cr[0], cr[1], cr[2], cr[3]);
+}
+
 template <typename Tout, typename Tst, bool X2, int B>
 __global__ void k_gather(Tout *__restrict__ dense, int nx, int ny, int nz,
                          const int4 *__restrict__ blocks, int64_t begin, int64_t count,
@@ -97,6 +146,22 @@ static sbg_status scatter_gather(sbg_grid g, sbg_state st, int geom, int species
                                                          (const TST *)val, lo, corr);            \
     } while (0)
     const bool in64 = dense_dtype == SBG_F64;
+    if (to_state && !in64 && st->dtype != SBG_F64) {
+        // FP32 input into an FP32-based state: the row kernel (16-byte loads where the dense
+        // array's base and row length allow them)
+        const bool vec_ok = (nx % 4 == 0) && ((reinterpret_cast<uintptr_t>(ddense) & 15) == 0);
+        const unsigned rgrid = (unsigned)((count * (B * B * B / 4) + 255) / 256);
+        if (st->dtype == SBG_F32)
+            k_scatter_rows<false, B><<<rgrid, 256, 0, s>>>((const float *)ddense, (int)nx, (int)ny, (int)nz,
+                                                           g->blocks, g->bitmap, begin, count, vec_ok,
+                                                           (float *)val, lo, corr);
+        else
+            k_scatter_rows<true, B><<<rgrid, 256, 0, s>>>((const float *)ddense, (int)nx, (int)ny, (int)nz,
+                                                          g->blocks, g->bitmap, begin, count, vec_ok,
+                                                          (float *)val, lo, corr);
+        SBG_LAUNCH_CHECK("state scatter");
+        return SBG_OK;
+    }
     if (st->dtype == SBG_F64) {
         if (in64) SG_LAUNCH(double, double, false);
         else SG_LAUNCH(float, double, false);

@@ -603,7 +603,9 @@ __device__ __forceinline__ float4 row_update(const float4 u, float xm, float xp,
 
 // AH: halo values copied one group ahead with per-thread cp.async into the
 // other half of a double halo buffer (no registers held across the group).
-template <int MODE, int B, bool REACT, int S, int MINB, bool AH>
+// WL: the groups come from a work list (a separate instance, so that the
+// plain walk over the block list keeps its registers).
+template <int MODE, int B, bool REACT, int S, int MINB, bool AH, bool WL>
 __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArgs a, const PipeIO io, int *err) {
     using L = Rows2Layout<B>;
     constexpr int B3 = L::B3;
@@ -621,12 +623,12 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
     const int nb = (int)a.nb;
     // groups: consecutive G-block spans of the block list, or an explicit list of
     // (first block, block count <= G) spans (the batch solver's active set)
-    const int ngroups = a.items ? (int)a.nitems : (nb + G - 1) / G;
+    const int ngroups = WL ? (int)a.nitems : (nb + G - 1) / G;
     const int g0 = (int)((int64_t)ngroups * blockIdx.x / gridDim.x);
     const int g1 = (int)((int64_t)ngroups * (blockIdx.x + 1) / gridDim.x);
     if (g0 >= g1) return;  // uniform over the CTA
     auto span = [&](int gi, int &b0, int &nblk) {
-        if (a.items) {
+        if (WL) {
             b0 = (int)__ldg(a.items + 2 * gi);
             nblk = (int)__ldg(a.items + 2 * gi + 1);
         } else {
@@ -953,7 +955,7 @@ static cudaError_t launch_pipe_hv(const StepArgs &a, const PipeIO &io, int ctas_
     return cudaGetLastError();
 }
 
-template <int MODE, int B, bool REACT, bool AH>
+template <int MODE, int B, bool REACT, bool AH, bool WL>
 static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_per_sm, int *err, cudaStream_t s) {
     constexpr int NA = 1;
     // Two ring stages (one group copied ahead while one computes) leave room for 9-10
@@ -961,14 +963,15 @@ static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_pe
     // latency: 9 CTAs (56 registers) for the SBG_F32R correction, 10 (51) for the rest,
     // fewer where the shared memory does not fit them (measured on grf256: 33.5 -> 28.4 us
     // and 29.6 -> 23.8 us against four stages and 5-6 CTAs).  Without cp.async halos the
-    // halo values wait in registers across the group, so that variant keeps 7.
+    // halo values wait in registers across the group, so that variant keeps 7.  The
+    // SBG_F32R work-list instance (batch solver) keeps 8, as 9 would spill.
     constexpr int S = 2;
     constexpr size_t smem = ((size_t)S * NA * kGroup2 + (AH ? 2 : 1) * Rows2Layout<B>::kHalo +
                              ((AH && REACT) ? 2 * kGroup2 : 0)) * sizeof(float) + S * sizeof(uint64_t);
     constexpr int kFit = (int)((228 * 1024) / (smem + 1024));
-    constexpr int kWant = !AH ? 7 : MODE == kSrc ? 9 : 10;
+    constexpr int kWant = !AH ? 7 : MODE == kSrc ? (WL ? 8 : 9) : 10;  // the work-list walk needs 4 more
     constexpr int MINB = kWant < kFit ? kWant : kFit;
-    auto kern = k_step_rows2<MODE, B, REACT, S, MINB, AH>;
+    auto kern = k_step_rows2<MODE, B, REACT, S, MINB, AH, WL>;
     static int occ = -1, nsm = 0;
     if (occ < 0) {
         int dev = 0;
@@ -980,7 +983,7 @@ static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_pe
     }
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
     constexpr int G = kGroup2 / (B * B * B);
-    const int64_t ngroups = a.items ? a.nitems : (a.nb + G - 1) / G;
+    const int64_t ngroups = WL ? a.nitems : (a.nb + G - 1) / G;
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ngroups) grid = ngroups;
     if (grid < 1) return cudaSuccess;
@@ -991,11 +994,18 @@ static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_pe
 template <int MODE, bool AH>
 static cudaError_t launch_rows2_a(const StepArgs &a, const PipeIO &io, int B, bool react, int ctas_per_sm, int *err,
                                   cudaStream_t s) {
+    if (a.items) {
+        if (B == 8)
+            return react ? launch_rows2<MODE, 8, true, AH, true>(a, io, ctas_per_sm, err, s)
+                         : launch_rows2<MODE, 8, false, AH, true>(a, io, ctas_per_sm, err, s);
+        return react ? launch_rows2<MODE, 4, true, AH, true>(a, io, ctas_per_sm, err, s)
+                     : launch_rows2<MODE, 4, false, AH, true>(a, io, ctas_per_sm, err, s);
+    }
     if (B == 8)
-        return react ? launch_rows2<MODE, 8, true, AH>(a, io, ctas_per_sm, err, s)
-                     : launch_rows2<MODE, 8, false, AH>(a, io, ctas_per_sm, err, s);
-    return react ? launch_rows2<MODE, 4, true, AH>(a, io, ctas_per_sm, err, s)
-                 : launch_rows2<MODE, 4, false, AH>(a, io, ctas_per_sm, err, s);
+        return react ? launch_rows2<MODE, 8, true, AH, false>(a, io, ctas_per_sm, err, s)
+                     : launch_rows2<MODE, 8, false, AH, false>(a, io, ctas_per_sm, err, s);
+    return react ? launch_rows2<MODE, 4, true, AH, false>(a, io, ctas_per_sm, err, s)
+                 : launch_rows2<MODE, 4, false, AH, false>(a, io, ctas_per_sm, err, s);
 }
 // halo variant 0: loads when the group comes up; 2: cp.async one group ahead
 template <int MODE>

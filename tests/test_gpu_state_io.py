@@ -1,0 +1,57 @@
+"""Dense <-> block-layout transfers: setting a state from FP32 input (the
+row kernel, with and without 16-byte dense loads) gives the same state as
+setting it from the same values in FP64 (the per-slot kernel), for every
+state type and ragged boxes; inactive voxels read back as 0 and NaN input
+stays NaN."""
+import numpy as np
+import pytest
+
+from workloads import Physics, random_blob_phi
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2304_11165_b300 import Grid, State, make_params  # noqa: E402
+
+
+@pytest.mark.parametrize("dims", [(24, 19, 13), (23, 18, 11)])
+@pytest.mark.parametrize("block", [4, 8])
+@pytest.mark.parametrize("dtype", ["f32", "f32x2", "f32r"])
+def test_fp32_input_equals_fp64_input(dims, block, dtype):
+    phi = random_blob_phi(dims, 61, porosity=0.55, ell=1.6)
+    rng = np.random.default_rng(61)
+    u32 = rng.uniform(-1, 1, phi.shape).astype(np.float32)
+    act = phi > np.finfo(np.float32).eps
+    idx = np.argwhere(act)
+    u32[tuple(idx[3])] = np.nan
+    u32[tuple(idx[5])] = np.inf
+    g = Grid(phi, block=block)
+    a = State(g, 1, dtype).set(u32)                      # FP32 input: row kernel
+    b = State(g, 1, dtype).set(u32.astype(np.float64))   # FP64 input: per-slot kernel
+    ga, gb = a.get(), b.get()
+    np.testing.assert_array_equal(ga, gb)
+    np.testing.assert_array_equal(ga[~act], 0.0)
+    assert np.isnan(ga[tuple(idx[3])]) and np.isinf(ga[tuple(idx[5])])
+    ok = act & np.isfinite(u32)
+    np.testing.assert_array_equal(ga[ok], u32[ok].astype(np.float64))
+
+
+def test_unaligned_device_input_and_steps_agree():
+    dims = (32, 20, 17)
+    phi = random_blob_phi(dims, 62, porosity=0.6, ell=1.7)
+    rng = np.random.default_rng(62)
+    u = rng.uniform(0, 1, phi.shape).astype(np.float32)
+    ph = Physics(dims=dims, dt=0.05, D=(1.0, 0.0), dirichlet=(True, True, False, False, False, False),
+                 face_value=(1.0, 0.0, 0, 0, 0, 0))
+    p = make_params(ph)
+    g = Grid(phi, block=4)
+    flat = torch.zeros(u.size + 1, dtype=torch.float32, device="cuda")
+    flat[1:] = torch.from_numpy(u.ravel()).cuda()
+    view = flat[1:].view(u.shape)  # 4-byte offset: no 16-byte loads
+    for dtype in ("f32", "f32r"):
+        a = State(g, 1, dtype).set(view).step(p, 40).get()
+        b = State(g, 1, dtype).set(u.astype(np.float64)).step(p, 40).get()
+        np.testing.assert_array_equal(a, b)
