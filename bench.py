@@ -739,6 +739,8 @@ def run_gradient256(args):
         return out, a.elapsed_time(b)
 
     st = State(g, 1, "f32").set_kernel(args.variant).set(u0)
+    st.step(p, 3 * 64)  # warm-up: module load, launch set-up, step-graph capture
+    st.set(u0)
     _, fwd_ms = timed(lambda: st.step(p, nsteps))
     st.set(u0)
     tape, rec_ms = timed(lambda: forward_record(st, p, nsteps, K))
