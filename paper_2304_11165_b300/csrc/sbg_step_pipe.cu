@@ -915,7 +915,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
 
 template <int MODE, int NA>
 struct PipeStages {
-    static constexpr int S = NA == 1 ? 6 : NA == 2 ? 4 : 3;
+    static constexpr int S = NA == 1 ? 6 : NA == 2 ? (MODE == kAdj ? 3 : 4) : 3;  // adjoint: 3 leaves room for 6 CTAs
 };
 
 template <int MODE, int B, int NS, bool REACT, int HV>
@@ -926,12 +926,13 @@ static cudaError_t launch_pipe_hv(const StepArgs &a, const PipeIO &io, int ctas_
     constexpr size_t smem = PipeSmem<MODE, B, NS, REACT, HV>::bytes(S);
     constexpr int G = kGroupVox / (B * B * B);
     // Without prefetch: 64 registers per thread (8 CTAs of 128 threads per SM)
-    // with one array, 80 (6 CTAs) with two (96, 5 CTAs, for the adjoint with
-    // its gradient sums), 128 (4 CTAs) with four.  With register prefetch
+    // with one array, 80 (6 CTAs) with two (the adjoint too, its gradient sums
+    // included: 6 CTAs and 3 stages measured 2% faster than 5 and 4), 128
+    // (4 CTAs) with four.  With register prefetch
     // (HV 1) the two register sets need up to 128 registers (4 CTAs per SM).
     // No more CTAs than fit in the SM's 228 KB of shared memory (1 KB of it
     // reserved per CTA) are asked for, so the registers go to those that fit.
-    constexpr int kBase = HV == 1 ? 4 : (NA == 1 ? 8 : NA == 2 ? (MODE == kAdj ? 5 : 6) : 4);
+    constexpr int kBase = HV == 1 ? 4 : (NA == 1 ? 8 : NA == 2 ? 6 : 4);
     constexpr int kFit = (int)((228 * 1024) / (smem + 1024));
     constexpr int MINB = kBase < kFit ? kBase : (kFit > 0 ? kFit : 1);
     auto kern = k_step_pipe<MODE, B, NS, REACT, S, MINB, HV>;
