@@ -12,9 +12,10 @@ reduction that decides convergence (which also refreshes r and folds d).
 
 Metric: active-voxel updates per second (GVox/s) = n_active * 128 * steps /
 time.  `value` is measured with CUDA events on the stream the library uses,
-inputs resident in HBM; `e2e` repeats the measurement through the public API
-with the dense initial field uploaded from pinned host memory every step and
-D_eff read back.  `roofline` reports the step kernel's algorithmic bytes
+inputs resident in HBM; each interval's check is enqueued behind its steps
+(sbg_reduce_async) and read on the host while the next interval runs.  `e2e`
+repeats the measurement through the public API with the dense initial field
+uploaded from pinned host memory every step and the check read back.  `roofline` reports the step kernel's algorithmic bytes
 (12 B per active voxel: d and r read, d written; 16 B for --dtype f32x2) per
 launch over its average launch time, against the measured HBM copy bandwidth.
 
@@ -280,12 +281,22 @@ def run_grf256(args):
     torch.cuda.synchronize(dev)
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
+    # each interval's check (residual, fluxes, mass; for SBG_F32R also the refresh of r) is
+    # enqueued behind its steps and read back while the next interval runs (the convergence
+    # decision lags one interval, as a pipelined solver's does)
+    red_buf = [torch.zeros(abi.NRED, dtype=torch.float64).pin_memory() for _ in range(2)]
+    red_done = [torch.cuda.Event() for _ in range(2)]
+    residuals = []
     start.record(stream)
     for i in range(args.steps):
         ev[i][0].record(stream)
         st.step(p, CHECK_EVERY, stream=stream)
         ev[i][1].record(stream)
-        st.effective_D(p, stream=stream)
+        st.reduce_async(p, red_buf[i % 2], stream=stream)
+        red_done[i % 2].record(stream)
+        if i > 0:
+            red_done[(i - 1) % 2].synchronize()
+            residuals.append(st.parse_reduction(red_buf[(i - 1) % 2])[0]["residual"])
     end.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -312,6 +323,9 @@ def run_grf256(args):
             staging[i % 2].copy_(u0_host, non_blocking=True)
             ready[i % 2].record(copy_stream)
 
+    e_buf = [torch.zeros(abi.NRED, dtype=torch.float64).pin_memory() for _ in range(2)]
+    e_done = [torch.cuda.Event() for _ in range(2)]
+
     def e2e_steps(n):
         upload(0)
         for i in range(n):
@@ -321,7 +335,12 @@ def run_grf256(args):
             st2.set(staging[i % 2], stream=stream)
             consumed[i % 2].record(stream)
             st2.step(p, CHECK_EVERY, stream=stream)
-            st2.effective_D(p, stream=stream)  # device -> host read of the step's result
+            st2.reduce_async(p, e_buf[i % 2], stream=stream)  # device -> host copy of the step's result
+            e_done[i % 2].record(stream)
+            if i > 0:
+                e_done[(i - 1) % 2].synchronize()  # the previous step's result, read on the host
+                st2.parse_reduction(e_buf[(i - 1) % 2])
+        e_done[(n - 1) % 2].synchronize()
 
     e2e_steps(2)
     torch.cuda.synchronize(dev)
@@ -365,7 +384,8 @@ def run_grf256(args):
         # reduction, its final pass and (SBG_F32R) the fold of the correction
         "gpu_launches": (CHECK_EVERY + (3 if args.dtype == "f32r" else 2)) * args.steps,
         "clocks": clocks,
-        "result": {"D_eff_after_warmup_and_timed_steps": d_eff, "tau": tau},
+        "result": {"D_eff_after_warmup_and_timed_steps": d_eff, "tau": tau,
+                   "residual_first_last_timed_check": [residuals[0], residuals[-1]] if residuals else None},
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu

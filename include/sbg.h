@@ -301,6 +301,18 @@ double sbg_stability_limit(const sbg_params *params, const int64_t dims[3], doub
 sbg_status sbg_reduce(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom,
                       double *out, void *stream);
 
+/* sbg_reduce without the synchronisation: enqueues the same reductions (and,
+ * for SBG_F32R states, the same refresh of r and fold of the correction) on
+ * `stream`, then an asynchronous copy of the results into `out`
+ * (nspecies * SBG_NRED doubles, same layout; host memory, page-locked for the
+ * copy to be asynchronous, or device memory).  `out` holds the results once
+ * `stream` has passed this call (an event, a synchronisation); until then it
+ * must stay allocated and untouched.  The device error word of bounded waits
+ * is not read here: the next synchronising call reports it.  This lets a
+ * solver enqueue the next steps before it reads a convergence check. */
+sbg_status sbg_reduce_async(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom, double *out,
+                            void *stream);
+
 /* The same FP64 reduction for callers that may not allocate device memory
  * (their memory belongs to another allocator, such as a framework's caching
  * allocator or a fixed serving arena, or allocation latency is not allowed in

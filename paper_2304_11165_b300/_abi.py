@@ -74,6 +74,7 @@ SIGNATURES = [
     ("sbg_step_source", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     ("sbg_redistance", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p,
                                  c_void_p, c_void_p]),
+    ("sbg_reduce_async", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     ("sbg_reduce_box", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("sbg_frap_curve", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_int64,
                                  c_int32, c_void_p, c_void_p, c_void_p]),

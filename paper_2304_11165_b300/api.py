@@ -271,12 +271,27 @@ class State:
                                         f.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)))
         return self
 
+    _RED_KEYS = ("mass", "J_in", "J_out", "residual", "min", "max", "nonfinite", "n_active")
+
     def reduce(self, params: Params, geom: int = 0, stream=None):
         out = np.zeros(self.nspecies * NRED)
         check(self._lib.sbg_reduce(self.grid.handle, self.handle, ctypes.byref(params), geom,
                                    out.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)))
-        keys = ("mass", "J_in", "J_out", "residual", "min", "max", "nonfinite", "n_active")
-        return [dict(zip(keys, out[s * NRED:(s + 1) * NRED])) for s in range(self.nspecies)]
+        return self.parse_reduction(out)
+
+    def parse_reduction(self, out):
+        """Per-species dicts from an array of nspecies * SBG_NRED results."""
+        out = np.asarray(out, dtype=np.float64)
+        return [dict(zip(self._RED_KEYS, out[s * NRED:(s + 1) * NRED])) for s in range(self.nspecies)]
+
+    def reduce_async(self, params: Params, out, geom: int = 0, stream=None):
+        """Enqueue the reductions (``sbg_reduce_async``) into ``out``: a float64
+        torch tensor of nspecies * SBG_NRED elements, page-locked host memory
+        or device memory; read it (``parse_reduction``) once the stream has
+        passed this call."""
+        check(self._lib.sbg_reduce_async(self.grid.handle, self.handle, ctypes.byref(params), geom,
+                                         ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
 
     def box_sum(self, lo, hi, species: int = 0, geom: int = 0, stream=None):
         """(sum of u over the active voxels with lo <= (x, y, z) < hi, their count)."""

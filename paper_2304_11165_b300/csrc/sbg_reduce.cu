@@ -779,11 +779,11 @@ sbg_status refresh_source(sbg_grid g, sbg_state st, const sbg_params *p, cudaStr
     return SBG_OK;
 }
 
-// Reduces species `species` of buffer `which` (st->cur when < 0) into
-// out_host[kNumRed].  SBG_F32R states: also refreshes r and folds d over the
-// reduced range.
-sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species,
-                          int which, double *out_host, cudaStream_t s) {
+// Enqueues the reduction of species `species` of buffer `which` (st->cur when
+// < 0) into g->red_dev[kNumRed] (kernel launches only).  SBG_F32R states: also
+// refreshes r and folds d over the reduced range.
+static sbg_status enqueue_reduce(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species, int which,
+                                 cudaStream_t s) {
     const int buf = which < 0 ? st->cur : which;
     RedArgs a;
     fill_red_args(g, st, p, geom, species, buf, g->partials, a);
@@ -801,6 +801,15 @@ sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geo
             st->since_refresh = 0;
         }
     }
+    return SBG_OK;
+}
+
+// Reduces species `species` of buffer `which` (st->cur when < 0) into
+// out_host[kNumRed] and synchronises.
+sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species,
+                          int which, double *out_host, cudaStream_t s) {
+    sbg_status rc = enqueue_reduce(g, st, p, geom, species, which, s);
+    if (rc != SBG_OK) return rc;
     SBG_CUDA(cudaMemcpyAsync(g->red_host, g->red_dev, sizeof(double) * kNumRed, cudaMemcpyDeviceToHost, s));
     SBG_CUDA(cudaStreamSynchronize(s));
     std::memcpy(out_host, g->red_host, sizeof(double) * kNumRed);
@@ -970,6 +979,21 @@ extern "C" sbg_status sbg_reduce(sbg_grid g, sbg_state st, const sbg_params *p, 
     for (int s = 0; s < st->ns; ++s) {
         rc = reduce_species(g, st, p, geom, s, -1, out + s * kNumRed, (cudaStream_t)stream);
         if (rc != SBG_OK) return rc;
+    }
+    return SBG_OK;
+}
+
+extern "C" sbg_status sbg_reduce_async(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom,
+                                       double *out, void *stream) {
+    sbg_status rc = check_common(g, st, p, geom);
+    if (rc != SBG_OK) return rc;
+    if (!out) return fail(SBG_ERR_INVALID_ARG, "sbg_reduce_async: null output");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int sp = 0; sp < st->ns; ++sp) {
+        rc = enqueue_reduce(g, st, p, geom, sp, -1, s);
+        if (rc != SBG_OK) return rc;
+        // stream order keeps the next species' final pass off g->red_dev until this copy is done
+        SBG_CUDA(cudaMemcpyAsync(out + sp * kNumRed, g->red_dev, sizeof(double) * kNumRed, cudaMemcpyDefault, s));
     }
     return SBG_OK;
 }

@@ -55,3 +55,29 @@ def test_unaligned_device_input_and_steps_agree():
         a = State(g, 1, dtype).set(view).step(p, 40).get()
         b = State(g, 1, dtype).set(u.astype(np.float64)).step(p, 40).get()
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype,ns", [("f32", 2), ("f64", 1), ("f32r", 1), ("f32x2", 1)])
+def test_async_reduction_equals_the_synchronous_one(dtype, ns):
+    dims = (26, 22, 18)
+    phi = random_blob_phi(dims, 63, porosity=0.6, ell=1.7)
+    rng = np.random.default_rng(63)
+    u0 = rng.uniform(0, 1, (ns,) + phi.shape)
+    ph = Physics(dims=dims, dt=0.05, nspecies=ns, D=(1.0, 0.5)[:ns] + (0.0,) * (2 - ns),
+                 decay=(0.01, 0.02), k_surf=0.2 if ns == 2 else 0.0,
+                 dirichlet=(True, True, False, False, False, False), face_value=(1.0, 0.0, 0, 0, 0, 0))
+    p = make_params(ph)
+    g = Grid(phi, block=4)
+    a = State(g, ns, dtype).set_all(u0 if ns == 2 else u0[0]).step(p, 70)
+    b = State(g, ns, dtype).set_all(u0 if ns == 2 else u0[0]).step(p, 70)
+    ref = a.reduce(p)
+    host = torch.zeros(ns * 8, dtype=torch.float64).pin_memory()
+    dev = torch.zeros(ns * 8, dtype=torch.float64, device="cuda")
+    b.reduce_async(p, host)
+    torch.cuda.synchronize()
+    assert b.parse_reduction(host) == ref
+    c = State(g, ns, dtype).set_all(u0 if ns == 2 else u0[0]).step(p, 70)
+    c.reduce_async(p, dev)
+    assert c.parse_reduction(dev.cpu()) == ref
+    # the states go on identically after either call (SBG_F32R: the same refresh)
+    np.testing.assert_array_equal(a.step(p, 30).get_all(), b.step(p, 30).get_all())
