@@ -114,3 +114,26 @@ def test_maximum_principle_with_a_varying_factor():
         u = P.run(u, 10)
         act = P.active > 0
         assert u[0][act].min() >= -1e-15 and u[0][act].max() <= 1.0 + 1e-15
+
+
+def test_inhomogeneous_reduction_terms_against_their_definitions():
+    """Fluxes with the face-mean factor and the residual (u' - u) / dt over the
+    free voxels, by numpy, for a random factor and held x faces."""
+    dims = (10, 8, 7)
+    phi = blob(dims, 12)
+    eps = np.random.default_rng(12).uniform(0.2, 1.3, phi.shape)
+    ph = Physics(dims=dims, dt=0.03, D=(0.7, 0.0), decay=(0.03, 0.0), dx=(0.9, 1.0, 1.2),
+                 dirichlet=(True, True, False, False, False, False), face_value=(1.0, 0.0, 0, 0, 0, 0))
+    P = oracle.Problem(phi, ph, eps=eps)
+    u = P.shape_state(np.random.default_rng(13).uniform(0, 1, phi.shape)[None])
+    red = P.reduce(u)[0]
+    act = P.active > 0
+    free = act & (P.fixed == 0)
+    lhs = (P.step(u)[0] - u[0]) / 0.03
+    res = float(np.sqrt(np.sum(lhs[free] ** 2)))
+    assert abs(red["residual"] - res) <= 1e-9 * res
+    for key, p0 in (("J_in", 0), ("J_out", dims[0] - 2)):
+        both = act[:, :, p0] & act[:, :, p0 + 1]
+        f = 0.5 * (eps[:, :, p0] + eps[:, :, p0 + 1])
+        j = 0.7 * float(np.sum((f * (u[0][:, :, p0] - u[0][:, :, p0 + 1]))[both])) / 0.9 * (1.0 * 1.2)
+        assert abs(red[key] - j) <= 1e-12 * max(1.0, abs(j)), (key, red[key], j)

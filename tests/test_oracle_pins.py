@@ -451,3 +451,36 @@ def test_surface_weight_is_half_a_unit_delta():
     P2 = oracle.Problem(phi2, phys((4, 1, 1), 0.0))
     np.testing.assert_allclose(P2.w[0, 0], [0.5, 0.0, 0.0, 0.0], atol=1e-7)
     assert list(P2.active[0, 0]) == [1, 1, 1, 0]
+
+
+# ---------------------------------------------------------------------------
+# the monitoring reductions against their plain definitions
+# ---------------------------------------------------------------------------
+def test_reduction_terms_against_their_definitions():
+    """Mass, active count, inlet/outlet x-fluxes and the residual of a
+    two-species reactive state with held x faces, against numpy brute force
+    over the active voxels; the residual against the step (pinned above on
+    its own): L_h u = (u' - u) / dt on the free voxels."""
+    dims = (11, 9, 8)
+    phi = random_blob_phi(dims, 71, porosity=0.6, ell=1.5)
+    d, v = dirich(0, 1, values=(1.0, 0.0))
+    ph = phys(dims, 0.04, nspecies=2, D=(0.9, 0.4), decay=(0.02, 0.05), k_surf=0.7, dx=(0.8, 1.1, 1.3),
+              dirichlet=d, face_value=v)
+    P = oracle.Problem(phi, ph)
+    u = P.shape_state(np.random.default_rng(71).uniform(0, 1, (2,) + phi.shape))
+    red = P.reduce(u)
+    act = P.active > 0
+    free = act & (P.fixed == 0)
+    step = P.step(u)
+    dv = 0.8 * 1.1 * 1.3
+    for s in range(2):
+        r = red[s]
+        assert r["n_active"] == int(act.sum())
+        assert abs(r["mass"] - float(np.sum(u[s][act])) * dv) <= 1e-12 * r["mass"]
+        lhs = (step[s] - u[s]) / 0.04
+        res = math.sqrt(float(np.sum(lhs[free] ** 2)))
+        assert abs(r["residual"] - res) <= 1e-9 * res
+        for key, p0 in (("J_in", 0), ("J_out", dims[0] - 2)):
+            both = act[:, :, p0] & act[:, :, p0 + 1]
+            j = (0.9, 0.4)[s] * float(np.sum((u[s][:, :, p0] - u[s][:, :, p0 + 1])[both])) / 0.8 * (1.1 * 1.3)
+            assert abs(r[key] - j) <= 1e-12 * max(1.0, abs(j)), (s, key, r[key], j)
