@@ -245,8 +245,11 @@ sbg_status sbg_step_source(sbg_grid grid, sbg_state state, const sbg_params *par
  * counterpart in the paper).  variant: SBG_KERNEL_AUTO (the pipelined kernel
  * with cp.async halos where it exists, else the one-thread-per-voxel kernel), SBG_KERNEL_PLAIN
  * (one thread per voxel, block tile in shared memory, one launch-sized grid)
- * SBG_KERNEL_PIPELINED (persistent CTAs streaming 512-voxel groups
- * through a bulk-copy ring; FP32 and SBG_F32X2 states only) or
+ * SBG_KERNEL_PIPELINED (persistent CTAs streaming groups of blocks
+ * through a bulk-copy ring: 1024-voxel groups and two z-paired rows of four
+ * voxels per thread for one FP32 species and SBG_F32R states, 512-voxel
+ * groups and one row per thread for the other FP32-based states; not for
+ * SBG_F64) or
  * SBG_KERNEL_PIPELINED_PREFETCH (the same, with face halos prefetched one
  * group ahead in registers: fewer CTAs per SM, less exposed latency) or
  * SBG_KERNEL_PIPELINED_ASYNC (face halos copied one group ahead into shared
