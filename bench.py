@@ -7,10 +7,10 @@ c = 1 / c = 0 held on the x faces, D = 1, dt = 0.15, an SBG_F32R state (FP32
 correction d on a compensated base b = hi + lo: each step is FP32 forward
 Euler on d with the source r = L_h b; the check folds d into b) with
 double-float/FP64 reductions.  One bench step = one check interval of the
-steady-state solve: 128 forward-Euler steps plus the residual and flux
+steady-state solve: 256 forward-Euler steps plus the residual and flux
 reduction that decides convergence (which also refreshes r and folds d).
 
-Metric: active-voxel updates per second (GVox/s) = n_active * 128 * steps /
+Metric: active-voxel updates per second (GVox/s) = n_active * 256 * steps /
 time.  `value` is measured with CUDA events on the stream the library uses,
 inputs resident in HBM; each interval's check is enqueued behind its steps
 (sbg_reduce_async) and read on the host while the next interval runs.  `e2e`
@@ -52,7 +52,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-CHECK_EVERY = 128
+CHECK_EVERY = 256  # RD steps per check, the SBG_F32R refresh interval
 # per active voxel and step: read and write the state; f32r reads the correction d and the source r
 # and writes d
 BYTES_PER_VOXEL = {"f32": 8, "f32x2": 16, "f64": 16, "f32r": 12}

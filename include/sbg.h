@@ -60,7 +60,7 @@ typedef enum {
                       b = hi + lo (FP32 pair) and d an FP32 correction.  Each step advances d
                       by forward Euler with the source r = L_h b (stored as FP32), which in
                       exact arithmetic is the forward-Euler step of b + d; every reduction and
-                      every 128 steps the library recomputes r from b + d in double-float
+                      every 256 steps the library recomputes r from b + d in double-float
                       arithmetic and folds d into b.  The step moves 12 B per voxel in plain
                       FP32 arithmetic; the rounding of d is relative to the change since the
                       last fold, so steady states reach residuals like SBG_F32X2's         */

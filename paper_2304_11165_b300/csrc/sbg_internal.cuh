@@ -169,7 +169,7 @@ sbg_status step_n(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps,
 // (kernel launches only, no synchronisation)
 sbg_status refresh_source(sbg_grid g, sbg_state st, const sbg_params *p, cudaStream_t stream);
 // steps between refreshes of an SBG_F32R state inside sbg_step
-constexpr int64_t kRefreshSteps = 128;
+constexpr int64_t kRefreshSteps = 256;
 // implemented in sbg_step.cu: makes g->heldbits match the Dirichlet faces of
 // p (one small kernel when they changed); call before any stream capture
 sbg_status prepare_held_bits(sbg_grid g, const sbg_params *p, cudaStream_t s);

@@ -1,5 +1,5 @@
 """SBG_F32R states (FP32 correction d on a compensated base b, source
-r = L_h b refreshed and d folded every 128 steps and at every reduction):
+r = L_h b refreshed and d folded every 256 steps and at every reduction):
 parity with the FP64 oracle, bitwise consistency across block sizes and step
 kernels, steady states against the oracle's CG solve, and the batch solver."""
 import numpy as np
@@ -35,13 +35,13 @@ def blob_case(dims, k, seed, faces=(0, 1)):
 
 @pytest.mark.parametrize("block,k", [(4, 0.0), (8, 0.4), (4, 0.4)])
 def test_f32r_steps_match_the_oracle(block, k):
-    """300 steps cross two refreshes (at 128 and 256); the error is far below
+    """600 steps cross two refreshes (at 256 and 512); the error is far below
     plain FP32's because d only carries the change since the last fold."""
     phi, phys, u0 = blob_case((29, 23, 19), k, 40 + block)
-    ref = oracle.Problem(phi, phys).run(u0[None], 300)[0]
+    ref = oracle.Problem(phi, phys).run(u0[None], 600)[0]
     g = Grid(phi, block=block)
     st = State(g, 1, "f32r").set(u0)
-    st.step(make_params(phys), 300)
+    st.step(make_params(phys), 600)
     assert rel_err(st.get(), ref) < 2e-7
 
 
@@ -76,7 +76,7 @@ def test_f32r_step_counts_do_not_depend_on_call_pattern():
 def test_f32r_reduction_matches_the_oracle_and_leaves_the_field(k, res_tol):
     """The reduction of an SBG_F32R state against the oracle's reduction of the
     same field (read back in FP64), and the field against the oracle's run.
-    The first 128 steps after a set carry the whole change in d, so the field
+    The first 256 steps after a set carry the whole change in d, so the field
     is FP32-accurate there; the reduction itself is double-float.  With a
     surface reaction the residual uses the FP32 surface weights the step uses
     (the oracle's are FP64), which bounds its agreement at ~1e-7."""
