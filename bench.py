@@ -380,7 +380,7 @@ def run_grf256(args):
                      "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": step_kernel_ms * 1e3},
         "e2e": {"value": e2e_value, "unit": "GVox/s", "h2d_bytes_per_step": int(u0.size * 4),
                 "d2h_bytes_per_step": abi.NRED * 8},
-        # per bench step: CHECK_EVERY step kernels (two replayed 64-step graphs) and the check:
+        # per bench step: CHECK_EVERY step kernels (replayed 64-step graphs) and the check:
         # reduction, its final pass and (SBG_F32R) the fold of the correction
         "gpu_launches": (CHECK_EVERY + (3 if args.dtype == "f32r" else 2)) * args.steps,
         "clocks": clocks,
