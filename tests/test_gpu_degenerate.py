@@ -93,3 +93,30 @@ def test_batch_with_empty_and_one_voxel_geometries(dtype):
     tol = 1e-6 if dtype == "f32r" else 2e-4
     steps, rel = sb.batch_run_to_steady(p, tol, check_every=128, max_steps=200_000, raise_on_max=False)
     assert steps[1] == 0 and np.all(rel[[0, 2, 3, 4]] < tol), (steps, rel)
+
+
+@pytest.mark.parametrize("zyx", [(1, 1, 17), (1, 9, 11), (3, 3, 3)])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 2e-4)])
+def test_adjoint_on_thin_boxes_matches_the_oracle(zyx, dtype, tol):
+    from paper_2304_11165_b300.autograd import adjoint, forward_record
+    nz, ny, nx = zyx
+    phi = np.full(zyx, 0.6, np.float32)  # every voxel in the surface band: the reaction acts everywhere
+    ph = Physics(dims=(nx, ny, nz), dt=0.05, nspecies=2, D=(1.0, 0.5), decay=(0.01, 0.1), k_surf=0.5,
+                 dirichlet=(nx > 1, False, False, False, False, False), face_value=(0.0,) * 6)
+    rng = np.random.default_rng(sum(zyx))
+    u0 = rng.uniform(0.2, 1.0, (2,) + zyx)
+    if nx > 1:
+        u0[:, :, :, 0] = 0.0
+    lamN = rng.uniform(0, 1, (2,) + zyx)
+    P = oracle.Problem(phi, ph)
+    lam0_ref, grad_ref, _ = P.adjoint_run(u0, 25, lamN * P.active[None])
+    g = Grid(phi, block=4)
+    st = State(g, 2, dtype).set_all(u0)
+    tape = forward_record(st, make_params(ph), 25, 6)
+    lam = State(g, 2, dtype).set_all(lamN * P.active[None])
+    grad = adjoint(tape, lam)
+    lam0 = lam.get_all()
+    assert np.max(np.abs(lam0 - lam0_ref)) <= tol * np.max(np.abs(lam0_ref))
+    for s in range(2):
+        assert abs(grad[s] - grad_ref[s]) <= tol * max(abs(grad_ref[s]), 1e-12), (s, grad, grad_ref)
+    assert abs(grad[2] - grad_ref[2]) <= tol * max(abs(grad_ref[2]), 1e-12)
