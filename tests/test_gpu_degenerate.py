@@ -120,3 +120,22 @@ def test_adjoint_on_thin_boxes_matches_the_oracle(zyx, dtype, tol):
     for s in range(2):
         assert abs(grad[s] - grad_ref[s]) <= tol * max(abs(grad_ref[s]), 1e-12), (s, grad, grad_ref)
     assert abs(grad[2] - grad_ref[2]) <= tol * max(abs(grad_ref[2]), 1e-12)
+
+
+@pytest.mark.parametrize("zyx", [(1, 1, 15), (1, 8, 10), (2, 5, 6), (1, 1, 1)])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32", 2e-6)])
+def test_inhomogeneous_thin_boxes_match_the_oracle(zyx, dtype, tol):
+    nz, ny, nx = zyx
+    phi = np.full(zyx, 3.0, np.float32)
+    eps = np.random.default_rng(sum(zyx) + 1).uniform(0.2, 1.0, zyx)
+    if dtype == "f32":
+        eps = eps.astype(np.float32).astype(np.float64)
+    ph = Physics(dims=(nx, ny, nz), dt=0.1, D=(1.0, 0.0), decay=(0.02, 0.0),
+                 dirichlet=(nx > 1, False, False, False, False, False), face_value=(1.0, 0, 0, 0, 0, 0))
+    u0 = np.random.default_rng(sum(zyx)).uniform(0, 1, zyx)
+    ref = oracle.Problem(phi, ph, eps=eps).run(u0[None], 60)[0]
+    for variant in (["plain", "async"] if dtype == "f32" else ["plain"]):
+        g = Grid(phi, block=4).set_diffusivity(eps if dtype == "f64" else eps.astype(np.float32))
+        st = State(g, 1, dtype).set_kernel(variant).set(u0)
+        st.step(make_params(ph), 60)
+        assert np.max(np.abs(st.get() - ref)) <= tol * max(1.0, np.max(np.abs(ref))), (variant, zyx)
