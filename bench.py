@@ -396,6 +396,12 @@ def run_grf256(args):
     return 0
 
 
+def two_array_kernel(variant):
+    """Step kernel of the FP32 modes with two haloed arrays (two species; u and
+    the diffusivity factor) for a kernel variant."""
+    return {"plain": "k_step", "pipelined": "k_step_pipe", "prefetch": "k_step_pipe"}.get(variant, "k_step_rows2")
+
+
 # ---------------------------------------------------------------------------
 def run_reactive512(args):
     import torch
@@ -446,10 +452,12 @@ def run_reactive512(args):
                                  % (n, phys.extra["pore_fraction"], phys.steps),
                      "block": args.block, "kernel": args.variant, "n_active": g.n_active, "n_blocks": g.n_blocks,
                      "band_blocks": g.info["n_band_blocks"]},
-          "roofline": {"bound": "hbm", "kernel": "k_step_pipe", "achieved": algo_bytes / (per_launch_ms / 1e3) / 1e9,
+          "roofline": {"bound": "hbm", "kernel": two_array_kernel(args.variant),
+                       "achieved": algo_bytes / (per_launch_ms / 1e3) / 1e9,
                        "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                        "frac": algo_bytes / (per_launch_ms / 1e3) / 1e9 / peak,
-                       "traffic": profile_traffic("k_step_pipe_%s_f32_reactive512.md" % args.variant),
+                       "traffic": profile_traffic("%s_%s_f32_reactive512.md"
+                                                  % (two_array_kernel(args.variant), args.variant)),
                        "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": per_launch_ms * 1e3},
           "result": {"mass_A0_B0": [red0[0]["mass"], red0[1]["mass"]], "mass_A_B_end": list(masses[-1]),
                      "total_mass_change": (masses[-1][0] + masses[-1][1]) - (red0[0]["mass"] + red0[1]["mass"])},
@@ -524,10 +532,11 @@ def run_inhom512(args):
                                  "Eq. 6 (D_min 0, D_max 1, gamma2 4, gamma1 %.3g), c = 1 held on x = 0, %d steps"
                                  % (n, phys.extra["pore_fraction"], g1, phys.steps),
                      "block": args.block, "kernel": args.variant, "n_active": g.n_active, "n_blocks": g.n_blocks},
-          "roofline": {"bound": "hbm", "kernel": "k_step_pipe", "achieved": algo_bytes / (per_launch_ms / 1e3) / 1e9,
+          "roofline": {"bound": "hbm", "kernel": two_array_kernel(args.variant),
+                       "achieved": algo_bytes / (per_launch_ms / 1e3) / 1e9,
                        "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                        "frac": algo_bytes / (per_launch_ms / 1e3) / 1e9 / peak,
-                       "traffic": profile_traffic("k_step_pipe_%s_inhom512.md" % args.variant),
+                       "traffic": profile_traffic("%s_%s_inhom512.md" % (two_array_kernel(args.variant), args.variant)),
                        "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": per_launch_ms * 1e3},
           "result": {"mass_start": red0[0]["mass"], "mass_end": masses[-1]},
           "clocks": clocks, "cpu_baseline": cpu})

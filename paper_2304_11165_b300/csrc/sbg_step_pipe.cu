@@ -543,7 +543,8 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
 
 // ---------------------------------------------------------------------------
 // Two rows per thread, for the modes with one haloed array (FP32 one species,
-// SBG_F32R correction).  Groups of 1024 voxels (sixteen 4^3 blocks or two 8^3
+// SBG_F32R correction) and, with cp.async halos, two (species A and B; u and
+// the diffusivity factor).  Groups of 1024 voxels (sixteen 4^3 blocks or two 8^3
 // blocks); each thread updates the rows (y, z0) and (y, z0 + B/2) of four
 // voxels, so the per-group work (face ids, Dirichlet bits, the stage barrier,
 // spans) is shared by eight voxels, and a quarter-warp's row loads cover
@@ -601,22 +602,113 @@ __device__ __forceinline__ float4 row_update(const float4 u, float xm, float xp,
     return make_float4(res[0], res[1], res[2], res[3]);
 }
 
+// One row of one array with its neighbour values as read (sentinels where a
+// neighbour is outside Omega or its block is absent).
+struct RowVals {
+    float4 u;
+    float xm, xp;
+    float4 ym, yp, zm, zp;
+};
+
+// x differences along a row (R = xm, the four values, xp: Dx[j] = R[j+1] - R[j]).
+__device__ __forceinline__ void row_dx(const RowVals &v, float Dx[5]) {
+    const float R[6] = {v.xm, v.u.x, v.u.y, v.u.z, v.u.w, v.xp};
+#pragma unroll
+    for (int jj = 0; jj < 5; ++jj) Dx[jj] = __fsub_rn(R[jj + 1], R[jj]);
+}
+
+// Two species A (v0) and B (v1) with the surface transfer k w A: A loses it,
+// B gains it.  Which neighbours are outside Omega is read from species A for
+// both species, as in the one-row kernel.
+template <bool REACT>
+__device__ __forceinline__ void row_update_fwd2(const RowVals &v0, const RowVals &v1, const float4 w4, uint32_t hb,
+                                                const StepCoef<float> &kc, float4 &o0, float4 &o1) {
+    bool actx[6];
+    actx[0] = !is_sent(v0.xm);
+    actx[5] = !is_sent(v0.xp);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) actx[i + 1] = !is_sent(f4get(v0.u, i));
+    float D0[5], D1[5];
+    row_dx(v0, D0);
+    row_dx(v1, D1);
+    float r0[4], r1[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float c0 = f4get(v0.u, i), c1 = f4get(v1.u, i);
+        const float y0[4] = {f4get(v0.ym, i), f4get(v0.yp, i), f4get(v0.zm, i), f4get(v0.zp, i)};
+        const float y1[4] = {f4get(v1.ym, i), f4get(v1.yp, i), f4get(v1.zm, i), f4get(v1.zp, i)};
+        float n0[4], n1[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const bool out = is_sent(y0[f]);
+            n0[f] = out ? c0 : y0[f];
+            n1[f] = out ? c1 : y1[f];
+        }
+        const float dxs0 = __fsub_rn(actx[i + 2] ? D0[i + 1] : 0.f, actx[i] ? D0[i] : 0.f);
+        const float dxs1 = __fsub_rn(actx[i + 2] ? D1[i + 1] : 0.f, actx[i] ? D1[i] : 0.f);
+        const float t = REACT ? __fmul_rn(__fmul_rn(kc.k, f4get(w4, i)), c0) : 0.f;
+        const float nr0 = fused_update_dx(c0, dxs0, n0[0], n0[1], n0[2], n0[3], kc.c[0], kc.dt, kc.decay[0], -t);
+        const float nr1 = fused_update_dx(c1, dxs1, n1[0], n1[1], n1[2], n1[3], kc.c[1], kc.dt, kc.decay[1], t);
+        const bool upd = actx[i + 1] && !((hb >> i) & 1u);
+        r0[i] = upd ? nr0 : c0;
+        r1[i] = upd ? nr1 : c1;
+    }
+    o0 = make_float4(r0[0], r0[1], r0[2], r0[3]);
+    o1 = make_float4(r1[0], r1[1], r1[2], r1[3]);
+}
+
+// Inhomogeneous diffusion (Eq. 6 factor e, v1): one-sided differences of u
+// (v0; 0 towards a neighbour outside Omega) and the neighbours' raw factors.
+__device__ __forceinline__ float4 row_update_inh(const RowVals &v0, const RowVals &v1, uint32_t hb,
+                                                 const StepCoef<float> &kc) {
+    bool actx[6];
+    actx[0] = !is_sent(v0.xm);
+    actx[5] = !is_sent(v0.xp);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) actx[i + 1] = !is_sent(f4get(v0.u, i));
+    float D0[5];
+    row_dx(v0, D0);
+    float res[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float c = f4get(v0.u, i);
+        const float yv[4] = {f4get(v0.ym, i), f4get(v0.yp, i), f4get(v0.zm, i), f4get(v0.zp, i)};
+        float nv[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) nv[f] = is_sent(yv[f]) ? c : yv[f];
+        const float dp[3] = {actx[i + 2] ? D0[i + 1] : 0.f, __fsub_rn(nv[1], c), __fsub_rn(nv[3], c)};
+        const float dm[3] = {actx[i] ? D0[i] : 0.f, __fsub_rn(c, nv[0]), __fsub_rn(c, nv[2])};
+        const float en[6] = {i == 0 ? v1.xm : f4get(v1.u, i - 1), i == 3 ? v1.xp : f4get(v1.u, i + 1),
+                             f4get(v1.ym, i), f4get(v1.yp, i), f4get(v1.zm, i), f4get(v1.zp, i)};
+        const float nr = inh_update(c, dp, dm, f4get(v1.u, i), en, kc.c[0], kc.dt, kc.decay[0]);
+        const bool upd = actx[i + 1] && !((hb >> i) & 1u);
+        res[i] = upd ? nr : c;
+    }
+    return make_float4(res[0], res[1], res[2], res[3]);
+}
+
 // AH: halo values copied one group ahead with per-thread cp.async into the
 // other half of a double halo buffer (no registers held across the group).
 // WL: the groups come from a work list (a separate instance, so that the
 // plain walk over the block list keeps its registers).
-template <int MODE, int B, bool REACT, int S, int MINB, bool AH, bool WL>
+// NH: arrays streamed, each with halos: 1 (u, or the SBG_F32R correction d,
+// whose source r is read per row from global memory) or 2 (species A and B, or
+// u and the diffusivity factor).  With two arrays the surface weights are read
+// per row from global memory too: without a weight buffer one more CTA fits
+// in an SM's shared memory.
+template <int MODE, int NH, int B, bool REACT, int S, int MINB, bool AH, bool WL>
 __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArgs a, const PipeIO io, int *err) {
     using L = Rows2Layout<B>;
     constexpr int B3 = L::B3;
     constexpr int G = L::G;
     constexpr int TPB = L::TPB;
-    constexpr int NA = 1;  // streamed array (u or d); the SBG_F32R source r is read per row from global memory
+    constexpr int NA = NH;
+    constexpr bool WSM = AH && REACT && NH == 1;  // row weights staged in shared memory by cp.async
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *stages = reinterpret_cast<float *>(smem_raw);  // [S][NA][1024]
-    float *halo = stages + (size_t)S * NA * kGroup2;      // [AH ? 2 : 1][kHalo]
-    float *wbuf = halo + (AH ? 2 : 1) * L::kHalo;         // AH and REACT: [2][1024] row weights
-    uint64_t *full = reinterpret_cast<uint64_t *>(wbuf + ((AH && REACT) ? 2 * kGroup2 : 0));
+    float *halo = stages + (size_t)S * NA * kGroup2;      // [AH ? 2 : 1][NH][kHalo]
+    float *wbuf = halo + (AH ? 2 : 1) * NH * L::kHalo;    // WSM: [2][1024] row weights
+    uint64_t *full = reinterpret_cast<uint64_t *>(wbuf + (WSM ? 2 * kGroup2 : 0));
 
     const int tid = threadIdx.x;
     // (the launcher guarantees nb * B^3 < 2^31: 32-bit block ids and slots)
@@ -677,15 +769,14 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
     const int sxm = L::face(j, 0) + z0 * B + y, sxp = L::face(j, 1) + z0 * B + y;
     const int sym = L::face(j, 2) + z0 * B + x0, syp = L::face(j, 3) + z0 * B + x0;
     const int szm = L::face(j, 4) + y * B + x0, szp = L::face(j, 5) + y * B + x0;
-    const float *s0 = io.src[0];
 
     struct Ids {
         int xm, xp, ym, yp, zm, zp, ws;
         uint32_t hb;  // held bits: row a in bits 0-3, row b in bits 4-7
     };
     struct Halo {
-        float vxm[2], vxp[2];
-        float4 vym[2], vyp[2], vzm, vzp;
+        float vxm[NH][2], vxp[NH][2];
+        float4 vym[NH][2], vyp[NH][2], vzm[NH], vzp[NH];
         float4 w[2];
         int ixm, ixp;  // x neighbour inside the group: row a's offset in the stage tile, else -1
         uint32_t hb;
@@ -720,44 +811,57 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
         if (gi < g1) span(gi, b0, nblk);
         h.ixm = (hxm && (unsigned)(id.xm - b0) < (unsigned)nblk) ? (id.xm - b0) * B3 + oxm : -1;
         h.ixp = (hxp && (unsigned)(id.xp - b0) < (unsigned)nblk) ? (id.xp - b0) * B3 + oxp : -1;
-        const float SENT = sentinel_f32();
-        const float4 SENT4 = make_float4(SENT, SENT, SENT, SENT);
+#pragma unroll
+        for (int k = 0; k < NH; ++k) {
+            const float *sk = io.src[k];
+            // the diffusivity factor of an absent block reads 0
+            const float ab = (MODE == kInh && k == 1) ? 0.f : sentinel_f32();
+            const float4 ab4 = make_float4(ab, ab, ab, ab);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                h.vxm[k][q] = (id.xm >= 0 && h.ixm < 0) ? __ldg(sk + id.xm * B3 + oxm + q * ZB) : ab;
+                h.vxp[k][q] = (id.xp >= 0 && h.ixp < 0) ? __ldg(sk + id.xp * B3 + oxp + q * ZB) : ab;
+                h.vym[k][q] = (id.ym >= 0) ? __ldg(reinterpret_cast<const float4 *>(sk + id.ym * B3 + oym + q * ZB)) : ab4;
+                h.vyp[k][q] = (id.yp >= 0) ? __ldg(reinterpret_cast<const float4 *>(sk + id.yp * B3 + oyp + q * ZB)) : ab4;
+            }
+            h.vzm[k] = (id.zm >= 0) ? __ldg(reinterpret_cast<const float4 *>(sk + id.zm * B3 + ozm)) : ab4;
+            h.vzp[k] = (id.zp >= 0) ? __ldg(reinterpret_cast<const float4 *>(sk + id.zp * B3 + ozp)) : ab4;
+        }
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            h.vxm[q] = (id.xm >= 0 && h.ixm < 0) ? __ldg(s0 + id.xm * B3 + oxm + q * ZB) : SENT;
-            h.vxp[q] = (id.xp >= 0 && h.ixp < 0) ? __ldg(s0 + id.xp * B3 + oxp + q * ZB) : SENT;
-            h.vym[q] = (id.ym >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.ym * B3 + oym + q * ZB)) : SENT4;
-            h.vyp[q] = (id.yp >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.yp * B3 + oyp + q * ZB)) : SENT4;
             h.w[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (REACT && id.ws >= 0) h.w[q] = __ldg(reinterpret_cast<const float4 *>(a.w + id.ws * B3 + la + q * ZB));
         }
-        h.vzm = (id.zm >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.zm * B3 + ozm)) : SENT4;
-        h.vzp = (id.zp >= 0) ? __ldg(reinterpret_cast<const float4 *>(s0 + id.zp * B3 + ozp)) : SENT4;
         h.hb = id.hb;
     };
     auto park = [&](const Halo &h) {
-        if (hxm && h.ixm < 0) {
-            halo[sxm] = h.vxm[0];
-            halo[sxm + HB] = h.vxm[1];
+#pragma unroll
+        for (int k = 0; k < NH; ++k) {
+            float *hk = halo + k * L::kHalo;
+            if (hxm && h.ixm < 0) {
+                hk[sxm] = h.vxm[k][0];
+                hk[sxm + HB] = h.vxm[k][1];
+            }
+            if (hxp && h.ixp < 0) {
+                hk[sxp] = h.vxp[k][0];
+                hk[sxp + HB] = h.vxp[k][1];
+            }
+            if (hym) {
+                *reinterpret_cast<float4 *>(hk + sym) = h.vym[k][0];
+                *reinterpret_cast<float4 *>(hk + sym + HB) = h.vym[k][1];
+            }
+            if (hyp) {
+                *reinterpret_cast<float4 *>(hk + syp) = h.vyp[k][0];
+                *reinterpret_cast<float4 *>(hk + syp + HB) = h.vyp[k][1];
+            }
+            if (hzm) *reinterpret_cast<float4 *>(hk + szm) = h.vzm[k];
+            if (hzp) *reinterpret_cast<float4 *>(hk + szp) = h.vzp[k];
         }
-        if (hxp && h.ixp < 0) {
-            halo[sxp] = h.vxp[0];
-            halo[sxp + HB] = h.vxp[1];
-        }
-        if (hym) {
-            *reinterpret_cast<float4 *>(halo + sym) = h.vym[0];
-            *reinterpret_cast<float4 *>(halo + sym + HB) = h.vym[1];
-        }
-        if (hyp) {
-            *reinterpret_cast<float4 *>(halo + syp) = h.vyp[0];
-            *reinterpret_cast<float4 *>(halo + syp + HB) = h.vyp[1];
-        }
-        if (hzm) *reinterpret_cast<float4 *>(halo + szm) = h.vzm;
-        if (hzp) *reinterpret_cast<float4 *>(halo + szp) = h.vzp;
     };
 
-    // AH: per halo buffer, the row's x offsets inside the group and held bits
-    int aixm0 = -1, aixm1 = -1, aixp0 = -1, aixp1 = -1;
+    // AH: per halo buffer, the row's x offsets inside the group, held bits and
+    // (two arrays) the group's weight slab
+    int aixm0 = -1, aixm1 = -1, aixp0 = -1, aixp1 = -1, aws0 = -1, aws1 = -1;
     uint32_t ahb0 = 0u, ahb1 = 0u;
     auto issue_async = [&](int gi, const Ids &id, int buf) {
         if (!AH) return;
@@ -768,49 +872,53 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
             if (j < nblk) {
                 ixm = (hxm && (unsigned)(id.xm - b0) < (unsigned)nblk) ? (id.xm - b0) * B3 + oxm : -1;
                 ixp = (hxp && (unsigned)(id.xp - b0) < (unsigned)nblk) ? (id.xp - b0) * B3 + oxp : -1;
-                const float SENT = sentinel_f32();
-                const float4 SENT4 = make_float4(SENT, SENT, SENT, SENT);
-                float *hb = halo + buf * L::kHalo;
-                if (hxm && ixm < 0) {
-                    if (id.xm >= 0) {
-                        cp_async4(hb + sxm, s0 + id.xm * B3 + oxm);
-                        cp_async4(hb + sxm + HB, s0 + id.xm * B3 + oxm + ZB);
-                    } else {
-                        hb[sxm] = SENT;
-                        hb[sxm + HB] = SENT;
-                    }
-                }
-                if (hxp && ixp < 0) {
-                    if (id.xp >= 0) {
-                        cp_async4(hb + sxp, s0 + id.xp * B3 + oxp);
-                        cp_async4(hb + sxp + HB, s0 + id.xp * B3 + oxp + ZB);
-                    } else {
-                        hb[sxp] = SENT;
-                        hb[sxp + HB] = SENT;
-                    }
-                }
-                if (hzm) {
-                    if (id.zm >= 0) cp_async16(hb + szm, s0 + id.zm * B3 + ozm);
-                    else *reinterpret_cast<float4 *>(hb + szm) = SENT4;
-                }
-                if (hzp) {
-                    if (id.zp >= 0) cp_async16(hb + szp, s0 + id.zp * B3 + ozp);
-                    else *reinterpret_cast<float4 *>(hb + szp) = SENT4;
-                }
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    if (hym) {
-                        if (id.ym >= 0) cp_async16(hb + sym + q * HB, s0 + id.ym * B3 + oym + q * ZB);
-                        else *reinterpret_cast<float4 *>(hb + sym + q * HB) = SENT4;
+                for (int k = 0; k < NH; ++k) {
+                    const float *sk = io.src[k];
+                    const float ab = (MODE == kInh && k == 1) ? 0.f : sentinel_f32();
+                    const float4 ab4 = make_float4(ab, ab, ab, ab);
+                    float *hb = halo + (buf * NH + k) * L::kHalo;
+                    if (hxm && ixm < 0) {
+                        if (id.xm >= 0) {
+                            cp_async4(hb + sxm, sk + id.xm * B3 + oxm);
+                            cp_async4(hb + sxm + HB, sk + id.xm * B3 + oxm + ZB);
+                        } else {
+                            hb[sxm] = ab;
+                            hb[sxm + HB] = ab;
+                        }
                     }
-                    if (hyp) {
-                        if (id.yp >= 0) cp_async16(hb + syp + q * HB, s0 + id.yp * B3 + oyp + q * ZB);
-                        else *reinterpret_cast<float4 *>(hb + syp + q * HB) = SENT4;
+                    if (hxp && ixp < 0) {
+                        if (id.xp >= 0) {
+                            cp_async4(hb + sxp, sk + id.xp * B3 + oxp);
+                            cp_async4(hb + sxp + HB, sk + id.xp * B3 + oxp + ZB);
+                        } else {
+                            hb[sxp] = ab;
+                            hb[sxp + HB] = ab;
+                        }
                     }
-                    if (REACT) {
-                        float *wb = wbuf + buf * kGroup2 + va + q * ZB;
-                        if (id.ws >= 0) cp_async16(wb, a.w + id.ws * B3 + la + q * ZB);
-                        else *reinterpret_cast<float4 *>(wb) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (hzm) {
+                        if (id.zm >= 0) cp_async16(hb + szm, sk + id.zm * B3 + ozm);
+                        else *reinterpret_cast<float4 *>(hb + szm) = ab4;
+                    }
+                    if (hzp) {
+                        if (id.zp >= 0) cp_async16(hb + szp, sk + id.zp * B3 + ozp);
+                        else *reinterpret_cast<float4 *>(hb + szp) = ab4;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (hym) {
+                            if (id.ym >= 0) cp_async16(hb + sym + q * HB, sk + id.ym * B3 + oym + q * ZB);
+                            else *reinterpret_cast<float4 *>(hb + sym + q * HB) = ab4;
+                        }
+                        if (hyp) {
+                            if (id.yp >= 0) cp_async16(hb + syp + q * HB, sk + id.yp * B3 + oyp + q * ZB);
+                            else *reinterpret_cast<float4 *>(hb + syp + q * HB) = ab4;
+                        }
+                        if (WSM && k == 0) {
+                            float *wb = wbuf + buf * kGroup2 + va + q * ZB;
+                            if (id.ws >= 0) cp_async16(wb, a.w + id.ws * B3 + la + q * ZB);
+                            else *reinterpret_cast<float4 *>(wb) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
                     }
                 }
             }
@@ -819,10 +927,12 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
             aixm1 = ixm;
             aixp1 = ixp;
             ahb1 = id.hb;
+            aws1 = id.ws;
         } else {
             aixm0 = ixm;
             aixp0 = ixp;
             ahb0 = id.hb;
+            aws0 = id.ws;
         }
         cp_async_commit();
     };
@@ -841,6 +951,15 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
         if (MODE == kSrc && valid) {
             ra = __ldg(reinterpret_cast<const float4 *>(io.src[1] + b * B3 + la));
             rb = __ldg(reinterpret_cast<const float4 *>(io.src[1] + b * B3 + la + ZB));
+        }
+        // two arrays, cp.async halos: this row pair's surface weights (read now, used after the barrier)
+        float4 wga = make_float4(0.f, 0.f, 0.f, 0.f), wgb = wga;
+        if (REACT && AH && !WSM && valid) {
+            const int ws = (it & 1) ? aws1 : aws0;
+            if (ws >= 0) {
+                wga = __ldg(reinterpret_cast<const float4 *>(a.w + ws * B3 + la));
+                wgb = __ldg(reinterpret_cast<const float4 *>(a.w + ws * B3 + la + ZB));
+            }
         }
         if (AH) {
             issue_async(gi + 1, id1, (it + 1) & 1);
@@ -866,14 +985,46 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
         if (!valid) return true;
         if (!AH) park(cur);
         const int buf = AH ? (it & 1) : 0;
-        const float *hbase = halo + buf * L::kHalo;
+        const float *hbase = halo + buf * NH * L::kHalo;
         const int ixm = AH ? (buf ? aixm1 : aixm0) : cur.ixm;
         const int ixp = AH ? (buf ? aixp1 : aixp0) : cur.ixp;
         const uint32_t hbits = AH ? (buf ? ahb1 : ahb0) : cur.hb;
         float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0;
         if (REACT) {
-            w0 = AH ? *reinterpret_cast<const float4 *>(wbuf + buf * kGroup2 + va) : cur.w[0];
-            w1 = AH ? *reinterpret_cast<const float4 *>(wbuf + buf * kGroup2 + va + ZB) : cur.w[1];
+            w0 = WSM ? *reinterpret_cast<const float4 *>(wbuf + buf * kGroup2 + va) : AH ? wga : cur.w[0];
+            w1 = WSM ? *reinterpret_cast<const float4 *>(wbuf + buf * kGroup2 + va + ZB) : AH ? wgb : cur.w[1];
+        }
+        if constexpr (NH == 2) {
+            // row q (a: 0, b: 1) of array k with its neighbours
+            auto gather = [&](int k, int q) {
+                const float *t = stages + ((size_t)s * NA + k) * kGroup2;
+                const float *hk = hbase + k * L::kHalo;
+                const int o = q * ZB, ho = q * HB;
+                RowVals v;
+                v.u = *reinterpret_cast<const float4 *>(t + va + o);
+                v.xm = hxm ? (ixm >= 0 ? t[ixm + o] : hk[sxm + ho]) : t[va + o - 1];
+                v.xp = hxp ? (ixp >= 0 ? t[ixp + o] : hk[sxp + ho]) : t[va + o + 4];
+                v.ym = *reinterpret_cast<const float4 *>(hym ? hk + sym + ho : t + va + o - B);
+                v.yp = *reinterpret_cast<const float4 *>(hyp ? hk + syp + ho : t + va + o + B);
+                v.zm = *reinterpret_cast<const float4 *>((q == 0 && hzm) ? hk + szm : t + va + o - B * B);
+                v.zp = *reinterpret_cast<const float4 *>((q == 1 && hzp) ? hk + szp : t + va + o + B * B);
+                return v;
+            };
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const RowVals v0 = gather(0, q), v1 = gather(1, q);
+                const uint32_t hq = hbits >> (4 * q);
+                float *d0 = io.dst[0] + b * B3 + la + q * ZB;
+                if (MODE == kInh) {
+                    *reinterpret_cast<float4 *>(d0) = row_update_inh(v0, v1, hq, a.cf);
+                } else {
+                    float4 o0, o1;
+                    row_update_fwd2<REACT>(v0, v1, q ? w1 : w0, hq, a.cf, o0, o1);
+                    *reinterpret_cast<float4 *>(d0) = o0;
+                    *reinterpret_cast<float4 *>(io.dst[1] + b * B3 + la + q * ZB) = o1;
+                }
+            }
+            return true;
         }
 
         const float *t = stages + (size_t)s * NA * kGroup2;
@@ -956,23 +1107,25 @@ static cudaError_t launch_pipe_hv(const StepArgs &a, const PipeIO &io, int ctas_
     return cudaGetLastError();
 }
 
-template <int MODE, int B, bool REACT, bool AH, bool WL>
+template <int MODE, int NH, int B, bool REACT, bool AH, bool WL>
 static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_per_sm, int *err, cudaStream_t s) {
-    constexpr int NA = 1;
+    constexpr int NA = NH;
+    constexpr bool WSM = AH && REACT && NH == 1;
     // Two ring stages (one group copied ahead while one computes) leave room for 9-10
     // CTAs per SM; the row loads are conflict-free, so resident warps are what hides the
     // latency: 9 CTAs (56 registers) for the SBG_F32R correction, 10 (51) for the rest,
     // fewer where the shared memory does not fit them (measured on grf256: 33.5 -> 28.4 us
     // and 29.6 -> 23.8 us against four stages and 5-6 CTAs).  Without cp.async halos the
     // halo values wait in registers across the group, so that variant keeps 7.  The
-    // SBG_F32R work-list instance (batch solver) keeps 8, as 9 would spill.
+    // SBG_F32R work-list instance (batch solver) keeps 8, as 9 would spill.  Two arrays:
+    // the shared memory holds 5 CTAs with 4^3 blocks (40 KB each), 7 with 8^3 blocks.
     constexpr int S = 2;
-    constexpr size_t smem = ((size_t)S * NA * kGroup2 + (AH ? 2 : 1) * Rows2Layout<B>::kHalo +
-                             ((AH && REACT) ? 2 * kGroup2 : 0)) * sizeof(float) + S * sizeof(uint64_t);
+    constexpr size_t smem = ((size_t)S * NA * kGroup2 + (AH ? 2 : 1) * NH * Rows2Layout<B>::kHalo +
+                             (WSM ? 2 * kGroup2 : 0)) * sizeof(float) + S * sizeof(uint64_t);
     constexpr int kFit = (int)((228 * 1024) / (smem + 1024));
-    constexpr int kWant = !AH ? 7 : MODE == kSrc ? (WL ? 8 : 9) : 10;  // the work-list walk needs 4 more
+    constexpr int kWant = NH == 2 ? 5 : !AH ? 7 : MODE == kSrc ? (WL ? 8 : 9) : 10;  // the work-list walk needs 4 more
     constexpr int MINB = kWant < kFit ? kWant : kFit;
-    auto kern = k_step_rows2<MODE, B, REACT, S, MINB, AH, WL>;
+    auto kern = k_step_rows2<MODE, NH, B, REACT, S, MINB, AH, WL>;
     static int occ = -1, nsm = 0;
     if (occ < 0) {
         int dev = 0;
@@ -997,16 +1150,32 @@ static cudaError_t launch_rows2_a(const StepArgs &a, const PipeIO &io, int B, bo
                                   cudaStream_t s) {
     if (a.items) {
         if (B == 8)
-            return react ? launch_rows2<MODE, 8, true, AH, true>(a, io, ctas_per_sm, err, s)
-                         : launch_rows2<MODE, 8, false, AH, true>(a, io, ctas_per_sm, err, s);
-        return react ? launch_rows2<MODE, 4, true, AH, true>(a, io, ctas_per_sm, err, s)
-                     : launch_rows2<MODE, 4, false, AH, true>(a, io, ctas_per_sm, err, s);
+            return react ? launch_rows2<MODE, 1, 8, true, AH, true>(a, io, ctas_per_sm, err, s)
+                         : launch_rows2<MODE, 1, 8, false, AH, true>(a, io, ctas_per_sm, err, s);
+        return react ? launch_rows2<MODE, 1, 4, true, AH, true>(a, io, ctas_per_sm, err, s)
+                     : launch_rows2<MODE, 1, 4, false, AH, true>(a, io, ctas_per_sm, err, s);
     }
     if (B == 8)
-        return react ? launch_rows2<MODE, 8, true, AH, false>(a, io, ctas_per_sm, err, s)
-                     : launch_rows2<MODE, 8, false, AH, false>(a, io, ctas_per_sm, err, s);
-    return react ? launch_rows2<MODE, 4, true, AH, false>(a, io, ctas_per_sm, err, s)
-                 : launch_rows2<MODE, 4, false, AH, false>(a, io, ctas_per_sm, err, s);
+        return react ? launch_rows2<MODE, 1, 8, true, AH, false>(a, io, ctas_per_sm, err, s)
+                     : launch_rows2<MODE, 1, 8, false, AH, false>(a, io, ctas_per_sm, err, s);
+    return react ? launch_rows2<MODE, 1, 4, true, AH, false>(a, io, ctas_per_sm, err, s)
+                 : launch_rows2<MODE, 1, 4, false, AH, false>(a, io, ctas_per_sm, err, s);
+}
+// two arrays (species A and B, or u and the diffusivity factor): cp.async
+// halos and the walk over the block list only
+template <int MODE>
+static cudaError_t launch_rows2_two(const StepArgs &a, const PipeIO &io, int B, bool react, int ctas_per_sm,
+                                    int *err, cudaStream_t s) {
+    if constexpr (MODE == kInh) {
+        return B == 8 ? launch_rows2<kInh, 2, 8, false, true, false>(a, io, ctas_per_sm, err, s)
+                      : launch_rows2<kInh, 2, 4, false, true, false>(a, io, ctas_per_sm, err, s);
+    } else {
+        if (B == 8)
+            return react ? launch_rows2<MODE, 2, 8, true, true, false>(a, io, ctas_per_sm, err, s)
+                         : launch_rows2<MODE, 2, 8, false, true, false>(a, io, ctas_per_sm, err, s);
+        return react ? launch_rows2<MODE, 2, 4, true, true, false>(a, io, ctas_per_sm, err, s)
+                     : launch_rows2<MODE, 2, 4, false, true, false>(a, io, ctas_per_sm, err, s);
+    }
 }
 // halo variant 0: loads when the group comes up; 2: cp.async one group ahead
 template <int MODE>
@@ -1036,12 +1205,16 @@ static cudaError_t launch_pipe_b(const StepArgs &a, const PipeIO &io, int B, boo
 
 // The single-array modes (FP32 one species, SBG_F32R) run the two-row kernel
 // unless register-prefetched halos are asked for; its groups (and work-list
-// spans) hold up to 1024 voxels, the one-row kernel's 512.
-static bool rows2_path(sbg_dtype dtype, int ns, bool eps, int hv) {
-    return hv != 1 && ns == 1 && !eps && (dtype == SBG_F32 || dtype == SBG_F32R);
+// spans) hold up to 1024 voxels, the one-row kernel's 512.  The two-array FP32
+// modes (two species; one species with a diffusivity factor) run it with
+// cp.async halos when they walk the block list; work lists and the other halo
+// variants keep the one-row kernel.
+static bool rows2_path(sbg_dtype dtype, int ns, bool eps, int hv, bool worklist) {
+    if (hv != 1 && ns == 1 && !eps && (dtype == SBG_F32 || dtype == SBG_F32R)) return true;
+    return hv == 2 && !worklist && dtype == SBG_F32 && ((ns == 2 && !eps) || (ns == 1 && eps));
 }
 int step_work_group_voxels(sbg_dtype dtype, int ns, bool eps, int halo_variant) {
-    return rows2_path(dtype, ns, eps, halo_variant) ? kGroup2 : kGroupVox;
+    return rows2_path(dtype, ns, eps, halo_variant, true) ? kGroup2 : kGroupVox;
 }
 
 bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool react, int halo_variant,
@@ -1061,25 +1234,29 @@ bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool re
         io.src[0] = (const float *)a.in[0];
         io.src[1] = a.src_term;
         io.dst[0] = (float *)a.out[0];
-        e = rows2_path(dtype, ns, a.eps != nullptr, hv)
+        e = rows2_path(dtype, ns, a.eps != nullptr, hv, a.items != nullptr)
                 ? launch_rows2_b<kSrc>(a, io, B, react, hv, ctas_per_sm, err_flag, s)
                 : launch_pipe_b<kSrc, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
     } else if (dtype == SBG_F32 && ns == 1 && a.eps) {
         io.src[0] = (const float *)a.in[0];
         io.src[1] = a.eps;
         io.dst[0] = (float *)a.out[0];
-        e = launch_pipe_b<kInh, 1>(a, io, B, false, hv, ctas_per_sm, err_flag, s);
+        e = rows2_path(dtype, ns, true, hv, a.items != nullptr)
+                ? launch_rows2_two<kInh>(a, io, B, false, ctas_per_sm, err_flag, s)
+                : launch_pipe_b<kInh, 1>(a, io, B, false, hv, ctas_per_sm, err_flag, s);
     } else if (dtype == SBG_F32 && (ns == 1 || ns == 2)) {
         for (int k = 0; k < ns; ++k) {
             io.src[k] = (const float *)a.in[k];
             io.dst[k] = (float *)a.out[k];
         }
         if (ns == 1)
-            e = rows2_path(dtype, ns, false, hv)
+            e = rows2_path(dtype, ns, false, hv, a.items != nullptr)
                     ? launch_rows2_b<kFwd>(a, io, B, react, hv, ctas_per_sm, err_flag, s)
                     : launch_pipe_b<kFwd, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
         else
-            e = launch_pipe_b<kFwd, 2>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
+            e = rows2_path(dtype, ns, false, hv, a.items != nullptr)
+                    ? launch_rows2_two<kFwd>(a, io, B, react, ctas_per_sm, err_flag, s)
+                    : launch_pipe_b<kFwd, 2>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
     } else {
         return false;
     }

@@ -59,6 +59,20 @@ def test_fp32_kernels_match_the_oracle_and_each_other(block):
     assert rel_err(outs[0], ref) < 2e-5
 
 
+@pytest.mark.parametrize("block", [4, 8])
+def test_two_row_kernel_with_few_ctas(block):
+    """u and the factor on the two-row kernel (cp.async halos) with one and two
+    persistent CTAs per SM: many groups per CTA, the same field as the
+    one-thread-per-voxel kernel."""
+    phi, eps, ph, u0 = case((64, 60, 56), 14)
+    g = Grid(phi, block=block).set_diffusivity(eps.astype(np.float32))
+    p = make_params(ph)
+    a = State(g, 1, "f32").set_kernel("plain").set(u0).step(p, 33).get()
+    for per_sm in (1, 2, 0):
+        b = State(g, 1, "f32").set_kernel("async", ctas_per_sm=per_sm).set(u0).step(p, 33).get()
+        np.testing.assert_array_equal(a, b)
+
+
 def test_eq6_factor_on_the_device_matches_the_oracle():
     phi, _, ph, u0 = case((21, 18, 15), 13)
     args = (0.05, 0.95, -0.8, 2.5)

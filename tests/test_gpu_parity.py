@@ -269,3 +269,17 @@ def test_pipelined_kernel_with_few_ctas_walks_long_ranges():
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(a, c)
     np.testing.assert_array_equal(a, d)
+
+
+@pytest.mark.parametrize("block", [4, 8])
+def test_two_species_two_row_kernel_with_few_ctas(block):
+    """Two species with the surface transfer on the two-row kernel (cp.async
+    halos), one and two persistent CTAs per SM: many groups per CTA, both
+    halo buffers reused, the same fields as the one-thread-per-voxel kernel."""
+    phi, phys, u0 = make_case((64, 60, 56), 2, 0.6, (0, 1), 13)
+    p = make_params(phys)
+    g = Grid(phi, block=block)
+    a = State(g, 2, "f32").set_kernel("plain").set_all(u0).step(p, 31).get_all()
+    for per_sm in (1, 2, 0):
+        b = State(g, 2, "f32").set_kernel("async", ctas_per_sm=per_sm).set_all(u0).step(p, 31).get_all()
+        np.testing.assert_array_equal(a, b)
