@@ -293,7 +293,8 @@ static sbg_status launch_adj_pipe(sbg_tape tp, const void *u, sbg_state lam, cud
     io.gsum = tp->partials;
     for (int ax = 0; ax < 3; ++ax) io.inv2[ax] = (float)(1.0 / (tp->p.dx[ax] * tp->p.dx[ax]));
     int grid = 0;
-    cudaError_t e = launch_adjoint_pipe(a, io, tp->ns, g->B, tp->p.k_surf != 0.0, (int)tp->nctas, g->err, s, &grid);
+    // the surface terms always: dL/dk is not 0 at k = 0 (and with k = 0 they leave lambda unchanged)
+    cudaError_t e = launch_adjoint_pipe(a, io, tp->ns, g->B, true, (int)tp->nctas, g->err, s, &grid);
     if (e != cudaSuccess) return cuda_fail(e, "pipelined adjoint kernel launch");
     lam->cur = 1 - lam->cur;
     return SBG_OK;

@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
 // ---------------------------------------------------------------------------
 // Two rows per thread, for the modes with one haloed array (FP32 one species,
 // SBG_F32R correction) and, with cp.async halos, two (species A and B; u and
-// the diffusivity factor).  Groups of 1024 voxels (sixteen 4^3 blocks or two 8^3
+// the diffusivity factor; the one-species adjoint's lambda and u^n).  Groups of 1024 voxels (sixteen 4^3 blocks or two 8^3
 // blocks); each thread updates the rows (y, z0) and (y, z0 + B/2) of four
 // voxels, so the per-group work (face ids, Dirichlet bits, the stage barrier,
 // spans) is shared by eight voxels, and a quarter-warp's row loads cover
@@ -687,13 +687,63 @@ __device__ __forceinline__ float4 row_update_inh(const RowVals &v0, const RowVal
     return make_float4(res[0], res[1], res[2], res[3]);
 }
 
+// Adjoint of one species (lambda^{n+1}: v0, u^n: v1): lambda^n = M^T lambda^{n+1}
+// on free voxels, 0 on held ones; adds this row's terms of dL/dD (lambda dt
+// g(u^n)) to qd and of dL/dk (dt w u (0 - lambda)) to qk, voxel by voxel in x
+// order, as the one-row kernel does.
+template <bool REACT>
+__device__ __forceinline__ float4 row_adjoint1(const RowVals &v0, const RowVals &v1, const float4 w4, uint32_t hb,
+                                               const StepCoef<float> &kc, float i0, float i1, float i2, float &qd,
+                                               float &qk) {
+    bool actx[6];
+    actx[0] = !is_sent(v0.xm);
+    actx[5] = !is_sent(v0.xp);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) actx[i + 1] = !is_sent(f4get(v0.u, i));
+    float D0[5], D1[5];
+    row_dx(v0, D0);
+    row_dx(v1, D1);
+    float res[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float c = f4get(v0.u, i), u = f4get(v1.u, i);
+        const float y0[4] = {f4get(v0.ym, i), f4get(v0.yp, i), f4get(v0.zm, i), f4get(v0.zp, i)};
+        const float y1[4] = {f4get(v1.ym, i), f4get(v1.yp, i), f4get(v1.zm, i), f4get(v1.zp, i)};
+        float n0[4], n1[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const bool out = is_sent(y0[f]);
+            n0[f] = out ? c : y0[f];
+            n1[f] = out ? u : y1[f];
+        }
+        const float dxs0 = __fsub_rn(actx[i + 2] ? D0[i + 1] : 0.f, actx[i] ? D0[i] : 0.f);
+        const float dp1 = actx[i + 2] ? D1[i + 1] : 0.f, dm1 = actx[i] ? D1[i] : 0.f;
+        const float kw = REACT ? __fmul_rn(kc.k, f4get(w4, i)) : 0.f;
+        const float rate = REACT ? __fadd_rn(kc.decay[0], kw) : kc.decay[0];
+        const float nr = fused_update_dx(c, dxs0, n0[0], n0[1], n0[2], n0[3], kc.c[0], kc.dt, rate, 0.f);
+        float g = __fmul_rn(i0, __fadd_rn(-dm1, dp1));
+        g = __fmaf_rn(i1, __fadd_rn(__fsub_rn(n1[0], u), __fsub_rn(n1[1], u)), g);
+        g = __fmaf_rn(i2, __fadd_rn(__fsub_rn(n1[2], u), __fsub_rn(n1[3], u)), g);
+        const float term = __fmul_rn(__fmul_rn(c, kc.dt), g);
+        const bool act = actx[i + 1];
+        const bool upd = act && !((hb >> i) & 1u);
+        qd = __fadd_rn(qd, upd ? term : 0.f);
+        if (REACT) {
+            const float tk = __fmul_rn(__fmul_rn(__fmul_rn(kc.dt, f4get(w4, i)), u), __fsub_rn(0.f, c));
+            qk = __fadd_rn(qk, upd ? tk : 0.f);
+        }
+        res[i] = upd ? nr : (act ? 0.f : c);
+    }
+    return make_float4(res[0], res[1], res[2], res[3]);
+}
+
 // AH: halo values copied one group ahead with per-thread cp.async into the
 // other half of a double halo buffer (no registers held across the group).
 // WL: the groups come from a work list (a separate instance, so that the
 // plain walk over the block list keeps its registers).
 // NH: arrays streamed, each with halos: 1 (u, or the SBG_F32R correction d,
-// whose source r is read per row from global memory) or 2 (species A and B, or
-// u and the diffusivity factor).  With two arrays the surface weights are read
+// whose source r is read per row from global memory) or 2 (species A and B,
+// u and the diffusivity factor, or the adjoint's lambda and u^n).  With two arrays the surface weights are read
 // per row from global memory too: without a weight buffer one more CTA fits
 // in an SM's shared memory.
 template <int MODE, int NH, int B, bool REACT, int S, int MINB, bool AH, bool WL>
@@ -937,6 +987,9 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
         cp_async_commit();
     };
 
+    // adjoint: this thread's sums of dL/dD and dL/dk, double-float (hi, lo)
+    float gh[2] = {0.f, 0.f}, gl[2] = {0.f, 0.f};
+
     // AH: id1 holds the ids of group gi + 1 and id2 receives those of gi + 2;
     // otherwise id1 holds this group's ids and id2 receives the next group's.
     auto body = [&](int gi, int it, Halo &cur, const Ids &id1, Ids &id2) -> bool {
@@ -1017,6 +1070,12 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
                 float *d0 = io.dst[0] + b * B3 + la + q * ZB;
                 if (MODE == kInh) {
                     *reinterpret_cast<float4 *>(d0) = row_update_inh(v0, v1, hq, a.cf);
+                } else if (MODE == kAdj) {
+                    float qd = 0.f, qk = 0.f;
+                    *reinterpret_cast<float4 *>(d0) = row_adjoint1<REACT>(v0, v1, q ? w1 : w0, hq, a.cf, io.inv2[0],
+                                                                          io.inv2[1], io.inv2[2], qd, qk);
+                    df_add(gh[0], gl[0], qd, 0.f);
+                    if (REACT) df_add(gh[1], gl[1], qk, 0.f);
                 } else {
                     float4 o0, o1;
                     row_update_fwd2<REACT>(v0, v1, q ? w1 : w0, hq, a.cf, o0, o1);
@@ -1056,12 +1115,41 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
         idA = load_ids(g0 + 1);
     }
     int it = 0;
+    bool ok = true;
     for (int gi = g0; gi < g1; gi += 2, it += 2) {
-        if (!body(gi, it, hc, idA, idB)) break;
+        if (!body(gi, it, hc, idA, idB)) {
+            ok = false;
+            break;
+        }
         if (gi + 1 >= g1) break;
-        if (!body(gi + 1, it + 1, hc, idB, idA)) break;
+        if (!body(gi + 1, it + 1, hc, idB, idA)) {
+            ok = false;
+            break;
+        }
     }
     if (AH) cp_async_wait_all();  // no copy may land after the CTA's shared memory is gone
+    if constexpr (MODE == kAdj) {
+        if (!ok) return;  // uniform over the CTA (the time-out test is a CTA-wide vote)
+        // CTA sums: double-float across the warp, FP64 across the warps, added to
+        // the CTA's own slots (dL/dD_0 and dL/dk), so the order of additions is fixed
+        __shared__ double red[kPipeThreads / 32][2];
+#pragma unroll
+        for (int qq = 0; qq < 2; ++qq) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float h2 = __shfl_down_sync(0xffffffffu, gh[qq], o);
+                const float l2 = __shfl_down_sync(0xffffffffu, gl[qq], o);
+                df_add(gh[qq], gl[qq], h2, l2);
+            }
+            if ((tid & 31) == 0) red[tid >> 5][qq] = (double)gh[qq] + (double)gl[qq];
+        }
+        __syncthreads();
+        if (tid < 2) {
+            double v = 0.0;
+            for (int w = 0; w < kPipeThreads / 32; ++w) v += red[w][tid];
+            io.gsum[(int64_t)blockIdx.x * 3 + (tid == 0 ? 0 : 2)] += v;
+        }
+    }
 }
 
 template <int MODE, int NA>
@@ -1108,7 +1196,8 @@ static cudaError_t launch_pipe_hv(const StepArgs &a, const PipeIO &io, int ctas_
 }
 
 template <int MODE, int NH, int B, bool REACT, bool AH, bool WL>
-static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_per_sm, int *err, cudaStream_t s) {
+static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_per_sm, int *err, cudaStream_t s,
+                                int max_ctas = 0, int *grid_out = nullptr) {
     constexpr int NA = NH;
     constexpr bool WSM = AH && REACT && NH == 1;
     // Two ring stages (one group copied ahead while one computes) leave room for 9-10
@@ -1140,6 +1229,8 @@ static cudaError_t launch_rows2(const StepArgs &a, const PipeIO &io, int ctas_pe
     const int64_t ngroups = WL ? a.nitems : (a.nb + G - 1) / G;
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ngroups) grid = ngroups;
+    if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+    if (grid_out) *grid_out = (int)(grid > 0 ? grid : 0);
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, kPipeThreads, smem, s>>>(a, io, err);
     return cudaGetLastError();
@@ -1268,7 +1359,15 @@ cudaError_t launch_adjoint_pipe(const StepArgs &a, const PipeIO &io, int ns, int
                                 int *err_flag, cudaStream_t s, int *grid_out) {
     if (a.nb * (int64_t)(B * B * B) >= (int64_t(1) << 31)) return cudaErrorInvalidValue;  // 32-bit slot indices
     // halo values copied one group ahead with cp.async (2% faster than loading them when the
-    // group comes up, gradients bitwise the same)
+    // group comes up, gradients bitwise the same); one species (lambda and u^n) on the
+    // two-row kernel
+    if (ns == 1 && !a.items) {
+        if (B == 8)
+            return react ? launch_rows2<kAdj, 2, 8, true, true, false>(a, io, 0, err_flag, s, max_ctas, grid_out)
+                         : launch_rows2<kAdj, 2, 8, false, true, false>(a, io, 0, err_flag, s, max_ctas, grid_out);
+        return react ? launch_rows2<kAdj, 2, 4, true, true, false>(a, io, 0, err_flag, s, max_ctas, grid_out)
+                     : launch_rows2<kAdj, 2, 4, false, true, false>(a, io, 0, err_flag, s, max_ctas, grid_out);
+    }
     if (ns == 1) {
         if (B == 8)
             return react ? launch_pipe_hv<kAdj, 8, 1, true, 2>(a, io, 0, max_ctas, err_flag, s, grid_out)

@@ -71,6 +71,26 @@ def test_fp32_adjoint_within_1e4_of_oracle():
         assert abs(grad[q] - grad_ref[qr]) <= 1e-4 * abs(grad_ref[qr])
 
 
+@pytest.mark.parametrize("block", [4, 8])
+@pytest.mark.parametrize("k", [0.0, 0.4])
+def test_fp32_one_species_adjoint_within_1e4_of_oracle(block, k):
+    """One species (lambda and u^n on the two-row kernel): a box whose block
+    count leaves a ragged last group, Dirichlet faces, with and without the
+    surface sink; at k = 0 the FP32 path still returns dL/dk, as the FP64 one
+    does."""
+    phi, phys, u0, wts = small_case(21, 1, dims=(37, 29, 23))
+    phys = dataclasses.replace(phys, k_surf=k)
+    P = oracle.Problem(phi, phys)
+    lamN = wts * P.active[None]
+    lam0_ref, grad_ref, _ = P.adjoint_run(u0, 50, lamN)
+    lam0, grad, _, _ = gpu_grad(phi, phys, u0, lamN, 50, 8, "f32", block)
+    assert rel(lam0, lam0_ref) < 1e-4
+    assert abs(grad[0] - grad_ref[0]) <= 1e-4 * abs(grad_ref[0])
+    # dL/dk is defined at k = 0 too (the sink's first-order effect)
+    assert grad_ref[1] != 0.0
+    assert abs(grad[2] - grad_ref[1]) <= 1e-4 * abs(grad_ref[1])
+
+
 def test_fp64_adjoint_matches_central_differences_of_the_gpu_forward():
     phi, phys, u0, wts = small_case(13, 2)
     nsteps = 40
