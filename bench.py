@@ -359,8 +359,9 @@ def run_grf256(args):
     d_eff, tau, psi = st.effective_D(p, stream=stream)
     if args.variant == "plain":
         kernel_name = "k_step_x2" if args.dtype == "f32x2" else "k_step"
-    else:  # single-array modes run the two-rows-per-thread pipelined kernel
-        kernel_name = "k_step_rows2" if args.dtype in ("f32", "f32r") and args.variant != "prefetch" else "k_step_pipe"
+    else:  # the two-rows-per-thread kernel: single-array modes, and SBG_F32X2 with cp.async halos
+        rows2 = (args.dtype in ("f32", "f32r") and args.variant != "prefetch") or args.variant == "async"
+        kernel_name = "k_step_rows2" if rows2 else "k_step_pipe"
     traffic = None
     if (n, args.block) == (256, 4):
         traffic = profile_traffic("%s_%s_%s_grf256.md" % (kernel_name, args.variant, args.dtype))

@@ -254,8 +254,8 @@ sbg_status sbg_step_source(sbg_grid grid, sbg_state state, const sbg_params *par
  * group ahead in registers: fewer CTAs per SM, less exposed latency) or
  * SBG_KERNEL_PIPELINED_ASYNC (face halos copied one group ahead into shared
  * memory with per-thread cp.async: no extra registers; with it the FP32 states
- * of two species or with a diffusivity factor run two z-paired rows per thread
- * too, except in batched steps).  ctas_per_sm:
+ * of two species or with a diffusivity factor and SBG_F32X2 states run two
+ * z-paired rows per thread too, except in batched steps).  ctas_per_sm:
  * persistent CTAs per SM for the pipelined kernel (0 = as many as fit).
  * Results are bitwise identical across variants. */
 enum {

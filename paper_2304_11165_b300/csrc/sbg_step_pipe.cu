@@ -544,7 +544,8 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
 // ---------------------------------------------------------------------------
 // Two rows per thread, for the modes with one haloed array (FP32 one species,
 // SBG_F32R correction) and, with cp.async halos, two (species A and B; u and
-// the diffusivity factor; the one-species adjoint's lambda and u^n).  Groups of 1024 voxels (sixteen 4^3 blocks or two 8^3
+// the diffusivity factor; the compensated hi and lo parts; the one-species
+// adjoint's lambda and u^n).  Groups of 1024 voxels (sixteen 4^3 blocks or two 8^3
 // blocks); each thread updates the rows (y, z0) and (y, z0 + B/2) of four
 // voxels, so the per-group work (face ids, Dirichlet bits, the stage barrier,
 // spans) is shared by eight voxels, and a quarter-warp's row loads cover
@@ -657,6 +658,38 @@ __device__ __forceinline__ void row_update_fwd2(const RowVals &v0, const RowVals
     o1 = make_float4(r1[0], r1[1], r1[2], r1[3]);
 }
 
+// Compensated state (hi: v0, lo: v1): every neighbour outside Omega (read from
+// hi, x included) mirrored in both parts, the update of fused_update_x2.
+template <bool REACT>
+__device__ __forceinline__ void row_update_x2(const RowVals &v0, const RowVals &v1, const float4 w4, uint32_t hb,
+                                              const StepCoef<float> &kc, float4 &o0, float4 &o1) {
+    float r0[4], r1[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float c0 = f4get(v0.u, i), c1 = f4get(v1.u, i);
+        const float h[6] = {i == 0 ? v0.xm : f4get(v0.u, i - 1), i == 3 ? v0.xp : f4get(v0.u, i + 1),
+                            f4get(v0.ym, i), f4get(v0.yp, i), f4get(v0.zm, i), f4get(v0.zp, i)};
+        const float l[6] = {i == 0 ? v1.xm : f4get(v1.u, i - 1), i == 3 ? v1.xp : f4get(v1.u, i + 1),
+                            f4get(v1.ym, i), f4get(v1.yp, i), f4get(v1.zm, i), f4get(v1.zp, i)};
+        float nh[6], nl[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const bool out = is_sent(h[f]);
+            nh[f] = out ? c0 : h[f];
+            nl[f] = out ? c1 : l[f];
+        }
+        float rate = kc.decay[0];
+        if (REACT) rate = __fmaf_rn(kc.k, f4get(w4, i), rate);
+        float rh, rl;
+        fused_update_x2(c0, c1, nh, nl, kc.c[0], kc.dt, rate, rh, rl);
+        const bool upd = !is_sent(c0) && !((hb >> i) & 1u);
+        r0[i] = upd ? rh : c0;
+        r1[i] = upd ? rl : c1;
+    }
+    o0 = make_float4(r0[0], r0[1], r0[2], r0[3]);
+    o1 = make_float4(r1[0], r1[1], r1[2], r1[3]);
+}
+
 // Inhomogeneous diffusion (Eq. 6 factor e, v1): one-sided differences of u
 // (v0; 0 towards a neighbour outside Omega) and the neighbours' raw factors.
 __device__ __forceinline__ float4 row_update_inh(const RowVals &v0, const RowVals &v1, uint32_t hb,
@@ -743,7 +776,7 @@ __device__ __forceinline__ float4 row_adjoint1(const RowVals &v0, const RowVals 
 // plain walk over the block list keeps its registers).
 // NH: arrays streamed, each with halos: 1 (u, or the SBG_F32R correction d,
 // whose source r is read per row from global memory) or 2 (species A and B,
-// u and the diffusivity factor, or the adjoint's lambda and u^n).  With two arrays the surface weights are read
+// u and the diffusivity factor, hi and lo, or the adjoint's lambda and u^n).  With two arrays the surface weights are read
 // per row from global memory too: without a weight buffer one more CTA fits
 // in an SM's shared memory.
 template <int MODE, int NH, int B, bool REACT, int S, int MINB, bool AH, bool WL>
@@ -864,8 +897,8 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
 #pragma unroll
         for (int k = 0; k < NH; ++k) {
             const float *sk = io.src[k];
-            // the diffusivity factor of an absent block reads 0
-            const float ab = (MODE == kInh && k == 1) ? 0.f : sentinel_f32();
+            // the diffusivity factor and the compensated lo part of an absent block read 0
+            const float ab = ((MODE == kInh || MODE == kX2) && k == 1) ? 0.f : sentinel_f32();
             const float4 ab4 = make_float4(ab, ab, ab, ab);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
@@ -925,7 +958,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
 #pragma unroll
                 for (int k = 0; k < NH; ++k) {
                     const float *sk = io.src[k];
-                    const float ab = (MODE == kInh && k == 1) ? 0.f : sentinel_f32();
+                    const float ab = ((MODE == kInh || MODE == kX2) && k == 1) ? 0.f : sentinel_f32();
                     const float4 ab4 = make_float4(ab, ab, ab, ab);
                     float *hb = halo + (buf * NH + k) * L::kHalo;
                     if (hxm && ixm < 0) {
@@ -1078,7 +1111,8 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
                     if (REACT) df_add(gh[1], gl[1], qk, 0.f);
                 } else {
                     float4 o0, o1;
-                    row_update_fwd2<REACT>(v0, v1, q ? w1 : w0, hq, a.cf, o0, o1);
+                    if (MODE == kX2) row_update_x2<REACT>(v0, v1, q ? w1 : w0, hq, a.cf, o0, o1);
+                    else row_update_fwd2<REACT>(v0, v1, q ? w1 : w0, hq, a.cf, o0, o1);
                     *reinterpret_cast<float4 *>(d0) = o0;
                     *reinterpret_cast<float4 *>(io.dst[1] + b * B3 + la + q * ZB) = o1;
                 }
@@ -1296,13 +1330,14 @@ static cudaError_t launch_pipe_b(const StepArgs &a, const PipeIO &io, int B, boo
 
 // The single-array modes (FP32 one species, SBG_F32R) run the two-row kernel
 // unless register-prefetched halos are asked for; its groups (and work-list
-// spans) hold up to 1024 voxels, the one-row kernel's 512.  The two-array FP32
-// modes (two species; one species with a diffusivity factor) run it with
-// cp.async halos when they walk the block list; work lists and the other halo
-// variants keep the one-row kernel.
+// spans) hold up to 1024 voxels, the one-row kernel's 512.  The two-array
+// modes (two FP32 species; one species with a diffusivity factor; SBG_F32X2)
+// run it with cp.async halos when they walk the block list; work lists and
+// the other halo variants keep the one-row kernel.
 static bool rows2_path(sbg_dtype dtype, int ns, bool eps, int hv, bool worklist) {
     if (hv != 1 && ns == 1 && !eps && (dtype == SBG_F32 || dtype == SBG_F32R)) return true;
-    return hv == 2 && !worklist && dtype == SBG_F32 && ((ns == 2 && !eps) || (ns == 1 && eps));
+    if (hv != 2 || worklist) return false;
+    return (dtype == SBG_F32 && ((ns == 2 && !eps) || (ns == 1 && eps))) || (dtype == SBG_F32X2 && ns == 1 && !eps);
 }
 int step_work_group_voxels(sbg_dtype dtype, int ns, bool eps, int halo_variant) {
     return rows2_path(dtype, ns, eps, halo_variant, true) ? kGroup2 : kGroupVox;
@@ -1320,7 +1355,9 @@ bool launch_step_pipe(const StepArgs &a, sbg_dtype dtype, int ns, int B, bool re
         io.src[1] = a.in_lo[0];
         io.dst[0] = (float *)a.out[0];
         io.dst[1] = a.out_lo[0];
-        e = launch_pipe_b<kX2, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
+        e = rows2_path(dtype, ns, a.eps != nullptr, hv, a.items != nullptr)
+                ? launch_rows2_two<kX2>(a, io, B, react, ctas_per_sm, err_flag, s)
+                : launch_pipe_b<kX2, 1>(a, io, B, react, hv, ctas_per_sm, err_flag, s);
     } else if (dtype == SBG_F32R && ns == 1) {
         io.src[0] = (const float *)a.in[0];
         io.src[1] = a.src_term;

@@ -283,3 +283,18 @@ def test_two_species_two_row_kernel_with_few_ctas(block):
     for per_sm in (1, 2, 0):
         b = State(g, 2, "f32").set_kernel("async", ctas_per_sm=per_sm).set_all(u0).step(p, 31).get_all()
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("block", [4, 8])
+def test_compensated_two_row_kernel_with_few_ctas(block):
+    """SBG_F32X2 (hi and lo, both with halos) with the surface sink on the
+    two-row kernel, one and two persistent CTAs per SM and all that fit: the
+    same hi and lo parts as the one-thread-per-voxel kernel (read back as
+    hi + lo in FP64, which is exact)."""
+    phi, phys, u0 = make_case((64, 60, 56), 1, 0.5, (0, 1), 14)
+    p = make_params(phys)
+    g = Grid(phi, block=block)
+    a = State(g, 1, "f32x2").set_kernel("plain").set_all(u0).step(p, 29).get_all()
+    for per_sm in (1, 2, 0):
+        b = State(g, 1, "f32x2").set_kernel("async", ctas_per_sm=per_sm).set_all(u0).step(p, 29).get_all()
+        np.testing.assert_array_equal(a, b)
