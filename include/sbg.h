@@ -433,7 +433,8 @@ sbg_status sbg_forward_record(sbg_grid grid, sbg_state state, const sbg_params *
  * dL/du^0 (0 on held and inactive voxels); same grid, dtype and species as
  * the recorded state.  grad (host, 3 doubles):
  *   grad[0] = dL/dD_0, grad[1] = dL/dD_1 (0 with one species),
- *   grad[2] = dL/dk_surf,
+ *   grad[2] = dL/dk_surf (also at k_surf = 0: the first-order effect of a
+ *             surface sink on the loss),
  * accumulated over steps and voxels: FP64 tapes in FP64; SBG_F32 tapes (run
  * by the pipelined kernel) in double-float pairs per thread and warp and FP64
  * per CTA; each CTA adds to its own slot and the slots are summed once in a

@@ -371,6 +371,32 @@ def test_adjoint_matches_central_differences():
     assert abs(float((lam0 * direction).sum()) - fd) <= 1e-6 * abs(fd)
 
 
+def test_adjoint_sink_gradient_at_zero_rate():
+    """One species without a sink (k = 0): dL/dk is the first-order effect of
+    switching a surface sink on, nonzero and equal to the central difference
+    of the forward over k = +-h (k < 0 is a surface source; the update is
+    affine in k, so the difference is exact up to rounding and the O(h^2)
+    term)."""
+    import dataclasses
+    phi, p2 = adjoint_problem(7)
+    p = dataclasses.replace(p2, nspecies=1, D=(1.0, 0.0), decay=(0.01, 0.0), k_surf=0.0)
+    P = oracle.Problem(phi, p)
+    rng = np.random.default_rng(4)
+    nsteps = 25
+    u0 = rng.uniform(0.2, 1.0, size=(1,) + phi.shape)
+    weights = rng.uniform(0, 1, size=(1,) + phi.shape) * P.active[None]
+    _, grad, _ = P.adjoint_run(u0, nsteps, weights)
+    assert grad[1] < 0  # a sink lowers a positive-weighted sum of a positive field
+
+    def loss(k):
+        q = dataclasses.replace(p, k_surf=k)
+        return float((oracle.Problem(phi, q).run(u0, nsteps) * weights).sum())
+
+    h = 1e-4
+    fd = (loss(h) - loss(-h)) / (2 * h)
+    assert abs(grad[1] - fd) <= 1e-6 * abs(fd), (grad, fd)
+
+
 # ---------------------------------------------------------------------------
 # symmetry: the operator commutes with reflections and axis swaps
 # ---------------------------------------------------------------------------
