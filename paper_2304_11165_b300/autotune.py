@@ -25,7 +25,7 @@ import torch
 from .api import Grid, State, make_params
 
 DEFAULT_CANDIDATES = [(4, "pipelined", 0), (4, "prefetch", 0), (4, "async", 0), (8, "pipelined", 0),
-                      (8, "prefetch", 0), (4, "pipelined", 4), (8, "pipelined", 4)]
+                      (8, "prefetch", 0), (8, "async", 0), (4, "pipelined", 4), (8, "pipelined", 4)]
 
 
 def cache_path() -> str:
