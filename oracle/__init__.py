@@ -8,6 +8,10 @@ shares no code with it.  The only inputs the two sides share come from the
 
 Every function is the plain definition computed on the whole dense box; see
 the C source for the passage of the paper each one follows.
+
+SBG_ORACLE_LIB, when set, names a prebuilt library to load instead of
+building ``sbg_oracle.c`` (the mutation tests point it at copies of the
+oracle with one planted mistake each and check that a pin fails).
 """
 from __future__ import annotations
 
@@ -20,7 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sbg_oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+_LIB = os.environ.get("SBG_ORACLE_LIB") or os.path.join(_HERE, "liboracle.so")
 FLT_EPSILON = float(np.finfo(np.float32).eps)
 
 _lib = None
@@ -28,6 +32,8 @@ _lib = None
 
 def build_oracle(force: bool = False) -> str:
     """Compile the oracle with gcc (plain -O2, OpenMP, no FMA contraction)."""
+    if os.environ.get("SBG_ORACLE_LIB"):
+        return _LIB
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
