@@ -66,6 +66,15 @@ MUTANTS = [
      "out[IDX(x, y, z)] = c + dalpha * sigma * (1.0 - g);", "out[IDX(x, y, z)] = c + dalpha * sigma * (g - 1.0);"),
     ("box sum over inactive voxels",
      "if (!active[i]) continue;\n                kadd(&m, u[i]);", "kadd(&m, u[i]);"),
+    ("D_eff over the box length N dx instead of the distance (N - 1) dx between the held planes",
+     "const double L = (double)(dims[0] - 1) * dx[0];", "const double L = (double)dims[0] * dx[0];"),
+    ("tau without the porosity",
+     "*tau = (*D_eff > 0.0) ? (*psi) * D / (*D_eff) : INFINITY;", "*tau = (*D_eff > 0.0) ? D / (*D_eff) : INFINITY;"),
+    ("inhomogeneous flux with the centre's factor only",
+     "const double j = D * (eps[i] + eps[i + 1]) / 2.0 * (u[i] - u[i + 1]) / dx[0] * area;",
+     "const double j = D * eps[i] * (u[i] - u[i + 1]) / dx[0] * area;"),
+    ("inhomogeneous update without decay",
+     "return lap - decay * uc;", "return lap;"),
 ]
 
 
