@@ -257,7 +257,11 @@ sbg_status sbg_step_source(sbg_grid grid, sbg_state state, const sbg_params *par
  * of two species or with a diffusivity factor and SBG_F32X2 states run two
  * z-paired rows per thread too, except in batched steps).  ctas_per_sm:
  * persistent CTAs per SM for the pipelined kernel (0 = as many as fit).
- * Results are bitwise identical across variants. */
+ * Results are bitwise identical across variants.  The pipelined kernels index
+ * voxel slots with 32-bit integers: a grid of 2^31 or more slots (blocks x
+ * B^3) runs the one-thread-per-voxel kernel under SBG_KERNEL_AUTO, and
+ * sbg_step fails with SBG_ERR_INVALID_ARG under the explicit pipelined
+ * variants (as do batched steps and the FP32 adjoint on such a grid). */
 enum {
     SBG_KERNEL_AUTO = 0,
     SBG_KERNEL_PLAIN = 1,

@@ -280,6 +280,8 @@ static sbg_status zero_held(sbg_tape tp, sbg_state lam, cudaStream_t s) {
 // One FP32 adjoint step with the pipelined kernel.
 static sbg_status launch_adj_pipe(sbg_tape tp, const void *u, sbg_state lam, cudaStream_t s) {
     sbg_grid g = tp->grid;
+    if (g->nb * (int64_t)g->b3() >= (int64_t(1) << 31))  // 32-bit slot indices in the kernel
+        return fail(SBG_ERR_INVALID_ARG, "the FP32 adjoint needs fewer than 2^31 voxel slots (blocks x B^3)");
     StepArgs a;
     fill_step_args(g, &tp->p, a);
     PipeIO io;

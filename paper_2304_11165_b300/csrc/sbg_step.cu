@@ -371,7 +371,9 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
             return SBG_OK;
         }
         if (st->variant >= SBG_KERNEL_PIPELINED)
-            return fail(SBG_ERR_INVALID_ARG, "the pipelined kernel handles FP32-based states only");
+            return fail(SBG_ERR_INVALID_ARG,
+                        st->dtype == SBG_F64 ? "the pipelined kernel handles FP32-based states only"
+                                             : "the pipelined kernel needs fewer than 2^31 voxel slots (blocks x B^3)");
     }
     if (st->dtype == SBG_F32X2) {
         if (g->B == 8) launch_x2<8>(a, react, s);
@@ -612,7 +614,8 @@ sbg_status launch_step_work(sbg_grid g, sbg_state st, const sbg_params *p, int s
     cudaError_t e = cudaSuccess;
     if (!launch_step_pipe(a, st->dtype, st->ns, g->B, p->k_surf != 0.0,
                           halo_variant_of(st->variant), st->ctas_per_sm, g->err, s, &e))
-        return fail(SBG_ERR_INVALID_ARG, "batched stepping needs an FP32 or SBG_F32X2 state");
+        return fail(SBG_ERR_INVALID_ARG, "batched stepping needs an FP32-based state (SBG_F32, SBG_F32X2 or "
+                                         "SBG_F32R) and fewer than 2^31 voxel slots (blocks x B^3)");
     if (e != cudaSuccess) return cuda_fail(e, "pipelined step kernel launch (work list)");
     return SBG_OK;
 }
