@@ -162,27 +162,79 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(phi, u0, phys, n_active, seconds):
-    """The FP64 dense oracle as it stands, on the host cores, on a bounded
-    number of steps of the same workload."""
-    import oracle
-    P = oracle.Problem(phi, phys)
-    u = P.shape_state(u0)
+def _timed_steps(P, u, seconds):
+    """(steps, seconds) of a bounded oracle run: one step to size it, then as
+    many as fit in `seconds` (at least one)."""
     t0 = time.perf_counter()
     u = P.run(u, 1)
     one = time.perf_counter() - t0
     nsteps = max(1, int(seconds / max(one, 1e-6)))
     t0 = time.perf_counter()
     P.run(u, nsteps)
-    dt = time.perf_counter() - t0
-    species = int(phys.nspecies)
-    return {"value": species * n_active * nsteps / dt / 1e9, "unit": "GVox/s", "cores": oracle.num_threads(),
+    return nsteps, time.perf_counter() - t0
+
+
+def _single_thread(P, u, seconds):
+    """The same oracle on one OpenMP thread (the process's OpenMP runtime is
+    set to one thread for the run and restored after), or None when the
+    runtime cannot be reached."""
+    import ctypes
+    import oracle
+    try:
+        gomp = ctypes.CDLL("libgomp.so.1")
+    except OSError:
+        return None
+    n0 = oracle.num_threads()
+    gomp.omp_set_num_threads(1)
+    try:
+        if oracle.num_threads() != 1:
+            return None
+        return _timed_steps(P, u, seconds)
+    finally:
+        gomp.omp_set_num_threads(n0)
+
+
+def cpu_baseline(phi, u0, phys, n_active, seconds):
+    """The FP64 dense oracle as it stands, on the host cores, on a bounded
+    number of steps of the same workload; beside it the same oracle on one
+    thread for a few seconds."""
+    import oracle
+    P = oracle.Problem(phi, phys)
+    u = P.shape_state(u0)
+    cores = oracle.num_threads()
+    nsteps, dt = _timed_steps(P, u, seconds)
+    updates = int(phys.nspecies) * n_active
+    one = _single_thread(P, u, min(3.0, seconds / 4))
+    return {"value": updates * nsteps / dt / 1e9, "unit": "GVox/s", "cores": cores,
             "kind": "oracle",
             "sample": "%d FP64 dense steps of the full %s box (all %d voxels visited per step)"
-                      % (nsteps, "x".join(str(d) for d in phys.dims), int(np.prod(phys.dims)))}
+                      % (nsteps, "x".join(str(d) for d in phys.dims), int(np.prod(phys.dims))),
+            "host_cpu_count": os.cpu_count(), "omp_num_threads_env": os.environ.get("OMP_NUM_THREADS"),
+            "single_thread": None if one is None else
+            {"value": updates * one[0] / one[1] / 1e9, "unit": "GVox/s", "steps": one[0]}}
+
+
+NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e, NVIDIA's nominal figure (context beside the measured copy peak)
+
+
+def roofline_extras(r):
+    """Adds to an HBM roofline object the fraction of the nominal HBM
+    bandwidth and, where an ncu traffic figure exists, the DRAM throughput it
+    implies over the same event-timed launch."""
+    if not r or r.get("bound") != "hbm" or r.get("achieved") is None:
+        return r
+    r["peak_nominal"] = NOMINAL_HBM_GBS
+    r["frac_nominal"] = r["achieved"] / NOMINAL_HBM_GBS
+    us = r.get("avg_launch_us")
+    if r.get("traffic") and us:
+        r["dram_gbs_from_traffic"] = r["traffic"] / (us * 1e-6) / 1e9
+        r["dram_frac_from_traffic"] = r["dram_gbs_from_traffic"] / r["peak"]
+    return r
 
 
 def emit(line):
+    if isinstance(line.get("roofline"), dict):
+        roofline_extras(line["roofline"])
     print(json.dumps(line), flush=True)
 
 
