@@ -30,6 +30,7 @@
 
 #include "sbg_internal.cuh"
 #include "sbg_step.cuh"
+#include "sbg_trace.cuh"
 
 struct sbg_tape_s {
     sbg_grid grid = nullptr;
@@ -342,6 +343,7 @@ using namespace sbg;
 
 extern "C" sbg_status sbg_forward_record(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps,
                                          int64_t checkpoint_every, void *stream, sbg_tape *out) {
+    TraceRange trace_range("sbg_forward_record");
     if (!g || !st || !p || !out) return fail(SBG_ERR_INVALID_ARG, "sbg_forward_record: null pointer");
     if (st->grid != g) return fail(SBG_ERR_INVALID_ARG, "sbg_forward_record: state of another grid");
     if (nsteps < 0 || checkpoint_every < 1) return fail(SBG_ERR_INVALID_ARG, "sbg_forward_record: nsteps >= 0, checkpoint_every >= 1");
@@ -389,6 +391,7 @@ extern "C" sbg_status sbg_forward_record(sbg_grid g, sbg_state st, const sbg_par
 }
 
 extern "C" sbg_status sbg_adjoint(sbg_grid g, sbg_tape tp, sbg_state lam, double *grad, void *stream) {
+    TraceRange trace_range("sbg_adjoint");
     if (!g || !tp || !lam || !grad) return fail(SBG_ERR_INVALID_ARG, "sbg_adjoint: null pointer");
     if (tp->grid != g || lam->grid != g) return fail(SBG_ERR_INVALID_ARG, "sbg_adjoint: tape or state of another grid");
     if (lam->dtype != tp->dtype || lam->ns != tp->ns)

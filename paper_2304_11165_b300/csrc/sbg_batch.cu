@@ -16,6 +16,7 @@
 
 #include "sbg_internal.cuh"
 #include "sbg_step.cuh"
+#include "sbg_trace.cuh"
 
 namespace sbg {
 sbg_status launch_step_work(sbg_grid g, sbg_state st, const sbg_params *p, int src, const int64_t *items,
@@ -27,6 +28,7 @@ using namespace sbg;
 extern "C" sbg_status sbg_batch_run_to_steady(sbg_grid g, sbg_state st, const sbg_params *p, double tol,
                                               int64_t check_every, int64_t max_steps, int64_t *steps_done,
                                               double *rel_residual, void *stream) {
+    TraceRange trace_range("sbg_batch_run_to_steady");
     if (!g || !st || !p || !steps_done || !rel_residual)
         return fail(SBG_ERR_INVALID_ARG, "sbg_batch_run_to_steady: null pointer");
     if (st->grid != g) return fail(SBG_ERR_INVALID_ARG, "sbg_batch_run_to_steady: state of another grid");

@@ -17,6 +17,7 @@
 #include <string>
 
 #include "sbg_internal.cuh"
+#include "sbg_trace.cuh"
 
 namespace sbg {
 
@@ -569,6 +570,7 @@ using namespace sbg;
 
 extern "C" sbg_status sbg_build_batch(int32_t n, const float *const *phis, const int64_t *dims,
                                       const sbg_build_opts *opts, void *stream, sbg_grid *out) {
+    TraceRange trace_range("sbg_build_batch");
     sbg_status rc = check_build_args(n, phis, dims, opts, out);
     if (rc != SBG_OK) return rc;
     *out = nullptr;
@@ -579,6 +581,7 @@ extern "C" sbg_status sbg_build_batch(int32_t n, const float *const *phis, const
 
 extern "C" sbg_status sbg_build(const float *phi, const int64_t dims[3], const sbg_build_opts *opts,
                                 void *stream, sbg_grid *out) {
+    TraceRange trace_range("sbg_build");
     const float *phis[1] = {phi};
     return sbg_build_batch(1, phis, dims, opts, stream, out);
 }

@@ -10,6 +10,7 @@
 #include <string>
 
 #include "sbg_internal.cuh"
+#include "sbg_trace.cuh"
 
 namespace sbg {
 
@@ -134,12 +135,14 @@ using namespace sbg;
 
 extern "C" sbg_status sbg_grid_set_diffusivity(sbg_grid g, int32_t geom, const void *dense, int32_t dense_dtype,
                                                int32_t on_device, void *stream) {
+    TraceRange trace_range("sbg_grid_set_diffusivity");
     return set_eps(g, geom, dense, dense_dtype, on_device, 0, 0.0, 0.0, 0.0, 0.0, (cudaStream_t)stream);
 }
 
 extern "C" sbg_status sbg_grid_set_diffusivity_sigmoid(sbg_grid g, int32_t geom, const float *phi,
                                                        int32_t phi_on_device, double d_min, double d_max,
                                                        double gamma1, double gamma2, void *stream) {
+    TraceRange trace_range("sbg_grid_set_diffusivity_sigmoid");
     if (!(d_min >= 0.0) || !(d_max >= 0.0) || !isfinite(d_min) || !isfinite(d_max) || !isfinite(gamma1) ||
         !isfinite(gamma2))
         return fail(SBG_ERR_INVALID_ARG, "sbg_grid_set_diffusivity_sigmoid: d_min, d_max >= 0 and finite parameters");

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "sbg_internal.cuh"
+#include "sbg_trace.cuh"
 
 namespace sbg {
 
@@ -40,6 +41,7 @@ using namespace sbg;
 extern "C" sbg_status sbg_frap_curve(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom, int32_t species,
                                      const int64_t lo[3], const int64_t hi[3], int64_t steps_per_sample,
                                      int32_t n_samples, double *sums, int64_t *count, void *stream) {
+    TraceRange trace_range("sbg_frap_curve");
     sbg_status rc = check_box_args(g, st, geom, species, "sbg_frap_curve");
     if (rc != SBG_OK) return rc;
     if (!p || !lo || !hi || !sums) return fail(SBG_ERR_INVALID_ARG, "sbg_frap_curve: null pointer");

@@ -21,6 +21,7 @@
 #include <string>
 
 #include "sbg_internal.cuh"
+#include "sbg_trace.cuh"
 
 namespace sbg {
 
@@ -958,6 +959,7 @@ using namespace sbg;
 
 extern "C" sbg_status sbg_reduce_box(sbg_grid g, sbg_state st, int32_t geom, int32_t species, const int64_t lo[3],
                                      const int64_t hi[3], double *out, void *stream) {
+    TraceRange trace_range("sbg_reduce_box");
     sbg_status rc = check_box_args(g, st, geom, species, "sbg_reduce_box");
     if (rc != SBG_OK) return rc;
     if (!lo || !hi || !out) return fail(SBG_ERR_INVALID_ARG, "sbg_reduce_box: null pointer");
@@ -973,6 +975,7 @@ extern "C" sbg_status sbg_reduce_box(sbg_grid g, sbg_state st, int32_t geom, int
 
 extern "C" sbg_status sbg_reduce(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom,
                                  double *out, void *stream) {
+    TraceRange trace_range("sbg_reduce");
     sbg_status rc = check_common(g, st, p, geom);
     if (rc != SBG_OK) return rc;
     if (!out) return fail(SBG_ERR_INVALID_ARG, "sbg_reduce: null output");
@@ -985,6 +988,7 @@ extern "C" sbg_status sbg_reduce(sbg_grid g, sbg_state st, const sbg_params *p, 
 
 extern "C" sbg_status sbg_reduce_async(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom,
                                        double *out, void *stream) {
+    TraceRange trace_range("sbg_reduce_async");
     sbg_status rc = check_common(g, st, p, geom);
     if (rc != SBG_OK) return rc;
     if (!out) return fail(SBG_ERR_INVALID_ARG, "sbg_reduce_async: null output");
@@ -1000,6 +1004,7 @@ extern "C" sbg_status sbg_reduce_async(sbg_grid g, sbg_state st, const sbg_param
 
 extern "C" sbg_status sbg_effective_D(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom,
                                       double *D_eff, double *tau, double *psi, void *stream) {
+    TraceRange trace_range("sbg_effective_D");
     sbg_status rc = check_common(g, st, p, geom);
     if (rc != SBG_OK) return rc;
     if (geom < 0) return fail(SBG_ERR_INVALID_ARG, "sbg_effective_D: needs one geometry");
@@ -1021,6 +1026,7 @@ extern "C" sbg_status sbg_effective_D(sbg_grid g, sbg_state st, const sbg_params
 extern "C" sbg_status sbg_run_to_steady(sbg_grid g, sbg_state st, const sbg_params *p, double tol,
                                         int64_t check_every, int64_t max_steps, int64_t *steps_done,
                                         double *rel_residual, void *stream) {
+    TraceRange trace_range("sbg_run_to_steady");
     sbg_status rc = check_common(g, st, p, -1);
     if (rc != SBG_OK) return rc;
     if (check_every < 1 || max_steps < 0 || !(tol > 0.0))
@@ -1103,6 +1109,7 @@ static sbg_status noalloc_scratch(double **out) {
 
 extern "C" sbg_status sbg_reduce_noalloc(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom,
                                          int32_t species, double *out_dev, void *stream) {
+    TraceRange trace_range("sbg_reduce_noalloc");
     sbg_status rc = check_common(g, st, p, geom);
     if (rc != SBG_OK) return rc;
     if (!out_dev) return fail(SBG_ERR_INVALID_ARG, "sbg_reduce_noalloc: null output");

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "sbg_internal.cuh"
+#include "sbg_trace.cuh"
 
 namespace sbg {
 
@@ -45,6 +46,7 @@ using namespace sbg;
 
 extern "C" sbg_status sbg_state_set_source(sbg_grid g, sbg_state st, int32_t geom, int32_t species,
                                            const void *dense, int32_t dense_dtype, int32_t on_device, void *stream) {
+    TraceRange trace_range("sbg_state_set_source");
     if (!g || !st || !dense) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_source: null pointer");
     if (st->grid != g) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_source: state of another grid");
     if (geom < 0 || geom >= g->n_geoms) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_source: bad geometry");
@@ -137,6 +139,7 @@ extern "C" sbg_status sbg_state_clear_source(sbg_state st) {
 
 extern "C" sbg_status sbg_step_source(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps,
                                       const double *factors, void *stream) {
+    TraceRange trace_range("sbg_step_source");
     if (!g || !st || !p) return fail(SBG_ERR_INVALID_ARG, "sbg_step_source: null pointer");
     if (st->grid != g) return fail(SBG_ERR_INVALID_ARG, "sbg_step_source: state of another grid");
     if (nsteps < 0) return fail(SBG_ERR_INVALID_ARG, "sbg_step_source: nsteps < 0");

@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "sbg_internal.cuh"
+#include "sbg_trace.cuh"
 
 namespace sbg {
 
@@ -262,11 +263,13 @@ extern "C" sbg_status sbg_state_create(sbg_grid g, int32_t nspecies, sbg_dtype d
 extern "C" sbg_status sbg_state_set(sbg_grid g, sbg_state st, int32_t geom, int32_t species,
                                     const void *dense, int32_t dense_dtype, int32_t on_device,
                                     void *stream) {
+    TraceRange trace_range("sbg_state_set");
     return dense_io(g, st, geom, species, const_cast<void *>(dense), dense_dtype, on_device, true, stream);
 }
 
 extern "C" sbg_status sbg_state_get(sbg_grid g, sbg_state st, int32_t geom, int32_t species,
                                     void *dense, int32_t dense_dtype, int32_t on_device, void *stream) {
+    TraceRange trace_range("sbg_state_get");
     return dense_io(g, st, geom, species, dense, dense_dtype, on_device, false, stream);
 }
 

@@ -19,6 +19,7 @@
 
 #include "sbg_internal.cuh"
 #include "sbg_step.cuh"
+#include "sbg_trace.cuh"
 
 namespace sbg {
 
@@ -580,6 +581,7 @@ extern "C" double sbg_stability_limit(const sbg_params *p, const int64_t dims[3]
 }
 
 extern "C" sbg_status sbg_step(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, void *stream) {
+    TraceRange trace_range("sbg_step");
     if (!g || !st || !p) return fail(SBG_ERR_INVALID_ARG, "sbg_step: null pointer");
     if (st->grid != g) return fail(SBG_ERR_INVALID_ARG, "sbg_step: state of another grid");
     if (nsteps < 0) return fail(SBG_ERR_INVALID_ARG, "sbg_step: nsteps < 0");
