@@ -232,6 +232,19 @@ def roofline_extras(r):
     return r
 
 
+def interval_stats(ms, steps_per_interval):
+    """Mean and standard error of the per-interval stepping times (each
+    interval: `steps_per_interval` RD steps, CUDA events on the stream), per
+    RD step, as the paper reports its timings."""
+    if not ms:
+        return None
+    per = [m / steps_per_interval for m in ms]
+    mean = statistics.mean(per)
+    se = statistics.stdev(per) / len(per) ** 0.5 if len(per) > 1 else None
+    return {"n_intervals": len(per), "rd_steps_per_interval": steps_per_interval,
+            "mean_us_per_rd_step": mean * 1e3, "stderr_us": None if se is None else se * 1e3}
+
+
 def emit(line):
     if isinstance(line.get("roofline"), dict):
         roofline_extras(line["roofline"])
@@ -355,7 +368,8 @@ def run_grf256(args):
         torch.distributed.barrier()
     clocks = sampler.stop()
     total_ms = start.elapsed_time(end)
-    step_kernel_ms = sum(a.elapsed_time(b) for a, b in ev) / (args.steps * CHECK_EVERY)
+    interval_ms = [a.elapsed_time(b) for a, b in ev]  # the stepping of each bench step
+    step_kernel_ms = sum(interval_ms) / (args.steps * CHECK_EVERY)
     total_ms = max_over_ranks(total_ms, dev)
     value = replica_throughput(n_active * CHECK_EVERY * args.steps, world, total_ms) / 1e9
 
@@ -437,6 +451,7 @@ def run_grf256(args):
         # reduction, its final pass and (SBG_F32R) the fold of the correction
         "gpu_launches": (CHECK_EVERY + (3 if args.dtype == "f32r" else 2)) * args.steps,
         "clocks": clocks,
+        "interval_stats": interval_stats(interval_ms, CHECK_EVERY),
         "result": {"D_eff_after_warmup_and_timed_steps": d_eff, "tau": tau,
                    "residual_first_last_timed_check": [residuals[0], residuals[-1]] if residuals else None},
     }
