@@ -79,3 +79,42 @@ def test_null_handles_are_rejected():
     assert lib.sbg_step(None, None, ctypes.byref(p), 1, None) == _abi.SBG_ERR_INVALID_ARG
     assert lib.sbg_reduce(None, None, ctypes.byref(p), 0, None, None) == _abi.SBG_ERR_INVALID_ARG
     assert lib.sbg_state_create(None, 1, 0, ctypes.byref(ctypes.c_void_p())) == _abi.SBG_ERR_INVALID_ARG
+
+
+def test_redistance_rejects_bad_arguments_before_touching_the_device():
+    """sbg_redistance validates every argument on the host: null pointers,
+    dims outside [1, 2^20], a non-positive spacing, an unknown dtype, options
+    out of range, a step that breaks the upwind scheme's monotonicity, a
+    launch grid beyond the y/z limits, and a host call that would write over
+    its own input."""
+    lib = _abi.load()
+    buf_in = (ctypes.c_float * 8)()
+    buf_out = (ctypes.c_float * 8)()
+    ok_dims = (ctypes.c_int64 * 3)(2, 2, 2)
+    ok_dx = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    ok = _abi.RedistOpts(0.3, 10, 1e-3, 2.0, 5)
+
+    def call(dims=ok_dims, dx=ok_dx, a=buf_in, b=buf_out, dtype=_abi.SBG_F32, opts=ok):
+        rc = lib.sbg_redistance(dims, dx, a, b, dtype, 0, ctypes.byref(opts) if opts is not None else None,
+                                None, None, None)
+        return rc, lib.sbg_last_error().decode()
+
+    assert call(dims=None)[0] == _abi.SBG_ERR_INVALID_ARG
+    assert call(opts=None)[0] == _abi.SBG_ERR_INVALID_ARG
+    assert call(dims=(ctypes.c_int64 * 3)(0, 2, 2))[0] == _abi.SBG_ERR_INVALID_ARG
+    assert call(dims=(ctypes.c_int64 * 3)(2, 2, (1 << 20) + 1))[0] == _abi.SBG_ERR_INVALID_ARG
+    assert call(dx=(ctypes.c_double * 3)(1.0, 0.0, 1.0))[0] == _abi.SBG_ERR_INVALID_ARG
+    assert call(dx=(ctypes.c_double * 3)(1.0, float("nan"), 1.0))[0] == _abi.SBG_ERR_INVALID_ARG
+    assert call(dtype=7)[0] == _abi.SBG_ERR_INVALID_ARG
+    assert call(opts=_abi.RedistOpts(0.3, -1, 1e-3, 2.0, 5))[0] == _abi.SBG_ERR_INVALID_ARG
+    assert call(opts=_abi.RedistOpts(0.3, 10, 1e-3, 2.0, 0))[0] == _abi.SBG_ERR_INVALID_ARG
+    assert call(opts=_abi.RedistOpts(0.0, 10, 1e-3, 2.0, 5))[0] == _abi.SBG_ERR_INVALID_ARG
+    assert call(opts=_abi.RedistOpts(0.3, 10, 1e-3, 0.0, 5))[0] == _abi.SBG_ERR_INVALID_ARG
+    rc, msg = call(opts=_abi.RedistOpts(0.4, 10, 1e-3, 2.0, 5))  # 0.4 * 1 * 3 = 1.2 > 1
+    assert rc == _abi.SBG_ERR_INVALID_ARG and "above 1" in msg
+    # anisotropic spacing: cfl * min(dx) * sum(1/dx) = 0.3 * 0.5 * (2 + 1 + 1) = 0.6 passes the test
+    assert "above 1" not in call(dx=(ctypes.c_double * 3)(0.5, 1.0, 1.0), a=buf_in, b=buf_in)[1]
+    rc, msg = call(dims=(ctypes.c_int64 * 3)(2, 8 * 65536, 1))
+    assert rc == _abi.SBG_ERR_INVALID_ARG and "Ny" in msg
+    rc, msg = call(b=buf_in)
+    assert rc == _abi.SBG_ERR_INVALID_ARG and "differ" in msg
