@@ -75,6 +75,11 @@ MUTANTS = [
      "const double j = D * eps[i] * (u[i] - u[i + 1]) / dx[0] * area;"),
     ("inhomogeneous update without decay",
      "return lap - decay * uc;", "return lap;"),
+    ("dL/dD from the full right-hand side instead of the Laplacian",
+     "decay, k_surf, 1);", "decay, k_surf, 0);"),
+    ("adjoint keeps lambda on held voxels",
+     "if (!active[i] || fixed[i]) {\n                    for (int s = 0; s < nspecies; ++s) lam_n",
+     "if (!active[i]) {\n                    for (int s = 0; s < nspecies; ++s) lam_n"),
 ]
 
 
