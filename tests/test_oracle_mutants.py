@@ -77,6 +77,14 @@ MUTANTS = [
      "return lap - decay * uc;", "return lap;"),
     ("dL/dD from the full right-hand side instead of the Laplacian",
      "decay, k_surf, 1);", "decay, k_surf, 0);"),
+    ("external source subtracted instead of added",
+     "if (src) r += src[si];", "if (src) r -= src[si];"),
+    ("steady-state operator with the x spacing on every axis",
+     "(dx[a] * dx[a]) * (eps ? 0.5 * (eps[i] + eps[j]) : 1.0);\n                        /* held",
+     "(dx[0] * dx[0]) * (eps ? 0.5 * (eps[i] + eps[j]) : 1.0);\n                        /* held"),
+    ("steady-state operator with the neighbour's factor only",
+     "(dx[a] * dx[a]) * (eps ? 0.5 * (eps[i] + eps[j]) : 1.0);\n                        /* held",
+     "(dx[a] * dx[a]) * (eps ? eps[j] : 1.0);\n                        /* held"),
     ("adjoint keeps lambda on held voxels",
      "if (!active[i] || fixed[i]) {\n                    for (int s = 0; s < nspecies; ++s) lam_n",
      "if (!active[i]) {\n                    for (int s = 0; s < nspecies; ++s) lam_n"),

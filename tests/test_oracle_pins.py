@@ -267,11 +267,14 @@ def test_channel_steady_profile_and_deff():
     assert abs(r["J_in"] - r["J_out"]) < 1e-12
 
 
-def test_cg_equals_time_stepping_steady_state():
+@pytest.mark.parametrize("dx", [(1.0, 1.0, 1.0), (1.0, 0.8, 1.3)])
+def test_cg_equals_time_stepping_steady_state(dx):
+    """The steady state by CG equals the limit of time stepping, also with a
+    different spacing per axis (so that each axis's coefficient is pinned)."""
     dims = (16, 14, 12)
     phi = random_blob_phi(dims, 31, porosity=0.6, ell=2.0)
     d, v = dirich(0, 1, values=[1.0, 0.0])
-    p = phys(dims, 0.15, D=(1.0, 0.0), dirichlet=d, face_value=v)
+    p = phys(dims, 0.15, D=(1.0, 0.0), dx=dx, dirichlet=d, face_value=v)
     P = oracle.Problem(phi, p)
     u0 = np.zeros(phi.shape)
     u0[:, :, 0] = 1.0
