@@ -85,6 +85,12 @@ MUTANTS = [
     ("steady-state operator with the neighbour's factor only",
      "(dx[a] * dx[a]) * (eps ? 0.5 * (eps[i] + eps[j]) : 1.0);\n                        /* held",
      "(dx[a] * dx[a]) * (eps ? eps[j] : 1.0);\n                        /* held"),
+    ("active set includes phi equal to the threshold",
+     "active[i] = (phi[i] > eps_mask) ? 1 : 0;", "active[i] = (phi[i] >= eps_mask) ? 1 : 0;"),
+    ("Dirichlet mask on the wrong x face",
+     "(dirichlet[1] && x == nx - 1)", "(dirichlet[1] && x == nx - 2)"),
+    ("surface weight outside the band",
+     "(active[i] && p < band_eps)", "(active[i] && p <= 2.0 * band_eps)"),
     ("adjoint keeps lambda on held voxels",
      "if (!active[i] || fixed[i]) {\n                    for (int s = 0; s < nspecies; ++s) lam_n",
      "if (!active[i]) {\n                    for (int s = 0; s < nspecies; ++s) lam_n"),

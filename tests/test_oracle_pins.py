@@ -167,6 +167,17 @@ def test_step_equals_edge_list_matrix(seed):
     assert (P.w > 0).sum() > 10 and P.fixed.sum() > 0
 
 
+def test_active_set_is_strictly_above_the_threshold():
+    """A voxel is in Omega only when phi exceeds the FP32 machine epsilon
+    (Sec. 3.2; the insertion test of Appendix B Listing 5): phi equal to it,
+    zero and negative values are outside, the next FP32 value above is in."""
+    eps = np.float32(np.finfo(np.float32).eps)
+    vals = np.array([-1.0, 0.0, eps, np.nextafter(eps, np.float32(1)), 0.5], dtype=np.float32)
+    phi = vals.reshape(1, 1, 5)
+    P = oracle.Problem(phi, phys((5, 1, 1), 0.1, D=(1.0, 0.0)))
+    assert P.active.ravel().tolist() == [0, 0, 0, 1, 1]
+
+
 # ---------------------------------------------------------------------------
 # conservation and balance
 # ---------------------------------------------------------------------------
