@@ -139,3 +139,18 @@ def test_inhomogeneous_thin_boxes_match_the_oracle(zyx, dtype, tol):
         st = State(g, 1, dtype).set_kernel(variant).set(u0)
         st.step(make_params(ph), 60)
         assert np.max(np.abs(st.get() - ref)) <= tol * max(1.0, np.max(np.abs(ref))), (variant, zyx)
+
+
+@pytest.mark.parametrize("block", [4, 8])
+def test_activity_threshold_is_strict(block):
+    """phi equal to the FP32 epsilon is outside Omega, the next FP32 value is
+    inside (the same test as the oracle's): the grid counts and the state
+    reads back accordingly."""
+    eps = np.float32(np.finfo(np.float32).eps)
+    vals = np.array([-1.0, 0.0, eps, np.nextafter(eps, np.float32(1)), 0.5], dtype=np.float32)
+    phi = vals.reshape(1, 1, 5)
+    g = Grid(phi, block=block)
+    P = oracle.Problem(phi, Physics(dims=(5, 1, 1), dt=0.1, D=(1.0, 0.0)))
+    assert g.n_active == int(P.active.sum()) == 2
+    out = State(g, 1, "f64").set(np.ones(phi.shape)).get()
+    np.testing.assert_array_equal(out.ravel(), [0.0, 0.0, 0.0, 1.0, 1.0])
