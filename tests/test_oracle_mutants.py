@@ -91,6 +91,19 @@ MUTANTS = [
      "(dirichlet[1] && x == nx - 1)", "(dirichlet[1] && x == nx - 2)"),
     ("surface weight outside the band",
      "(active[i] && p < band_eps)", "(active[i] && p <= 2.0 * band_eps)"),
+    ("stability limit without the surface rate",
+     "if (s == 0 && k_surf > 0.0) rate += k_surf / band_eps;", "(void)0;"),
+    ("inlet flux at the wrong plane",
+     "if (x == 0) kadd(&jin, j);\n                        if (x == nx - 2) kadd(&jout, j);\n                    }\n"
+     "                }\n            part[0 * nz + z] = m.s;",
+     "if (x == 1) kadd(&jin, j);\n                        if (x == nx - 2) kadd(&jout, j);\n                    }\n"
+     "                }\n            part[0 * nz + z] = m.s;"),
+    ("adjoint diagonal without the reaction rate",
+     "double diag = 1.0 - dt * sum_c - dt * rate;", "double diag = 1.0 - dt * sum_c;"),
+    ("smoothed sign without the gradient term",
+     "const double sigma = c / sqrt(c * c + g * g * h * h);", "const double sigma = c / sqrt(c * c + h * h);"),
+    ("voxels with phi = 0 updated by the redistancing",
+     "if (c == 0.0) {\n                        out[IDX(x, y, z)] = c;\n                        continue;\n                    }", ""),
     ("adjoint keeps lambda on held voxels",
      "if (!active[i] || fixed[i]) {\n                    for (int s = 0; s < nspecies; ++s) lam_n",
      "if (!active[i]) {\n                    for (int s = 0; s < nspecies; ++s) lam_n"),

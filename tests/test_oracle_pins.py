@@ -431,7 +431,10 @@ def test_reflection_and_axis_swap_symmetry():
 # ---------------------------------------------------------------------------
 # the paper's printed numbers
 # ---------------------------------------------------------------------------
-def test_stability_limit_reduces_to_eq_238():
+def test_stability_limit_reduces_to_eq_10():
+    """In 2-D with one species and no reaction the limit is Eq. 10's
+    1/(2 D (dx^-2 + dy^-2)), above the dt = h^2/8 of Sec. 3.1; the 3-D
+    reactive form adds each species' loss rate."""
     g = GOLDEN["stability_2d"]
     h = 0.05
     p = phys((16, 16, 1), 0.0, D=(1.0, 0.0), dx=(h, h, 1.0))

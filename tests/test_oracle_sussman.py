@@ -71,3 +71,30 @@ def test_unit_ball_error_is_first_order_in_the_band():
         l2.append(math.sqrt(np.mean(e * e)))
         assert np.max(np.abs(e)) <= 0.35 * h and l2[-1] <= 0.2 * h, (n, l2[-1] / h)
     assert math.log(l2[0] / l2[-1], 2.0) / 2.0 >= 0.9, l2
+
+
+def test_smoothed_sign_does_not_depend_on_the_steepness_of_phi():
+    """The smoothed sign phi / sqrt(phi^2 + |grad phi|^2 h^2) is the same for
+    phi and a*phi, the property it is chosen for (the form phi / sqrt(phi^2 +
+    h^2) is not).  On a linear field of slope s along x, |grad phi| = s at
+    every voxel, so one iteration moves each voxel by dalpha sigma (1 - s):
+    the sigma recovered from a*phi (slope a*s) equals that from phi."""
+    nx, h, cfl = 16, 1.0, 0.3
+    x = np.arange(nx, dtype=np.float64) * h
+    base = 0.5 * (x - 7.3)
+    sig = []
+    for a in (1.0, 3.0):
+        phi = (a * base).reshape(1, 1, nx)
+        out = oracle.sussman(phi, dx=(h, 1.0, 1.0), cfl=cfl, iters=1)
+        move = (out - phi).ravel()
+        sig.append(move / (cfl * h * (1.0 - a * 0.5)))
+    np.testing.assert_allclose(sig[0], sig[1], rtol=1e-12, atol=0)
+    assert np.all(np.sign(sig[0]) == np.sign(base))
+
+
+def test_a_zero_field_stays_zero():
+    """phi = 0 everywhere (no interface to measure from) is left unchanged and
+    finite: a voxel with phi = 0 does not move."""
+    phi = np.zeros((4, 5, 6))
+    out = oracle.sussman(phi, cfl=0.3, iters=5)
+    assert np.all(out == 0.0)
