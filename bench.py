@@ -1,26 +1,32 @@
 #!/usr/bin/env python3
 """Throughput of the sparse-block-grid reaction-diffusion step on one B300.
 
-Default workload (`--workload grf256`): the 256^3 tortuosity solve - a
-thresholded Gaussian random field (correlation length 8, porosity 0.35),
-c = 1 / c = 0 held on the x faces, D = 1, dt = 0.15, an SBG_F32R state (FP32
-correction d on a compensated base b = hi + lo: each step is FP32 forward
-Euler on d with the source r = L_h b; the check folds d into b) with
-double-float/FP64 reductions.  One bench step = one check interval of the
-steady-state solve: 256 forward-Euler steps plus the residual and flux
-reduction that decides convergence (which also refreshes r and folds d).
+Default workload (`--workload reactive512`): the two-species reactive run
+on a 512^3 Boolean packing of polydisperse spheres (pore fraction 0.40):
+species A diffuses (D = 1) and reacts to B at the pore surface (Sec. 3.5's
+surface sink, k = 0.05 times the smoothed delta weight of phi), B diffuses
+(D = 0.5) and decays (0.001); FP32 state, FP64 checks.  One bench step is
+one whole run: 2000 forward-Euler steps from the initial field with an FP64
+mass/flux/min/max check of both species every 100 steps.
 
-Metric: active-voxel updates per second (GVox/s) = n_active * 256 * steps /
-time.  `value` is measured with CUDA events on the stream the library uses,
-inputs resident in HBM; each interval's check is enqueued behind its steps
-(sbg_reduce_async) and read on the host while the next interval runs.  `e2e`
-repeats the measurement through the public API with the dense initial field
-uploaded from pinned host memory every step and the check read back.  `roofline` reports the step kernel's algorithmic bytes
-(12 B per active voxel: d and r read, d written; 16 B for --dtype f32x2) per
-launch over its average launch time, against the measured HBM copy bandwidth.
+Metric: species-voxel updates per second (GVox/s) = 2 * n_active * 2000 *
+runs / time.  `value` is measured with CUDA events on the stream the library
+uses, inputs resident in HBM; each check is enqueued behind its steps
+(sbg_reduce_async) and read on the host while the next steps run.  `e2e`
+repeats the runs through the C ABI's host-pointer path (the initial fields
+uploaded by sbg_state_set from page-locked host memory, the final fields read
+back by sbg_state_get).  `roofline` reports the step kernel's algorithmic
+bytes (16 B per active voxel, plus 4 B per slot of the blocks that hold
+surface-band voxels) per launch over its average launch time, against the
+measured HBM copy bandwidth.
+
+`--workload grf256`: the 256^3 tortuosity solve (thresholded Gaussian random
+field, porosity 0.35, c = 1 / c = 0 held on the x faces, SBG_F32R state); one
+bench step = one check interval of 256 steps plus the residual and flux
+check.  With `--converge` it runs the whole solve to R < 1e-8 and reports the
+wall time, D_eff, tau and psi.
 
 Other workloads print one JSON line each:
-  --workload reactive512   two species, surface reaction A -> B, 2000 steps (512^3)
   --workload inhom512      inhomogeneous diffusion (Eq. 6 factor) from one face, 2000 steps (512^3)
   --workload frap256       simulated FRAP (bleached cube, pore and bulk recovery, D_eff fit) (256^3)
   --workload mms           the unit-disk manufactured solution of Sec. 3.1, 32^2..1024^2, errors and orders
@@ -53,6 +59,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 CHECK_EVERY = 256  # RD steps per check, the SBG_F32R refresh interval
+REACT_CHECK_EVERY = 100  # RD steps between the FP64 mass/flux checks of a reactive run
 # per active voxel and step: read and write the state; f32r reads the correction d and the source r
 # and writes d
 BYTES_PER_VOXEL = {"f32": 8, "f32x2": 16, "f64": 16, "f32r": 12}
@@ -64,10 +71,11 @@ KERNEL_SOURCES = ["paper_2304_11165_b300/csrc/sbg_step_pipe.cu", "paper_2304_111
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="bench steps (default: 5 whole runs for reactive512, 200 check intervals for grf256)")
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sbg", choices=["sbg", "reference"])
-    ap.add_argument("--workload", default="grf256",
+    ap.add_argument("--workload", default="reactive512",
                     choices=["grf256", "reactive512", "inhom512", "frap256", "mms", "redist512", "gradient256",
                              "batch64"])
     ap.add_argument("--n", type=int, default=None, help="box side (default: the workload's)")
@@ -77,7 +85,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fd", action="store_true", help="gradient256: FP64 central differences")
-    ap.add_argument("--converge", action="store_true", help="batch64: steady solves to 1e-6")
+    ap.add_argument("--converge", action="store_true",
+                    help="grf256: the steady solve to 1e-8 (and 1e-10); batch64: steady solves to 1e-6")
     ap.add_argument("--sides", default="64,96,128,192,256", help="batch64: box sides")
     ap.add_argument("--count", type=int, default=64, help="batch64: number of geometries")
     return ap.parse_args()
@@ -174,10 +183,11 @@ def _timed_steps(P, u, seconds):
     return nsteps, time.perf_counter() - t0
 
 
-def _single_thread(P, u, seconds):
+def _single_thread(P, u, seconds, nsteps=None):
     """The same oracle on one OpenMP thread (the process's OpenMP runtime is
     set to one thread for the run and restored after), or None when the
-    runtime cannot be reached."""
+    runtime cannot be reached; `nsteps` fixes the number of steps instead of
+    sizing the run to `seconds`."""
     import ctypes
     import oracle
     try:
@@ -189,22 +199,26 @@ def _single_thread(P, u, seconds):
     try:
         if oracle.num_threads() != 1:
             return None
+        if nsteps:
+            t0 = time.perf_counter()
+            P.run(u, nsteps)
+            return nsteps, time.perf_counter() - t0
         return _timed_steps(P, u, seconds)
     finally:
         gomp.omp_set_num_threads(n0)
 
 
-def cpu_baseline(phi, u0, phys, n_active, seconds):
+def cpu_baseline(phi, u0, phys, n_active, seconds, single_thread_steps=None):
     """The FP64 dense oracle as it stands, on the host cores, on a bounded
     number of steps of the same workload; beside it the same oracle on one
-    thread for a few seconds."""
+    thread for a few seconds (or for exactly `single_thread_steps` steps)."""
     import oracle
     P = oracle.Problem(phi, phys)
     u = P.shape_state(u0)
     cores = oracle.num_threads()
     nsteps, dt = _timed_steps(P, u, seconds)
     updates = int(phys.nspecies) * n_active
-    one = _single_thread(P, u, min(3.0, seconds / 4))
+    one = _single_thread(P, u, min(3.0, seconds / 4), single_thread_steps)
     return {"value": updates * nsteps / dt / 1e9, "unit": "GVox/s", "cores": cores,
             "kind": "oracle",
             "sample": "%d FP64 dense steps of the full %s box (all %d voxels visited per step)"
@@ -270,41 +284,68 @@ def replica_throughput(units_per_rank, world, max_ms):
 
 
 # ---------------------------------------------------------------------------
+REACT_METRIC = "species-voxel updates/s (two-species reactive run, reactive512)"
+
+
+def reactive_workload_name(n, phys, nsteps, per):
+    return ("reactive512: %d^3 Boolean sphere packing (lognormal radii, median 12, sigma 0.3), "
+            "pore fraction %.3f; A: D=1, surface reaction A->B k=0.05 in 0<phi<1; B: D=0.5, "
+            "decay 0.001; A=1 for x<32; closed box; dt=%.6f (0.9 x limit); one bench step = "
+            "one run of %d steps with an FP64 check every %d"
+            % (n, phys.extra["pore_fraction"], phys.dt, nsteps, per))
+
+
 def run_reference(args):
+    """The reference arm: the FP64 dense oracle as it stands, on the host
+    cores, on the same workload, metric and unit as the library's line; each
+    bench step is a bounded sample (two dense steps of the whole box for
+    reactive512, two for grf256)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    if args.workload != "grf256":
-        emit({"impl": "reference", "unavailable": "the reference arm times the default workload only"})
+    if args.workload not in ("grf256", "reactive512"):
+        emit({"impl": "reference", "unavailable": "the reference arm times the reactive512 and grf256 workloads"})
         return 0
-    from workloads import grf256
     import oracle
-    phi, u0, phys = grf256(n=args.n or 256)
+    per_step = 2
+    if args.workload == "reactive512":
+        from workloads import reactive512
+        n = args.n or 512
+        phi, u0, phys = reactive512(n=n)
+        metric, counted = REACT_METRIC, 2
+        workload = reactive_workload_name(n, phys, phys.steps, REACT_CHECK_EVERY)
+    else:
+        from workloads import grf256
+        phi, u0, phys = grf256(n=args.n or 256)
+        metric, counted = METRIC, 1
+        workload = "grf256 tortuosity solve (%d^3 GRF, porosity 0.35)" % phys.dims[0]
     P = oracle.Problem(phi, phys)
     n_active = int(P.active.sum())
     u = P.shape_state(u0)
-    per_step = 2
     for _ in range(args.warmup):
         u = P.run(u, 1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         u = P.run(u, per_step)
     dt = time.perf_counter() - t0
-    value = n_active * per_step * args.steps / dt / 1e9
-    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "GVox/s",
+    value = counted * n_active * per_step * args.steps / dt / 1e9
+    sample = "%d FP64 dense steps of the full %s box per bench step" % (
+        per_step, "x".join(str(d) for d in phys.dims))
+    emit({"impl": "reference", "metric": metric, "value": value, "unit": "GVox/s",
           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
           "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-          "config": {"workload": "grf256 tortuosity solve (256^3 GRF, porosity 0.35)",
-                     "box": list(phys.dims), "steps_per_bench_step": per_step},
+          "config": {"workload": workload, "box": list(phys.dims), "steps_per_bench_step": per_step},
           "cpu_baseline": {"value": value, "unit": "GVox/s", "cores": oracle.num_threads(), "kind": "oracle",
-                           "sample": "%d FP64 dense steps of the full box per bench step" % per_step},
+                           "sample": sample},
           "e2e": {"value": value, "unit": "GVox/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
     return 0
 
 
 # ---------------------------------------------------------------------------
 def run_grf256(args):
+    if args.converge:
+        return run_grf256_converge(args)
     import torch
     from paper_2304_11165_b300 import Grid, State, make_params
     import paper_2304_11165_b300._abi as abi
@@ -373,33 +414,17 @@ def run_grf256(args):
     total_ms = max_over_ranks(total_ms, dev)
     value = replica_throughput(n_active * CHECK_EVERY * args.steps, world, total_ms) / 1e9
 
-    # end-to-end through the public API: every step uploads its dense input field from pinned host
-    # memory (on a copy stream, one step ahead, into one of two device staging buffers, so the upload
-    # overlaps the previous step's compute), scatters it into the state, steps, and reads D_eff back
+    # end to end through the C ABI's host-pointer path: every bench step sets its dense input field
+    # from page-locked host memory (sbg_state_set with on_device = 0: the library copies it to the
+    # device and scatters it), steps, and reads its check into host memory
     u0_host = torch.from_numpy(u0.astype(np.float32)).pin_memory()
     st2 = State(g, 1, args.dtype).set_kernel(args.variant)
-    copy_stream = torch.cuda.Stream(dev)
-    staging = [torch.empty(u0.shape, dtype=torch.float32, device=dev) for _ in range(2)]
-    ready = [torch.cuda.Event() for _ in range(2)]
-    consumed = [torch.cuda.Event() for _ in range(2)]
-
-    def upload(i):
-        with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(consumed[i % 2])  # the scatter of step i - 2 has read this buffer
-            staging[i % 2].copy_(u0_host, non_blocking=True)
-            ready[i % 2].record(copy_stream)
-
     e_buf = [torch.zeros(abi.NRED, dtype=torch.float64).pin_memory() for _ in range(2)]
     e_done = [torch.cuda.Event() for _ in range(2)]
 
     def e2e_steps(n):
-        upload(0)
         for i in range(n):
-            if i + 1 < n:
-                upload(i + 1)
-            stream.wait_event(ready[i % 2])
-            st2.set(staging[i % 2], stream=stream)
-            consumed[i % 2].record(stream)
+            st2.set(u0_host, stream=stream)
             st2.step(p, CHECK_EVERY, stream=stream)
             st2.reduce_async(p, e_buf[i % 2], stream=stream)  # device -> host copy of the step's result
             e_done[i % 2].record(stream)
@@ -439,8 +464,11 @@ def run_grf256(args):
                                "c=1/c=0 on the x faces, D=1, dt=0.15" % n,
                    "block": args.block, "kernel": args.variant, "rd_steps_per_bench_step": CHECK_EVERY,
                    "n_active": n_active, "n_blocks": g.n_blocks, "porosity": psi,
-                   "state_bytes": g.n_blocks * args.block ** 3 * BYTES_PER_VOXEL[args.dtype] * 2,
-                   "l2": "working set (two state buffers) larger than the 126 MB L2; no flush",
+                   "step_working_set_bytes": g.n_blocks * args.block ** 3 * BYTES_PER_VOXEL[args.dtype],
+                   "l2": ("one step reads and writes %.0f MB of %d-slot arrays: about the size of the 126 MB "
+                          "L2, so part of the step is served from L2 (the roofline case is reactive512)"
+                          % (g.n_blocks * args.block ** 3 * BYTES_PER_VOXEL[args.dtype] / 1e6,
+                             g.n_blocks * args.block ** 3)),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
@@ -452,7 +480,8 @@ def run_grf256(args):
         "gpu_launches": (CHECK_EVERY + (3 if args.dtype == "f32r" else 2)) * args.steps,
         "clocks": clocks,
         "interval_stats": interval_stats(interval_ms, CHECK_EVERY),
-        "result": {"D_eff_after_warmup_and_timed_steps": d_eff, "tau": tau,
+        "result": {"note": "the state after warm-up and timed intervals is not converged; --converge runs "
+                           "the solve to R < 1e-8",
                    "residual_first_last_timed_check": [residuals[0], residuals[-1]] if residuals else None},
     }
     if cpu is not None:
@@ -464,6 +493,74 @@ def run_grf256(args):
     return 0
 
 
+def run_grf256_converge(args):
+    """The tortuosity workflow of Eq. 2 / Sec. 3.3 on grf256: the steady-state
+    solve from the initial field to a relative residual below 1e-8 (the
+    config's criterion), timed on the host clock around sbg_run_to_steady,
+    then continued to 1e-10; D_eff, tau and psi at both points against the
+    FP64 oracle's conjugate-gradient steady state stored in
+    tests/golden/grf256_steady.json."""
+    import torch
+    from paper_2304_11165_b300 import Grid, State, make_params
+    from workloads import grf256
+    torch.cuda.set_device(0)
+    n = args.n or 256
+    phi, u0, phys = grf256(n=n)
+    stream = torch.cuda.current_stream()
+    g = Grid(phi, block=args.block, stream=stream)
+    p = make_params(phys)
+    st = State(g, 1, args.dtype).set_kernel(args.variant)
+    st.set(u0.astype(np.float32), stream=stream)  # warm-up: graphs, clocks; then restart
+    st.run_to_steady(p, 1e-3, check_every=CHECK_EVERY, stream=stream)
+    st.set(u0.astype(np.float32), stream=stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    steps1, rel1 = st.run_to_steady(p, 1e-8, check_every=CHECK_EVERY, stream=stream)
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter() - t0
+    d1, tau1, psi1 = st.effective_D(p, stream=stream)
+    t0 = time.perf_counter()
+    steps2, rel2 = st.run_to_steady(p, 1e-10, check_every=CHECK_EVERY, stream=stream)
+    torch.cuda.synchronize()
+    wall2 = time.perf_counter() - t0
+    clocks = sampler.stop()
+    d2, tau2, psi2 = st.effective_D(p, stream=stream)
+    gold = None
+    gpath = os.path.join(ROOT, "tests", "golden", "grf256_steady.json")
+    if n == 256 and os.path.exists(gpath):
+        gold = json.load(open(gpath))
+    line = {"metric": "wall time of the tortuosity solve to R < 1e-8 (grf256)", "value": wall1, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": "grf256 tortuosity solve: %d^3 GRF (correlation length 8, porosity 0.35), "
+                                   "c=1/c=0 on the x faces, D=1, dt=0.15, check every %d steps" % (n, CHECK_EVERY),
+                       "block": args.block, "kernel": args.variant, "n_active": g.n_active},
+            "result": {"to_1e-8": {"steps": steps1, "rel_residual": rel1, "wall_s": wall1, "D_eff": d1,
+                                   "tau": tau1, "psi": psi1,
+                                   "gvox_s": g.n_active * steps1 / wall1 / 1e9},
+                       "to_1e-10": {"extra_steps": steps2, "rel_residual": rel2, "extra_wall_s": wall2,
+                                    "D_eff": d2, "tau": tau2, "psi": psi2}},
+            "clocks": clocks}
+    if gold is not None:
+        line["result"]["oracle_cg"] = {"D_eff": gold["D_eff"], "tau": gold["tau"], "psi": gold["psi"],
+                                       "cg_relres": gold["cg_relres"]}
+        line["result"]["to_1e-8"]["D_eff_rel_err"] = abs(d1 - gold["D_eff"]) / gold["D_eff"]
+        line["result"]["to_1e-10"]["D_eff_rel_err"] = abs(d2 - gold["D_eff"]) / gold["D_eff"]
+    emit(line)
+    return 0
+
+
+def step_kernel_name(ns, variant):
+    """The step kernel a state of `ns` FP32 species runs for a kernel variant."""
+    return two_array_kernel(variant) if ns == 2 else ("k_step" if variant == "plain" else "k_step_rows2")
+
+
+def step_kernel_sources(kernel_name):
+    """Source files whose hash keys a committed ncu summary of that kernel."""
+    return KERNEL_SOURCES
+
+
 def two_array_kernel(variant):
     """Step kernel of the FP32 modes with two haloed arrays (two species; u and
     the diffusivity factor) for a kernel variant."""
@@ -471,65 +568,191 @@ def two_array_kernel(variant):
 
 
 # ---------------------------------------------------------------------------
+
+
+def reactive_algo_bytes(n_active, n_band_blocks, block):
+    """Algorithmic bytes of one two-species step: both species read and
+    written (16 B per active voxel) plus the surface weight read in every
+    slot of the blocks that hold surface-band voxels (4 B per slot)."""
+    return 16 * n_active + 4 * n_band_blocks * block ** 3
+
+
+def reactive_state_bytes(n_blocks, block):
+    """Bytes one step kernel touches in HBM besides the weights: two species
+    read from one buffer and written to the other, every slot of every block."""
+    return 2 * 2 * 4 * n_blocks * block ** 3
+
+
 def run_reactive512(args):
+    """The default bench line: the two-species reactive run of Sec. 3.5's
+    surface-sink model on the 512^3 Boolean sphere packing.  One bench step
+    is one whole run: the state reset to the initial field, 2000 FTCS steps
+    of A and B with the surface transfer and B's decay, and an FP64
+    mass/flux/min/max check of both species every 100 steps (enqueued behind
+    its steps and read on the host while the next 100 run).  `value` counts
+    species-voxel updates (two per active voxel and step) over the device
+    time of K runs with every input resident in HBM; `e2e` repeats the runs
+    through the C ABI's host-pointer path: the initial fields copied from
+    page-locked host memory by sbg_state_set (on_device = 0), the checks read
+    into host memory, and the final fields of both species copied back by
+    sbg_state_get (on_device = 0)."""
     import torch
     from paper_2304_11165_b300 import Grid, State, make_params
+    import paper_2304_11165_b300._abi as abi
     from workloads import reactive512
-    torch.cuda.set_device(0)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     n = args.n or 512
     phi, u0, phys = reactive512(n=n)
-    stream = torch.cuda.current_stream()
+    nsteps = phys.steps
+    per = REACT_CHECK_EVERY
+    stream = torch.cuda.current_stream(dev)
+    t_build = time.perf_counter()
     g = Grid(phi, block=args.block, stream=stream)
-    st = State(g, 2, "f32").set_kernel(args.variant).set_all(u0, stream=stream)
+    torch.cuda.synchronize(dev)
+    build_ms = (time.perf_counter() - t_build) * 1e3
     p = make_params(phys)
-    red0 = st.reduce(p)
-    per = 100
-    st.step(p, 3 * per, stream=stream)  # warm-up, then restart from the initial state
-    st.set_all(u0, stream=stream)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(0)
+    u0_f32 = np.ascontiguousarray(u0.astype(np.float32))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(phi, u0, phys, g.n_active, args.cpu_seconds, single_thread_steps=1)
+    st0 = State(g, 2, "f32").set_all(torch.from_numpy(u0_f32).to(dev), stream=stream)
+    st = State(g, 2, "f32").set_kernel(args.variant)
+    red_buf = [torch.zeros(2 * abi.NRED, dtype=torch.float64).pin_memory() for _ in range(2)]
+    red_done = [torch.cuda.Event() for _ in range(2)]
+
+    def one_run(state, ev=None, set_from_host=None, get_to_host=None):
+        """One whole reactive run; returns the masses read at its checks."""
+        if set_from_host is None:
+            state.copy_from(st0, stream=stream)
+        else:
+            for s in range(2):
+                state.set(set_from_host[s], species=s, stream=stream)
+        masses = []
+        for i in range(nsteps // per):
+            if ev is not None:
+                ev[i][0].record(stream)
+            state.step(p, per, stream=stream)
+            if ev is not None:
+                ev[i][1].record(stream)
+            state.reduce_async(p, red_buf[i % 2], stream=stream)
+            red_done[i % 2].record(stream)
+            if i > 0:
+                red_done[(i - 1) % 2].synchronize()
+                r = state.parse_reduction(red_buf[(i - 1) % 2])
+                masses.append((r[0]["mass"], r[1]["mass"]))
+        last = nsteps // per - 1
+        red_done[last % 2].synchronize()
+        r = state.parse_reduction(red_buf[last % 2])
+        masses.append((r[0]["mass"], r[1]["mass"]))
+        if get_to_host is not None:
+            for s in range(2):
+                state.get(s, out=get_to_host[s], stream=stream)
+        return masses
+
+    for _ in range(args.warmup):
+        one_run(st)
+    torch.cuda.synchronize(dev)
+
+    nint = nsteps // per
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nint)]
+          for _ in range(args.steps)]
+    sampler = ClockSampler(local)
     sampler.start()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kernel_ms = 0.0
-    masses = []
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for i in range(phys.steps // per):
-        a.record(stream)
-        st.step(p, per, stream=stream)
-        b.record(stream)
-        red = st.reduce(p)  # synchronises
-        kernel_ms += a.elapsed_time(b)
-        masses.append((red[0]["mass"], red[1]["mass"]))
-    t_end.record(stream)
-    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    masses = None
+    for k in range(args.steps):
+        masses = one_run(st, ev[k])
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
     clocks = sampler.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    updates = 2 * g.n_active * phys.steps
+    total_ms = max_over_ranks(start.elapsed_time(end), dev)
+    interval_ms = [a.elapsed_time(b) for evk in ev for a, b in evk]
+    per_launch_ms = sum(interval_ms) / (args.steps * nsteps)
+    updates_per_run = 2 * g.n_active * nsteps
+    value = replica_throughput(updates_per_run * args.steps, world, total_ms) / 1e9
+
+    # end to end through the C ABI's host-pointer path
+    host_in = [torch.from_numpy(u0_f32[s]).pin_memory() for s in range(2)]
+    host_out = [torch.empty(u0_f32.shape[1:], dtype=torch.float32).pin_memory() for _ in range(2)]
+    st_e = State(g, 2, "f32").set_kernel(args.variant)
+    one_run(st_e, set_from_host=host_in, get_to_host=host_out)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for _ in range(args.steps):
+        one_run(st_e, set_from_host=host_in, get_to_host=host_out)
+    e_end.record(stream)
+    torch.cuda.synchronize(dev)
+    e_wall_ms = (time.perf_counter() - t0) * 1e3
+    e2e_ms = max_over_ranks(max(e_start.elapsed_time(e_end), e_wall_ms), dev)
+    e2e_value = replica_throughput(updates_per_run * args.steps, world, e2e_ms) / 1e9
+    # the e2e run's final fields against the device-resident run's (same kernels, same inputs)
+    same_as_device_run = bool(np.array_equal(host_out[0].numpy(), st.get(0).astype(np.float32)) and
+                              np.array_equal(host_out[1].numpy(), st.get(1).astype(np.float32)))
+
     peak, peak_kind = load_peaks()
-    band_slots = g.info["n_band_blocks"] * args.block ** 3
-    algo_bytes = g.n_active * 16 + band_slots * 4
-    per_launch_ms = kernel_ms / phys.steps
-    cpu = None if args.no_cpu_baseline else cpu_baseline(phi, u0, phys, g.n_active, args.cpu_seconds)
-    emit({"metric": "species-voxel updates/s (two-species reactive run)", "value": updates / (total_ms / 1e3) / 1e9,
-          "unit": "GVox/s", "n_gpus": 1, "steps": phys.steps, "ms_per_step": total_ms / phys.steps,
-          "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-          "config": {"workload": "reactive512: %d^3 Boolean sphere packing (median radius 12, sigma 0.3), "
-                                 "pore fraction %.3f, A->B surface reaction k=0.05, decay_B=0.001, %d steps"
-                                 % (n, phys.extra["pore_fraction"], phys.steps),
-                     "block": args.block, "kernel": args.variant, "n_active": g.n_active, "n_blocks": g.n_blocks,
-                     "band_blocks": g.info["n_band_blocks"]},
-          "roofline": {"bound": "hbm", "kernel": two_array_kernel(args.variant),
-                       "achieved": algo_bytes / (per_launch_ms / 1e3) / 1e9,
-                       "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                       "frac": algo_bytes / (per_launch_ms / 1e3) / 1e9 / peak,
-                       "traffic": profile_traffic("%s_%s_f32_reactive512.md"
-                                                  % (two_array_kernel(args.variant), args.variant)),
-                       "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": per_launch_ms * 1e3},
-          "result": {"mass_A0_B0": [red0[0]["mass"], red0[1]["mass"]], "mass_A_B_end": list(masses[-1]),
-                     "total_mass_change": (masses[-1][0] + masses[-1][1]) - (red0[0]["mass"] + red0[1]["mass"])},
-          "clocks": clocks, "cpu_baseline": cpu})
+    algo_bytes = reactive_algo_bytes(g.n_active, g.info["n_band_blocks"], args.block)
+    achieved = algo_bytes / (per_launch_ms / 1e3) / 1e9
+    kernel_name = step_kernel_name(2, args.variant)
+    red0 = st0.reduce(p)
+    line = {
+        "metric": REACT_METRIC,
+        "value": value, "unit": "GVox/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": reactive_workload_name(n, phys, nsteps, per),
+                   "block": args.block, "kernel": args.variant, "n_active": g.n_active, "n_blocks": g.n_blocks,
+                   "n_band_blocks": g.info["n_band_blocks"], "build_ms": build_ms,
+                   "step_working_set_bytes": reactive_state_bytes(g.n_blocks, args.block)
+                   + 4 * g.info["n_band_blocks"] * args.block ** 3,
+                   "l2": "each step reads %.0f MB and writes %.0f MB of state (plus the weights), far beyond the "
+                         "126 MB L2; no flush needed" % (reactive_state_bytes(g.n_blocks, args.block) / 2e6,
+                                                        reactive_state_bytes(g.n_blocks, args.block) / 2e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": profile_traffic("%s_%s_f32_reactive512.md" % (kernel_name, args.variant),
+                                                step_kernel_sources(kernel_name)) if n == 512 else None,
+                     "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": per_launch_ms * 1e3,
+                     "algorithmic_bytes_rule": "16 B per active voxel (A and B read and written) + 4 B per slot "
+                                               "of the blocks holding surface-band voxels (w read)"},
+        "e2e": {"value": e2e_value, "unit": "GVox/s", "h2d_bytes_per_step": int(u0_f32.nbytes),
+                "d2h_bytes_per_step": int(u0_f32.nbytes) + nint * 2 * abi.NRED * 8,
+                "path": "sbg_state_set / sbg_state_get with host pointers (page-locked), sbg_reduce_async "
+                        "into page-locked host memory", "final_fields_equal_device_run": same_as_device_run},
+        # per run: the state copy (memcpy, not a kernel), per check interval `per` step kernels and the
+        # check (per species: reduction and final pass)
+        "gpu_launches": args.steps * nint * (per + 2 * 2),
+        "clocks": clocks,
+        "interval_stats": interval_stats(interval_ms, per),
+        "result": {"mass_A_B_initial": [red0[0]["mass"], red0[1]["mass"]], "mass_A_B_end": list(masses[-1]),
+                   "A_plus_B_end_over_initial": (masses[-1][0] + masses[-1][1]) / (red0[0]["mass"] + red0[1]["mass"])},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        emit(line)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -990,9 +1213,11 @@ def run_batch64(args):
 
 def main():
     args = parse()
+    if args.steps is None:
+        args.steps = 200 if args.workload == "grf256" else 5
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload != "grf256" and int(os.environ.get("RANK", "0")) != 0:
+    if args.workload not in ("grf256", "reactive512") and int(os.environ.get("RANK", "0")) != 0:
         return 0
     return {"grf256": run_grf256, "reactive512": run_reactive512, "inhom512": run_inhom512,
             "frap256": run_frap256, "mms": run_mms, "redist512": run_redist512,
