@@ -80,8 +80,13 @@ def parse():
                              "batch64"])
     ap.add_argument("--n", type=int, default=None, help="box side (default: the workload's)")
     ap.add_argument("--block", type=int, default=4)
+    ap.add_argument("--rd-steps", type=int, default=None,
+                    help="reactive512: RD steps per run (default: the workload's 2000; smaller for profiling)")
     ap.add_argument("--dtype", default="f32r", choices=["f32", "f32x2", "f32r"])
-    ap.add_argument("--variant", default="async", choices=["plain", "pipelined", "prefetch", "async"])
+    ap.add_argument("--variant", default=None, choices=["auto", "plain", "pipelined", "prefetch", "async", "stream"],
+                    help="step kernel (default: stream for reactive512, async for the others)")
+    ap.add_argument("--order", default=None, choices=["tiled", "planes"],
+                    help="block order of the grid (default: planes for reactive512, tiled for the others)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fd", action="store_true", help="gradient256: FP64 central differences")
@@ -553,12 +558,17 @@ def run_grf256_converge(args):
 
 def step_kernel_name(ns, variant):
     """The step kernel a state of `ns` FP32 species runs for a kernel variant."""
+    if variant == "stream":
+        return "k_step_stream"
     return two_array_kernel(variant) if ns == 2 else ("k_step" if variant == "plain" else "k_step_rows2")
+
+
+STREAM_SOURCES = ["paper_2304_11165_b300/csrc/sbg_step_stream.cu", "paper_2304_11165_b300/csrc/sbg_step.cuh"]
 
 
 def step_kernel_sources(kernel_name):
     """Source files whose hash keys a committed ncu summary of that kernel."""
-    return KERNEL_SOURCES
+    return STREAM_SOURCES if kernel_name == "k_step_stream" else KERNEL_SOURCES
 
 
 def two_array_kernel(variant):
@@ -611,11 +621,12 @@ def run_reactive512(args):
     dev = torch.device("cuda", local)
     n = args.n or 512
     phi, u0, phys = reactive512(n=n)
-    nsteps = phys.steps
-    per = REACT_CHECK_EVERY
+    nsteps = args.rd_steps or phys.steps
+    per = min(REACT_CHECK_EVERY, nsteps)
+    nsteps -= nsteps % per
     stream = torch.cuda.current_stream(dev)
     t_build = time.perf_counter()
-    g = Grid(phi, block=args.block, stream=stream)
+    g = Grid(phi, block=args.block, stream=stream, order=args.order)
     torch.cuda.synchronize(dev)
     build_ms = (time.perf_counter() - t_build) * 1e3
     p = make_params(phys)
@@ -720,8 +731,8 @@ def run_reactive512(args):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": reactive_workload_name(n, phys, nsteps, per),
-                   "block": args.block, "kernel": args.variant, "n_active": g.n_active, "n_blocks": g.n_blocks,
-                   "n_band_blocks": g.info["n_band_blocks"], "build_ms": build_ms,
+                   "block": args.block, "kernel": args.variant, "order": args.order, "n_active": g.n_active,
+                   "n_blocks": g.n_blocks, "n_band_blocks": g.info["n_band_blocks"], "build_ms": build_ms,
                    "step_working_set_bytes": reactive_state_bytes(g.n_blocks, args.block)
                    + 4 * g.info["n_band_blocks"] * args.block ** 3,
                    "l2": "each step reads %.0f MB and writes %.0f MB of state (plus the weights), far beyond the "
@@ -1213,6 +1224,10 @@ def run_batch64(args):
 
 def main():
     args = parse()
+    if args.variant is None:
+        args.variant = "stream" if args.workload == "reactive512" else "async"
+    if args.order is None:
+        args.order = "planes" if args.workload == "reactive512" else "tiled"
     if args.steps is None:
         args.steps = 200 if args.workload == "grf256" else 5
     if args.impl == "reference":

@@ -78,7 +78,18 @@ typedef struct {
     float band_eps;         /* half-width eps_b of the surface delta
                                w = (1 + cos(pi phi / eps_b)) / (2 eps_b) for 0 < phi < eps_b;
                                0 selects 1.0                                                    */
+    int32_t order;          /* order of the active blocks in the list (a layout choice of this
+                               library; results do not depend on it):
+                               SBG_ORDER_TILED (0): tiles of 32^3 voxels, x-fastest, blocks
+                               x-fastest inside a tile, so that a CTA walking a contiguous range
+                               of the list meets a block's face neighbours soon after it;
+                               SBG_ORDER_PLANES (1): plain x-fastest order of the box blocks
+                               (z slowest), so that a kernel whose CTAs take the list's groups
+                               in turn sweeps the box plane by plane and finds every face
+                               neighbour in L2 (the streaming kernel, SBG_KERNEL_STREAM)        */
 } sbg_build_opts;
+
+enum { SBG_ORDER_TILED = 0, SBG_ORDER_PLANES = 1 };
 
 /* Physics of a run (constant D per species; Eq. 1 with a linear f).
  * Species 0 (A) loses k_surf * w * A + decay[0] * A per unit time; with two
@@ -257,6 +268,12 @@ sbg_status sbg_step_source(sbg_grid grid, sbg_state state, const sbg_params *par
  * of two species or with a diffusivity factor and SBG_F32X2 states run two
  * z-paired rows per thread too, except in batched steps).  ctas_per_sm:
  * persistent CTAs per SM for the pipelined kernel (0 = as many as fit).
+ * SBG_KERNEL_STREAM (SBG_F32 states of one or two species on 4^3 blocks,
+ * without a diffusivity factor: CTAs take groups of 16 blocks in turn, one
+ * x-row of four voxels per thread, every neighbour row read straight from
+ * global memory through L1, the groups a few sweeps ahead prefetched into L2
+ * with bulk prefetches; best with SBG_ORDER_PLANES grids; states of other
+ * kinds fall back to SBG_KERNEL_AUTO's choice).
  * Results are bitwise identical across variants.  The pipelined kernels index
  * voxel slots with 32-bit integers: a grid of 2^31 or more slots (blocks x
  * B^3) runs the one-thread-per-voxel kernel under SBG_KERNEL_AUTO, and
@@ -267,7 +284,8 @@ enum {
     SBG_KERNEL_PLAIN = 1,
     SBG_KERNEL_PIPELINED = 2,
     SBG_KERNEL_PIPELINED_PREFETCH = 3,
-    SBG_KERNEL_PIPELINED_ASYNC = 4
+    SBG_KERNEL_PIPELINED_ASYNC = 4,
+    SBG_KERNEL_STREAM = 5
 };
 sbg_status sbg_state_set_kernel(sbg_state state, int32_t variant, int32_t ctas_per_sm);
 

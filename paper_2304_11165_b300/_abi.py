@@ -23,6 +23,8 @@ SBG_ERR_NOT_CONVERGED = 7
 SBG_F32, SBG_F64, SBG_F32X2, SBG_F32R = 0, 1, 2, 3
 SBG_FACE_NOFLUX, SBG_FACE_DIRICHLET = 0, 1
 SBG_KERNEL_AUTO, SBG_KERNEL_PLAIN, SBG_KERNEL_PIPELINED, SBG_KERNEL_PIPELINED_PREFETCH, SBG_KERNEL_PIPELINED_ASYNC = 0, 1, 2, 3, 4
+SBG_KERNEL_STREAM = 5
+SBG_ORDER_TILED, SBG_ORDER_PLANES = 0, 1
 
 RED_MASS, RED_JIN, RED_JOUT, RED_RESIDUAL, RED_MIN, RED_MAX, RED_NONFINITE, RED_NACTIVE = range(8)
 NRED = 8
@@ -36,7 +38,7 @@ c_float = ctypes.c_float
 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("block", c_int32), ("phi_on_device", c_int32), ("eps_mask", c_float),
-                ("band_eps", c_float)]
+                ("band_eps", c_float), ("order", c_int32)]
 
 
 class RedistOpts(ctypes.Structure):

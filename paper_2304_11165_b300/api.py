@@ -12,6 +12,7 @@ from . import _abi
 from ._abi import NRED, Params, check, load
 
 _DTYPES = {"f32": _abi.SBG_F32, "f64": _abi.SBG_F64, "f32x2": _abi.SBG_F32X2, "f32r": _abi.SBG_F32R}
+_ORDERS = {"tiled": _abi.SBG_ORDER_TILED, "planes": _abi.SBG_ORDER_PLANES}
 
 
 def _stream_handle(stream):
@@ -84,13 +85,13 @@ class Grid:
     """A sparse block grid built on the device from one or more phi fields."""
 
     def __init__(self, phi=None, block: int = 8, eps_mask: float = 0.0, band_eps: float = 1.0,
-                 stream=None, _handle=None, _keep=None):
+                 stream=None, order: str = "tiled", _handle=None, _keep=None):
         lib = load()
         self._lib = lib
         if _handle is not None:
             self.handle = _handle
         else:
-            opts = _abi.BuildOpts(block, 0, eps_mask, band_eps)
+            opts = _abi.BuildOpts(block, 0, eps_mask, band_eps, _ORDERS[order])
             ptr, code, on_dev, keep = _phi_ptr(phi)
             opts.phi_on_device = on_dev
             nz, ny, nx = phi.shape
@@ -101,7 +102,8 @@ class Grid:
         self._refresh_info()
 
     @classmethod
-    def batch(cls, phis, block: int = 8, eps_mask: float = 0.0, band_eps: float = 1.0, stream=None):
+    def batch(cls, phis, block: int = 8, eps_mask: float = 0.0, band_eps: float = 1.0, stream=None,
+              order: str = "tiled"):
         lib = load()
         n = len(phis)
         ptrs = (ctypes.c_void_p * n)()
@@ -118,7 +120,7 @@ class Grid:
             ptrs[i] = ptr
             nz, ny, nx = phi.shape
             dims[3 * i:3 * i + 3] = [nx, ny, nz]
-        opts = _abi.BuildOpts(block, on_dev or 0, eps_mask, band_eps)
+        opts = _abi.BuildOpts(block, on_dev or 0, eps_mask, band_eps, _ORDERS[order])
         h = ctypes.c_void_p()
         check(lib.sbg_build_batch(n, ptrs, dims, ctypes.byref(opts), _stream_handle(stream),
                                   ctypes.byref(h)))
@@ -240,7 +242,8 @@ class State:
     def set_kernel(self, variant: str = "auto", ctas_per_sm: int = 0):
         code = {"auto": _abi.SBG_KERNEL_AUTO, "plain": _abi.SBG_KERNEL_PLAIN,
                 "pipelined": _abi.SBG_KERNEL_PIPELINED,
-                "prefetch": _abi.SBG_KERNEL_PIPELINED_PREFETCH, "async": _abi.SBG_KERNEL_PIPELINED_ASYNC}[variant]
+                "prefetch": _abi.SBG_KERNEL_PIPELINED_PREFETCH, "async": _abi.SBG_KERNEL_PIPELINED_ASYNC,
+                "stream": _abi.SBG_KERNEL_STREAM}[variant]
         check(self._lib.sbg_state_set_kernel(self.handle, code, int(ctas_per_sm)))
         return self
 

@@ -134,36 +134,48 @@ static sbg_status exclusive_scan(const int32_t *in, int64_t n, bool as_flags, in
 }
 
 // ---------------------------------------------------------------------------
-// Block order.  Box blocks are enumerated tile by tile (tiles of T x T x T
-// blocks, T = 32 / B, i.e. 32^3 voxels; tiles and the blocks inside a tile in
-// x-fastest order), and the active ones are compacted in that order.  All six
-// face neighbours of a block are then close to it in the list, so a CTA that
-// walks a contiguous range of the list finds most halo values in L2 and meets
-// a neighbour block soon after reading its halo.
+// Block order.  Box blocks are enumerated tile by tile (tiles of tx x ty x tz
+// blocks; tiles and the blocks inside a tile in x-fastest order), and the
+// active ones are compacted in that order.
+//  - SBG_ORDER_TILED: tiles of 32^3 voxels (T = 32 / B blocks per side).  All
+//    six face neighbours of a block are close to it in the list, so a CTA that
+//    walks a contiguous range of the list finds most halo values in L2 and
+//    meets a neighbour block soon after reading its halo.
+//  - SBG_ORDER_PLANES: one tile per plane of blocks (the whole x-y extent, one
+//    block thick), i.e. plain x-fastest order.  CTAs that take the list's
+//    groups in turn then sweep the box one plane of blocks after another: the
+//    -z neighbours were read one sweep earlier and the +z ones are read one
+//    sweep later, so both stay in L2.
 struct BlockEnum {
-    int nbx, nby, nbz, T, ntx, nty, ntz;
-    __host__ __device__ int64_t count() const { return (int64_t)ntx * nty * ntz * T * T * T; }
+    int nbx, nby, nbz, tx, ty, tz, ntx, nty, ntz;
+    __host__ __device__ int64_t count() const { return (int64_t)ntx * nty * ntz * tx * ty * tz; }
     // enumeration index -> block coordinates; false when the slot is padding
     __host__ __device__ bool decode(int64_t k, int &bx, int &by, int &bz) const {
-        const int64_t t3 = (int64_t)T * T * T;
+        const int64_t t3 = (int64_t)tx * ty * tz;
         const int64_t tile = k / t3;
         const int inner = (int)(k - tile * t3);
-        const int tx = (int)(tile % ntx), ty = (int)((tile / ntx) % nty), tz = (int)(tile / ((int64_t)ntx * nty));
-        bx = tx * T + inner % T;
-        by = ty * T + (inner / T) % T;
-        bz = tz * T + inner / (T * T);
+        const int ix = (int)(tile % ntx), iy = (int)((tile / ntx) % nty), iz = (int)(tile / ((int64_t)ntx * nty));
+        bx = ix * tx + inner % tx;
+        by = iy * ty + (inner / tx) % ty;
+        bz = iz * tz + inner / (tx * ty);
         return bx < nbx && by < nby && bz < nbz;
     }
 };
-static BlockEnum make_enum(int64_t nx, int64_t ny, int64_t nz, int B) {
+static BlockEnum make_enum(int64_t nx, int64_t ny, int64_t nz, int B, int order) {
     BlockEnum e;
     e.nbx = (int)((nx + B - 1) / B);
     e.nby = (int)((ny + B - 1) / B);
     e.nbz = (int)((nz + B - 1) / B);
-    e.T = 32 / B;
-    e.ntx = (e.nbx + e.T - 1) / e.T;
-    e.nty = (e.nby + e.T - 1) / e.T;
-    e.ntz = (e.nbz + e.T - 1) / e.T;
+    if (order == SBG_ORDER_PLANES) {
+        e.tx = e.nbx;
+        e.ty = e.nby;
+        e.tz = 1;
+    } else {
+        e.tx = e.ty = e.tz = 32 / B;
+    }
+    e.ntx = (e.nbx + e.tx - 1) / e.tx;
+    e.nty = (e.nby + e.ty - 1) / e.ty;
+    e.ntz = (e.nbz + e.tz - 1) / e.tz;
     return e;
 }
 
@@ -274,6 +286,48 @@ __global__ void k_select_slab(const int32_t *band, const int32_t *pos, int64_t n
     if (i < nb) ws[i] = band[i] ? pos[i] : -1;
 }
 
+// Band rows of 4^3 blocks: a row (four x-consecutive voxels) is a band row iff
+// one of its surface weights is non-zero.  count[b] = number of band rows.
+__global__ void k_band_rows(const int32_t *__restrict__ wslab, const float *__restrict__ w, int64_t nb,
+                            int32_t *count) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int ws = wslab[b];
+    int c = 0;
+    if (ws >= 0)
+        for (int r = 0; r < 16; ++r) {
+            const float *q = w + (int64_t)ws * 64 + r * 4;
+            c += (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f || q[3] != 0.f);
+        }
+    count[b] = c;
+}
+
+// wmeta[b] = (index of the block's first band row in wrow, mask of its band
+// rows), wmeta[nb].x = the number of band rows; wrow = the rows' weights,
+// copied bit for bit from the slabs.  One thread per (block, row).
+__global__ void k_band_rows_fill(const int32_t *__restrict__ wslab, const float *__restrict__ w, int64_t nb,
+                                 const int32_t *__restrict__ off, int2 *wmeta, float4 *wrow) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb * 16) return;
+    const int64_t b = t >> 4;
+    const int r = (int)(t & 15);
+    const int ws = wslab[b];
+    uint32_t mask = 0;
+    if (ws >= 0)
+        for (int q = 0; q < 16; ++q) {
+            const float *p = w + (int64_t)ws * 64 + q * 4;
+            if (p[0] != 0.f || p[1] != 0.f || p[2] != 0.f || p[3] != 0.f) mask |= 1u << q;
+        }
+    if (r == 0) {
+        wmeta[b] = make_int2(off[b], (int)mask);
+        if (b == nb - 1) wmeta[nb] = make_int2(off[b] + __popc(mask), 0);
+    }
+    if ((mask >> r) & 1u) {
+        const float *p = w + (int64_t)ws * 64 + r * 4;
+        wrow[off[b] + __popc(mask & ((1u << r) - 1u))] = make_float4(p[0], p[1], p[2], p[3]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // device hash: key = geometry, bz, by, bx packed in 16 bits each
 __host__ __device__ __forceinline__ unsigned long long block_key(int bx, int by, int bz, int g) {
@@ -377,6 +431,8 @@ static void grid_free(sbg_grid g) {
     cudaFree(g->heldbits);
     cudaFree(g->eps);
     cudaFree(g->eps64);
+    cudaFree(g->wmeta);
+    cudaFree(g->wrow);
     cudaFreeHost(g->err_host);
     delete g;
 }
@@ -390,6 +446,7 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
     g->n_geoms = n;
     g->eps_mask = opts->eps_mask > 0.f ? opts->eps_mask : 1.1920928955078125e-7f;
     g->band_eps = opts->band_eps > 0.f ? opts->band_eps : 1.0f;
+    g->order = opts->order;
     g->dims.assign(dims, dims + 3 * (size_t)n);
     g->geom_nactive.assign(n, 0);
     g->geom_begin.assign(n, 0);
@@ -431,7 +488,7 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
             TRYC(cudaMalloc(&dphi[i], sizeof(float) * nvox));
             TRYC(cudaMemcpyAsync(dphi[i], phis[i], sizeof(float) * nvox, cudaMemcpyHostToDevice, st));
         }
-        const BlockEnum en = make_enum(nx, ny, nz, B);
+        const BlockEnum en = make_enum(nx, ny, nz, B, opts->order);
         const int64_t nbox = en.count();
         TRYC(cudaMalloc(&dcount[i], sizeof(int32_t) * nbox));
         TRYC(cudaMalloc(&dpos[i], sizeof(int32_t) * nbox));
@@ -481,7 +538,7 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
     // pass 2: compaction, bitmaps, band flags
     for (int i = 0; i < n; ++i) {
         const int64_t nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
-        const BlockEnum en = make_enum(nx, ny, nz, B);
+        const BlockEnum en = make_enum(nx, ny, nz, B, opts->order);
         const int64_t nbox = en.count();
         k_compact<<<(unsigned)((nbox + 255) / 256), 256, 0, st>>>(dcount[i], dpos[i], nbox, en, i,
                                                                  g->geom_begin[i], g->blocks);
@@ -520,6 +577,36 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
         k_fill_w<B><<<(unsigned)((g->geom_count[i] * B3 + 255) / 256), 256, 0, st>>>(
             dphi[i], (int)nx, (int)ny, (int)nz, g->blocks, g->geom_begin[i], g->geom_count[i],
             g->wslab, g->eps_mask, (double)g->band_eps, g->w, g->w64);
+    }
+
+    // band rows (4^3 blocks): the rows of four voxels that hold surface weight,
+    // packed in list order, for the streaming step kernel
+    if (B == 4) {
+        TRY(dalloc(g, &g->wmeta, total + 1));
+        TRYC(cudaMemsetAsync(g->wmeta, 0, sizeof(int2) * (total + 1), st));
+        if (total > 0 && nband > 0) {
+            int32_t *rcount = nullptr, *roff = nullptr;
+            cudaError_t e1 = cudaMallocAsync(&rcount, sizeof(int32_t) * total, st);
+            cudaError_t e2 = cudaMallocAsync(&roff, sizeof(int32_t) * total, st);
+            int64_t nrows = 0;
+            sbg_status r2 = (e1 == cudaSuccess && e2 == cudaSuccess) ? SBG_OK : cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaMallocAsync (band rows)");
+            if (r2 == SBG_OK) {
+                k_band_rows<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g->wslab, g->w, total, rcount);
+                r2 = exclusive_scan(rcount, total, false, roff, &nrows, st);
+            }
+            if (r2 == SBG_OK) {
+                g->n_wrows = nrows;
+                r2 = dalloc(g, &g->wrow, (size_t)nrows);
+            }
+            if (r2 == SBG_OK) {
+                k_band_rows_fill<<<(unsigned)((total * 16 + 255) / 256), 256, 0, st>>>(g->wslab, g->w, total, roff,
+                                                                                       g->wmeta, g->wrow);
+                r2 = cuda_ok(cudaGetLastError(), "k_band_rows_fill");
+            }
+            cudaFreeAsync(rcount, st);
+            cudaFreeAsync(roff, st);
+            TRY(r2);
+        }
     }
 
     // hash and neighbour table
@@ -561,6 +648,8 @@ static sbg_status check_build_args(int32_t n, const float *const *phis, const in
     }
     if (!(opts->eps_mask >= 0.f) || !(opts->band_eps >= 0.f))
         return fail(SBG_ERR_INVALID_ARG, "sbg_build: eps_mask and band_eps must be >= 0");
+    if (opts->order != SBG_ORDER_TILED && opts->order != SBG_ORDER_PLANES)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_build: order must be SBG_ORDER_TILED or SBG_ORDER_PLANES");
     return SBG_OK;
 }
 
@@ -637,4 +726,4 @@ extern "C" const char *sbg_status_string(sbg_status s) {
     return "unknown status";
 }
 
-extern "C" int32_t sbg_abi_version(void) { return 1; }
+extern "C" int32_t sbg_abi_version(void) { return 2; }

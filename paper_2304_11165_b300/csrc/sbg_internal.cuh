@@ -109,6 +109,10 @@ struct sbg_grid_s {
     int eps_version = 0;           // bumped when the factor is set or cleared (captured graphs)
     uint64_t *heldbits = nullptr;  // [nb * words]: voxels held by the Dirichlet faces of heldbits_mask
     int heldbits_mask = -1;        // face set heldbits was computed for (-1: none yet)
+    int2 *wmeta = nullptr;         // 4^3 blocks: [nb + 1] (first band row in wrow, band-row mask)
+    float4 *wrow = nullptr;        // 4^3 blocks: surface weights of the band rows, in list order
+    int64_t n_wrows = 0;
+    int order = SBG_ORDER_TILED;   // block order of the list (sbg_build_opts.order)
     int *err = nullptr;            // device error word written by bounded waits (0 = none)
     int *err_host = nullptr;       // pinned copy
     int64_t bytes = 0;
@@ -135,6 +139,8 @@ struct sbg_state_s {
     int graph_ctas = -1;
     int graph_eps_version = -1;
     int variant = SBG_KERNEL_AUTO;  // step kernel choice (sbg_state_set_kernel)
+    bool has_ghost = false;         // every val array is preceded by a ghost block of sentinels
+                                    // (states made by sbg_state_create; not the adjoint's views)
     int ctas_per_sm = 0;
     // SBG_F32R (one species): val[b][0] holds the FP32 correction d; the base
     // b = bh + bl and the source r = L_h b are single arrays updated in place

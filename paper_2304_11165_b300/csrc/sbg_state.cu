@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include <cstring>
+#include <vector>
 
 #include "sbg_internal.cuh"
 #include "sbg_trace.cuh"
@@ -224,9 +225,13 @@ extern "C" sbg_status sbg_state_create(sbg_grid g, int32_t nspecies, sbg_dtype d
     st->dtype = dtype;
     st->nslots = g->nb * (int64_t)g->b3();
     const size_t per = (size_t)st->nslots * st->elem();
+    // each species array is preceded by one ghost block of sentinels (block id -1, the id the
+    // face table gives an absent neighbour), which the streaming step kernel reads for an absent
+    // neighbour block; 256-byte multiples keep every array 256-byte aligned
+    const size_t ghost = ((size_t)g->b3() * st->elem() + 255) / 256 * 256;
     const size_t perlo = dtype == SBG_F32X2 ? (size_t)st->nslots * 4 : 0;
     const size_t extra = dtype == SBG_F32R ? 3 * (size_t)st->nslots * 4 : 0;  // base hi, lo and source
-    const size_t total = 2 * (size_t)nspecies * (per + perlo) + extra;
+    const size_t total = 2 * (size_t)nspecies * (per + ghost + perlo) + extra;
     cudaError_t e = cudaMalloc(&st->base, total > 0 ? total : 16);
     if (e != cudaSuccess) {
         delete st;
@@ -236,8 +241,8 @@ extern "C" sbg_status sbg_state_create(sbg_grid g, int32_t nspecies, sbg_dtype d
     char *p = (char *)st->base;
     for (int b = 0; b < 2; ++b)
         for (int s = 0; s < nspecies; ++s) {
-            st->val[b][s] = p;
-            p += per;
+            st->val[b][s] = p + ghost;
+            p += ghost + per;
             if (perlo) {
                 st->lo[b][s] = (float *)p;
                 p += perlo;
@@ -251,11 +256,28 @@ extern "C" sbg_status sbg_state_create(sbg_grid g, int32_t nspecies, sbg_dtype d
     // every slot starts as the sentinel until sbg_state_set (0xff.. bytes: a NaN, not the sentinel,
     // so an unset state is reported as non-finite)
     e = cudaMemset(st->base, 0xff, total > 0 ? total : 16);
+    if (e == cudaSuccess) {
+        // the ghost blocks hold the sentinel for good (no kernel writes block -1)
+        std::vector<unsigned char> gh(ghost);
+        for (size_t i = 0; i < ghost; i += st->elem()) {
+            if (st->elem() == 8) {
+                const double v = sentinel_f64();
+                std::memcpy(&gh[i], &v, 8);
+            } else {
+                const float v = sentinel_f32();
+                std::memcpy(&gh[i], &v, 4);
+            }
+        }
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+            for (int s = 0; s < nspecies && e == cudaSuccess; ++s)
+                e = cudaMemcpy((char *)st->val[b][s] - ghost, gh.data(), ghost, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaFree(st->base);
         delete st;
         return cuda_fail(e, "cudaMemset (state)");
     }
+    st->has_ghost = true;
     *out = st;
     return SBG_OK;
 }

@@ -364,6 +364,11 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
     const bool inh = a.eps != nullptr;
     if (inh && ((st->dtype != SBG_F32 && st->dtype != SBG_F64) || st->ns != 1))
         return fail(SBG_ERR_INVALID_ARG, "a diffusivity factor is set: SBG_F32 or SBG_F64 states of one species only");
+    if (st->variant == SBG_KERNEL_STREAM && stream_kernel_applies(g, st)) {
+        cudaError_t e = launch_step_stream(a, g, st->ns, react, st->ctas_per_sm, s);
+        if (e != cudaSuccess) return cuda_fail(e, "streaming step kernel launch");
+        return SBG_OK;
+    }
     if (st->variant != SBG_KERNEL_PLAIN) {
         cudaError_t e = cudaSuccess;
         if (launch_step_pipe(a, st->dtype, st->ns, g->B, react, halo_variant_of(st->variant),
@@ -371,7 +376,7 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
             if (e != cudaSuccess) return cuda_fail(e, "pipelined step kernel launch");
             return SBG_OK;
         }
-        if (st->variant >= SBG_KERNEL_PIPELINED)
+        if (st->variant >= SBG_KERNEL_PIPELINED && st->variant != SBG_KERNEL_STREAM)
             return fail(SBG_ERR_INVALID_ARG,
                         st->dtype == SBG_F64 ? "the pipelined kernel handles FP32-based states only"
                                              : "the pipelined kernel needs fewer than 2^31 voxel slots (blocks x B^3)");
@@ -594,9 +599,9 @@ extern "C" sbg_status sbg_step(sbg_grid g, sbg_state st, const sbg_params *p, in
 
 extern "C" sbg_status sbg_state_set_kernel(sbg_state st, int32_t variant, int32_t ctas_per_sm) {
     if (!st) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: null state");
-    if (variant < SBG_KERNEL_AUTO || variant > SBG_KERNEL_PIPELINED_ASYNC || ctas_per_sm < 0 || ctas_per_sm > 64)
+    if (variant < SBG_KERNEL_AUTO || variant > SBG_KERNEL_STREAM || ctas_per_sm < 0 || ctas_per_sm > 64)
         return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: bad variant or ctas_per_sm");
-    if (variant >= SBG_KERNEL_PIPELINED && st->dtype == SBG_F64)
+    if (variant >= SBG_KERNEL_PIPELINED && variant != SBG_KERNEL_STREAM && st->dtype == SBG_F64)
         return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: no pipelined kernel for FP64 states");
     st->variant = variant;
     st->ctas_per_sm = ctas_per_sm;

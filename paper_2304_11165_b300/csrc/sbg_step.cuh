@@ -197,6 +197,11 @@ inline int halo_variant_of(int variant) {
     return variant == SBG_KERNEL_PIPELINED_PREFETCH ? 1 : variant == SBG_KERNEL_PIPELINED ? 0 : 2;
 }
 
+// Streaming step kernel (sbg_step_stream.cu): SBG_F32 states of one or two
+// species on 4^3 blocks with ghost blocks, no diffusivity factor, no work list.
+bool stream_kernel_applies(sbg_grid g, sbg_state st);
+cudaError_t launch_step_stream(const StepArgs &a, sbg_grid g, int ns, bool react, int ctas_per_sm, cudaStream_t s);
+
 // One adjoint step on FP32 arrays with the pipelined kernel: io.src = lambda^{n+1}
 // (NS arrays) then u^n (NS arrays), io.dst = lambda^n.  *grid_out receives the
 // number of CTAs (each adds to io.gsum[cta * 3 + q]); at most max_ctas are used.

@@ -1,0 +1,339 @@
+// Streaming step kernel: the forward-Euler FTCS step of Eq. 1 (Sec. 2.3, the
+// no-flux rule of Appendix B Listing 6, the surface sink of Sec. 3.5) for
+// FP32 states of one or two species on 4^3 blocks.
+//
+// Why this form: the step moves 8 B per species and voxel and does ~12 FP32
+// operations for it, so on B300 it is bound by HBM bytes and by how many of
+// them are in flight, not by arithmetic.  The ring-buffer kernels
+// (sbg_step_pipe.cu) stage every group through shared memory and fetch the
+// face halos of each group with extra copies; with two species they fit only
+// a few CTAs per SM and stay latency-bound.  Here:
+//  - CTAs of 256 threads take groups of 16 consecutive blocks of the list in
+//    turn (group g goes to CTA g mod gridDim), so at any moment the whole GPU
+//    works on one window of the list.  On a grid built in plane order
+//    (SBG_ORDER_PLANES: x fastest, z slowest) that window sweeps the box plane
+//    by plane, and the face neighbours of every block (in the same plane, one
+//    plane below or one above) were read less than one sweep ago or are read
+//    within one sweep: they come from L2, never again from HBM;
+//  - one thread per x-row of four voxels: its own row, the four y/z
+//    neighbour rows and the two x neighbour values are read straight from
+//    global memory (16-byte loads through L1; rows of the same block are read
+//    by the same half-warp).  An absent neighbour block reads the state's
+//    ghost block (block id nb, all sentinels), so no pointer selects;
+//  - thread 0 of each CTA issues bulk L2 prefetches (cp.async.bulk.prefetch)
+//    of the state rows, face table, band rows and held bits of the group it
+//    will take kStreamSweeps sweeps later, so the loads of the current group
+//    find their data in L2 and the HBM reads run ahead with nothing waiting
+//    on them;
+//  - the face ids, band-row metadata and held bits of the next group are
+//    loaded while the current group computes.
+// The per-voxel arithmetic is the plain kernel's (sbg_step.cu) with every
+// rounding pinned: the x differences of a row are formed once and shared by
+// neighbouring voxels (the same values), and an inactive neighbour (sentinel)
+// is mirrored.  States are bitwise equal to the plain kernel's (tested).
+// There is no wait on another thread or CTA in this kernel.
+#include "sbg_step.cuh"
+
+namespace sbg {
+
+constexpr int kStreamThreads = 256;  // 16 blocks x 16 rows of 4 voxels
+constexpr int kStreamSweeps = 3;     // how many sweeps ahead the L2 prefetches run
+
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    bytes &= ~15u;  // whole 16-byte units only: never past the range asked for
+    if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
+__device__ __forceinline__ float f4at(const float4 &v, int i) {
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Packed FP32 pairs (one 64-bit register pair, two lanes): the .f32x2
+// arithmetic of sm_100 and later, each lane rounded exactly as the scalar
+// instruction of the same name, so a pair (A, B) of species values is updated
+// with half the instructions and bitwise the same results.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f32x2 r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Mask of a stored value: all ones where it is the sentinel (outside Omega),
+// else 0; and the select (v where the mask is 0, c where it is all ones) as
+// one logical operation on the bits.
+__device__ __forceinline__ uint32_t sent_mask(float v) { return __float_as_uint(v) == kSent32 ? ~0u : 0u; }
+__device__ __forceinline__ float pick(float v, float c, uint32_t m) {
+    return __uint_as_float((__float_as_uint(v) & ~m) | (__float_as_uint(c) & m));
+}
+__device__ __forceinline__ float zero_if(float v, uint32_t m) { return __uint_as_float(__float_as_uint(v) & ~m); }
+__device__ __forceinline__ f32x2 zero_if2(f32x2 v, uint32_t m0, uint32_t m1) {
+    float a, b;
+    upk(v, a, b);
+    return pk(zero_if(a, m0), zero_if(b, m1));
+}
+
+// Update of one row of four voxels of one species (the plain kernel's
+// expression, voxel by voxel, with the rounding of every operation pinned):
+//   u' = u + dt ( c_x dxx + c_y dyy + c_z dzz - decay u + t ),
+//   dxx = (u~_{x+1} - u) - (u - u~_{x-1}), likewise along y and z,
+// where a neighbour outside Omega (sentinel) reads as the centre value, i.e.
+// its one-sided difference is +0.  The x differences between voxels of the
+// row are formed once and shared; the y and z terms, the Laplacian and the
+// update run on packed voxel pairs (0,1) and (2,3).  keep: mask of voxels
+// that keep their value (outside Omega or held).
+__device__ __forceinline__ float4 row_update(const float4 c, float xm, float xp, const float4 ym, const float4 yp,
+                                             const float4 zm, const float4 zp, const float cc[3], float dt,
+                                             float decay, f32x2 t01, f32x2 t23, const uint32_t keep[4]) {
+    const float u[4] = {c.x, c.y, c.z, c.w};
+    uint32_t mc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) mc[i] = sent_mask(u[i]);
+    // one-sided x differences d[i] = u_i - u_{i-1} (i = 0..4 with u_{-1} = xm, u_4 = xp), +0 where
+    // either end lies outside Omega (an inactive centre's result is discarded anyway)
+    float d[5];
+    d[0] = zero_if(__fsub_rn(u[0], xm), sent_mask(xm));
+#pragma unroll
+    for (int i = 1; i < 4; ++i) d[i] = zero_if(__fsub_rn(u[i], u[i - 1]), mc[i - 1] | mc[i]);
+    d[4] = zero_if(__fsub_rn(xp, u[3]), sent_mask(xp));
+    float dxx[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dxx[i] = __fsub_rn(d[i + 1], d[i]);
+    const float ya[4] = {ym.x, ym.y, ym.z, ym.w}, yb[4] = {yp.x, yp.y, yp.z, yp.w};
+    const float za[4] = {zm.x, zm.y, zm.z, zm.w}, zb[4] = {zp.x, zp.y, zp.z, zp.w};
+    const f32x2 cx = pk(cc[0], cc[0]), cy = pk(cc[1], cc[1]), cz = pk(cc[2], cc[2]);
+    const f32x2 dt2 = pk(dt, dt), nd = pk(-decay, -decay);
+    float r[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i0 = 2 * h, i1 = 2 * h + 1;
+        const f32x2 uu = pk(u[i0], u[i1]);
+        const f32x2 dyp = zero_if2(sub2(pk(yb[i0], yb[i1]), uu), sent_mask(yb[i0]), sent_mask(yb[i1]));
+        const f32x2 dym = zero_if2(sub2(uu, pk(ya[i0], ya[i1])), sent_mask(ya[i0]), sent_mask(ya[i1]));
+        const f32x2 dzp = zero_if2(sub2(pk(zb[i0], zb[i1]), uu), sent_mask(zb[i0]), sent_mask(zb[i1]));
+        const f32x2 dzm = zero_if2(sub2(uu, pk(za[i0], za[i1])), sent_mask(za[i0]), sent_mask(za[i1]));
+        const f32x2 lap = fma2(cz, sub2(dzp, dzm), fma2(cy, sub2(dyp, dym), mul2(cx, pk(dxx[i0], dxx[i1]))));
+        const f32x2 react = fma2(nd, uu, h == 0 ? t01 : t23);
+        const f32x2 v = fma2(dt2, add2(lap, react), uu);
+        float v0, v1;
+        upk(v, v0, v1);
+        r[i0] = pick(v0, u[i0], keep[i0] | mc[i0]);
+        r[i1] = pick(v1, u[i1], keep[i1] | mc[i1]);
+    }
+    return make_float4(r[0], r[1], r[2], r[3]);
+}
+
+template <int NS, bool REACT, bool HELD, int MINB>
+__global__ void __launch_bounds__(kStreamThreads, MINB)
+k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__restrict__ wrow, float negzero) {
+    const int t = threadIdx.x;
+    const int j = t >> 4, rr = t & 15, y = rr & 3, z = rr >> 2;
+    const int nb = (int)a.nb;  // the launcher guarantees (nb + 2) * 64 < 2^31
+    const int ngroups = (nb + 15) >> 4;
+    const int G = (int)gridDim.x;
+    // every species array is preceded by a ghost block of sentinels, block id -1: offsets
+    // below are taken from that block's start, so block f sits at (f + 1) * 64 and an
+    // absent neighbour (f = -1) at 0
+    const float *gb[NS];
+    float *out[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        gb[s] = (const float *)a.in[s] - 64;
+        out[s] = (float *)a.out[s];
+    }
+    // neighbour rows of this thread's row inside the neighbour block
+    const int oxm = 64 + rr * 4 + 3, oxp = 64 + rr * 4;
+    const int oym = 64 + rr * 4 + 12, oyp = 64 + rr * 4 - 12;
+    const int ozm = 64 + rr * 4 + 48, ozp = 64 + rr * 4 - 48;
+
+    // per thread: the face neighbours of its block it reads (-x, +x, the y side, the z side),
+    // its block's band rows and its row's held bits
+    struct Meta {
+        int f[4];
+        int woff;
+        uint32_t wmask, held;
+    };
+    auto load_meta = [&](int gi, Meta &m) {
+        const int b = gi * 16 + j;
+        if (gi < ngroups && b < nb) {
+            const int32_t *fp = a.face + (int64_t)b * 6;
+            m.f[0] = __ldg(fp + 0);
+            m.f[1] = __ldg(fp + 1);
+            m.f[2] = (y == 0) ? __ldg(fp + 2) : (y == 3) ? __ldg(fp + 3) : -1;
+            m.f[3] = (z == 0) ? __ldg(fp + 4) : (z == 3) ? __ldg(fp + 5) : -1;
+            if (REACT) {
+                const int2 wm = __ldg(wmeta + b);
+                m.woff = wm.x;
+                m.wmask = (uint32_t)wm.y;
+            } else {
+                m.woff = 0;
+                m.wmask = 0;
+            }
+            m.held = HELD ? (uint32_t)(__ldg(a.heldbits + b) >> (rr * 4)) & 0xFu : 0u;
+        } else {
+            m.f[0] = m.f[1] = m.f[2] = m.f[3] = -1;
+            m.woff = 0;
+            m.wmask = 0;
+            m.held = 0;
+        }
+    };
+
+    // L2 prefetch of one group (thread 0): state rows of every species, face ids,
+    // band-row metadata, held bits; the band rows themselves need the group's row
+    // range [wlo, whi), read from wmeta one group earlier
+    auto prefetch_group = [&](int gp) {
+        if (gp >= ngroups) return;
+        const int b0 = gp * 16, nblk = min(16, nb - b0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) prefetch_l2(gb[s] + (int64_t)(b0 + 1) * 64, (uint32_t)nblk * 256u);
+        prefetch_l2(a.face + (int64_t)b0 * 6, (uint32_t)nblk * 24u);
+        if (REACT) prefetch_l2(wmeta + b0, (uint32_t)(nblk + 1) * 8u);
+        if (HELD) prefetch_l2(a.heldbits + b0, (uint32_t)nblk * 8u);
+    };
+    auto wrange = [&](int gp, int &wlo, int &whi) {
+        wlo = whi = 0;
+        if (!REACT || gp >= ngroups) return;
+        const int b0 = gp * 16, nblk = min(16, nb - b0);
+        wlo = __ldg(&wmeta[b0].x);
+        whi = __ldg(&wmeta[b0 + nblk].x);
+    };
+    int pf_wlo = 0, pf_whi = 0;  // band-row range of the group kStreamSweeps - 1 sweeps ahead
+    if (t == 0) {
+        for (int k = 0; k < kStreamSweeps; ++k) prefetch_group(blockIdx.x + k * G);
+        for (int k = 0; k + 1 < kStreamSweeps; ++k) {
+            int lo, hi;
+            wrange(blockIdx.x + k * G, lo, hi);
+            if (hi > lo) prefetch_l2(wrow + lo, (uint32_t)(hi - lo) * 16u);
+        }
+        wrange(blockIdx.x + (kStreamSweeps - 1) * G, pf_wlo, pf_whi);
+    }
+
+    Meta cur, nxt;
+    load_meta(blockIdx.x, cur);
+    for (int gi = blockIdx.x; gi < ngroups; gi += G) {
+        const int* f = cur.f;
+        const int woff = cur.woff;
+        const uint32_t wmask = cur.wmask, held = cur.held;
+        if (t == 0) {
+            prefetch_group(gi + kStreamSweeps * G);
+            if (REACT) {
+                if (pf_whi > pf_wlo) prefetch_l2(wrow + pf_wlo, (uint32_t)(pf_whi - pf_wlo) * 16u);
+                wrange(gi + kStreamSweeps * G, pf_wlo, pf_whi);
+            }
+        }
+        const int b = gi * 16 + j;
+        const bool valid = b < nb;
+        // offsets from the ghost block's start of every value this row reads
+        const int row = (b + 1) * 64 + rr * 4;
+        const int o_xm = f[0] * 64 + oxm;
+        const int o_xp = f[1] * 64 + oxp;
+        const int o_ym = y > 0 ? row - 4 : f[2] * 64 + oym;
+        const int o_yp = y < 3 ? row + 4 : f[2] * 64 + oyp;
+        const int o_zm = z > 0 ? row - 16 : f[3] * 64 + ozm;
+        const int o_zp = z < 3 ? row + 16 : f[3] * 64 + ozp;
+        float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (REACT && valid && ((wmask >> rr) & 1u)) w4 = __ldg(wrow + woff + __popc(wmask & ((1u << rr) - 1u)));
+        load_meta(gi + G, nxt);  // the next group's tables, in flight while this one computes
+        uint32_t keep[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) keep[i] = ((held >> i) & 1u) ? ~0u : 0u;
+        f32x2 tr01 = 0ull, tr23 = 0ull;  // the surface transfer k w u_A, from species A's pass
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if (!valid) break;
+            const float *q = gb[s];
+            const float4 c = ldg4(q + row);
+            const float4 ym = ldg4(q + o_ym), yp = ldg4(q + o_yp);
+            const float4 zm = ldg4(q + o_zm), zp = ldg4(q + o_zp);
+            const float xm = __ldg(q + o_xm), xp = __ldg(q + o_xp);
+            if (s == 0 && REACT) {
+                const f32x2 k2 = pk(a.cf.k, a.cf.k);
+                tr01 = mul2(mul2(k2, pk(w4.x, w4.y)), pk(c.x, c.y));
+                tr23 = mul2(mul2(k2, pk(w4.z, w4.w)), pk(c.z, c.w));
+            }
+            float ta, tb, tc, td;
+            upk(tr01, ta, tb);
+            upk(tr23, tc, td);
+            // species A loses the transfer, B gains it (the plain kernel's -/+ of the same product;
+            // without a surface reaction the product is +0 and A's term is -0).  That -0 comes in
+            // as a kernel argument: an addend the compiler knows to be -0 would let it turn the
+            // packed fma of the decay term into a product and fuse it with the add that follows,
+            // which rounds once where the plain kernel rounds twice
+            const f32x2 t01 = s == 0 ? (REACT ? pk(-ta, -tb) : pk(negzero, negzero)) : tr01;
+            const f32x2 t23 = s == 0 ? (REACT ? pk(-tc, -td) : pk(negzero, negzero)) : tr23;
+            const float4 r = row_update(c, xm, xp, ym, yp, zm, zp, a.cf.c[s], a.cf.dt, a.cf.decay[s], t01, t23, keep);
+            *reinterpret_cast<float4 *>(out[s] + (row - 64)) = r;
+        }
+        cur = nxt;
+    }
+}
+
+template <int NS, bool REACT, bool HELD>
+static cudaError_t launch_stream_t(const StepArgs &a, const int2 *wmeta, const float4 *wrow, int ctas_per_sm,
+                                   cudaStream_t s) {
+    constexpr int MINB = 3;
+    auto kern = k_step_stream<NS, REACT, HELD, MINB>;
+    static int occ = -1, nsm = 0;
+    if (occ < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);  // all of it as L1
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStreamThreads, 0);
+        if (occ < 1) occ = 1;
+    }
+    const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
+    const int64_t ngroups = (a.nb + 15) / 16;
+    int64_t grid = (int64_t)nsm * per_sm;
+    if (grid > ngroups) grid = ngroups;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, kStreamThreads, 0, s>>>(a, wmeta, wrow, -0.0f);
+    return cudaGetLastError();
+}
+
+bool stream_kernel_applies(sbg_grid g, sbg_state st) {
+    return st->dtype == SBG_F32 && (st->ns == 1 || st->ns == 2) && g->B == 4 && st->has_ghost && !g->has_eps &&
+           g->wmeta != nullptr && (g->nb + 2) * 64 < (int64_t(1) << 31);
+}
+
+cudaError_t launch_step_stream(const StepArgs &a, sbg_grid g, int ns, bool react, int ctas_per_sm,
+                               cudaStream_t s) {
+    const bool held = a.held_mask != 0;
+    const int2 *wm = g->wmeta;
+    const float4 *wr = g->wrow;
+    if (ns == 1) {
+        if (react) return held ? launch_stream_t<1, true, true>(a, wm, wr, ctas_per_sm, s)
+                               : launch_stream_t<1, true, false>(a, wm, wr, ctas_per_sm, s);
+        return held ? launch_stream_t<1, false, true>(a, wm, wr, ctas_per_sm, s)
+                    : launch_stream_t<1, false, false>(a, wm, wr, ctas_per_sm, s);
+    }
+    if (react) return held ? launch_stream_t<2, true, true>(a, wm, wr, ctas_per_sm, s)
+                           : launch_stream_t<2, true, false>(a, wm, wr, ctas_per_sm, s);
+    return held ? launch_stream_t<2, false, true>(a, wm, wr, ctas_per_sm, s)
+                : launch_stream_t<2, false, false>(a, wm, wr, ctas_per_sm, s);
+}
+
+}  // namespace sbg

@@ -52,7 +52,7 @@ def test_build_rejects_bad_block_edge_without_touching_the_device():
     lib = _abi.load()
     phi = (ctypes.c_float * 8)(*([1.0] * 8))
     dims = (ctypes.c_int64 * 3)(2, 2, 2)
-    opts = _abi.BuildOpts(5, 0, 0.0, 1.0)
+    opts = _abi.BuildOpts(5, 0, 0.0, 1.0, 0)
     out = ctypes.c_void_p()
     rc = lib.sbg_build(phi, dims, ctypes.byref(opts), None, ctypes.byref(out))
     assert rc == _abi.SBG_ERR_INVALID_ARG
