@@ -20,11 +20,11 @@
 //    global memory (16-byte loads through L1; rows of the same block are read
 //    by the same half-warp).  An absent neighbour block reads the state's
 //    ghost block (block id nb, all sentinels), so no pointer selects;
-//  - thread 0 of each CTA issues bulk L2 prefetches (cp.async.bulk.prefetch)
-//    of the state rows, face table, band rows and held bits of the group it
-//    will take kStreamSweeps sweeps later, so the loads of the current group
-//    find their data in L2 and the HBM reads run ahead with nothing waiting
-//    on them;
+//  - no explicit prefetch: the +x neighbour values a group reads sit in the
+//    blocks of the next groups, so every sweep pulls the rows of the sweep
+//    after it into L2 as a side effect (bulk L2 prefetches a few sweeps ahead
+//    measured 12-29% slower on the 512^3 two-species run: they compete for L2
+//    with the sweep in flight);
 //  - the face ids, band-row metadata and held bits of the next group are
 //    loaded while the current group computes.
 // The per-voxel arithmetic is the plain kernel's (sbg_step.cu) with every
@@ -37,12 +37,6 @@
 namespace sbg {
 
 constexpr int kStreamThreads = 256;  // 16 blocks x 16 rows of 4 voxels
-constexpr int kStreamSweeps = 3;     // how many sweeps ahead the L2 prefetches run
-
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
-    bytes &= ~15u;  // whole 16-byte units only: never past the range asked for
-    if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
 
 __device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 
@@ -201,49 +195,12 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
         }
     };
 
-    // L2 prefetch of one group (thread 0): state rows of every species, face ids,
-    // band-row metadata, held bits; the band rows themselves need the group's row
-    // range [wlo, whi), read from wmeta one group earlier
-    auto prefetch_group = [&](int gp) {
-        if (gp >= ngroups) return;
-        const int b0 = gp * 16, nblk = min(16, nb - b0);
-#pragma unroll
-        for (int s = 0; s < NS; ++s) prefetch_l2(gb[s] + (int64_t)(b0 + 1) * 64, (uint32_t)nblk * 256u);
-        prefetch_l2(a.face + (int64_t)b0 * 6, (uint32_t)nblk * 24u);
-        if (REACT) prefetch_l2(wmeta + b0, (uint32_t)(nblk + 1) * 8u);
-        if (HELD) prefetch_l2(a.heldbits + b0, (uint32_t)nblk * 8u);
-    };
-    auto wrange = [&](int gp, int &wlo, int &whi) {
-        wlo = whi = 0;
-        if (!REACT || gp >= ngroups) return;
-        const int b0 = gp * 16, nblk = min(16, nb - b0);
-        wlo = __ldg(&wmeta[b0].x);
-        whi = __ldg(&wmeta[b0 + nblk].x);
-    };
-    int pf_wlo = 0, pf_whi = 0;  // band-row range of the group kStreamSweeps - 1 sweeps ahead
-    if (t == 0) {
-        for (int k = 0; k < kStreamSweeps; ++k) prefetch_group(blockIdx.x + k * G);
-        for (int k = 0; k + 1 < kStreamSweeps; ++k) {
-            int lo, hi;
-            wrange(blockIdx.x + k * G, lo, hi);
-            if (hi > lo) prefetch_l2(wrow + lo, (uint32_t)(hi - lo) * 16u);
-        }
-        wrange(blockIdx.x + (kStreamSweeps - 1) * G, pf_wlo, pf_whi);
-    }
-
     Meta cur, nxt;
     load_meta(blockIdx.x, cur);
     for (int gi = blockIdx.x; gi < ngroups; gi += G) {
         const int* f = cur.f;
         const int woff = cur.woff;
         const uint32_t wmask = cur.wmask, held = cur.held;
-        if (t == 0) {
-            prefetch_group(gi + kStreamSweeps * G);
-            if (REACT) {
-                if (pf_whi > pf_wlo) prefetch_l2(wrow + pf_wlo, (uint32_t)(pf_whi - pf_wlo) * 16u);
-                wrange(gi + kStreamSweeps * G, pf_wlo, pf_whi);
-            }
-        }
         const int b = gi * 16 + j;
         const bool valid = b < nb;
         // offsets from the ghost block's start of every value this row reads
