@@ -253,7 +253,8 @@ sbg_status sbg_step_source(sbg_grid grid, sbg_state state, const sbg_params *par
                            const double *factors, void *stream);
 
 /* Step-kernel choice for a state (this library's tuning knob; no
- * counterpart in the paper).  variant: SBG_KERNEL_AUTO (the pipelined kernel
+ * counterpart in the paper).  variant: SBG_KERNEL_AUTO (the streaming kernel
+ * for SBG_F32 states of two species on 4^3 blocks, else the pipelined kernel
  * with cp.async halos where it exists, else the one-thread-per-voxel kernel), SBG_KERNEL_PLAIN
  * (one thread per voxel, block tile in shared memory, one launch-sized grid)
  * SBG_KERNEL_PIPELINED (persistent CTAs streaming groups of blocks

@@ -198,13 +198,14 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
     Meta cur, nxt;
     load_meta(blockIdx.x, cur);
     for (int gi = blockIdx.x; gi < ngroups; gi += G) {
-        const int* f = cur.f;
+        const int *f = cur.f;
         const int woff = cur.woff;
         const uint32_t wmask = cur.wmask, held = cur.held;
         const int b = gi * 16 + j;
         const bool valid = b < nb;
-        // offsets from the ghost block's start of every value this row reads
-        const int row = (b + 1) * 64 + rr * 4;
+        // offsets from the ghost block's start of every value this row reads (a thread past the
+        // end of the list reads the ghost block and stores nothing)
+        const int row = valid ? (b + 1) * 64 + rr * 4 : rr * 4;
         const int o_xm = f[0] * 64 + oxm;
         const int o_xp = f[1] * 64 + oxp;
         const int o_ym = y > 0 ? row - 4 : f[2] * 64 + oym;
@@ -220,7 +221,6 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
         f32x2 tr01 = 0ull, tr23 = 0ull;  // the surface transfer k w u_A, from species A's pass
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            if (!valid) break;
             const float *q = gb[s];
             const float4 c = ldg4(q + row);
             const float4 ym = ldg4(q + o_ym), yp = ldg4(q + o_yp);
@@ -242,7 +242,7 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
             const f32x2 t01 = s == 0 ? (REACT ? pk(-ta, -tb) : pk(negzero, negzero)) : tr01;
             const f32x2 t23 = s == 0 ? (REACT ? pk(-tc, -td) : pk(negzero, negzero)) : tr23;
             const float4 r = row_update(c, xm, xp, ym, yp, zm, zp, a.cf.c[s], a.cf.dt, a.cf.decay[s], t01, t23, keep);
-            *reinterpret_cast<float4 *>(out[s] + (row - 64)) = r;
+            if (valid) *reinterpret_cast<float4 *>(out[s] + (row - 64)) = r;
         }
         cur = nxt;
     }

@@ -9,10 +9,12 @@ times (pipelined kernel with cp.async halos, block edge 4).
   of inlet and outlet flux, the next one does not; R < 1e-8 gives 1.1e-6)
   while the field error is ~3000 R (that mode's amplitude), so the solve runs
   to R < 1e-10.
-* 512^3 two-species reactive run: after n steps every voxel depends only on
-  voxels at most n steps away, so the oracle recomputes sampled voxels exactly
-  on a (2n+1)^3 crop around each; plus the exact per-step balance of the total
-  mass, sum(A+B)^{n+1} = sum(A+B)^n - dt * decay_B * sum B^n.
+* 512^3 two-species reactive run: the state after the stated 2000 steps
+  against the FP64 oracle's stored by tests/golden/make_golden_reactive512.py
+  (sampled voxels, x profiles, masses); after n steps every voxel depends only
+  on voxels at most n steps away, so the oracle also recomputes sampled voxels
+  exactly on a (2n+1)^3 crop around each; plus the exact per-step balance of
+  the total mass, sum(A+B)^{n+1} = sum(A+B)^n - dt * decay_B * sum B^n.
 * 512^3 inhomogeneous diffusion (Eq. 6 factor from phi, c = 1 held on x = 0):
   sampled voxels against the oracle on crops, as above, with the held face
   kept where a crop touches it.
@@ -99,6 +101,40 @@ def test_reactive512_sampled_voxels_match_the_oracle(reactive):
     for c in picks:
         ref = crop_reference(phi, u0, phys, c, n)
         assert abs(A[c] - ref[0]) <= 1e-5 and abs(B[c] - ref[1]) <= 1e-5, (c, A[c], B[c], ref)
+
+
+GOLDEN_R512 = os.path.join(os.path.dirname(__file__), "golden", "reactive512_2000.json")
+
+
+def test_reactive512_after_2000_steps_matches_the_oracle(reactive):
+    """The whole stated run (2000 steps) in the bench's launch configuration
+    (plane-ordered grid, the automatic kernel choice: the streaming kernel)
+    against the FP64 oracle's state after 2000 steps, stored by
+    tests/golden/make_golden_reactive512.py: 8192 sampled voxels (anywhere,
+    in the front region, on surface-band voxels) within 1e-5 of each
+    species' maximum, the x profiles (sums over every x plane) within 1e-5
+    of their maximum, and both masses within 1e-6 relative."""
+    gold = json.load(open(GOLDEN_R512))
+    phi, u0, phys = reactive
+    assert gold["steps"] == phys.steps == 2000
+    g = Grid(phi, block=4, order="planes")
+    st = State(g, 2, "f32").set_all(u0)
+    p = make_params(phys)
+    st.step(p, phys.steps)
+    red = st.reduce(p)
+    z, y, x = np.array(gold["samples_zyx"]).T
+    for s in range(2):
+        field = st.get(s)
+        ref = np.array(gold["samples_u"][s])
+        err = np.max(np.abs(field[z, y, x] - ref)) / gold["max"][s]
+        assert err <= 1e-5, (s, err)
+        prof = field.sum(axis=(0, 1))
+        gp = np.array(gold["x_profile"][s])
+        perr = np.max(np.abs(prof - gp)) / np.max(np.abs(gp))
+        assert perr <= 1e-5, (s, perr)
+        merr = abs(red[s]["mass"] - gold["mass"][s]) / abs(gold["mass"][s])
+        assert merr <= 1e-6, (s, merr)
+        assert abs(red[s]["max"] - gold["max"][s]) <= 1e-5 * gold["max"][s]
 
 
 def test_reactive512_total_mass_balance_per_step(reactive):
