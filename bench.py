@@ -857,7 +857,7 @@ def run_frap256(args):
     the steps included)."""
     import torch
     from paper_2304_11165_b300 import Grid, State, make_params
-    from paper_2304_11165_b300.api import frap_fit
+    from paper_2304_11165_b300.api import frap_effective_D
     from paper_2304_11165_b300.frap import recovery
     from workloads import frap256
     torch.cuda.set_device(0)
@@ -879,11 +879,11 @@ def run_frap256(args):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     t0 = time.perf_counter()
     ev[0].record(stream)
-    t, F = recovery(states[0], p, lo, hi, sps, ns, phys.dt, stream=stream)
+    t, F = recovery(states[0], p, lo, hi, sps, ns, stream=stream)
     ev[1].record(stream)
-    _, Fb = recovery(states[1], p, lo, hi, sps, ns, phys.dt, stream=stream)
+    _, Fb = recovery(states[1], p, lo, hi, sps, ns, stream=stream)
     ev[2].record(stream)
-    s, rss = frap_fit(t, F, t, Fb, 1e-3, 1.0)
+    d_eff, tau_frap, s, rss = frap_effective_D(t, F, t, Fb, float(phys.D[0]), 1e-3, 1.0)
     wall = time.perf_counter() - t0
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -913,7 +913,7 @@ def run_frap256(args):
                        "frac": achieved / peak, "traffic": None,
                        "algorithmic_bytes_per_launch": algo_bytes,
                        "avg_launch_us": [m * 1e3 / steps for m in ms]},
-          "result": {"D_eff": s * phys.D[0], "tau_frap": 1.0 / s, "rss": rss,
+          "result": {"D_eff": d_eff, "tau_frap": tau_frap, "scale": s, "rss": rss,
                      "F_end": [float(F[-1]), float(Fb[-1])], "curve_ms": ms},
           "clocks": clocks, "cpu_baseline": cpu})
     return 0

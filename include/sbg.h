@@ -47,7 +47,10 @@ typedef enum {
     SBG_ERR_UNSTABLE_DT = 4,   /* dt above sbg_stability_limit() and allow_unstable == 0       */
     SBG_ERR_NONFINITE = 5,     /* a NaN or Inf was found in the state by a reduction           */
     SBG_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                                 */
-    SBG_ERR_NOT_CONVERGED = 7  /* sbg_run_to_steady reached max_steps first                     */
+    SBG_ERR_NOT_CONVERGED = 7, /* sbg_run_to_steady reached max_steps first                     */
+    SBG_ERR_BOUNDS = 8         /* debug build only (libsbg_debug.so, SBG_DEBUG): a step kernel met a
+                                  block, neighbour or band-row index outside its table, skipped
+                                  the access and recorded this in the grid's error word         */
 } sbg_status;
 
 typedef enum {
@@ -354,8 +357,11 @@ sbg_status sbg_reduce_async(sbg_grid grid, sbg_state state, const sbg_params *pa
  *   limit    the reduced range (one geometry, or all with geom = -1) may hold
  *            at most 2^28 voxel slots (blocks x B^3); larger ranges return
  *            SBG_ERR_INVALID_ARG - use sbg_reduce for them.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call looks up the array's device address (cudaGetSymbolAddress, a
+ * host-side lookup that allocates nothing), so a device reset or a re-created
+ * context never leaves a stale address; the first call on a device loads the
+ * library's device code there, so make that first call before any stream
+ * capture.
  * All calls share the array: calls whose kernels may overlap on the GPU
  * (unordered streams) race and must be serialised by the caller.  Unlike
  * sbg_reduce it does not read the grid's device error word.  Results equal
@@ -400,6 +406,36 @@ sbg_status sbg_frap_curve(sbg_grid grid, sbg_state state, const sbg_params *para
  * sum of squares.  Pure host code; no device work. */
 sbg_status sbg_frap_fit(const double *t, const double *f, int64_t n, const double *t_ref, const double *f_ref,
                         int64_t m, double s_lo, double s_hi, double *scale, double *rss);
+
+/* The normalised recovery curve of a simulated FRAP run (Sec. 3.3): runs
+ * sbg_frap_curve (n_samples * steps_per_sample steps of `params`, the box sum
+ * of `species` over lo <= (x, y, z) < hi before the first step and after
+ * every steps_per_sample steps) and writes, for i = 0..n_samples (host
+ * arrays of n_samples + 1 doubles),
+ *   t[i] = i * steps_per_sample * dt,
+ *   F[i] = M_box(t_i) / (c n_box),
+ * c the mean of the species over every active voxel of the geometry before
+ * the first step (conserved in a closed box: the level the box recovers to)
+ * and n_box the active voxels in the box (*count, may be NULL).  Each curve
+ * is thus normalised by its own equilibrium, so that the pore curve and a
+ * bulk reference curve both tend to 1.  Synchronises `stream`.  Errors:
+ * those of sbg_frap_curve; SBG_ERR_INVALID_ARG when the box holds no active
+ * voxel or the field sums to zero. */
+sbg_status sbg_frap_recovery(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom,
+                             int32_t species, const int64_t lo[3], const int64_t hi[3], int64_t steps_per_sample,
+                             int32_t n_samples, double *t, double *F, int64_t *count, void *stream);
+
+/* The FRAP estimate of the pore-space effective diffusivity (Sec. 3.3 and
+ * Eq. 2): fits the reference curve (t_ref, F_ref), recorded in the bulk at
+ * diffusivity D_ref, to the measured curve (t, F) over a time scale s
+ * (sbg_frap_fit, same arguments and bounds) and returns
+ *   D_eff = s D_ref,  tau = D_ref / D_eff = 1 / s (inf when s <= 0),
+ * plus s (scale) and the residual sum of squares (rss); scale and rss may be
+ * NULL.  Host arrays and outputs; no device work.  Errors: those of
+ * sbg_frap_fit; SBG_ERR_INVALID_ARG for D_ref not finite and > 0. */
+sbg_status sbg_frap_effective_D(const double *t, const double *F, int64_t n, const double *t_ref, const double *F_ref,
+                                int64_t m, double D_ref, double s_lo, double s_hi, double *D_eff, double *tau,
+                                double *scale, double *rss);
 
 /* Effective diffusivity and diffusive tortuosity (Eq. 2: tau = D / D_eff with
  * the pore-space D_eff) from the x-face fluxes of species 0:
@@ -499,6 +535,42 @@ typedef struct {
 sbg_status sbg_redistance(const int64_t dims[3], const double dx[3], const void *phi_in, void *phi_out,
                           int32_t dtype, int32_t on_device, const sbg_redist_opts *opts, int64_t *iters_out,
                           double *residual_out, void *stream);
+
+/* ---- test hooks (no counterpart in the paper) ---------------------------------
+ * Failure detection is tested without a fault on the device: these hooks make
+ * a bounded wait run out or an allocation fail on purpose.
+ *
+ * sbg_debug_stall_stage: the ring-buffer step kernels (SBG_KERNEL_PIPELINED*,
+ * and the adjoint) launched on `grid` after this call never copy the group of
+ * blocks `group` (index of the kernel's work unit: 512 voxels for the one-row
+ * kernel, 1024 for the two-row kernel), so the wait of the CTA that owns it
+ * on that ring stage runs out after `wait_cycles` SM cycles (1 <= wait_cycles
+ * <= 2^31; every wait of those kernels uses that bound while the hook is
+ * set).  The CTA then records SBG_ERR_TIMEOUT in the grid's device error word,
+ * waits (bounded) for its copies in flight and exits; the next synchronising
+ * call on the grid (sbg_reduce, sbg_effective_D, ...) returns SBG_ERR_TIMEOUT
+ * and clears the word.  The device context stays usable.  group < 0 clears
+ * the hook.  Captured step graphs are re-captured after every change. */
+sbg_status sbg_debug_stall_stage(sbg_grid grid, int64_t group, int64_t wait_cycles);
+
+/* sbg_debug_fail_alloc: the n-th next device or page-locked host allocation
+ * of the library (any entry point, any thread) fails as if the memory were
+ * exhausted: the entry point returns SBG_ERR_OOM and must release what it had
+ * allocated.  n = 0 disarms.  sbg_debug_live_allocations: the number and
+ * total bytes of the library's live allocations (grids, states, tapes,
+ * temporaries not yet freed), for a test to check that a failed call leaves
+ * nothing behind.  Host-side bookkeeping; no device work. */
+sbg_status sbg_debug_fail_alloc(int64_t n);
+
+/* sbg_debug_set_face: overwrites the face-neighbour entry `face` (0..5: -x,
+ * +x, -y, +y, -z, +z) of block `block` with `id` and returns the previous
+ * entry in *old_id (may be NULL), so that a test can plant an index outside
+ * the block list and check that the debug build (libsbg_debug.so) reports
+ * SBG_ERR_BOUNDS instead of reading outside the state.  A release build does
+ * not check these ids: step a grid with a planted index only with the debug
+ * build, and restore the entry afterwards.  Synchronous. */
+sbg_status sbg_debug_set_face(sbg_grid grid, int64_t block, int32_t face, int32_t id, int32_t *old_id);
+sbg_status sbg_debug_live_allocations(int64_t *count, int64_t *bytes);
 
 /* ---- errors -------------------------------------------------------------------- */
 const char *sbg_last_error(void);            /* thread-local; "" when none                      */

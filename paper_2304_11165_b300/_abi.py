@@ -9,7 +9,10 @@ import ctypes
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libsbg.so")
+# SBG_LIB_VARIANT=debug selects the debug build (libsbg_debug.so, compiled with
+# SBG_DEBUG: index checks in the step kernels); the default is the release build
+LIB_NAME = "libsbg_debug.so" if os.environ.get("SBG_LIB_VARIANT") == "debug" else "libsbg.so"
+LIB_PATH = os.path.join(PKG, LIB_NAME)
 
 SBG_OK = 0
 SBG_ERR_INVALID_ARG = 1
@@ -19,6 +22,7 @@ SBG_ERR_UNSTABLE_DT = 4
 SBG_ERR_NONFINITE = 5
 SBG_ERR_TIMEOUT = 6
 SBG_ERR_NOT_CONVERGED = 7
+SBG_ERR_BOUNDS = 8
 
 SBG_F32, SBG_F64, SBG_F32X2, SBG_F32R = 0, 1, 2, 3
 SBG_FACE_NOFLUX, SBG_FACE_DIRICHLET = 0, 1
@@ -82,6 +86,10 @@ SIGNATURES = [
                                  c_int32, c_void_p, c_void_p, c_void_p]),
     ("sbg_frap_fit", c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int64, c_double, c_double,
                                c_void_p, c_void_p]),
+    ("sbg_frap_recovery", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_int64,
+                                    c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("sbg_frap_effective_D", c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int64, c_double, c_double,
+                                       c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("sbg_state_create", c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(c_void_p)]),
     ("sbg_state_set", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p]),
     ("sbg_state_get", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p]),
@@ -107,6 +115,10 @@ SIGNATURES = [
     ("sbg_last_error", ctypes.c_char_p, []),
     ("sbg_status_string", ctypes.c_char_p, [c_int32]),
     ("sbg_abi_version", c_int32, []),
+    ("sbg_debug_stall_stage", c_int32, [c_void_p, c_int64, c_int64]),
+    ("sbg_debug_fail_alloc", c_int32, [c_int64]),
+    ("sbg_debug_live_allocations", c_int32, [c_void_p, c_void_p]),
+    ("sbg_debug_set_face", c_int32, [c_void_p, c_int64, c_int32, c_int32, c_void_p]),
 ]
 
 _lib = None
@@ -119,10 +131,11 @@ def load(build_if_missing: bool = True):
         return _lib
     if build_if_missing:
         from . import build as _build
-        if _build.needs_build():
-            _build.build()
+        debug = LIB_NAME == "libsbg_debug.so"
+        if _build.needs_build(debug):
+            _build.build(debug=debug)
     if not os.path.exists(LIB_PATH):
-        raise RuntimeError("libsbg.so is missing: build it with `python -m paper_2304_11165_b300.build`")
+        raise RuntimeError("%s is missing: build it with `python -m paper_2304_11165_b300.build`" % LIB_NAME)
     lib = ctypes.CDLL(LIB_PATH)
     for name, res, args in SIGNATURES:
         fn = getattr(lib, name)
@@ -141,7 +154,7 @@ class SbgError(RuntimeError):
 def _status_name(s):
     names = {0: "SBG_OK", 1: "SBG_ERR_INVALID_ARG", 2: "SBG_ERR_OOM", 3: "SBG_ERR_CUDA",
              4: "SBG_ERR_UNSTABLE_DT", 5: "SBG_ERR_NONFINITE", 6: "SBG_ERR_TIMEOUT",
-             7: "SBG_ERR_NOT_CONVERGED"}
+             7: "SBG_ERR_NOT_CONVERGED", 8: "SBG_ERR_BOUNDS"}
     return names.get(s, "SBG_STATUS_%d" % s)
 
 

@@ -320,6 +320,22 @@ class State:
                                        ctypes.byref(count), _stream_handle(stream)))
         return sums, int(count.value)
 
+    def frap_recovery(self, params: Params, lo, hi, steps_per_sample: int, n_samples: int, species: int = 0,
+                      geom: int = 0, stream=None):
+        """(t, F, n_box): the recovery curve of the box normalised by its own
+        equilibrium (``sbg_frap_recovery``)."""
+        lo_a = np.asarray(lo, dtype=np.int64)
+        hi_a = np.asarray(hi, dtype=np.int64)
+        t = np.zeros(int(n_samples) + 1)
+        F = np.zeros(int(n_samples) + 1)
+        count = ctypes.c_int64(0)
+        v = ctypes.c_void_p
+        check(self._lib.sbg_frap_recovery(self.grid.handle, self.handle, ctypes.byref(params), geom, species,
+                                          lo_a.ctypes.data_as(v), hi_a.ctypes.data_as(v), int(steps_per_sample),
+                                          int(n_samples), t.ctypes.data_as(v), F.ctypes.data_as(v),
+                                          ctypes.byref(count), _stream_handle(stream)))
+        return t, F, int(count.value)
+
     def effective_D(self, params: Params, geom: int = 0, stream=None):
         d, t, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         check(self._lib.sbg_effective_D(self.grid.handle, self.handle, ctypes.byref(params), geom,
@@ -379,6 +395,20 @@ def frap_fit(t, f, t_ref, f_ref, s_lo: float = 1e-3, s_hi: float = 1.0):
                               f_ref.ctypes.data_as(v), t_ref.size, float(s_lo), float(s_hi), ctypes.byref(scale),
                               ctypes.byref(rss)))
     return scale.value, rss.value
+
+
+def frap_effective_D(t, F, t_ref, F_ref, D_ref: float, s_lo: float = 1e-3, s_hi: float = 1.0):
+    """(D_eff, tau, scale, rss) of the FRAP fit (``sbg_frap_effective_D``)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (t, F, t_ref, F_ref)]
+    if arrs[0].shape != arrs[1].shape or arrs[2].shape != arrs[3].shape:
+        raise ValueError("frap_effective_D: times and values differ in length")
+    d, tau, sc, rss = (ctypes.c_double(0.0) for _ in range(4))
+    v = ctypes.c_void_p
+    check(load().sbg_frap_effective_D(arrs[0].ctypes.data_as(v), arrs[1].ctypes.data_as(v), arrs[0].size,
+                                      arrs[2].ctypes.data_as(v), arrs[3].ctypes.data_as(v), arrs[2].size,
+                                      float(D_ref), float(s_lo), float(s_hi), ctypes.byref(d), ctypes.byref(tau),
+                                      ctypes.byref(sc), ctypes.byref(rss)))
+    return d.value, tau.value, sc.value, rss.value
 
 
 def redistance(phi0, dx=(1.0, 1.0, 1.0), cfl: float = 0.3, max_iter: int = 200, tol: float = 0.0,

@@ -1,8 +1,12 @@
 """Builds ``libsbg.so`` in-tree from ``csrc/*.cu`` with nvcc for sm_103a.
 
-Usage: ``python -m paper_2304_11165_b300.build [--verbose-ptxas]``.
+Usage: ``python -m paper_2304_11165_b300.build [--verbose-ptxas] [--debug]``.
 Objects go to ``_build/`` at the repository root (git-ignored); the shared
 library is written next to this file so that it ships with the source tree.
+``--debug`` builds ``libsbg_debug.so`` instead: the same sources compiled
+with SBG_DEBUG, which adds index checks to the step kernels (an index outside
+its table is skipped and reported as SBG_ERR_BOUNDS); the binding loads it
+when SBG_LIB_VARIANT=debug is set.
 """
 from __future__ import annotations
 
@@ -19,6 +23,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsbg.so")
+LIB_DEBUG = os.path.join(PKG, "libsbg_debug.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I" + INCLUDE,
@@ -33,21 +38,26 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(debug: bool = False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, ptxas_verbose: bool = False) -> str:
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, ptxas_verbose: bool = False, debug: bool = False) -> str:
+    lib = LIB_DEBUG if debug else LIB
+    if not force and not needs_build(debug):
+        return lib
+    objdir = os.path.join(OBJ, "debug") if debug else OBJ
+    os.makedirs(objdir, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
+    if debug:
+        extra = extra + ["-DSBG_DEBUG=1"]
 
     def compile_one(src):
-        obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -60,18 +70,19 @@ def build(force: bool = False, ptxas_verbose: bool = False) -> str:
         for _, err in results:
             sys.stderr.write(err)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--verbose-ptxas", action="store_true")
+    ap.add_argument("--debug", action="store_true")
     a = ap.parse_args()
-    print(build(force=a.force or a.verbose_ptxas, ptxas_verbose=a.verbose_ptxas))
+    print(build(force=a.force or a.verbose_ptxas, ptxas_verbose=a.verbose_ptxas, debug=a.debug))

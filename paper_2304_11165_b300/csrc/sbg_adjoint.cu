@@ -330,10 +330,10 @@ static sbg_status step_packed(sbg_tape tp, const void *src, void *dst, cudaStrea
 
 static void tape_free(sbg_tape tp) {
     if (!tp) return;
-    for (void *p : tp->ckpt) cudaFree(p);
-    for (void *p : tp->seg) cudaFree(p);
-    cudaFree(tp->partials);
-    cudaFree(tp->acc);
+    for (void *p : tp->ckpt) dfree(p);
+    for (void *p : tp->seg) dfree(p);
+    dfree(tp->partials);
+    dfree(tp->acc);
     delete tp;
 }
 
@@ -362,7 +362,7 @@ extern "C" sbg_status sbg_forward_record(sbg_grid g, sbg_state st, const sbg_par
     tp->state_bytes = (size_t)st->nslots * st->elem() * st->ns;
     const int64_t nck = nsteps == 0 ? 1 : (nsteps + checkpoint_every - 1) / checkpoint_every;
     auto alloc = [&](void **pp, size_t bytes) -> sbg_status {
-        cudaError_t e = cudaMalloc(pp, bytes > 0 ? bytes : 16);
+        cudaError_t e = dmalloc((void **)pp, bytes > 0 ? bytes : 16);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (tape)");
         tp->bytes += (int64_t)bytes;
         return SBG_OK;
@@ -405,7 +405,7 @@ extern "C" sbg_status sbg_adjoint(sbg_grid g, sbg_tape tp, sbg_state lam, double
     // recompute buffers for u^{n0+1} .. u^{n0+K-1} (u^{n0} is the checkpoint itself)
     while ((int64_t)tp->seg.size() < std::min<int64_t>(K, std::max<int64_t>(tp->nsteps, 1)) - 1) {
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, tp->state_bytes);
+        cudaError_t e = dmalloc((void **)&q, tp->state_bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (tape recompute buffer)");
         tp->bytes += (int64_t)tp->state_bytes;
         tp->seg.push_back(q);

@@ -62,14 +62,14 @@ extern "C" sbg_status sbg_batch_run_to_steady(sbg_grid g, sbg_state st, const sb
     int64_t max_items = 0;
     for (int i = 0; i < n; ++i) max_items += (g->geom_count[i] + G - 1) / G;
     int64_t *items = nullptr;
-    SBG_CUDA(cudaMalloc(&items, sizeof(int64_t) * 2 * std::max<int64_t>(max_items, 1)));
+    SBG_CUDA(dmalloc((void **)&items, sizeof(int64_t) * 2 * std::max<int64_t>(max_items, 1)));
     std::vector<int64_t> h;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cs = nullptr;
     auto cleanup = [&]() {
         if (exec) cudaGraphExecDestroy(exec);
         if (cs) cudaStreamDestroy(cs);
-        cudaFree(items);
+        dfree(items);
     };
     auto rebuild = [&]() -> sbg_status {
         h.clear();

@@ -121,13 +121,13 @@ static sbg_status exclusive_scan(const int32_t *in, int64_t n, bool as_flags, in
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     if (ntiles < 1) ntiles = 1;
     int32_t *tmp = nullptr;
-    SBG_CUDA(cudaMallocAsync(&tmp, sizeof(int32_t) * (ntiles + 1), st));
+    SBG_CUDA(dmalloc_async((void **)&tmp, sizeof(int32_t) * (ntiles + 1), st));
     k_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, n, as_flags, out, tmp);
     k_scan_sums<<<1, kScanThreads, 0, st>>>(tmp, ntiles, tmp + ntiles);
     k_scan_add<<<(unsigned)ntiles, 256, 0, st>>>(out, n, tmp);
     int32_t h = 0;
     SBG_CUDA(cudaMemcpyAsync(&h, tmp + ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    SBG_CUDA(cudaFreeAsync(tmp, st));
+    SBG_CUDA(dfree_async(tmp, st));
     SBG_CUDA(cudaStreamSynchronize(st));
     *total = h;
     return SBG_OK;
@@ -405,7 +405,7 @@ static inline sbg_status cuda_ok(cudaError_t e, const char *what) {
 template <typename T>
 static sbg_status dalloc(sbg_grid g, T **p, size_t count) {
     size_t bytes = sizeof(T) * (count > 0 ? count : 1);
-    cudaError_t e = cudaMalloc((void **)p, bytes);
+    cudaError_t e = dmalloc((void **)(void **)p, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (grid)");
     g->bytes += (int64_t)bytes;
     return SBG_OK;
@@ -413,27 +413,27 @@ static sbg_status dalloc(sbg_grid g, T **p, size_t count) {
 
 static void grid_free(sbg_grid g) {
     if (!g) return;
-    cudaFree(g->blocks);
-    cudaFree(g->nbr);
-    cudaFree(g->face_nbr);
-    cudaFree(g->hkeys);
-    cudaFree(g->hvals);
-    cudaFree(g->bitmap);
-    cudaFree(g->wslab);
-    cudaFree(g->w);
-    cudaFree(g->w64);
-    cudaFree(g->gdims);
-    cudaFree(g->partials);
-    cudaFree(g->red_dev);
-    cudaFreeHost(g->red_host);
-    cudaFree(g->err);
-    cudaFree(g->pad);
-    cudaFree(g->heldbits);
-    cudaFree(g->eps);
-    cudaFree(g->eps64);
-    cudaFree(g->wmeta);
-    cudaFree(g->wrow);
-    cudaFreeHost(g->err_host);
+    dfree(g->blocks);
+    dfree(g->nbr);
+    dfree(g->face_nbr);
+    dfree(g->hkeys);
+    dfree(g->hvals);
+    dfree(g->bitmap);
+    dfree(g->wslab);
+    dfree(g->w);
+    dfree(g->w64);
+    dfree(g->gdims);
+    dfree(g->partials);
+    dfree(g->red_dev);
+    hfree(g->red_host);
+    dfree(g->err);
+    dfree(g->pad);
+    dfree(g->heldbits);
+    dfree(g->eps);
+    dfree(g->eps64);
+    dfree(g->wmeta);
+    dfree(g->wrow);
+    hfree(g->err_host);
     delete g;
 }
 
@@ -458,13 +458,13 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
     sbg_status rc = SBG_OK;
     auto cleanup = [&]() {
         for (int i = 0; i < n; ++i) {
-            if (!opts->phi_on_device) cudaFree(dphi[i]);
-            cudaFree(dcount[i]);
-            cudaFree(dpos[i]);
+            if (!opts->phi_on_device) dfree(dphi[i]);
+            dfree(dcount[i]);
+            dfree(dpos[i]);
         }
-        cudaFree(band);
-        cudaFree(nact);
-        cudaFree(wpos);
+        dfree(band);
+        dfree(nact);
+        dfree(wpos);
     };
 #define TRY(x)                 \
     do {                       \
@@ -485,13 +485,13 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
         if (opts->phi_on_device) {
             dphi[i] = const_cast<float *>(phis[i]);
         } else {
-            TRYC(cudaMalloc(&dphi[i], sizeof(float) * nvox));
+            TRYC(dmalloc((void **)&dphi[i], sizeof(float) * nvox));
             TRYC(cudaMemcpyAsync(dphi[i], phis[i], sizeof(float) * nvox, cudaMemcpyHostToDevice, st));
         }
         const BlockEnum en = make_enum(nx, ny, nz, B, opts->order);
         const int64_t nbox = en.count();
-        TRYC(cudaMalloc(&dcount[i], sizeof(int32_t) * nbox));
-        TRYC(cudaMalloc(&dpos[i], sizeof(int32_t) * nbox));
+        TRYC(dmalloc((void **)&dcount[i], sizeof(int32_t) * nbox));
+        TRYC(dmalloc((void **)&dpos[i], sizeof(int32_t) * nbox));
         k_block_count<B><<<(unsigned)((nbox * 32 + 255) / 256), 256, 0, st>>>(
             dphi[i], (int)nx, (int)ny, (int)nz, en, nbox, g->eps_mask, dcount[i]);
         TRY(cuda_ok(cudaGetLastError(), "k_block_count"));
@@ -514,7 +514,7 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
     TRY(dalloc(g, &g->gdims, 4 * (size_t)n));
     TRY(dalloc(g, &g->partials, (size_t)kRedMaxCtas * kNumRed));
     TRY(dalloc(g, &g->red_dev, (size_t)kNumRed));
-    TRYC(cudaMallocHost(&g->red_host, sizeof(double) * kNumRed));
+    TRYC(hmalloc((void **)&g->red_host, sizeof(double) * kNumRed));
     TRY(dalloc(g, &g->err, 1));
     TRY(dalloc(g, &g->pad, 8));
     {
@@ -522,10 +522,10 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
         TRYC(cudaMemcpy(g->pad, hp, sizeof(hp), cudaMemcpyHostToDevice));
     }
     TRYC(cudaMemsetAsync(g->err, 0, sizeof(int), st));
-    TRYC(cudaMallocHost(&g->err_host, sizeof(int)));
-    TRYC(cudaMalloc(&band, sizeof(int32_t) * std::max<int64_t>(total, 1)));
-    TRYC(cudaMalloc(&nact, sizeof(int32_t) * std::max<int64_t>(total, 1)));
-    TRYC(cudaMalloc(&wpos, sizeof(int32_t) * std::max<int64_t>(total, 1)));
+    TRYC(hmalloc((void **)&g->err_host, sizeof(int)));
+    TRYC(dmalloc((void **)&band, sizeof(int32_t) * std::max<int64_t>(total, 1)));
+    TRYC(dmalloc((void **)&nact, sizeof(int32_t) * std::max<int64_t>(total, 1)));
+    TRYC(dmalloc((void **)&wpos, sizeof(int32_t) * std::max<int64_t>(total, 1)));
     {
         std::vector<int32_t> hd(4 * (size_t)n, 0);
         for (int i = 0; i < n; ++i)
@@ -586,8 +586,8 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
         TRYC(cudaMemsetAsync(g->wmeta, 0, sizeof(int2) * (total + 1), st));
         if (total > 0 && nband > 0) {
             int32_t *rcount = nullptr, *roff = nullptr;
-            cudaError_t e1 = cudaMallocAsync(&rcount, sizeof(int32_t) * total, st);
-            cudaError_t e2 = cudaMallocAsync(&roff, sizeof(int32_t) * total, st);
+            cudaError_t e1 = dmalloc_async((void **)&rcount, sizeof(int32_t) * total, st);
+            cudaError_t e2 = dmalloc_async((void **)&roff, sizeof(int32_t) * total, st);
             int64_t nrows = 0;
             sbg_status r2 = (e1 == cudaSuccess && e2 == cudaSuccess) ? SBG_OK : cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaMallocAsync (band rows)");
             if (r2 == SBG_OK) {
@@ -603,8 +603,8 @@ static sbg_status build_impl(int32_t n, const float *const *phis, const int64_t 
                                                                                        g->wmeta, g->wrow);
                 r2 = cuda_ok(cudaGetLastError(), "k_band_rows_fill");
             }
-            cudaFreeAsync(rcount, st);
-            cudaFreeAsync(roff, st);
+            dfree_async(rcount, st);
+            dfree_async(roff, st);
             TRY(r2);
         }
     }
@@ -722,6 +722,7 @@ extern "C" const char *sbg_status_string(sbg_status s) {
         case SBG_ERR_NONFINITE: return "non-finite value in the state";
         case SBG_ERR_TIMEOUT: return "bounded device wait timed out";
         case SBG_ERR_NOT_CONVERGED: return "not converged";
+        case SBG_ERR_BOUNDS: return "index outside its table (debug build)";
     }
     return "unknown status";
 }

@@ -60,8 +60,8 @@ static sbg_status set_eps(sbg_grid g, int geom, const void *dense, int dense_dty
         return fail(SBG_ERR_INVALID_ARG, "diffusivity factor: dense dtype must be SBG_F32 or SBG_F64");
     const int64_t slots = g->nb * g->b3();
     if (!g->eps) {
-        cudaError_t e = cudaMalloc(&g->eps, sizeof(float) * (slots > 0 ? slots : 1));
-        if (e == cudaSuccess) e = cudaMalloc(&g->eps64, sizeof(double) * (slots > 0 ? slots : 1));
+        cudaError_t e = dmalloc((void **)&g->eps, sizeof(float) * (slots > 0 ? slots : 1));
+        if (e == cudaSuccess) e = dmalloc((void **)&g->eps64, sizeof(double) * (slots > 0 ? slots : 1));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (diffusivity factor)");
         g->bytes += (int64_t)(12 * slots);
         SBG_CUDA(cudaMemsetAsync(g->eps, 0, sizeof(float) * (slots > 0 ? slots : 1), s));
@@ -77,15 +77,15 @@ static sbg_status set_eps(sbg_grid g, int geom, const void *dense, int dense_dty
         // on failure, free what this call allocated before returning
         cudaError_t e = cudaSuccess;
         if (!on_device) {
-            e = cudaMallocAsync(&d, bytes, s);
+            e = dmalloc_async((void **)&d, bytes, s);
             if (e != cudaSuccess) d = nullptr;
             if (e == cudaSuccess) e = cudaMemcpyAsync(d, dense, bytes, cudaMemcpyHostToDevice, s);
         }
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&stat, 2 * sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = dmalloc_async((void **)(void **)&stat, 2 * sizeof(unsigned int), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(stat, 0, 2 * sizeof(unsigned int), s);
         if (e != cudaSuccess) {
-            if (!on_device && d) cudaFreeAsync(d, s);
-            if (stat) cudaFreeAsync(stat, s);
+            if (!on_device && d) dfree_async(d, s);
+            if (stat) dfree_async(stat, s);
             cudaStreamSynchronize(s);
             return cuda_fail(e, "staging buffers");
         }
@@ -109,8 +109,8 @@ static sbg_status set_eps(sbg_grid g, int geom, const void *dense, int dense_dty
     cudaError_t le = cudaGetLastError();
     unsigned int host[2] = {0u, 0u};
     cudaError_t ce = cudaMemcpyAsync(host, stat, sizeof(host), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(stat, s);
-    if (!on_device) cudaFreeAsync(d, s);
+    dfree_async(stat, s);
+    if (!on_device) dfree_async(d, s);
     cudaError_t se = cudaStreamSynchronize(s);
     if (le != cudaSuccess) return cuda_fail(le, "diffusivity factor kernel launch");
     if (ce != cudaSuccess) return cuda_fail(ce, "diffusivity factor statistics copy");

@@ -54,7 +54,7 @@ extern "C" sbg_status sbg_frap_curve(sbg_grid g, sbg_state st, const sbg_params 
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nrec = (size_t)n_samples + 1;
     double *rec = nullptr;
-    SBG_CUDA(cudaMallocAsync((void **)&rec, 2 * sizeof(double) * nrec, s));
+    SBG_CUDA(dmalloc_async((void **)(void **)&rec, 2 * sizeof(double) * nrec, s));
     for (size_t i = 0; i < nrec && rc == SBG_OK; ++i) {
         if (i > 0) rc = step_n(g, st, p, steps_per_sample, s);
         if (rc == SBG_OK) rc = launch_box_sum(g, st, geom, species, lo, hi, rec + 2 * i, s);
@@ -62,7 +62,7 @@ extern "C" sbg_status sbg_frap_curve(sbg_grid g, sbg_state st, const sbg_params 
     std::vector<double> host(2 * nrec);
     cudaError_t ce = cudaSuccess;
     if (rc == SBG_OK) ce = cudaMemcpyAsync(host.data(), rec, 2 * sizeof(double) * nrec, cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(rec, s);
+    dfree_async(rec, s);
     cudaError_t se = cudaStreamSynchronize(s);
     if (rc != SBG_OK) return rc;
     if (ce != cudaSuccess) return cuda_fail(ce, "sbg_frap_curve: copy of the curve");
@@ -137,5 +137,50 @@ extern "C" sbg_status sbg_frap_fit(const double *t, const double *f, int64_t n, 
     }
     *scale = sbest;
     if (rss) *rss = rbest;
+    return SBG_OK;
+}
+
+extern "C" sbg_status sbg_frap_recovery(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom,
+                                        int32_t species, const int64_t lo[3], const int64_t hi[3],
+                                        int64_t steps_per_sample, int32_t n_samples, double *t, double *F,
+                                        int64_t *count, void *stream) {
+    TraceRange trace_range("sbg_frap_recovery");
+    if (!t || !F) return fail(SBG_ERR_INVALID_ARG, "sbg_frap_recovery: null output");
+    sbg_status rc = check_box_args(g, st, geom, species, "sbg_frap_recovery");
+    if (rc != SBG_OK) return rc;
+    if (!p) return fail(SBG_ERR_INVALID_ARG, "sbg_frap_recovery: null params");
+    // the equilibrium level: the mean of the species over every active voxel of the
+    // geometry (conserved in a closed box), from the state before the first step
+    const int64_t all_lo[3] = {0, 0, 0};
+    const int64_t all_hi[3] = {g->dims[3 * geom], g->dims[3 * geom + 1], g->dims[3 * geom + 2]};
+    double tot[2] = {0.0, 0.0};
+    rc = sbg_reduce_box(g, st, geom, species, all_lo, all_hi, tot, stream);
+    if (rc != SBG_OK) return rc;
+    int64_t n_box = 0;
+    rc = sbg_frap_curve(g, st, p, geom, species, lo, hi, steps_per_sample, n_samples, F, &n_box, stream);
+    if (rc != SBG_OK) return rc;
+    if (count) *count = n_box;
+    if (n_box == 0 || tot[1] == 0.0 || tot[0] == 0.0)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_frap_recovery: the box holds no active voxel or the field is zero");
+    const double level = tot[0] / tot[1] * (double)n_box;  // mean u x active voxels in the box
+    for (int32_t i = 0; i <= n_samples; ++i) {
+        t[i] = p->dt * (double)steps_per_sample * (double)i;
+        F[i] = F[i] / level;
+    }
+    return SBG_OK;
+}
+
+extern "C" sbg_status sbg_frap_effective_D(const double *t, const double *F, int64_t n, const double *t_ref,
+                                           const double *F_ref, int64_t m, double D_ref, double s_lo, double s_hi,
+                                           double *D_eff, double *tau, double *scale, double *rss) {
+    if (!D_eff || !tau) return fail(SBG_ERR_INVALID_ARG, "sbg_frap_effective_D: null output");
+    if (!(D_ref > 0.0) || !isfinite(D_ref)) return fail(SBG_ERR_INVALID_ARG, "sbg_frap_effective_D: D_ref > 0");
+    double s = 0.0, r = 0.0;
+    sbg_status rc = sbg_frap_fit(t, F, n, t_ref, F_ref, m, s_lo, s_hi, &s, &r);
+    if (rc != SBG_OK) return rc;
+    *D_eff = s * D_ref;                        // the reference curve at s D_ref matches the measured one
+    *tau = s > 0.0 ? 1.0 / s : INFINITY;        // tau = D / D_eff (Eq. 2)
+    if (scale) *scale = s;
+    if (rss) *rss = r;
     return SBG_OK;
 }

@@ -29,6 +29,16 @@ sbg_status cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return sbg::cuda_fail(e_, what); \
     } while (0)
 
+// Every allocation of the library (sbg_alloc.cu): the CUDA call behind a test
+// hook that can make the n-th next allocation fail (sbg_debug_fail_alloc) and
+// a table of the live allocations (sbg_debug_live_allocations).
+cudaError_t dmalloc(void **p, size_t bytes);
+cudaError_t dmalloc_async(void **p, size_t bytes, cudaStream_t s);
+cudaError_t hmalloc(void **p, size_t bytes);
+cudaError_t dfree(void *p);
+cudaError_t dfree_async(void *p, cudaStream_t s);
+cudaError_t hfree(void *p);
+
 // ---------------------------------------------------------------------------
 // inactive-voxel sentinel: a quiet NaN with a payload that arithmetic never
 // produces (NVIDIA GPUs return the canonical 0x7fffffff for invalid ops), so a
@@ -114,6 +124,11 @@ struct sbg_grid_s {
     int64_t n_wrows = 0;
     int order = SBG_ORDER_TILED;   // block order of the list (sbg_build_opts.order)
     int *err = nullptr;            // device error word written by bounded waits (0 = none)
+    // test hook (sbg_debug_stall_stage): the ring kernels skip the bulk copy of this group
+    // (-1: none) and give up waiting after inject_wait_cycles
+    int inject_stall_group = -1;
+    long long inject_wait_cycles = 0;
+    int inject_version = 0;        // bumped when the hook changes (captured graphs are redone)
     int *err_host = nullptr;       // pinned copy
     int64_t bytes = 0;
     int words() const { return (B * B * B + 63) / 64; }
@@ -138,6 +153,7 @@ struct sbg_state_s {
     int graph_variant = -1;
     int graph_ctas = -1;
     int graph_eps_version = -1;
+    int graph_inject_version = -1;
     int variant = SBG_KERNEL_AUTO;  // step kernel choice (sbg_state_set_kernel)
     bool has_ghost = false;         // every val array is preceded by a ghost block of sentinels
                                     // (states made by sbg_state_create; not the adjoint's views)

@@ -115,10 +115,10 @@ static sbg_status redistance_t(const int64_t dims[3], const double dx[3], const 
     sbg_status rc = SBG_OK;
     auto done = [&](sbg_status r) {
         cudaStreamSynchronize(s);
-        if (!on_device || buf[0] != out) cudaFree(buf[0]);
-        cudaFree(buf[1]);
-        cudaFree(res);
-        cudaFreeHost(res_host);
+        if (!on_device || buf[0] != out) dfree(buf[0]);
+        dfree(buf[1]);
+        dfree(res);
+        hfree(res_host);
         return r;
     };
     cudaError_t e = cudaSuccess;
@@ -126,12 +126,12 @@ static sbg_status redistance_t(const int64_t dims[3], const double dx[3], const 
         buf[0] = (T *)out;
         if (out != in) e = cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s);
     } else {
-        e = cudaMalloc(&buf[0], bytes);
+        e = dmalloc((void **)&buf[0], bytes);
         if (e == cudaSuccess) e = cudaMemcpyAsync(buf[0], in, bytes, cudaMemcpyHostToDevice, s);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&buf[1], bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&res, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMallocHost(&res_host, sizeof(unsigned int));
+    if (e == cudaSuccess) e = dmalloc((void **)&buf[1], bytes);
+    if (e == cudaSuccess) e = dmalloc((void **)&res, sizeof(unsigned int));
+    if (e == cudaSuccess) e = hmalloc((void **)&res_host, sizeof(unsigned int));
     if (e != cudaSuccess) return done(cuda_fail(e, "sbg_redistance: allocation or upload"));
     RedistArgs<T> a;
     a.nx = nx;

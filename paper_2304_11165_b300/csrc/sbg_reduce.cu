@@ -1082,26 +1082,21 @@ namespace sbg {
 
 constexpr int kNoAllocRecords = 4096;
 constexpr int64_t kNoAllocSlotsPerCta = 65536;
-constexpr int kNoAllocMaxDevices = 64;
-
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocRecords * kNumRed];
 
 // Device address of g_noalloc_partials on the current device.  In host code
 // the symbol is only a host-side stand-in; the kernels need the address that
-// cudaGetSymbolAddress returns.  Looked up on the first call per device.
+// cudaGetSymbolAddress returns.  It is looked up on every call (a host-side
+// lookup, no allocation) rather than cached, so that a device reset or a
+// re-created context, which reloads the module at another address, never
+// leaves a stale pointer behind, and concurrent first calls from several host
+// threads share no mutable table.  The first lookup on a device loads the
+// library's device code there.
 static sbg_status noalloc_scratch(double **out) {
-    static double *ptrs[kNoAllocMaxDevices] = {};
-    int dev = 0;
-    SBG_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoAllocMaxDevices)
-        return fail(SBG_ERR_INVALID_ARG, "sbg_reduce_noalloc: device index out of range");
-    if (!ptrs[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (no-allocation reduction scratch)");
-        ptrs[dev] = (double *)p;
-    }
-    *out = ptrs[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (no-allocation reduction scratch)");
+    *out = (double *)p;
     return SBG_OK;
 }
 

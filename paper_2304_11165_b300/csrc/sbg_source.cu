@@ -59,7 +59,7 @@ extern "C" sbg_status sbg_state_set_source(sbg_grid g, sbg_state st, int32_t geo
     const size_t elem = st->elem();
     const int64_t slots = st->nslots > 0 ? st->nslots : 1;
     if (!st->ext[species]) {
-        cudaError_t e = cudaMalloc(&st->ext[species], elem * (size_t)slots);
+        cudaError_t e = dmalloc((void **)&st->ext[species], elem * (size_t)slots);
         if (e != cudaSuccess) {
             st->ext[species] = nullptr;
             return cuda_fail(e, "cudaMalloc (external source)");
@@ -76,15 +76,15 @@ extern "C" sbg_status sbg_state_set_source(sbg_grid g, sbg_state st, int32_t geo
         // on failure, free what this call allocated before returning
         cudaError_t e = cudaSuccess;
         if (!on_device) {
-            e = cudaMallocAsync(&d, bytes, s);
+            e = dmalloc_async((void **)&d, bytes, s);
             if (e != cudaSuccess) d = nullptr;
             if (e == cudaSuccess) e = cudaMemcpyAsync(d, dense, bytes, cudaMemcpyHostToDevice, s);
         }
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&bad, sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = dmalloc_async((void **)(void **)&bad, sizeof(unsigned int), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), s);
         if (e != cudaSuccess) {
-            if (!on_device && d) cudaFreeAsync(d, s);
-            if (bad) cudaFreeAsync(bad, s);
+            if (!on_device && d) dfree_async(d, s);
+            if (bad) dfree_async(bad, s);
             cudaStreamSynchronize(s);
             return cuda_fail(e, "staging buffers");
         }
@@ -115,8 +115,8 @@ extern "C" sbg_status sbg_state_set_source(sbg_grid g, sbg_state st, int32_t geo
     cudaError_t le = cudaGetLastError();
     unsigned int host_bad = 0;
     cudaError_t ce = cudaMemcpyAsync(&host_bad, bad, sizeof(host_bad), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(bad, s);
-    if (!on_device) cudaFreeAsync(d, s);
+    dfree_async(bad, s);
+    if (!on_device) dfree_async(d, s);
     cudaError_t se = cudaStreamSynchronize(s);
     if (le != cudaSuccess) return cuda_fail(le, "external source kernel launch");
     if (ce != cudaSuccess) return cuda_fail(ce, "external source flag copy");
@@ -129,7 +129,7 @@ extern "C" sbg_status sbg_state_clear_source(sbg_state st) {
     if (!st) return fail(SBG_ERR_INVALID_ARG, "sbg_state_clear_source: null state");
     for (int s = 0; s < 2; ++s) {
         if (st->ext[s]) {
-            cudaFree(st->ext[s]);
+            dfree(st->ext[s]);
             st->bytes -= (int64_t)(st->elem() * (size_t)(st->nslots > 0 ? st->nslots : 1));
             st->ext[s] = nullptr;
         }

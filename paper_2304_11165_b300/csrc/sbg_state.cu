@@ -192,7 +192,7 @@ static sbg_status dense_io(sbg_grid g, sbg_state st, int32_t geom, int32_t speci
     const size_t bytes = (size_t)nvox * (dense_dtype == SBG_F64 ? 8 : 4);
     void *ddense = dense;
     if (!on_device) {
-        SBG_CUDA(cudaMallocAsync(&ddense, bytes, s));
+        SBG_CUDA(dmalloc_async((void **)&ddense, bytes, s));
         if (to_state) SBG_CUDA(cudaMemcpyAsync(ddense, dense, bytes, cudaMemcpyHostToDevice, s));
     }
     if (!to_state) SBG_CUDA(cudaMemsetAsync(ddense, 0, bytes, s));
@@ -201,7 +201,7 @@ static sbg_status dense_io(sbg_grid g, sbg_state st, int32_t geom, int32_t speci
     if (!on_device) {
         if (rc == SBG_OK && !to_state)
             SBG_CUDA(cudaMemcpyAsync(dense, ddense, bytes, cudaMemcpyDeviceToHost, s));
-        SBG_CUDA(cudaFreeAsync(ddense, s));
+        SBG_CUDA(dfree_async(ddense, s));
         SBG_CUDA(cudaStreamSynchronize(s));
     }
     return rc;
@@ -232,7 +232,7 @@ extern "C" sbg_status sbg_state_create(sbg_grid g, int32_t nspecies, sbg_dtype d
     const size_t perlo = dtype == SBG_F32X2 ? (size_t)st->nslots * 4 : 0;
     const size_t extra = dtype == SBG_F32R ? 3 * (size_t)st->nslots * 4 : 0;  // base hi, lo and source
     const size_t total = 2 * (size_t)nspecies * (per + ghost + perlo) + extra;
-    cudaError_t e = cudaMalloc(&st->base, total > 0 ? total : 16);
+    cudaError_t e = dmalloc((void **)&st->base, total > 0 ? total : 16);
     if (e != cudaSuccess) {
         delete st;
         return cuda_fail(e, "cudaMalloc (state)");
@@ -273,7 +273,7 @@ extern "C" sbg_status sbg_state_create(sbg_grid g, int32_t nspecies, sbg_dtype d
                 e = cudaMemcpy((char *)st->val[b][s] - ghost, gh.data(), ghost, cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
-        cudaFree(st->base);
+        dfree(st->base);
         delete st;
         return cuda_fail(e, "cudaMemset (state)");
     }
@@ -319,8 +319,8 @@ extern "C" sbg_status sbg_state_copy(sbg_state dst, sbg_state src, void *stream)
 extern "C" void sbg_state_destroy(sbg_state st) {
     if (!st) return;
     if (st->graph) cudaGraphExecDestroy(st->graph);
-    cudaFree(st->ext[0]);
-    cudaFree(st->ext[1]);
-    cudaFree(st->base);
+    dfree(st->ext[0]);
+    dfree(st->ext[1]);
+    dfree(st->base);
     delete st;
 }

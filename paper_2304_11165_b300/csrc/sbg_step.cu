@@ -21,6 +21,10 @@
 #include "sbg_step.cuh"
 #include "sbg_trace.cuh"
 
+#ifndef SBG_DEBUG
+#define SBG_DEBUG 0
+#endif
+
 namespace sbg {
 
 // Plain FP32 / FP64 state, NS species, optional reaction (REACT: k_surf != 0).
@@ -46,9 +50,19 @@ k_step(const StepArgs a) {
     if (valid) {
         bc = a.blocks[b];
         const int32_t *fn = a.face + b * 6;
-        const int nxm = (x == 0) ? fn[0] : -1, nxp = (x == B - 1) ? fn[1] : -1;
-        const int nym = (y == 0) ? fn[2] : -1, nyp = (y == B - 1) ? fn[3] : -1;
-        const int nzm = (z == 0) ? fn[4] : -1, nzp = (z == B - 1) ? fn[5] : -1;
+        int nxm = (x == 0) ? fn[0] : -1, nxp = (x == B - 1) ? fn[1] : -1;
+        int nym = (y == 0) ? fn[2] : -1, nyp = (y == B - 1) ? fn[3] : -1;
+        int nzm = (z == 0) ? fn[4] : -1, nzp = (z == B - 1) ? fn[5] : -1;
+#if SBG_DEBUG
+        // the debug build checks every face id against the block list before using it
+        int *ids[6] = {&nxm, &nxp, &nym, &nyp, &nzm, &nzp};
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+            if (*ids[f] < -1 || *ids[f] >= a.nb) {
+                atomicExch(a.err, (int)SBG_ERR_BOUNDS);
+                *ids[f] = -1;
+            }
+#endif
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const T *in = (const T *)a.in[s];
@@ -217,7 +231,7 @@ sbg_status prepare_held_bits(sbg_grid g, const sbg_params *p, cudaStream_t s) {
     if (mask == 0 || g->nb == 0 || g->heldbits_mask == mask) return SBG_OK;
     const int64_t n = g->nb * g->words();
     if (!g->heldbits) {
-        cudaError_t e = cudaMalloc(&g->heldbits, sizeof(uint64_t) * n);
+        cudaError_t e = dmalloc((void **)&g->heldbits, sizeof(uint64_t) * n);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (held bits)");
         g->bytes += (int64_t)(sizeof(uint64_t) * n);
     }
@@ -244,6 +258,9 @@ void fill_step_args(sbg_grid g, const sbg_params *p, StepArgs &a) {
     a.eps = g->has_eps ? g->eps : nullptr;
     a.eps64 = g->has_eps ? g->eps64 : nullptr;
     a.heldbits = (a.held_mask && g->heldbits_mask == a.held_mask) ? g->heldbits : nullptr;
+    a.err = g->err;
+    a.stall_group = g->inject_stall_group;
+    a.wait_cycles = g->inject_stall_group >= 0 ? g->inject_wait_cycles : (1ll << 31);
     for (int s = 0; s < 2; ++s) {
         for (int ax = 0; ax < 3; ++ax) {
             double c = p->D[s] / (p->dx[ax] * p->dx[ax]);
@@ -502,6 +519,7 @@ constexpr int64_t kGraphSteps = 64;  // steps per captured graph (even: parity p
 static sbg_status ensure_graph(sbg_grid g, sbg_state st, const sbg_params *p) {
     if (st->graph && st->graph_cur == st->cur && st->graph_variant == st->variant &&
         st->graph_ctas == st->ctas_per_sm && st->graph_eps_version == g->eps_version &&
+        st->graph_inject_version == g->inject_version &&
         std::memcmp(&st->graph_params, p, sizeof(*p)) == 0)
         return SBG_OK;
     if (st->graph) {
@@ -533,6 +551,7 @@ static sbg_status ensure_graph(sbg_grid g, sbg_state st, const sbg_params *p) {
     st->graph_variant = st->variant;
     st->graph_ctas = st->ctas_per_sm;
     st->graph_eps_version = g->eps_version;
+    st->graph_inject_version = g->inject_version;
     st->graph_params = *p;
     st->graph_steps = kGraphSteps;
     return SBG_OK;
@@ -631,3 +650,24 @@ sbg_status launch_step_work(sbg_grid g, sbg_state st, const sbg_params *p, int s
     return SBG_OK;
 }
 }  // namespace sbg
+
+extern "C" sbg_status sbg_debug_stall_stage(sbg_grid g, int64_t group, int64_t wait_cycles) {
+    if (!g) return fail(SBG_ERR_INVALID_ARG, "sbg_debug_stall_stage: null grid");
+    if (group >= 0 && (wait_cycles < 1 || wait_cycles > (int64_t(1) << 31) || group > INT32_MAX))
+        return fail(SBG_ERR_INVALID_ARG, "sbg_debug_stall_stage: 0 <= group <= 2^31 - 1, 1 <= wait_cycles <= 2^31");
+    g->inject_stall_group = group >= 0 ? (int)group : -1;
+    g->inject_wait_cycles = group >= 0 ? (long long)wait_cycles : 0;
+    g->inject_version++;
+    return SBG_OK;
+}
+
+extern "C" sbg_status sbg_debug_set_face(sbg_grid g, int64_t block, int32_t face, int32_t id, int32_t *old_id) {
+    if (!g) return fail(SBG_ERR_INVALID_ARG, "sbg_debug_set_face: null grid");
+    if (block < 0 || block >= g->nb || face < 0 || face > 5)
+        return fail(SBG_ERR_INVALID_ARG, "sbg_debug_set_face: block or face out of range");
+    int32_t *slot = g->face_nbr + block * 6 + face;
+    if (old_id) SBG_CUDA(cudaMemcpy(old_id, slot, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    SBG_CUDA(cudaMemcpy(slot, &id, sizeof(int32_t), cudaMemcpyHostToDevice));
+    g->inject_version++;  // captured step graphs hold no table contents, but re-capture anyway
+    return SBG_OK;
+}

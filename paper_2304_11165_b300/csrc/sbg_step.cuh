@@ -34,6 +34,9 @@ struct StepArgs {
     const void *ext[2];      // external source S_s per slot (state precision; null: none)
     double ext_scale;        //   its time factor a_n for this step: the term a_n S_s(x)
     int held_mask;           // bit f: face f is Dirichlet
+    int stall_group;         // test hook: the ring kernels never copy this group (-1: none)
+    long long wait_cycles;   // bound of every wait on a ring stage (SM cycles)
+    int *err;                // the grid's device error word
     StepCoef<float> cf;
     StepCoef<double> cd;
 };

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
     __syncthreads();
 
     auto issue = [&](int gi, int s) {
+        if (gi == a.stall_group) return;  // test hook: this stage never completes
         int b0, nblk;
         span(gi, b0, nblk);
         const uint32_t bytes = (uint32_t)(nblk * B3 * sizeof(float));
@@ -322,13 +323,13 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_pipe(const StepArgs
         }
 
         bool ok = true;
-        if (tid == 0) ok = mbar_wait_bounded(&full[s], par);
+        if (tid == 0) ok = mbar_wait_bounded(&full[s], par, a.wait_cycles);
         if (__syncthreads_or(!ok)) {
             if (HV == 2) cp_async_wait_all();
             if (tid == 0) {
                 atomicExch(err, (int)SBG_ERR_TIMEOUT);
                 for (int q = it; q < it + S && g0 + q < g1; ++q)
-                    mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), 1ll << 28);
+                    mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), min(a.wait_cycles, 1ll << 28));
             }
             return false;
         }
@@ -817,6 +818,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
     }
     __syncthreads();
     auto issue = [&](int gi, int s) {
+        if (gi == a.stall_group) return;  // test hook: this stage never completes
         int b0, nblk;
         span(gi, b0, nblk);
         const uint32_t bytes = (uint32_t)(nblk * B3 * sizeof(float));
@@ -1056,13 +1058,13 @@ __global__ void __launch_bounds__(kPipeThreads, MINB) k_step_rows2(const StepArg
             id2 = load_ids(gi + 1);
         }
         bool ok = true;
-        if (tid == 0) ok = mbar_wait_bounded(&full[s], par);
+        if (tid == 0) ok = mbar_wait_bounded(&full[s], par, a.wait_cycles);
         if (__syncthreads_or(!ok)) {
             if (AH) cp_async_wait_all();
             if (tid == 0) {
                 atomicExch(err, (int)SBG_ERR_TIMEOUT);
                 for (int q = it; q < it + S && g0 + q < g1; ++q)
-                    mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), 1ll << 28);
+                    mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), min(a.wait_cycles, 1ll << 28));
             }
             return false;
         }

@@ -32,11 +32,21 @@
 // neighbouring voxels (the same values), and an inactive neighbour (sentinel)
 // is mirrored.  States are bitwise equal to the plain kernel's (tested).
 // There is no wait on another thread or CTA in this kernel.
+#include <algorithm>
+
 #include "sbg_step.cuh"
 
 namespace sbg {
 
 constexpr int kStreamThreads = 256;  // 16 blocks x 16 rows of 4 voxels
+
+// SBG_DEBUG (the libsbg_debug.so build): every face id and band-row index is
+// checked against its table before it is used; an index outside records
+// SBG_ERR_BOUNDS in the grid's error word and reads the ghost block (or no
+// weights) instead
+#ifndef SBG_DEBUG
+#define SBG_DEBUG 0
+#endif
 
 __device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 
@@ -142,7 +152,8 @@ __device__ __forceinline__ float4 row_update(const float4 c, float xm, float xp,
 
 template <int NS, bool REACT, bool HELD, int MINB>
 __global__ void __launch_bounds__(kStreamThreads, MINB)
-k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__restrict__ wrow, float negzero) {
+k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__restrict__ wrow, float negzero, int *err,
+              int n_wrows) {
     const int t = threadIdx.x;
     const int j = t >> 4, rr = t & 15, y = rr & 3, z = rr >> 2;
     const int nb = (int)a.nb;  // the launcher guarantees (nb + 2) * 64 < 2^31
@@ -187,6 +198,14 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
                 m.wmask = 0;
             }
             m.held = HELD ? (uint32_t)(__ldg(a.heldbits + b) >> (rr * 4)) & 0xFu : 0u;
+#if SBG_DEBUG
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (m.f[k] < -1 || m.f[k] >= nb) {
+                    atomicExch(err, (int)SBG_ERR_BOUNDS);
+                    m.f[k] = -1;
+                }
+#endif
         } else {
             m.f[0] = m.f[1] = m.f[2] = m.f[3] = -1;
             m.woff = 0;
@@ -213,7 +232,14 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
         const int o_zm = z > 0 ? row - 16 : f[3] * 64 + ozm;
         const int o_zp = z < 3 ? row + 16 : f[3] * 64 + ozp;
         float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (REACT && valid && ((wmask >> rr) & 1u)) w4 = __ldg(wrow + woff + __popc(wmask & ((1u << rr) - 1u)));
+        if (REACT && valid && ((wmask >> rr) & 1u)) {
+            const int wi = woff + __popc(wmask & ((1u << rr) - 1u));
+#if SBG_DEBUG
+            if (wi < 0 || wi >= n_wrows) atomicExch(err, (int)SBG_ERR_BOUNDS);
+            else
+#endif
+                w4 = __ldg(wrow + wi);
+        }
         load_meta(gi + G, nxt);  // the next group's tables, in flight while this one computes
         uint32_t keep[4];
 #pragma unroll
@@ -250,7 +276,7 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
 
 template <int NS, bool REACT, bool HELD>
 static cudaError_t launch_stream_t(const StepArgs &a, const int2 *wmeta, const float4 *wrow, int ctas_per_sm,
-                                   cudaStream_t s) {
+                                   int *err, int n_wrows, cudaStream_t s) {
     constexpr int MINB = 3;
     auto kern = k_step_stream<NS, REACT, HELD, MINB>;
     static int occ = -1, nsm = 0;
@@ -267,7 +293,7 @@ static cudaError_t launch_stream_t(const StepArgs &a, const int2 *wmeta, const f
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ngroups) grid = ngroups;
     if (grid < 1) return cudaSuccess;
-    kern<<<(unsigned)grid, kStreamThreads, 0, s>>>(a, wmeta, wrow, -0.0f);
+    kern<<<(unsigned)grid, kStreamThreads, 0, s>>>(a, wmeta, wrow, -0.0f, err, n_wrows);
     return cudaGetLastError();
 }
 
@@ -281,16 +307,18 @@ cudaError_t launch_step_stream(const StepArgs &a, sbg_grid g, int ns, bool react
     const bool held = a.held_mask != 0;
     const int2 *wm = g->wmeta;
     const float4 *wr = g->wrow;
+    int *err = g->err;
+    const int nw = (int)std::min<int64_t>(g->n_wrows, INT32_MAX);
     if (ns == 1) {
-        if (react) return held ? launch_stream_t<1, true, true>(a, wm, wr, ctas_per_sm, s)
-                               : launch_stream_t<1, true, false>(a, wm, wr, ctas_per_sm, s);
-        return held ? launch_stream_t<1, false, true>(a, wm, wr, ctas_per_sm, s)
-                    : launch_stream_t<1, false, false>(a, wm, wr, ctas_per_sm, s);
+        if (react) return held ? launch_stream_t<1, true, true>(a, wm, wr, ctas_per_sm, err, nw, s)
+                               : launch_stream_t<1, true, false>(a, wm, wr, ctas_per_sm, err, nw, s);
+        return held ? launch_stream_t<1, false, true>(a, wm, wr, ctas_per_sm, err, nw, s)
+                    : launch_stream_t<1, false, false>(a, wm, wr, ctas_per_sm, err, nw, s);
     }
-    if (react) return held ? launch_stream_t<2, true, true>(a, wm, wr, ctas_per_sm, s)
-                           : launch_stream_t<2, true, false>(a, wm, wr, ctas_per_sm, s);
-    return held ? launch_stream_t<2, false, true>(a, wm, wr, ctas_per_sm, s)
-                : launch_stream_t<2, false, false>(a, wm, wr, ctas_per_sm, s);
+    if (react) return held ? launch_stream_t<2, true, true>(a, wm, wr, ctas_per_sm, err, nw, s)
+                           : launch_stream_t<2, true, false>(a, wm, wr, ctas_per_sm, err, nw, s);
+    return held ? launch_stream_t<2, false, true>(a, wm, wr, ctas_per_sm, err, nw, s)
+                : launch_stream_t<2, false, false>(a, wm, wr, ctas_per_sm, err, nw, s);
 }
 
 }  // namespace sbg

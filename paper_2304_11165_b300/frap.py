@@ -18,7 +18,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .api import Grid, State, frap_fit, make_params
+from .api import Grid, State, frap_effective_D, make_params
 
 
 @dataclass
@@ -32,16 +32,12 @@ class FrapResult:
     F_bulk: np.ndarray    # normalised bulk curve
 
 
-def recovery(state: State, params, lo, hi, steps_per_sample: int, n_samples: int, dt: float, geom: int = 0,
-             stream=None):
+def recovery(state: State, params, lo, hi, steps_per_sample: int, n_samples: int, geom: int = 0, stream=None):
     """(t, F) of the normalised recovery of the box lo <= (x, y, z) < hi,
-    advancing ``state`` by ``steps_per_sample * n_samples`` steps."""
-    total, n_act = state.box_sum((0, 0, 0), (1 << 30,) * 3, geom=geom, stream=stream)
-    sums, count = state.frap_curve(params, lo, hi, steps_per_sample, n_samples, geom=geom, stream=stream)
-    if count == 0 or n_act == 0 or total == 0.0:
-        raise ValueError("recovery: the box holds no active voxel or the field is zero")
-    t = dt * steps_per_sample * np.arange(n_samples + 1)
-    return t, sums / (total / n_act * count)
+    advancing ``state`` by ``steps_per_sample * n_samples`` steps
+    (``sbg_frap_recovery``)."""
+    t, F, _ = state.frap_recovery(params, lo, hi, steps_per_sample, n_samples, geom=geom, stream=stream)
+    return t, F
 
 
 def effective_D(phi, phys, u0, lo, hi, steps_per_sample: int, n_samples: int, dtype: str = "f32r",
@@ -51,7 +47,6 @@ def effective_D(phi, phys, u0, lo, hi, steps_per_sample: int, n_samples: int, dt
     the initial field ``u0``; the bulk reference is the same box with every
     voxel in the pore space."""
     p = make_params(phys)
-    D = float(phys.D[0])
     curves = []
     for field in (phi, np.full(phi.shape, 1.0e3, np.float32)):
         g = Grid(field, block=block, stream=stream)
@@ -59,9 +54,9 @@ def effective_D(phi, phys, u0, lo, hi, steps_per_sample: int, n_samples: int, dt
         if variant is not None:
             st.set_kernel(variant)
         st.set(u0)
-        curves.append(recovery(st, p, lo, hi, steps_per_sample, n_samples, phys.dt, stream=stream))
+        curves.append(recovery(st, p, lo, hi, steps_per_sample, n_samples, stream=stream))
         st.close()
         g.close()
     (t, F), (_, Fb) = curves
-    s, rss = frap_fit(t, F, t, Fb, s_lo, 1.0)
-    return FrapResult(D_eff=s * D, tau=1.0 / s if s > 0 else float("inf"), scale=s, rss=rss, t=t, F=F, F_bulk=Fb)
+    d_eff, tau, s, rss = frap_effective_D(t, F, t, Fb, float(phys.D[0]), s_lo, 1.0)
+    return FrapResult(D_eff=d_eff, tau=tau, scale=s, rss=rss, t=t, F=F, F_bulk=Fb)

@@ -44,3 +44,19 @@ def test_argument_checks():
         frap_fit(t, t, t, t, 0.0, 1.0)                # s_lo must be positive
     with pytest.raises(SbgError):
         frap_fit(t, np.full(5, np.nan), t, t, 0.1, 1.0)
+
+
+def test_effective_D_and_tau_from_the_fit():
+    """sbg_frap_effective_D (Eq. 2): a bulk reference recorded at D_ref = 0.7
+    fitted with the exact scale 0.37 gives D_eff = 0.37 * 0.7 and tau = 1/0.37;
+    a measured curve equal to the reference gives D_eff = D_ref, tau = 1."""
+    from paper_2304_11165_b300.api import frap_effective_D
+    t = np.linspace(0, 10, 41)
+    tr = np.linspace(0, 10, 4001)
+    d_eff, tau, s, rss = frap_effective_D(t, 1 - np.exp(-0.37 * t), tr, 1 - np.exp(-tr), 0.7, 0.01, 1.0)
+    assert abs(s - 0.37) <= 1e-12 and abs(d_eff - 0.37 * 0.7) <= 1e-12 and abs(tau - 1 / 0.37) <= 1e-11
+    assert rss <= 1e-24
+    d1, tau1, s1, _ = frap_effective_D(tr, 1 - np.exp(-tr), tr, 1 - np.exp(-tr), 0.7, 0.01, 1.0)
+    assert abs(s1 - 1.0) <= 1e-12 and abs(d1 - 0.7) <= 1e-12 and abs(tau1 - 1.0) <= 1e-12
+    with pytest.raises(SbgError):
+        frap_effective_D(t, t, tr, tr, 0.0, 0.01, 1.0)    # D_ref must be positive

@@ -105,6 +105,27 @@ def test_effective_D_matches_the_oracle():
     assert abs(r1.scale - 1.0) <= 1e-12 and r1.rss == 0.0
 
 
+def test_recovery_is_normalised_by_the_library_like_the_oracle():
+    """sbg_frap_recovery: t_i = i sps dt and F_i = M_box(t_i) / (c n_box) with c
+    the conserved mean over the active voxels, against the oracle's box sums
+    normalised the same way (Sec. 3.3); D_eff = s D for a D other than 1."""
+    dims = (30, 27, 25)
+    phi = blob(dims, 27, porosity=0.65)
+    ph = Physics(dims=dims, dt=0.2, D=(0.7, 0.0))
+    lo, hi = centred_box(dims, 8)
+    u0 = frap_initial(phi.shape, lo, hi)
+    st = State(Grid(phi, block=4), 1, "f64").set(u0)
+    t, F, n_box = st.frap_recovery(make_params(ph), lo, hi, 6, 25)
+    P = oracle.Problem(phi, ph)
+    total, nact = P.box_sum(P.shape_state(u0[None]), (0, 0, 0), ph.dims)
+    sums, n = P.frap_curve(u0[None], lo, hi, 6, 25)
+    assert n_box == n
+    np.testing.assert_allclose(t, ph.dt * 6 * np.arange(26), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(F, sums / (total / nact * n), rtol=1e-12, atol=1e-14)
+    r = frap.effective_D(phi, ph, u0, lo, hi, 6, 25, dtype="f32r")
+    assert abs(r.D_eff - r.scale * 0.7) <= 1e-15 and abs(r.tau * r.scale - 1.0) <= 1e-15
+
+
 def test_argument_checks():
     dims = (12, 10, 9)
     phi = blob(dims, 26)

@@ -76,6 +76,68 @@ def test_noalloc_reduction_equals_sbg_reduce_on_consecutive_calls(dtype, block):
     assert_same(again[0], reference(st, p, -1)[0])
 
 
+def test_noalloc_f32r_state_is_read_only_and_multi_cta_ranges_follow_a_small_call():
+    """The tortuosity solve's state type (SBG_F32R: FP32 correction on a
+    compensated base): the entry point reduces b + d without refreshing the
+    source or folding the correction, so the state's field stays bitwise the
+    same; a 64^3 range of 8^3 blocks (several records of the fixed array)
+    right after a small one (a single record) gives sbg_reduce's results,
+    so records left by an earlier call do not leak into a later one."""
+    small = random_blob_phi((13, 11, 9), 5, porosity=0.6, ell=1.5)
+    big = random_blob_phi((64, 64, 64), 6, porosity=0.8, ell=4.0)
+    d = (True, True, False, False, False, False)
+    for phi in (small, big):
+        dims = tuple(reversed(phi.shape))
+        phys = Physics(dims=dims, dt=0.1, D=(1.0, 0.0), dirichlet=d, face_value=(1.0, 0.0, 0, 0, 0, 0))
+        g = Grid(phi, block=8)
+        st = State(g, 1, "f32r").set(np.random.default_rng(8).uniform(0, 1, phi.shape))
+        p = make_params(phys)
+        st.step(p, 37)  # a correction d that is not yet folded into the base
+        before = st.get()
+        a = noalloc(st, p, 0, 0)
+        np.testing.assert_array_equal(st.get(), before)
+        b = noalloc(st, p, 0, 0)
+        np.testing.assert_array_equal(a, b)
+        assert_same(a, reference(st, p, 0)[0])  # sbg_reduce refreshes and folds after it reduces
+        assert_same(noalloc(st, p, 0, 0), reference(st, p, 0)[0])
+
+
+def test_noalloc_reduction_of_one_geometry_of_a_batch():
+    phis = [random_blob_phi((20, 17, 15), 9, porosity=0.5, ell=1.6),
+            random_blob_phi((33, 25, 40), 10, porosity=0.6, ell=2.0)]
+    gb = Grid.batch(phis, block=4)
+    st = State(gb, 2, "f32")
+    for i, phi in enumerate(phis):
+        st.set_all(np.random.default_rng(i).uniform(0, 1, (2,) + phi.shape), geom=i)
+    phys = Physics(dims=(20, 17, 15), dt=0.05, nspecies=2, D=(1.0, 0.5), decay=(0.0, 0.1), k_surf=0.3)
+    p = make_params(phys)
+    st.step(p, 9)
+    for geom in (1, 0, -1):
+        ref = reference(st, p, geom)
+        for s in range(2):
+            assert_same(noalloc(st, p, geom, s), ref[s])
+
+
+def test_noalloc_reduction_rejects_a_range_beyond_its_fixed_array():
+    """2^28 voxel slots is the stated limit: a 648^3 box with every voxel in
+    the pore space has 81^3 blocks of 8^3 = 272M slots and is refused before
+    any launch; the same call with sbg_reduce works."""
+    lib = _abi.load()
+    n = 648
+    phi = torch.full((n, n, n), 2.0, dtype=torch.float32, device="cuda")
+    g = Grid(phi, block=8)
+    del phi
+    assert g.n_blocks * 512 > 2 ** 28
+    st = State(g, 1, "f32")
+    p = make_params(Physics(dims=(n, n, n), dt=0.1))
+    out = torch.zeros(_abi.NRED, dtype=torch.float64, device="cuda")
+    rc = lib.sbg_reduce_noalloc(g.handle, st.handle, ctypes.byref(p), 0, 0, ctypes.c_void_p(out.data_ptr()), 0)
+    assert rc == _abi.SBG_ERR_INVALID_ARG
+    assert b"exceed the limit" in lib.sbg_last_error()
+    st.close()
+    g.close()
+
+
 def test_noalloc_reduction_rejects_bad_arguments():
     lib = _abi.load()
     phi = np.full((8, 8, 8), 2.0, np.float32)
