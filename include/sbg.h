@@ -536,6 +536,40 @@ sbg_status sbg_redistance(const int64_t dims[3], const double dx[3], const void 
                           int32_t dtype, int32_t on_device, const sbg_redist_opts *opts, int64_t *iters_out,
                           double *residual_out, void *stream);
 
+/* ---- slab decomposition along x (Sec. 2.4: domain decomposition with ghost
+ * layers; the multi-GPU runs of Sec. 3.6) ------------------------------------
+ * A rank holds the sub-box of its slab of x planes plus one ghost plane on
+ * each side where another slab lies; it holds the ghost planes fixed in its
+ * steps (Dirichlet faces of its sub-box) and overwrites them after every step
+ * with the neighbour's first or last owned plane, so every owned voxel gets
+ * exactly its whole-box update.  The library provides the partition and the
+ * plane transfers; the exchange pattern and the transport are the caller's
+ * (the binding's slab module).
+ *
+ * sbg_slab_partition: x_bounds[0..nparts] (host, nparts + 1 entries) with
+ * x_bounds[0] = 0, x_bounds[nparts] = Nx and interior bounds on block
+ * boundaries (multiples of `block`), so that slab k = [x_bounds[k],
+ * x_bounds[k+1]) holds about 1/nparts of the active blocks (blocks with a
+ * voxel phi > eps_mask, 0 selecting FLT_EPSILON) and at least one block
+ * column.  phi: dense FP32 [Nz][Ny][Nx] on the host.  Host code.  Errors:
+ * SBG_ERR_INVALID_ARG for null pointers, block not 4/8, dims < 1, nparts < 1
+ * or more than the block columns. */
+sbg_status sbg_slab_partition(const float *phi, const int64_t dims[3], int32_t block, float eps_mask,
+                              int32_t nparts, int64_t *x_bounds);
+
+/* One x plane of species `species` of geometry `geom` between the state and a
+ * dense [Nz][Ny] buffer (host or device per on_device; its dtype must be the
+ * state's: SBG_F32 or SBG_F64 states only).  get writes the values of the
+ * active voxels of plane x and 0 elsewhere; set writes the active voxels of
+ * plane x from the buffer and leaves every other slot as it is.  Enqueued on
+ * `stream`; with a host buffer the call copies through a temporary device
+ * buffer and synchronises `stream`.  Errors: SBG_ERR_INVALID_ARG (null
+ * pointers, bad geometry, species or x, other state types or dtypes). */
+sbg_status sbg_state_get_xplane(sbg_grid grid, sbg_state state, int32_t geom, int32_t species, int64_t x,
+                                void *plane, int32_t plane_dtype, int32_t on_device, void *stream);
+sbg_status sbg_state_set_xplane(sbg_grid grid, sbg_state state, int32_t geom, int32_t species, int64_t x,
+                                const void *plane, int32_t plane_dtype, int32_t on_device, void *stream);
+
 /* ---- test hooks (no counterpart in the paper) ---------------------------------
  * Failure detection is tested without a fault on the device: these hooks make
  * a bounded wait run out or an allocation fail on purpose.

@@ -115,6 +115,11 @@ SIGNATURES = [
     ("sbg_last_error", ctypes.c_char_p, []),
     ("sbg_status_string", ctypes.c_char_p, [c_int32]),
     ("sbg_abi_version", c_int32, []),
+    ("sbg_slab_partition", c_int32, [c_void_p, c_void_p, c_int32, c_float, c_int32, c_void_p]),
+    ("sbg_state_get_xplane", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int64, c_void_p, c_int32, c_int32,
+                                       c_void_p]),
+    ("sbg_state_set_xplane", c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int64, c_void_p, c_int32, c_int32,
+                                       c_void_p]),
     ("sbg_debug_stall_stage", c_int32, [c_void_p, c_int64, c_int64]),
     ("sbg_debug_fail_alloc", c_int32, [c_int64]),
     ("sbg_debug_live_allocations", c_int32, [c_void_p, c_void_p]),
