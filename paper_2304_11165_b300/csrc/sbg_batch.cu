@@ -7,7 +7,9 @@
 // ONE persistent pipelined launch per step over a device work list of
 // 512-voxel spans that never straddle geometries, replays a captured CUDA
 // graph of `check_every` such launches, and after each interval computes every
-// active geometry's FP64 residual.  A geometry whose relative residual is
+// active geometry's FP64 residual in one segmented reduction (the records of
+// each geometry in a segment of their own, one final kernel over all
+// segments, one copy and one synchronisation).  A geometry whose relative residual is
 // below tol leaves the work list; its blocks are not touched again, and since
 // check_every is even its values stay in the current buffer.
 #include <algorithm>
@@ -63,6 +65,24 @@ extern "C" sbg_status sbg_batch_run_to_steady(sbg_grid g, sbg_state st, const sb
     for (int i = 0; i < n; ++i) max_items += (g->geom_count[i] + G - 1) / G;
     int64_t *items = nullptr;
     SBG_CUDA(dmalloc((void **)&items, sizeof(int64_t) * 2 * std::max<int64_t>(max_items, 1)));
+    // the segmented check: one record segment per geometry, one result row per geometry
+    int64_t nrec = 0;
+    for (int i = 0; i < n; ++i)
+        if (g->geom_count[i] > 0) nrec += reduce_records(g, st, p, i);
+    double *records = nullptr, *res_dev = nullptr;
+    int *seg_dev = nullptr;
+    cudaError_t ae = dmalloc((void **)&records, sizeof(double) * kNumRed * (size_t)std::max<int64_t>(nrec, 1));
+    if (ae == cudaSuccess) ae = dmalloc((void **)&res_dev, sizeof(double) * kNumRed * (size_t)std::max(n, 1));
+    if (ae == cudaSuccess) ae = dmalloc((void **)&seg_dev, sizeof(int) * 2 * (size_t)std::max(n, 1));
+    if (ae != cudaSuccess) {
+        dfree(items);
+        dfree(records);
+        dfree(res_dev);
+        dfree(seg_dev);
+        return cuda_fail(ae, "cudaMalloc (batch check buffers)");
+    }
+    std::vector<double> res_host(kNumRed * (size_t)std::max(n, 1));
+    std::vector<int> ids;
     std::vector<int64_t> h;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cs = nullptr;
@@ -70,6 +90,9 @@ extern "C" sbg_status sbg_batch_run_to_steady(sbg_grid g, sbg_state st, const sb
         if (exec) cudaGraphExecDestroy(exec);
         if (cs) cudaStreamDestroy(cs);
         dfree(items);
+        dfree(records);
+        dfree(res_dev);
+        dfree(seg_dev);
     };
     auto rebuild = [&]() -> sbg_status {
         h.clear();
@@ -120,16 +143,21 @@ extern "C" sbg_status sbg_batch_run_to_steady(sbg_grid g, sbg_state st, const sb
         }
         done += check_every;
         bool changed = false;
-        for (int i = 0; i < n && rc == SBG_OK; ++i) {
-            if (!active[i]) continue;
-            rc = reduce_species(g, st, p, i, 0, -1, red.data(), s);
-            if (rc != SBG_OK) break;
-            if (red[SBG_RED_NONFINITE] > 0) {
+        // every unconverged geometry's residual in one segmented reduction (one synchronisation)
+        ids.clear();
+        for (int i = 0; i < n; ++i)
+            if (active[i]) ids.push_back(i);
+        rc = reduce_geometries(g, st, p, ids.data(), (int)ids.size(), 0, records, seg_dev, res_dev, res_host.data(),
+                               s);
+        for (size_t k = 0; k < ids.size() && rc == SBG_OK; ++k) {
+            const int i = ids[k];
+            const double *r = &res_host[k * kNumRed];
+            if (r[SBG_RED_NONFINITE] > 0) {
                 rc = fail(SBG_ERR_NONFINITE, "sbg_batch_run_to_steady: non-finite value in geometry " + std::to_string(i));
                 break;
             }
             steps_done[i] = done;
-            rel_residual[i] = red[SBG_RED_RESIDUAL] / r0[i];
+            rel_residual[i] = r[SBG_RED_RESIDUAL] / r0[i];
             if (rel_residual[i] < tol) {
                 active[i] = 0;
                 changed = true;

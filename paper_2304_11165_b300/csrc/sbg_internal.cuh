@@ -177,6 +177,12 @@ sbg_status validate_params(sbg_grid g, const sbg_params *p, int ns);
 // implemented in sbg_reduce.cu
 sbg_status reduce_species(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species,
                           int which_buffer, double *out_host, cudaStream_t stream);
+// one segmented reduction over several geometries (sbg_reduce.cu): the CTA
+// records each geometry's reduction writes, and the reduction itself
+int64_t reduce_records(sbg_grid g, sbg_state st, const sbg_params *p, int geom);
+sbg_status reduce_geometries(sbg_grid g, sbg_state st, const sbg_params *p, const int *geoms, int ngeoms,
+                             int species, double *records, int *seg_dev, double *out_dev, double *out_host,
+                             cudaStream_t s);
 // sum of one species over the active voxels of a box and their count into
 // dst[0..1] (device); kernel launches only
 sbg_status launch_box_sum(sbg_grid g, sbg_state st, int geom, int species, const int64_t lo[3], const int64_t hi[3],

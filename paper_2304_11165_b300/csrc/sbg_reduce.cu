@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include <cstring>
+#include <vector>
 #include <string>
 
 #include "sbg_internal.cuh"
@@ -220,8 +221,10 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const RedArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_reduce_final(const double *partials, int nctas, double *out) {
-    __shared__ double sm[256][kNumRed];
+// The final pass of a reduction: the per-CTA records summed in a fixed order
+// (min and max for those two), the residual's square root taken last.
+__device__ __forceinline__ void reduce_final_body(const double *partials, int nctas, double *out,
+                                                  double (*sm)[kNumRed]) {
     double acc[kNumRed];
     for (int q = 0; q < kNumRed; ++q)
         acc[q] = (q == SBG_RED_MIN) ? INFINITY : (q == SBG_RED_MAX) ? -INFINITY : 0.0;
@@ -246,6 +249,20 @@ __global__ void __launch_bounds__(256) k_reduce_final(const double *partials, in
         if (threadIdx.x == SBG_RED_RESIDUAL) v = sqrt(v);
         out[threadIdx.x] = v;
     }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_final(const double *partials, int nctas, double *out) {
+    __shared__ double sm[256][kNumRed];
+    reduce_final_body(partials, nctas, out, sm);
+}
+
+// The same final pass for several reductions at once: CTA i sums the records
+// [seg[2i], seg[2i] + seg[2i+1]) into out[i * kNumRed ..], each exactly as
+// k_reduce_final would.
+__global__ void __launch_bounds__(256) k_reduce_final_seg(const double *records, const int *seg, double *out) {
+    __shared__ double sm[256][kNumRed];
+    const int i = blockIdx.x;
+    reduce_final_body(records + (int64_t)seg[2 * i] * kNumRed, seg[2 * i + 1], out + (int64_t)i * kNumRed, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -778,6 +795,52 @@ sbg_status refresh_source(sbg_grid g, sbg_state st, const sbg_params *p, cudaStr
     st->r_valid = true;
     st->since_refresh = 0;
     return SBG_OK;
+}
+
+// Records of a per-geometry reduction (reduce_geometries): the number of CTA
+// records the reduction of geometry `geom` writes.
+int64_t reduce_records(sbg_grid g, sbg_state st, const sbg_params *p, int geom) {
+    RedArgs a;
+    fill_red_args(g, st, p, geom, 0, st->cur, nullptr, a);
+    return reduce_ctas(a, g);
+}
+
+// One segmented reduction of species `species` (current buffer) over the
+// geometries geoms[0..ngeoms): every geometry's CTAs write their records into
+// their own segment of `records` (reduce_records(geom) each, in the order of
+// geoms), one final kernel sums every segment (CTA i -> out_dev[i * kNumRed]),
+// one copy brings all results to out_host and the stream is synchronised
+// once.  The results equal reduce_species' per geometry bit for bit (the same
+// kernels, records and summation order).  SBG_F32R states: also refreshes r
+// and folds d over every reduced geometry, as reduce_species does.
+sbg_status reduce_geometries(sbg_grid g, sbg_state st, const sbg_params *p, const int *geoms, int ngeoms,
+                             int species, double *records, int *seg_dev, double *out_dev, double *out_host,
+                             cudaStream_t s) {
+    if (ngeoms <= 0) return SBG_OK;
+    std::vector<int> seg(2 * (size_t)ngeoms);
+    int64_t off = 0;
+    const bool refresh = st->dtype == SBG_F32R;
+    for (int i = 0; i < ngeoms; ++i) {
+        RedArgs a;
+        fill_red_args(g, st, p, geoms[i], species, st->cur, records + off * kNumRed, a);
+        if (refresh) a.rout = st->rsrc;
+        const int nctas = reduce_ctas(a, g);
+        dispatch_reduce(g, st, a, nctas, s);
+        SBG_LAUNCH_CHECK("segmented reduction launch");
+        if (refresh) {
+            sbg_status rc = fold_range(g, st, a, s);
+            if (rc != SBG_OK) return rc;
+        }
+        seg[2 * i] = (int)off;
+        seg[2 * i + 1] = nctas;
+        off += nctas;
+    }
+    SBG_CUDA(cudaMemcpyAsync(seg_dev, seg.data(), sizeof(int) * seg.size(), cudaMemcpyHostToDevice, s));
+    k_reduce_final_seg<<<ngeoms, 256, 0, s>>>(records, seg_dev, out_dev);
+    SBG_LAUNCH_CHECK("segmented reduction final pass");
+    SBG_CUDA(cudaMemcpyAsync(out_host, out_dev, sizeof(double) * kNumRed * ngeoms, cudaMemcpyDeviceToHost, s));
+    SBG_CUDA(cudaStreamSynchronize(s));
+    return check_device_error(g, s);
 }
 
 // Enqueues the reduction of species `species` of buffer `which` (st->cur when

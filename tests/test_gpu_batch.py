@@ -93,3 +93,54 @@ def test_batched_steady_solve_matches_single_solves_and_the_oracle():
         # a converged geometry stays frozen while the others keep stepping
         field = dense_of(sb, i, phi)
         np.testing.assert_allclose(field, st.get(), rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f32x2"])
+def test_segmented_check_equals_per_geometry_reductions(dtype):
+    """One check of the batched solve (one segmented reduction over every
+    unconverged geometry) gives each geometry's relative residual exactly as
+    separate per-geometry reductions of the same states do."""
+    geos = small_batch()
+    gb = Grid.batch(geos, block=4)
+    sa = State(gb, 1, dtype)
+    sb = State(gb, 1, dtype)
+    for i, phi in enumerate(geos):
+        phys = tortuosity_physics(tuple(reversed(phi.shape)))
+        u0 = initial_with_faces(phys.dims, 0.0, phys)
+        sa.set(u0, geom=i)
+        sb.set(u0, geom=i)
+    p = make_params(tortuosity_physics((8, 8, 8)))
+    r0 = [sb.reduce(p, geom=i)[0]["residual"] for i in range(len(geos))]
+    steps, rel = sa.batch_run_to_steady(p, 1e-30, check_every=64, max_steps=64, raise_on_max=False)
+    assert np.all(steps == 64)
+    sb.step(p, 64)
+    for i in range(len(geos)):
+        r1 = sb.reduce(p, geom=i)[0]["residual"]
+        assert rel[i] == r1 / r0[i], (i, rel[i], r1 / r0[i])
+
+
+def test_autotuner_picks_the_fastest_and_a_cache_hit_skips_the_timing(tmp_path, monkeypatch):
+    from paper_2304_11165_b300 import autotune
+    monkeypatch.setenv("SBG_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    geos = small_batch()[:3]
+    phys = tortuosity_physics((8, 8, 8))
+    cands = [(4, "async", 0), (8, "pipelined", 0), (4, "pipelined", 2)]
+    fake = {cands[0]: 3.0, cands[1]: 1.5, cands[2]: 2.0}
+    calls = []
+
+    def timer(c):
+        calls.append(c)
+        return fake[c]
+
+    best, table = autotune.tune(geos, phys, "f32", candidates=cands, timer=timer)
+    assert (best["block"], best["variant"], best["ctas_per_sm"]) == cands[1] and not best["cached"]
+    assert len(table) == 3 and calls == cands
+    again, t2 = autotune.tune(geos, phys, "f32", candidates=cands, timer=timer)
+    assert again["cached"] and t2 is None and len(calls) == 3
+    # a different species count or state type is another key: timed again
+    autotune.tune(geos, phys, "f32x2", candidates=cands, timer=timer)
+    assert len(calls) == 6
+    # the real timing of two candidates, without the cache
+    real, table = autotune.tune(geos, phys, "f32", candidates=cands[:2], steps=8, use_cache=False)
+    assert all(r["ns_per_voxel_update"] > 0 for r in table)
+    assert real["ns_per_voxel_update"] == min(r["ns_per_voxel_update"] for r in table)
