@@ -275,9 +275,9 @@ sbg_status sbg_step_source(sbg_grid grid, sbg_state state, const sbg_params *par
  * SBG_KERNEL_STREAM (SBG_F32 states of one or two species on 4^3 blocks,
  * without a diffusivity factor: CTAs take groups of 16 blocks in turn, one
  * x-row of four voxels per thread, every neighbour row read straight from
- * global memory through L1, the groups a few sweeps ahead prefetched into L2
- * with bulk prefetches; best with SBG_ORDER_PLANES grids; states of other
- * kinds fall back to SBG_KERNEL_AUTO's choice).
+ * global memory through L1; best with SBG_ORDER_PLANES grids, whose plane
+ * order keeps the sweep's neighbour planes in L2; states of other kinds fall
+ * back to SBG_KERNEL_AUTO's choice).
  * Results are bitwise identical across variants.  The pipelined kernels index
  * voxel slots with 32-bit integers: a grid of 2^31 or more slots (blocks x
  * B^3) runs the one-thread-per-voxel kernel under SBG_KERNEL_AUTO, and

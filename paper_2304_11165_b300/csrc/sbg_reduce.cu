@@ -472,12 +472,13 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_f(const RedArgs a) {
     }
 }
 
-// The same reduction for the common case (no surface reaction, constant D),
-// one thread per x-row of four voxels: the row and its four y/z neighbour
-// rows are loaded and combined into double-float values once (not once per
-// voxel and face), x neighbours come from the row itself, and the per-voxel
-// arithmetic is that of k_reduce_f in the same order, so r and every
-// per-voxel term are bitwise the same.
+// The same reduction for constant D (with or without the surface reaction,
+// REACT), one thread per x-row of four voxels: the row and its four y/z
+// neighbour rows are loaded and combined into double-float values once (not
+// once per voxel and face), x neighbours come from the row itself, the
+// surface weights and (species B) the row of u_A are read as rows too, and
+// the per-voxel arithmetic is that of k_reduce_f in the same order, so r and
+// every per-voxel term are bitwise the same.
 template <int VM>
 __device__ __forceinline__ void load_row_df(const RedArgs &a, int s, int64_t slot, float h[4], float l[4],
                                             bool act[4]) {
@@ -508,7 +509,7 @@ __device__ __forceinline__ void load_row_df(const RedArgs &a, int s, int64_t slo
     }
 }
 
-template <int VM, int B>
+template <int VM, int B, bool REACT>
 __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_rows(const RedArgs a) {
     constexpr int B3 = B * B * B;
     constexpr int RX = B / 4;              // rows of four along x per block row
@@ -614,6 +615,26 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_rows(const RedArgs a)
 #pragma unroll
             for (int i = 0; i < 4; ++i) lap[i] = df_add(lap[i], df_mul(d[i], cax));
         }
+        // surface transfer: the row's weights and, for species B, the row of u_A
+        float wv[4] = {0.f, 0.f, 0.f, 0.f}, uah[4] = {0.f, 0.f, 0.f, 0.f}, ual[4] = {0.f, 0.f, 0.f, 0.f};
+        if (REACT) {
+            const int ws = a.wslab[b];
+            if (ws >= 0) {
+                const float4 w4 = *reinterpret_cast<const float4 *>(a.wf + (int64_t)ws * B3 + lrow);
+                wv[0] = w4.x;
+                wv[1] = w4.y;
+                wv[2] = w4.z;
+                wv[3] = w4.w;
+            }
+            if (s == 1) {
+                bool aa[4];
+                load_row_df<VM>(a, 0, b * B3 + lrow, uah, ual, aa);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (!aa[i]) uah[i] = ual[i] = 0.f;
+            }
+        }
+        const DF kk = {a.kh, a.kl};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (!ca[i]) continue;
@@ -631,8 +652,11 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_rows(const RedArgs a)
             const bool held = held_yz || ((a.held_mask & 1) && gx == 0) || ((a.held_mask & 2) && gx == nx - 1);
             const int64_t slot = b * B3 + lrow + i;
             if (!held) {
-                DF r = df_mul(dec, u);
+                DF rate = dec;
+                if (REACT && s == 0) rate = df_add(rate, df_mul(kk, {wv[i], 0.f}));
+                DF r = df_mul(rate, u);
                 r = df_add(lap[i], {-r.h, -r.l});
+                if (REACT && s == 1) r = df_add(r, df_mul(df_mul(kk, {wv[i], 0.f}), {uah[i], ual[i]}));
                 const float p = __fmul_rn(r.h, r.h);
                 res = df_add(res, {p, __fmaf_rn(r.h, r.h, -p) + 2.f * r.h * r.l});
                 if (VM == kVR && a.rout) a.rout[slot] = __fadd_rn(r.h, r.l);
@@ -707,7 +731,8 @@ __global__ void k_fold(float *__restrict__ d, float *__restrict__ bh, float *__r
 template <typename T, int VM, int B>
 static void launch_reduce(const RedArgs &a, int nctas, cudaStream_t s) {
     if (sizeof(T) == 8) k_reduce<double, false, B><<<nctas, kRedThreads, 0, s>>>(a);
-    else if (a.k == 0.0 && !a.epsf) k_reduce_rows<VM, B><<<nctas, kRedThreads, 0, s>>>(a);
+    else if (a.k == 0.0 && !a.epsf) k_reduce_rows<VM, B, false><<<nctas, kRedThreads, 0, s>>>(a);
+    else if (!a.epsf) k_reduce_rows<VM, B, true><<<nctas, kRedThreads, 0, s>>>(a);
     else k_reduce_f<VM, B><<<nctas, kRedThreads, 0, s>>>(a);
 }
 

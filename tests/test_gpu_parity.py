@@ -173,6 +173,39 @@ def test_reductions_match_oracle(dtype, tol):
         assert red[s]["nonfinite"] == 0
 
 
+@pytest.mark.parametrize("block,ns,k", [(4, 2, 0.4), (8, 2, 0.4), (4, 1, 0.3), (4, 2, 0.0)])
+def test_fp32_reduction_of_a_state_matches_the_oracle_on_the_same_values(block, ns, k):
+    """The reduction arithmetic alone: the FP32 state's checks against the
+    oracle's FP64 checks of the very same stored values.  Mass and fluxes agree
+    to the double-float accumulation (1e-12 of their scale); the residual also
+    carries the FP32 rounding of the surface weights (the kernels read the
+    weights the step uses), so it gets 1e-6 of the transfer term's scale."""
+    phi, phys, u0 = make_case((27, 22, 18), ns, k, (0, 2), 12)
+    P = oracle.Problem(phi, phys)
+    g = Grid(phi, block=block)
+    st = State(g, ns, "f32").set_all(u0)
+    p = make_params(phys)
+    st.step(p, 30)
+    u = st.get_all()
+    ref = P.reduce(u)
+    red = st.reduce(p)
+    act = P.active > 0
+    for s in range(ns):
+        a = np.abs(u[s]) * act
+        D = phys.D[s]
+        rate = 4 * D * sum(1 / d ** 2 for d in phys.dx) + phys.decay[s] + k
+        scale = {"mass": a.sum() * np.prod(phys.dx),
+                 "J_in": D * (a[:, :, 0] + a[:, :, 1]).sum() * phys.dx[1] * phys.dx[2] / phys.dx[0],
+                 "J_out": D * (a[:, :, -2] + a[:, :, -1]).sum() * phys.dx[1] * phys.dx[2] / phys.dx[0]}
+        for key in ("mass", "J_in", "J_out"):
+            assert abs(red[s][key] - ref[s][key]) <= 1e-12 * scale[key], (s, key, red[s][key], ref[s][key])
+        transfer = np.sqrt(((k * np.abs(u[0]) * act) ** 2).sum())
+        res_tol = 1e-12 * np.sqrt(((rate * a) ** 2).sum()) + 1e-6 * transfer
+        assert abs(red[s]["residual"] - ref[s]["residual"]) <= res_tol, (s, red[s]["residual"], ref[s]["residual"])
+        assert red[s]["n_active"] == ref[s]["n_active"]
+        assert red[s]["min"] == u[s][act].min() and red[s]["max"] == u[s][act].max()
+
+
 def test_spheres64_fp64_matches_oracle():
     """64^3, 20 spheres, FP64, c = 1 held on x = 0, D = 1, dt = 0.1, 100 steps."""
     phi, u0, phys = spheres64()
