@@ -299,7 +299,7 @@ def reactive_workload_name(n, phys, nsteps, per):
     return ("reactive512: %d^3 Boolean sphere packing (lognormal radii, median 12, sigma 0.3), "
             "pore fraction %.3f; A: D=1, surface reaction A->B k=0.05 in 0<phi<1; B: D=0.5, "
             "decay 0.001; A=1 for x<32; closed box; dt=%.6f (0.9 x limit); one bench step = "
-            "one run of %d steps with an FP64 check every %d"
+            "one run of %d steps with an FP64 mass/flux/min/max check (no residual) every %d"
             % (n, phys.extra["pore_fraction"], phys.dt, nsteps, per))
 
 
@@ -607,14 +607,15 @@ def run_reactive512(args):
     surface-sink model on the 512^3 Boolean sphere packing.  One bench step
     is one whole run: the state reset to the initial field, 2000 FTCS steps
     of A and B with the surface transfer and B's decay, and an FP64
-    mass/flux/min/max check of both species every 100 steps (enqueued behind
-    its steps and read on the host while the next 100 run).  `value` counts
-    species-voxel updates (two per active voxel and step) over the device
-    time of K runs with every input resident in HBM; `e2e` repeats the runs
-    through the C ABI's host-pointer path: the initial fields copied from
-    page-locked host memory by sbg_state_set (on_device = 0), the checks read
-    into host memory, and the final fields of both species copied back by
-    sbg_state_get (on_device = 0)."""
+    mass/flux/min/max check of both species every 100 steps (sbg_check_async:
+    the reduction without the residual, which a transient run does not use;
+    enqueued behind its steps and read on the host while the next 100 run).
+    `value` counts species-voxel updates (two per active voxel and step) over
+    the device time of K runs with every input resident in HBM; `e2e` repeats
+    the runs through the C ABI's host-pointer path: the initial fields copied
+    from page-locked host memory by sbg_state_set (on_device = 0), the checks
+    read into host memory, and the final fields of both species copied back
+    by sbg_state_get (on_device = 0)."""
     import torch
     from paper_2304_11165_b300 import Grid, State, make_params
     import paper_2304_11165_b300._abi as abi
@@ -662,7 +663,7 @@ def run_reactive512(args):
             state.step(p, per, stream=stream)
             if ev is not None:
                 ev[i][1].record(stream)
-            state.reduce_async(p, red_buf[i % 2], stream=stream)
+            state.check_async(p, red_buf[i % 2], stream=stream)
             red_done[i % 2].record(stream)
             if i > 0:
                 red_done[(i - 1) % 2].synchronize()
@@ -757,7 +758,7 @@ def run_reactive512(args):
                                                "of the blocks holding surface-band voxels (w read)"},
         "e2e": {"value": e2e_value, "unit": "GVox/s", "h2d_bytes_per_step": int(u0_f32.nbytes),
                 "d2h_bytes_per_step": int(u0_f32.nbytes) + nint * 2 * abi.NRED * 8,
-                "path": "sbg_state_set / sbg_state_get with host pointers (page-locked), sbg_reduce_async "
+                "path": "sbg_state_set / sbg_state_get with host pointers (page-locked), sbg_check_async "
                         "into page-locked host memory", "final_fields_equal_device_run": same_as_device_run},
         # per run: the state copy (memcpy, not a kernel), per check interval `per` step kernels and the
         # check (per species: reduction and final pass)

@@ -344,6 +344,19 @@ sbg_status sbg_reduce(sbg_grid grid, sbg_state state, const sbg_params *params, 
 sbg_status sbg_reduce_async(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom, double *out,
                             void *stream);
 
+/* The monitoring check of a transient run (the mass total of Sec. 3.4, the
+ * x-face fluxes, min/max and the non-finite and active counts), enqueued like
+ * sbg_reduce_async, without the residual ||L_h u||: the SBG_RED_RESIDUAL slot
+ * of every species reads NaN.  Every other scalar is bitwise the value
+ * sbg_reduce_async gives for the same state (same kernels' accumulation
+ * order).  It reads each species' values once (plus the +x neighbours of the
+ * inlet and outlet planes) instead of evaluating the stencil, so it costs a
+ * memory pass rather than the residual's double-float arithmetic.  SBG_F32R
+ * states: no refresh of the source and no fold (the state is not touched).
+ * Same ownership, ordering and error rules as sbg_reduce_async. */
+sbg_status sbg_check_async(sbg_grid grid, sbg_state state, const sbg_params *params, int32_t geom, double *out,
+                           void *stream);
+
 /* The same FP64 reduction for callers that may not allocate device memory
  * (their memory belongs to another allocator, such as a framework's caching
  * allocator or a fixed serving arena, or allocation latency is not allowed in

@@ -296,6 +296,14 @@ class State:
                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
         return out
 
+    def check_async(self, params: Params, out, geom: int = 0, stream=None):
+        """Enqueue the monitoring check (``sbg_check_async``: every scalar of
+        ``reduce_async`` but the residual, which reads NaN) into ``out``, with
+        the same rules as ``reduce_async``."""
+        check(self._lib.sbg_check_async(self.grid.handle, self.handle, ctypes.byref(params), geom,
+                                        ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
     def box_sum(self, lo, hi, species: int = 0, geom: int = 0, stream=None):
         """(sum of u over the active voxels with lo <= (x, y, z) < hi, their count)."""
         lo_a = np.asarray(lo, dtype=np.int64)

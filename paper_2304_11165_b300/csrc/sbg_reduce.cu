@@ -51,6 +51,8 @@ struct RedArgs {
     // inhomogeneous diffusion: diffusivity factor per slot (null: constant D)
     const float *epsf;
     const double *eps64;
+    // 1: the residual is not evaluated (its slot reads NaN); the other scalars are unchanged
+    int no_residual;
 };
 
 template <typename T, bool X2>
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const RedArgs a) {
                           ((a.held_mask & 4) && gy == 0) || ((a.held_mask & 8) && gy == ny - 1) ||
                           ((a.held_mask & 16) && gz == 0) || ((a.held_mask & 32) && gz == nz - 1);
         const double ec = a.eps64 ? a.eps64[b * B3 + l] : 1.0;
-        if (!held) {
+        if (!held && !a.no_residual) {
             double lap = 0.0;
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
@@ -217,6 +219,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const RedArgs a) {
         double v = sm[0][q];
         for (int wi = 1; wi < kRedThreads / 32; ++wi)
             v = (q == SBG_RED_MIN) ? fmin(v, sm[wi][q]) : (q == SBG_RED_MAX) ? fmax(v, sm[wi][q]) : v + sm[wi][q];
+        if (q == SBG_RED_RESIDUAL && a.no_residual) v = NAN;
         a.partials[(int64_t)blockIdx.x * kNumRed + q] = v;
     }
 }
@@ -376,7 +379,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_f(const RedArgs a) {
         const bool held = ((a.held_mask & 1) && gx == 0) || ((a.held_mask & 2) && gx == nx - 1) ||
                           ((a.held_mask & 4) && gy == 0) || ((a.held_mask & 8) && gy == ny - 1) ||
                           ((a.held_mask & 16) && gz == 0) || ((a.held_mask & 32) && gz == nz - 1);
-        if (!held) {
+        if (!held && !a.no_residual) {
             // L_h u = sum_a c_a [(u~- - u) + (u~+ - u)] - rate u (+ transfer), double-float
             DF lap = {0.f, 0.f};
             const float ec = a.epsf ? a.epsf[slot] : 1.f;
@@ -468,6 +471,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_f(const RedArgs a) {
         double v = sm[0][q];
         for (int wi = 1; wi < kRedThreads / 32; ++wi)
             v = (q == SBG_RED_MIN) ? fmin(v, sm[wi][q]) : (q == SBG_RED_MAX) ? fmax(v, sm[wi][q]) : v + sm[wi][q];
+        if (q == SBG_RED_RESIDUAL && a.no_residual) v = NAN;
         a.partials[(int64_t)blockIdx.x * kNumRed + q] = v;
     }
 }
@@ -509,7 +513,7 @@ __device__ __forceinline__ void load_row_df(const RedArgs &a, int s, int64_t slo
     }
 }
 
-template <int VM, int B, bool REACT>
+template <int VM, int B, bool REACT, bool RESID>
 __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_rows(const RedArgs a) {
     constexpr int B3 = B * B * B;
     constexpr int RX = B / 4;              // rows of four along x per block row
@@ -537,6 +541,9 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_rows(const RedArgs a)
         const int gy = bc.y * B + y, gz = bc.z * B + z;
         const bool held_yz = ((a.held_mask & 4) && gy == 0) || ((a.held_mask & 8) && gy == ny - 1) ||
                              ((a.held_mask & 16) && gz == 0) || ((a.held_mask & 32) && gz == nz - 1);
+        // without the residual only the +x values of rows on the inlet or outlet flux plane are read
+        const int gx0 = bc.x * B + x0;
+        const bool flux_row = nx >= 2 && (gx0 == 0 || (gx0 <= nx - 2 && nx - 2 <= gx0 + 3));
         // the Laplacian, built one axis and one side at a time: d_a = (0 + diff_-) + diff_+,
         // lap = sum_a d_a c_a; the x-face differences u - u_{x+1} of the inlet and outlet
         // planes go to the fluxes on the way
@@ -551,6 +558,7 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_rows(const RedArgs a)
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
                 const bool minus = side == 0;
+                if (!RESID && (ax > 0 || minus || !flux_row)) continue;
                 float vh[4], vl[4];
                 bool va[4];
                 if (ax == 0) {
@@ -617,7 +625,7 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_rows(const RedArgs a)
         }
         // surface transfer: the row's weights and, for species B, the row of u_A
         float wv[4] = {0.f, 0.f, 0.f, 0.f}, uah[4] = {0.f, 0.f, 0.f, 0.f}, ual[4] = {0.f, 0.f, 0.f, 0.f};
-        if (REACT) {
+        if (REACT && RESID) {
             const int ws = a.wslab[b];
             if (ws >= 0) {
                 const float4 w4 = *reinterpret_cast<const float4 *>(a.wf + (int64_t)ws * B3 + lrow);
@@ -651,7 +659,7 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_rows(const RedArgs a)
             const int gx = bc.x * B + x0 + i;
             const bool held = held_yz || ((a.held_mask & 1) && gx == 0) || ((a.held_mask & 2) && gx == nx - 1);
             const int64_t slot = b * B3 + lrow + i;
-            if (!held) {
+            if (RESID && !held) {
                 DF rate = dec;
                 if (REACT && s == 0) rate = df_add(rate, df_mul(kk, {wv[i], 0.f}));
                 DF r = df_mul(rate, u);
@@ -683,7 +691,7 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_rows(const RedArgs a)
         sm[warp][SBG_RED_MASS] = df_to_d(mass) * a.dv;
         sm[warp][SBG_RED_JIN] = df_to_d(jin) * flux;
         sm[warp][SBG_RED_JOUT] = df_to_d(jout) * flux;
-        sm[warp][SBG_RED_RESIDUAL] = df_to_d(res);
+        sm[warp][SBG_RED_RESIDUAL] = RESID ? df_to_d(res) : (double)NAN;
         sm[warp][SBG_RED_MIN] = (double)mn;
         sm[warp][SBG_RED_MAX] = (double)mx;
         sm[warp][SBG_RED_NONFINITE] = (double)nonfin;
@@ -695,6 +703,7 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_reduce_rows(const RedArgs a)
         double v = sm[0][q];
         for (int wi = 1; wi < kRedThreads / 32; ++wi)
             v = (q == SBG_RED_MIN) ? fmin(v, sm[wi][q]) : (q == SBG_RED_MAX) ? fmax(v, sm[wi][q]) : v + sm[wi][q];
+        if (q == SBG_RED_RESIDUAL && a.no_residual) v = NAN;
         a.partials[(int64_t)blockIdx.x * kNumRed + q] = v;
     }
 }
@@ -731,8 +740,9 @@ __global__ void k_fold(float *__restrict__ d, float *__restrict__ bh, float *__r
 template <typename T, int VM, int B>
 static void launch_reduce(const RedArgs &a, int nctas, cudaStream_t s) {
     if (sizeof(T) == 8) k_reduce<double, false, B><<<nctas, kRedThreads, 0, s>>>(a);
-    else if (a.k == 0.0 && !a.epsf) k_reduce_rows<VM, B, false><<<nctas, kRedThreads, 0, s>>>(a);
-    else if (!a.epsf) k_reduce_rows<VM, B, true><<<nctas, kRedThreads, 0, s>>>(a);
+    else if (!a.epsf && a.no_residual) k_reduce_rows<VM, B, false, false><<<nctas, kRedThreads, 0, s>>>(a);
+    else if (a.k == 0.0 && !a.epsf) k_reduce_rows<VM, B, false, true><<<nctas, kRedThreads, 0, s>>>(a);
+    else if (!a.epsf) k_reduce_rows<VM, B, true, true><<<nctas, kRedThreads, 0, s>>>(a);
     else k_reduce_f<VM, B><<<nctas, kRedThreads, 0, s>>>(a);
 }
 
@@ -872,11 +882,13 @@ sbg_status reduce_geometries(sbg_grid g, sbg_state st, const sbg_params *p, cons
 // < 0) into g->red_dev[kNumRed] (kernel launches only).  SBG_F32R states: also
 // refreshes r and folds d over the reduced range.
 static sbg_status enqueue_reduce(sbg_grid g, sbg_state st, const sbg_params *p, int geom, int species, int which,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool residual = true) {
     const int buf = which < 0 ? st->cur : which;
     RedArgs a;
     fill_red_args(g, st, p, geom, species, buf, g->partials, a);
-    const bool refresh = st->dtype == SBG_F32R && buf == st->cur;
+    a.no_residual = residual ? 0 : 1;
+    // (without the residual there is no source r to refresh)
+    const bool refresh = st->dtype == SBG_F32R && buf == st->cur && residual;
     if (refresh) a.rout = st->rsrc;
     const int nctas = reduce_ctas(a, g);
     dispatch_reduce(g, st, a, nctas, s);
@@ -1085,6 +1097,21 @@ extern "C" sbg_status sbg_reduce_async(sbg_grid g, sbg_state st, const sbg_param
         rc = enqueue_reduce(g, st, p, geom, sp, -1, s);
         if (rc != SBG_OK) return rc;
         // stream order keeps the next species' final pass off g->red_dev until this copy is done
+        SBG_CUDA(cudaMemcpyAsync(out + sp * kNumRed, g->red_dev, sizeof(double) * kNumRed, cudaMemcpyDefault, s));
+    }
+    return SBG_OK;
+}
+
+extern "C" sbg_status sbg_check_async(sbg_grid g, sbg_state st, const sbg_params *p, int32_t geom, double *out,
+                                      void *stream) {
+    TraceRange trace_range("sbg_check_async");
+    sbg_status rc = check_common(g, st, p, geom);
+    if (rc != SBG_OK) return rc;
+    if (!out) return fail(SBG_ERR_INVALID_ARG, "sbg_check_async: null output");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int sp = 0; sp < st->ns; ++sp) {
+        rc = enqueue_reduce(g, st, p, geom, sp, -1, s, false);
+        if (rc != SBG_OK) return rc;
         SBG_CUDA(cudaMemcpyAsync(out + sp * kNumRed, g->red_dev, sizeof(double) * kNumRed, cudaMemcpyDefault, s));
     }
     return SBG_OK;

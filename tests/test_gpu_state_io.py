@@ -81,3 +81,38 @@ def test_async_reduction_equals_the_synchronous_one(dtype, ns):
     assert c.parse_reduction(dev.cpu()) == ref
     # the states go on identically after either call (SBG_F32R: the same refresh)
     np.testing.assert_array_equal(a.step(p, 30).get_all(), b.step(p, 30).get_all())
+
+
+@pytest.mark.parametrize("dtype,ns,block", [("f32", 2, 4), ("f32", 2, 8), ("f32", 1, 4), ("f64", 2, 4),
+                                            ("f32r", 1, 4), ("f32x2", 1, 8)])
+def test_check_is_the_reduction_without_the_residual(dtype, ns, block):
+    """sbg_check_async: every scalar bitwise that of the full reduction of the
+    same state, the residual NaN, the state untouched."""
+    dims = (29, 21, 17)
+    phi = random_blob_phi(dims, 64, porosity=0.6, ell=1.7)
+    rng = np.random.default_rng(64)
+    u0 = rng.uniform(0, 1, (ns,) + phi.shape)
+    ph = Physics(dims=dims, dt=0.05, nspecies=ns, D=(1.0, 0.5)[:ns] + (0.0,) * (2 - ns),
+                 decay=(0.01, 0.02), k_surf=0.2,
+                 dirichlet=(True, True, False, False, False, False), face_value=(1.0, 0.0, 0, 0, 0, 0))
+    p = make_params(ph)
+    g = Grid(phi, block=block)
+    a = State(g, ns, dtype).set_all(u0 if ns == 2 else u0[0]).step(p, 50)
+    before = a.get_all()
+    dev = torch.full((ns * 8,), 7.0, dtype=torch.float64, device="cuda")
+    a.check_async(p, dev)
+    chk = a.parse_reduction(dev.cpu())
+    host = torch.zeros(ns * 8, dtype=torch.float64).pin_memory()
+    a.check_async(p, host)
+    torch.cuda.synchronize()
+    chk_host = a.parse_reduction(host)
+    np.testing.assert_array_equal(a.get_all(), before)
+    # (SBG_F32R: the full reduction then folds the correction into the base, so it comes last)
+    ref = a.reduce(p)
+    keys = ("mass", "J_in", "J_out", "min", "max", "nonfinite", "n_active")
+    for s in range(ns):
+        assert np.isnan(chk[s]["residual"]) and np.isnan(chk_host[s]["residual"])
+        assert np.isfinite(ref[s]["residual"])
+        for key in keys:
+            assert chk[s][key] == ref[s][key], (s, key, chk[s][key], ref[s][key])
+            assert chk_host[s][key] == chk[s][key]
