@@ -86,7 +86,8 @@ def parse():
     ap.add_argument("--rd-steps", type=int, default=None,
                     help="reactive512: RD steps per run (default: the workload's 2000; smaller for profiling)")
     ap.add_argument("--dtype", default="f32r", choices=["f32", "f32x2", "f32r"])
-    ap.add_argument("--variant", default=None, choices=["auto", "plain", "pipelined", "prefetch", "async", "stream"],
+    ap.add_argument("--variant", default=None,
+                    choices=["auto", "plain", "pipelined", "prefetch", "async", "stream", "wave", "wave4"],
                     help="step kernel (default: stream for reactive512, async for the others)")
     ap.add_argument("--order", default=None, choices=["tiled", "planes"],
                     help="block order of the grid (default: planes for reactive512, tiled for the others)")
@@ -569,6 +570,8 @@ def step_kernel_name(ns, variant):
     """The step kernel a state of `ns` FP32 species runs for a kernel variant."""
     if variant == "stream":
         return "k_step_stream"
+    if variant in ("wave", "wave4"):
+        return "k_step_wave"
     return two_array_kernel(variant) if ns == 2 else ("k_step" if variant == "plain" else "k_step_rows2")
 
 
@@ -577,7 +580,13 @@ STREAM_SOURCES = ["paper_2304_11165_b300/csrc/sbg_step_stream.cu", "paper_2304_1
 
 def step_kernel_sources(kernel_name):
     """Source files whose hash keys a committed ncu summary of that kernel."""
-    return STREAM_SOURCES if kernel_name == "k_step_stream" else KERNEL_SOURCES
+    return STREAM_SOURCES if kernel_name in ("k_step_stream", "k_step_wave") else KERNEL_SOURCES
+
+
+def steps_per_launch(variant):
+    """RD steps one launch of the step kernel advances (the wavefront kernel runs
+    2 or 4 steps per launch)."""
+    return {"wave": 2, "wave4": 4}.get(variant, 1)
 
 
 def two_array_kernel(variant):
@@ -732,8 +741,11 @@ def run_reactive512(args):
 
     peak, peak_kind = load_peaks()
     algo_bytes = reactive_algo_bytes(g.n_active, g.info["n_band_blocks"], args.block)
+    spl = steps_per_launch(args.variant)
+    # per_launch_ms is the mean time of one RD step; a launch of the wavefront kernel runs spl of them
     achieved = algo_bytes / (per_launch_ms / 1e3) / 1e9
     kernel_name = step_kernel_name(2, args.variant)
+    launches_per_interval = per // spl + per % spl
     red0 = st0.reduce(p)
     line = {
         "metric": REACT_METRIC,
@@ -753,16 +765,19 @@ def run_reactive512(args):
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": profile_traffic("%s_%s_f32_reactive512.md" % (kernel_name, args.variant),
                                                 step_kernel_sources(kernel_name)) if n == 512 else None,
-                     "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": per_launch_ms * 1e3,
-                     "algorithmic_bytes_rule": "16 B per active voxel (A and B read and written) + 4 B per slot "
-                                               "of the blocks holding surface-band voxels (w read)"},
+                     "algorithmic_bytes_per_launch": algo_bytes * spl, "avg_launch_us": per_launch_ms * 1e3 * spl,
+                     "steps_per_launch": spl,
+                     "algorithmic_bytes_rule": "per RD step: 16 B per active voxel (A and B read and written) + 4 B "
+                                               "per slot of the blocks holding surface-band voxels (w read); a "
+                                               "launch of the wavefront kernel runs steps_per_launch steps and "
+                                               "moves the state through HBM once"},
         "e2e": {"value": e2e_value, "unit": "GVox/s", "h2d_bytes_per_step": int(u0_f32.nbytes),
                 "d2h_bytes_per_step": int(u0_f32.nbytes) + nint * 2 * abi.NRED * 8,
                 "path": "sbg_state_set / sbg_state_get with host pointers (page-locked), sbg_check_async "
                         "into page-locked host memory", "final_fields_equal_device_run": same_as_device_run},
         # per run: the state copy (memcpy, not a kernel), per check interval `per` step kernels and the
         # check (per species: reduction and final pass)
-        "gpu_launches": args.steps * nint * (per + 2 * 2),
+        "gpu_launches": args.steps * nint * (launches_per_interval + 2 * 2),
         "clocks": clocks,
         "interval_stats": interval_stats(interval_ms, per),
         "result": {"mass_A_B_initial": [red0[0]["mass"], red0[1]["mass"]], "mass_A_B_end": list(masses[-1]),

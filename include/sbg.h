@@ -278,6 +278,16 @@ sbg_status sbg_step_source(sbg_grid grid, sbg_state state, const sbg_params *par
  * global memory through L1; best with SBG_ORDER_PLANES grids, whose plane
  * order keeps the sweep's neighbour planes in L2; states of other kinds fall
  * back to SBG_KERNEL_AUTO's choice).
+ * SBG_KERNEL_WAVE / SBG_KERNEL_WAVE4 (the streaming kernel's states on an
+ * SBG_ORDER_PLANES grid of one geometry): 2 / 4 steps per launch, run as a
+ * wavefront over the planes of blocks (step n+1 on one plane while step n+2
+ * runs a few planes behind it), the intermediate steps kept in rings of a few
+ * planes that stay in L2, so that HBM sees one read and one write of the state
+ * per launch; a remainder of fewer steps runs the streaming kernel.  The first
+ * sbg_step of such a state builds its plan (a host synchronisation and ~5 MB
+ * per ring plane and species on a 512^3 grid); a wait of one work unit on
+ * another is bounded like the ring kernels' (SBG_ERR_TIMEOUT).  Other grids and
+ * states fall back to SBG_KERNEL_AUTO's choice.
  * Results are bitwise identical across variants.  The pipelined kernels index
  * voxel slots with 32-bit integers: a grid of 2^31 or more slots (blocks x
  * B^3) runs the one-thread-per-voxel kernel under SBG_KERNEL_AUTO, and
@@ -289,7 +299,9 @@ enum {
     SBG_KERNEL_PIPELINED = 2,
     SBG_KERNEL_PIPELINED_PREFETCH = 3,
     SBG_KERNEL_PIPELINED_ASYNC = 4,
-    SBG_KERNEL_STREAM = 5
+    SBG_KERNEL_STREAM = 5,
+    SBG_KERNEL_WAVE = 6,
+    SBG_KERNEL_WAVE4 = 7
 };
 sbg_status sbg_state_set_kernel(sbg_state state, int32_t variant, int32_t ctas_per_sm);
 
@@ -618,6 +630,22 @@ sbg_status sbg_debug_fail_alloc(int64_t n);
  * build, and restore the entry afterwards.  Synchronous. */
 sbg_status sbg_debug_set_face(sbg_grid grid, int64_t block, int32_t face, int32_t id, int32_t *old_id);
 sbg_status sbg_debug_live_allocations(int64_t *count, int64_t *bytes);
+
+/* sbg_debug_wave_plan: the work order of a wavefront launch (SBG_KERNEL_WAVE,
+ * SBG_KERNEL_WAVE4) over `nplanes` planes of blocks holding
+ * blocks_per_plane[p] blocks, for K steps per launch, a lag of L planes
+ * between consecutive steps, rings of R planes and tickets of up to
+ * ticket_blocks consecutive blocks of one plane.  Writes up to `capacity`
+ * tickets as int32 quadruples (first block, blocks, plane, step 0..K-1) in
+ * the order the kernel's CTAs take them, and their number in *count.  Fails
+ * with SBG_ERR_INVALID_ARG when K < 1, L < 1, R < L + 2 (some ticket would
+ * then wait on a later one) or ticket_blocks outside 1..4096.  Host code only,
+ * no device work: it lets a test check on the CPU that every ticket comes
+ * after the tickets it waits on (step s-1 on the planes p-1..p+1, step s+1 on
+ * the planes p-R-1..p-R+1), which makes the launch deadlock-free.  The kernel
+ * uses L = 4, R = 7 and tickets of 32 blocks. */
+sbg_status sbg_debug_wave_plan(const int32_t *blocks_per_plane, int32_t nplanes, int32_t K, int32_t L, int32_t R,
+                               int32_t ticket_blocks, int32_t *tickets, int64_t capacity, int64_t *count);
 
 /* ---- errors -------------------------------------------------------------------- */
 const char *sbg_last_error(void);            /* thread-local; "" when none                      */

@@ -28,6 +28,7 @@ SBG_F32, SBG_F64, SBG_F32X2, SBG_F32R = 0, 1, 2, 3
 SBG_FACE_NOFLUX, SBG_FACE_DIRICHLET = 0, 1
 SBG_KERNEL_AUTO, SBG_KERNEL_PLAIN, SBG_KERNEL_PIPELINED, SBG_KERNEL_PIPELINED_PREFETCH, SBG_KERNEL_PIPELINED_ASYNC = 0, 1, 2, 3, 4
 SBG_KERNEL_STREAM = 5
+SBG_KERNEL_WAVE, SBG_KERNEL_WAVE4 = 6, 7
 SBG_ORDER_TILED, SBG_ORDER_PLANES = 0, 1
 
 RED_MASS, RED_JIN, RED_JOUT, RED_RESIDUAL, RED_MIN, RED_MAX, RED_NONFINITE, RED_NACTIVE = range(8)
@@ -125,6 +126,8 @@ SIGNATURES = [
     ("sbg_debug_fail_alloc", c_int32, [c_int64]),
     ("sbg_debug_live_allocations", c_int32, [c_void_p, c_void_p]),
     ("sbg_debug_set_face", c_int32, [c_void_p, c_int64, c_int32, c_int32, c_void_p]),
+    ("sbg_debug_wave_plan", c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_int64,
+                                      c_void_p]),
 ]
 
 _lib = None

@@ -243,7 +243,8 @@ class State:
         code = {"auto": _abi.SBG_KERNEL_AUTO, "plain": _abi.SBG_KERNEL_PLAIN,
                 "pipelined": _abi.SBG_KERNEL_PIPELINED,
                 "prefetch": _abi.SBG_KERNEL_PIPELINED_PREFETCH, "async": _abi.SBG_KERNEL_PIPELINED_ASYNC,
-                "stream": _abi.SBG_KERNEL_STREAM}[variant]
+                "stream": _abi.SBG_KERNEL_STREAM, "wave": _abi.SBG_KERNEL_WAVE,
+                "wave4": _abi.SBG_KERNEL_WAVE4}[variant]
         check(self._lib.sbg_state_set_kernel(self.handle, code, int(ctas_per_sm)))
         return self
 

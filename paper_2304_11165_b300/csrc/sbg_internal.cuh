@@ -158,6 +158,7 @@ struct sbg_state_s {
     bool has_ghost = false;         // every val array is preceded by a ghost block of sentinels
                                     // (states made by sbg_state_create; not the adjoint's views)
     int ctas_per_sm = 0;
+    void *wave = nullptr;           // plan of the wavefront kernel (sbg_step_stream.cu), made at first use
     // SBG_F32R (one species): val[b][0] holds the FP32 correction d; the base
     // b = bh + bl and the source r = L_h b are single arrays updated in place
     float *bh = nullptr, *bl = nullptr, *rsrc = nullptr;
@@ -198,6 +199,8 @@ sbg_status step_n(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps,
 sbg_status refresh_source(sbg_grid g, sbg_state st, const sbg_params *p, cudaStream_t stream);
 // steps between refreshes of an SBG_F32R state inside sbg_step
 constexpr int64_t kRefreshSteps = 256;
+// implemented in sbg_step_stream.cu: frees a state's wavefront plan (if any)
+void wave_destroy(sbg_state st);
 // implemented in sbg_step.cu: makes g->heldbits match the Dirichlet faces of
 // p (one small kernel when they changed); call before any stream capture
 sbg_status prepare_held_bits(sbg_grid g, const sbg_params *p, cudaStream_t s);

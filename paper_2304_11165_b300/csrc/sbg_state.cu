@@ -319,6 +319,7 @@ extern "C" sbg_status sbg_state_copy(sbg_state dst, sbg_state src, void *stream)
 extern "C" void sbg_state_destroy(sbg_state st) {
     if (!st) return;
     if (st->graph) cudaGraphExecDestroy(st->graph);
+    wave_destroy(st);
     dfree(st->ext[0]);
     dfree(st->ext[1]);
     dfree(st->base);

@@ -383,8 +383,9 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
         return fail(SBG_ERR_INVALID_ARG, "a diffusivity factor is set: SBG_F32 or SBG_F64 states of one species only");
     // the streaming kernel: asked for, or the automatic choice for two FP32 species (measured
     // 259 us against 390 us for the two-row ring kernel per 512^3 two-species step)
-    const bool stream =
-        st->variant == SBG_KERNEL_STREAM || (st->variant == SBG_KERNEL_AUTO && st->dtype == SBG_F32 && st->ns == 2);
+    const bool stream = st->variant == SBG_KERNEL_STREAM || st->variant == SBG_KERNEL_WAVE ||
+                        st->variant == SBG_KERNEL_WAVE4 ||
+                        (st->variant == SBG_KERNEL_AUTO && st->dtype == SBG_F32 && st->ns == 2);
     if (stream && stream_kernel_applies(g, st)) {
         cudaError_t e = launch_step_stream(a, g, st->ns, react, st->ctas_per_sm, s);
         if (e != cudaSuccess) return cuda_fail(e, "streaming step kernel launch");
@@ -397,7 +398,7 @@ sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, c
             if (e != cudaSuccess) return cuda_fail(e, "pipelined step kernel launch");
             return SBG_OK;
         }
-        if (st->variant >= SBG_KERNEL_PIPELINED && st->variant != SBG_KERNEL_STREAM)
+        if (st->variant >= SBG_KERNEL_PIPELINED && st->variant < SBG_KERNEL_STREAM)
             return fail(SBG_ERR_INVALID_ARG,
                         st->dtype == SBG_F64 ? "the pipelined kernel handles FP32-based states only"
                                              : "the pipelined kernel needs fewer than 2^31 voxel slots (blocks x B^3)");
@@ -516,6 +517,27 @@ sbg_status validate_params(sbg_grid g, const sbg_params *p, int ns) {
 
 constexpr int64_t kGraphSteps = 64;  // steps per captured graph (even: parity preserved)
 
+// Steps one launch of the state's step kernel advances: K for the wavefront
+// kernel (SBG_KERNEL_WAVE: 2, SBG_KERNEL_WAVE4: 4) where it applies, else 1.
+// Each launch leaves the state in the other buffer, and kGraphSteps / K is
+// even, so a graph keeps the buffer parity.
+static int steps_per_launch(sbg_grid g, sbg_state st) {
+    if (st->variant != SBG_KERNEL_WAVE && st->variant != SBG_KERNEL_WAVE4) return 1;
+    if (!wave_kernel_applies(g, st)) return 1;
+    return st->variant == SBG_KERNEL_WAVE4 ? 4 : 2;
+}
+
+// k steps from buffer src into 1 - src: one wavefront launch (k > 1) or one step.
+static sbg_status launch_steps(sbg_grid g, sbg_state st, const sbg_params *p, int src, int k, cudaStream_t s) {
+    if (k == 1) return launch_step(g, st, p, src, s);
+    StepArgs a;
+    fill_args(g, st, p, src, a);
+    if (a.held_mask && !a.heldbits) return fail(SBG_ERR_INVALID_ARG, "internal: held bits not prepared");
+    cudaError_t e = launch_step_wave(a, g, st, p->k_surf != 0.0, s);
+    if (e != cudaSuccess) return cuda_fail(e, "wavefront step kernel launch");
+    return SBG_OK;
+}
+
 static sbg_status ensure_graph(sbg_grid g, sbg_state st, const sbg_params *p) {
     if (st->graph && st->graph_cur == st->cur && st->graph_variant == st->variant &&
         st->graph_ctas == st->ctas_per_sm && st->graph_eps_version == g->eps_version &&
@@ -533,8 +555,9 @@ static sbg_status ensure_graph(sbg_grid g, sbg_state st, const sbg_params *p) {
     sbg_status rc = SBG_OK;
     if (e == cudaSuccess) {
         int src = st->cur;
-        for (int64_t i = 0; i < kGraphSteps && rc == SBG_OK; ++i) {
-            rc = launch_step(g, st, p, src, cs);
+        const int k = steps_per_launch(g, st);
+        for (int64_t i = 0; i < kGraphSteps && rc == SBG_OK; i += k) {
+            rc = launch_steps(g, st, p, src, k, cs);
             src = 1 - src;
         }
         e = cudaStreamEndCapture(cs, &graph);
@@ -565,6 +588,11 @@ static sbg_status step_n_plain(sbg_grid g, sbg_state st, const sbg_params *p, in
 sbg_status step_n(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, cudaStream_t s) {
     sbg_status prc = prepare_held_bits(g, p, s);
     if (prc != SBG_OK) return prc;
+    const int k = steps_per_launch(g, st);
+    if (k > 1 && nsteps >= k) {
+        prc = prepare_wave(g, st, k, s);
+        if (prc != SBG_OK) return prc;
+    }
     if (st->dtype != SBG_F32R) return step_n_plain(g, st, p, nsteps, s);
     int64_t done = 0;
     while (done < nsteps) {
@@ -591,10 +619,13 @@ static sbg_status step_n_plain(sbg_grid g, sbg_state st, const sbg_params *p, in
             done += kGraphSteps;
         }
     }
-    for (; done < nsteps; ++done) {
-        sbg_status rc = launch_step(g, st, p, st->cur, s);
+    const int k = steps_per_launch(g, st);
+    while (done < nsteps) {
+        const int m = nsteps - done >= k ? k : 1;
+        sbg_status rc = launch_steps(g, st, p, st->cur, m, s);
         if (rc != SBG_OK) return rc;
         st->cur = 1 - st->cur;
+        done += m;
     }
     return SBG_OK;
 }
@@ -622,9 +653,9 @@ extern "C" sbg_status sbg_step(sbg_grid g, sbg_state st, const sbg_params *p, in
 
 extern "C" sbg_status sbg_state_set_kernel(sbg_state st, int32_t variant, int32_t ctas_per_sm) {
     if (!st) return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: null state");
-    if (variant < SBG_KERNEL_AUTO || variant > SBG_KERNEL_STREAM || ctas_per_sm < 0 || ctas_per_sm > 64)
+    if (variant < SBG_KERNEL_AUTO || variant > SBG_KERNEL_WAVE4 || ctas_per_sm < 0 || ctas_per_sm > 64)
         return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: bad variant or ctas_per_sm");
-    if (variant >= SBG_KERNEL_PIPELINED && variant != SBG_KERNEL_STREAM && st->dtype == SBG_F64)
+    if (variant >= SBG_KERNEL_PIPELINED && variant < SBG_KERNEL_STREAM && st->dtype == SBG_F64)
         return fail(SBG_ERR_INVALID_ARG, "sbg_state_set_kernel: no pipelined kernel for FP64 states");
     st->variant = variant;
     st->ctas_per_sm = ctas_per_sm;

@@ -205,6 +205,20 @@ inline int halo_variant_of(int variant) {
 bool stream_kernel_applies(sbg_grid g, sbg_state st);
 cudaError_t launch_step_stream(const StepArgs &a, sbg_grid g, int ns, bool react, int ctas_per_sm, cudaStream_t s);
 
+// Wavefront kernel (sbg_step_stream.cu): K steps per launch of the streaming
+// kernel's states on a plane-ordered grid of one geometry, the intermediate
+// steps in L2-sized plane rings.  prepare_wave builds the state's plan (host
+// synchronisation; call it before any stream capture); launch_step_wave runs
+// K steps from a.in into a.out; wave_destroy frees the plan.
+bool wave_kernel_applies(sbg_grid g, sbg_state st);
+sbg_status prepare_wave(sbg_grid g, sbg_state st, int K, cudaStream_t s);
+cudaError_t launch_step_wave(const StepArgs &a, sbg_grid g, sbg_state st, bool react, cudaStream_t s);
+// The ticket order of a wavefront launch over planes of the given block
+// counts, in tickets of up to ticket_blocks blocks: false when some ticket would wait on a later
+// one (or bad K, L, R, ticket_blocks).
+bool wave_plan_tickets(const std::vector<int> &blocks_per_plane, int K, int L, int R, int ticket_blocks,
+                       std::vector<int4> &tick, std::vector<int4> &plane, int &maxplane);
+
 // One adjoint step on FP32 arrays with the pipelined kernel: io.src = lambda^{n+1}
 // (NS arrays) then u^n (NS arrays), io.dst = lambda^n.  *grid_out receives the
 // number of CTAs (each adds to io.gsum[cta * 3 + q]); at most max_ctas are used.
