@@ -575,12 +575,15 @@ def step_kernel_name(ns, variant):
     return two_array_kernel(variant) if ns == 2 else ("k_step" if variant == "plain" else "k_step_rows2")
 
 
-STREAM_SOURCES = ["paper_2304_11165_b300/csrc/sbg_step_stream.cu", "paper_2304_11165_b300/csrc/sbg_step.cuh"]
+STREAM_SOURCES = ["paper_2304_11165_b300/csrc/sbg_step_stream.cu", "paper_2304_11165_b300/csrc/sbg_row.cuh",
+                  "paper_2304_11165_b300/csrc/sbg_step.cuh"]
+WAVE_SOURCES = ["paper_2304_11165_b300/csrc/sbg_step_wave.cu", "paper_2304_11165_b300/csrc/sbg_row.cuh",
+                "paper_2304_11165_b300/csrc/sbg_step.cuh", "paper_2304_11165_b300/csrc/sbg_ptx.cuh"]
 
 
 def step_kernel_sources(kernel_name):
     """Source files whose hash keys a committed ncu summary of that kernel."""
-    return STREAM_SOURCES if kernel_name in ("k_step_stream", "k_step_wave") else KERNEL_SOURCES
+    return {"k_step_stream": STREAM_SOURCES, "k_step_wave": WAVE_SOURCES}.get(kernel_name, KERNEL_SOURCES)
 
 
 def steps_per_launch(variant):

@@ -112,3 +112,24 @@ def test_empty_geometry_and_all_solid_state():
     st = State(g, 2, "f32").set_kernel("stream").set_all(np.zeros((2,) + phi.shape))
     st.step(make_params(phys), 5)
     assert np.all(st.get_all() == 0)
+
+
+def test_kernels_can_be_mixed_on_a_copied_state():
+    """A state filled by a copy (its other buffer never written), stepped by
+    the streaming kernel, then by the plain kernel (which reads every slot
+    the streaming kernel wrote), then by the streaming kernel again, gives
+    the plain kernel's fields bitwise, and its check counts no non-finite
+    voxel."""
+    phi, phys, u0 = case((45, 38, 41), 2, 0.6, (0,), 26, porosity=0.35)
+    p = make_params(phys)
+    g = Grid(phi, block=4, order="planes")
+    ref = State(g, 2, "f32").set_kernel("plain").set_all(u0).step(p, 19).get_all()
+    src = State(g, 2, "f32").set_all(u0)
+    st = State(g, 2, "f32").copy_from(src)
+    st.set_kernel("stream").step(p, 7)
+    st.set_kernel("plain").step(p, 5)
+    st.set_kernel("stream").step(p, 7)
+    np.testing.assert_array_equal(st.get_all(), ref)
+    r = st.reduce(p)
+    assert r[0]["nonfinite"] == 0 and r[1]["nonfinite"] == 0
+
