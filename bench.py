@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--dtype", default="f32r", choices=["f32", "f32x2", "f32r"])
     ap.add_argument("--variant", default=None,
                     choices=["auto", "plain", "pipelined", "prefetch", "async", "stream", "wave", "wave4"],
-                    help="step kernel (default: stream for reactive512, async for the others)")
+                    help="step kernel (default: stream for reactive512 and grf256, async for the others)")
     ap.add_argument("--order", default=None, choices=["tiled", "planes"],
                     help="block order of the grid (default: planes for reactive512, tiled for the others)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -459,12 +459,15 @@ def run_grf256(args):
     d_eff, tau, psi = st.effective_D(p, stream=stream)
     if args.variant == "plain":
         kernel_name = "k_step_x2" if args.dtype == "f32x2" else "k_step"
+    elif args.variant == "stream" and args.dtype in ("f32", "f32r") and args.block == 4:
+        kernel_name = "k_step_stream"
     else:  # the two-rows-per-thread kernel: single-array modes, and SBG_F32X2 with cp.async halos
         rows2 = (args.dtype in ("f32", "f32r") and args.variant != "prefetch") or args.variant == "async"
         kernel_name = "k_step_rows2" if rows2 else "k_step_pipe"
     traffic = None
     if (n, args.block) == (256, 4):
-        traffic = profile_traffic("%s_%s_%s_grf256.md" % (kernel_name, args.variant, args.dtype))
+        traffic = profile_traffic("%s_%s_%s_grf256.md" % (kernel_name, args.variant, args.dtype),
+                                  step_kernel_sources(kernel_name))
     line = {
         "metric": METRIC, "value": value, "unit": "GVox/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -1335,7 +1338,7 @@ def run_batch64(args):
 def main():
     args = parse()
     if args.variant is None:
-        args.variant = "stream" if args.workload == "reactive512" else "async"
+        args.variant = "stream" if args.workload in ("reactive512", "grf256") else "async"
     if args.order is None:
         args.order = "planes" if args.workload == "reactive512" else "tiled"
     if args.steps is None:

@@ -40,7 +40,10 @@ namespace sbg {
 
 constexpr int kStreamThreads = 256;  // 16 blocks x 16 rows of 4 voxels
 
-template <int NS, bool REACT, bool HELD, int MINB>
+// SRC: the correction d of an SBG_F32R state (one species, no surface
+// reaction): the stored source r = L_h b of the row takes the place of the
+// transfer term, d' = d + dt (L_h d - decay d + r), as in the plain kernel.
+template <int NS, bool REACT, bool HELD, int MINB, bool SRC = false>
 __global__ void __launch_bounds__(kStreamThreads, MINB)
 k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__restrict__ wrow, float negzero, int *err,
               int n_wrows) {
@@ -135,6 +138,11 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
 #pragma unroll
         for (int i = 0; i < 4; ++i) keep[i] = ((held >> i) & 1u) ? ~0u : 0u;
         f32x2 tr01 = 0ull, tr23 = 0ull;  // the surface transfer k w u_A, from species A's pass
+        if (SRC) {
+            const float4 r4 = valid ? ldg4(a.src_term + (row - 64)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            tr01 = pk(r4.x, r4.y);
+            tr23 = pk(r4.z, r4.w);
+        }
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const float *q = gb[s];
@@ -155,8 +163,8 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
             // as a kernel argument: an addend the compiler knows to be -0 would let it turn the
             // packed fma of the decay term into a product and fuse it with the add that follows,
             // which rounds once where the plain kernel rounds twice
-            const f32x2 t01 = s == 0 ? (REACT ? pk(-ta, -tb) : pk(negzero, negzero)) : tr01;
-            const f32x2 t23 = s == 0 ? (REACT ? pk(-tc, -td) : pk(negzero, negzero)) : tr23;
+            const f32x2 t01 = SRC ? tr01 : s == 0 ? (REACT ? pk(-ta, -tb) : pk(negzero, negzero)) : tr01;
+            const f32x2 t23 = SRC ? tr23 : s == 0 ? (REACT ? pk(-tc, -td) : pk(negzero, negzero)) : tr23;
             const float4 r = row_update(c, xm, xp, ym, yp, zm, zp, a.cf.c[s], a.cf.dt, a.cf.decay[s], t01, t23, keep);
             if (valid) *reinterpret_cast<float4 *>(out[s] + (row - 64)) = r;
         }
@@ -164,11 +172,11 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
     }
 }
 
-template <int NS, bool REACT, bool HELD>
+template <int NS, bool REACT, bool HELD, bool SRC = false>
 static cudaError_t launch_stream_t(const StepArgs &a, const int2 *wmeta, const float4 *wrow, int ctas_per_sm,
                                    int *err, int n_wrows, cudaStream_t s) {
     constexpr int MINB = 3;
-    auto kern = k_step_stream<NS, REACT, HELD, MINB>;
+    auto kern = k_step_stream<NS, REACT, HELD, MINB, SRC>;
     static int occ = -1, nsm = 0;
     if (occ < 0) {
         int dev = 0;
@@ -188,8 +196,9 @@ static cudaError_t launch_stream_t(const StepArgs &a, const int2 *wmeta, const f
 }
 
 bool stream_kernel_applies(sbg_grid g, sbg_state st) {
-    return st->dtype == SBG_F32 && (st->ns == 1 || st->ns == 2) && g->B == 4 && st->has_ghost && !g->has_eps &&
-           g->wmeta != nullptr && (g->nb + 2) * 64 < (int64_t(1) << 31);
+    const bool kind = (st->dtype == SBG_F32 && (st->ns == 1 || st->ns == 2)) || (st->dtype == SBG_F32R && st->ns == 1);
+    return kind && g->B == 4 && st->has_ghost && !g->has_eps && g->wmeta != nullptr &&
+           (g->nb + 2) * 64 < (int64_t(1) << 31);
 }
 
 cudaError_t launch_step_stream(const StepArgs &a, sbg_grid g, int ns, bool react, int ctas_per_sm,
@@ -199,6 +208,10 @@ cudaError_t launch_step_stream(const StepArgs &a, sbg_grid g, int ns, bool react
     const float4 *wr = g->wrow;
     int *err = g->err;
     const int nw = (int)std::min<int64_t>(g->n_wrows, INT32_MAX);
+    if (a.src_term) {  // SBG_F32R correction (the caller excludes a surface reaction)
+        return held ? launch_stream_t<1, false, true, true>(a, wm, wr, ctas_per_sm, err, nw, s)
+                    : launch_stream_t<1, false, false, true>(a, wm, wr, ctas_per_sm, err, nw, s);
+    }
     if (ns == 1) {
         if (react) return held ? launch_stream_t<1, true, true>(a, wm, wr, ctas_per_sm, err, nw, s)
                                : launch_stream_t<1, true, false>(a, wm, wr, ctas_per_sm, err, nw, s);

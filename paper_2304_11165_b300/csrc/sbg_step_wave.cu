@@ -526,7 +526,8 @@ constexpr int kWaveLag = SBG_WAVE_LAG;
 constexpr int kWaveRing = SBG_WAVE_RING;
 
 bool wave_kernel_applies(sbg_grid g, sbg_state st) {
-    return stream_kernel_applies(g, st) && g->order == SBG_ORDER_PLANES && g->n_geoms == 1 && g->nb > 0;
+    return st->dtype == SBG_F32 && stream_kernel_applies(g, st) && g->order == SBG_ORDER_PLANES && g->n_geoms == 1 &&
+           g->nb > 0;
 }
 
 void wave_destroy(sbg_state st) {
