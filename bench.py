@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--dtype", default="f32r", choices=["f32", "f32x2", "f32r"])
     ap.add_argument("--variant", default=None,
                     choices=["auto", "plain", "pipelined", "prefetch", "async", "stream", "wave", "wave4"],
-                    help="step kernel (default: stream for reactive512 and grf256, async for the others)")
+                    help="step kernel (default: stream for reactive512, grf256 and inhom512, async for the others)")
     ap.add_argument("--order", default=None, choices=["tiled", "planes"],
                     help="block order of the grid (default: planes for reactive512, tiled for the others)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -586,7 +586,8 @@ WAVE_SOURCES = ["paper_2304_11165_b300/csrc/sbg_step_wave.cu", "paper_2304_11165
 
 def step_kernel_sources(kernel_name):
     """Source files whose hash keys a committed ncu summary of that kernel."""
-    return {"k_step_stream": STREAM_SOURCES, "k_step_wave": WAVE_SOURCES}.get(kernel_name, KERNEL_SOURCES)
+    return {"k_step_stream": STREAM_SOURCES, "k_step_stream_inh": STREAM_SOURCES,
+            "k_step_wave": WAVE_SOURCES}.get(kernel_name, KERNEL_SOURCES)
 
 
 def steps_per_launch(variant):
@@ -598,7 +599,8 @@ def steps_per_launch(variant):
 def two_array_kernel(variant):
     """Step kernel of the FP32 modes with two haloed arrays (two species; u and
     the diffusivity factor) for a kernel variant."""
-    return {"plain": "k_step", "pipelined": "k_step_pipe", "prefetch": "k_step_pipe"}.get(variant, "k_step_rows2")
+    return {"plain": "k_step", "pipelined": "k_step_pipe", "prefetch": "k_step_pipe",
+            "stream": "k_step_stream_inh"}.get(variant, "k_step_rows2")
 
 
 # ---------------------------------------------------------------------------
@@ -951,7 +953,8 @@ def run_inhom512(args):
                        "achieved": algo_bytes / (per_launch_ms / 1e3) / 1e9,
                        "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                        "frac": algo_bytes / (per_launch_ms / 1e3) / 1e9 / peak,
-                       "traffic": profile_traffic("%s_%s_inhom512.md" % (two_array_kernel(args.variant), args.variant)),
+                       "traffic": profile_traffic("%s_%s_inhom512.md" % (two_array_kernel(args.variant), args.variant),
+                                                  step_kernel_sources(two_array_kernel(args.variant))),
                        "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": per_launch_ms * 1e3},
           "result": {"mass_start": red0[0]["mass"], "mass_end": masses[-1]},
           "clocks": clocks, "cpu_baseline": cpu})
@@ -1338,7 +1341,7 @@ def run_batch64(args):
 def main():
     args = parse()
     if args.variant is None:
-        args.variant = "stream" if args.workload in ("reactive512", "grf256") else "async"
+        args.variant = "stream" if args.workload in ("reactive512", "grf256", "inhom512") else "async"
     if args.order is None:
         args.order = "planes" if args.workload == "reactive512" else "tiled"
     if args.steps is None:

@@ -429,7 +429,7 @@ static void grid_free(sbg_grid g) {
     dfree(g->err);
     dfree(g->pad);
     dfree(g->heldbits);
-    dfree(g->eps);
+    dfree(g->eps ? g->eps - 64 : nullptr);  // the allocation starts with a ghost block
     dfree(g->eps64);
     dfree(g->wmeta);
     dfree(g->wrow);

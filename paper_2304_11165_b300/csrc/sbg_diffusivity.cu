@@ -60,11 +60,15 @@ static sbg_status set_eps(sbg_grid g, int geom, const void *dense, int dense_dty
         return fail(SBG_ERR_INVALID_ARG, "diffusivity factor: dense dtype must be SBG_F32 or SBG_F64");
     const int64_t slots = g->nb * g->b3();
     if (!g->eps) {
-        cudaError_t e = dmalloc((void **)&g->eps, sizeof(float) * (slots > 0 ? slots : 1));
+        // the FP32 factor is preceded by a ghost block of zeros (block id -1, the factor of an absent
+        // neighbour block for the streaming kernel; any finite value gives the same result there)
+        float *base = nullptr;
+        cudaError_t e = dmalloc((void **)&base, sizeof(float) * (64 + (slots > 0 ? slots : 1)));
+        if (e == cudaSuccess) g->eps = base + 64;
         if (e == cudaSuccess) e = dmalloc((void **)&g->eps64, sizeof(double) * (slots > 0 ? slots : 1));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (diffusivity factor)");
-        g->bytes += (int64_t)(12 * slots);
-        SBG_CUDA(cudaMemsetAsync(g->eps, 0, sizeof(float) * (slots > 0 ? slots : 1), s));
+        g->bytes += (int64_t)(12 * slots + 256);
+        SBG_CUDA(cudaMemsetAsync(base, 0, sizeof(float) * (64 + (slots > 0 ? slots : 1)), s));
         SBG_CUDA(cudaMemsetAsync(g->eps64, 0, sizeof(double) * (slots > 0 ? slots : 1), s));
     }
     const int64_t nx = g->dims[3 * geom], ny = g->dims[3 * geom + 1], nz = g->dims[3 * geom + 2];

@@ -112,7 +112,8 @@ struct sbg_grid_s {
     double *red_dev = nullptr;     // [kNumRed]
     double *red_host = nullptr;    // pinned [kNumRed]
     float *pad = nullptr;          // 16-byte-aligned page: 4 sentinels then 4 zeros (absent halo neighbours)
-    float *eps = nullptr;          // [nb * B^3] diffusivity factor (inhomogeneous diffusion), FP32
+    float *eps = nullptr;          // [nb * B^3] diffusivity factor (inhomogeneous diffusion), FP32, preceded
+                                   // by a ghost block of zeros (eps - 64, the start of its allocation)
     double *eps64 = nullptr;       // the same in FP64 (FP64 states, reductions of them)
     bool has_eps = false;
     float eps_max = 0.f;           // largest factor on an active voxel (stability limit)

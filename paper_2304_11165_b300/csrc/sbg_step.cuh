@@ -204,6 +204,10 @@ inline int halo_variant_of(int variant) {
 // species on 4^3 blocks with ghost blocks, no diffusivity factor, no work list.
 bool stream_kernel_applies(sbg_grid g, sbg_state st);
 cudaError_t launch_step_stream(const StepArgs &a, sbg_grid g, int ns, bool react, int ctas_per_sm, cudaStream_t s);
+// The streaming kernel's inhomogeneous-diffusion form: SBG_F32 states of one
+// species on 4^3 blocks with a diffusivity factor.
+bool stream_inh_applies(sbg_grid g, sbg_state st);
+cudaError_t launch_step_stream_inh(const StepArgs &a, sbg_grid g, int ctas_per_sm, cudaStream_t s);
 
 // Wavefront kernel (sbg_step_stream.cu): K steps per launch of the streaming
 // kernel's states on a plane-ordered grid of one geometry, the intermediate

@@ -172,6 +172,135 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
     }
 }
 
+// Inhomogeneous diffusion (the functor of Appendix B Listing 6 with the Eq. 6
+// factor, one FP32 species): the same group walk and row reads, for the state
+// u and for the diffusivity factor eps at the same offsets (an absent
+// neighbour block reads the ghost blocks: sentinels for u, zeros for eps).
+// Per voxel the plain kernel's inh_update: face fluxes with the mean of the
+// two factors, a neighbour outside Omega (sentinel u) giving a zero
+// difference; the x differences of a row are formed once and shared.
+template <bool HELD, int MINB>
+__global__ void __launch_bounds__(kStreamThreads, MINB)
+k_step_stream_inh(const StepArgs a, int *err) {
+    const int t = threadIdx.x;
+    const int j = t >> 4, rr = t & 15, y = rr & 3, z = rr >> 2;
+    const int nb = (int)a.nb;  // the launcher guarantees (nb + 2) * 64 < 2^31
+    const int ngroups = (nb + 15) >> 4;
+    const int G = (int)gridDim.x;
+    const float *gu = (const float *)a.in[0] - 64;
+    const float *ge = a.eps - 64;
+    float *out = (float *)a.out[0];
+    const int oxm = 64 + rr * 4 + 3, oxp = 64 + rr * 4;
+    const int oym = 64 + rr * 4 + 12, oyp = 64 + rr * 4 - 12;
+    const int ozm = 64 + rr * 4 + 48, ozp = 64 + rr * 4 - 48;
+    struct Meta {
+        int f[4];
+        uint32_t held;
+    };
+    auto load_meta = [&](int gi, Meta &m) {
+        const int b = gi * 16 + j;
+        if (gi < ngroups && b < nb) {
+            const int32_t *fp = a.face + (int64_t)b * 6;
+            m.f[0] = __ldg(fp + 0);
+            m.f[1] = __ldg(fp + 1);
+            m.f[2] = (y == 0) ? __ldg(fp + 2) : (y == 3) ? __ldg(fp + 3) : -1;
+            m.f[3] = (z == 0) ? __ldg(fp + 4) : (z == 3) ? __ldg(fp + 5) : -1;
+            m.held = HELD ? (uint32_t)(__ldg(a.heldbits + b) >> (rr * 4)) & 0xFu : 0u;
+#if SBG_DEBUG
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (m.f[k] < -1 || m.f[k] >= nb) {
+                    atomicExch(err, (int)SBG_ERR_BOUNDS);
+                    m.f[k] = -1;
+                }
+#endif
+        } else {
+            m.f[0] = m.f[1] = m.f[2] = m.f[3] = -1;
+            m.held = 0;
+        }
+    };
+    (void)err;
+    Meta cur, nxt;
+    load_meta(blockIdx.x, cur);
+    for (int gi = blockIdx.x; gi < ngroups; gi += G) {
+        const int *f = cur.f;
+        const uint32_t held = cur.held;
+        const int b = gi * 16 + j;
+        const bool valid = b < nb;
+        const int row = valid ? (b + 1) * 64 + rr * 4 : rr * 4;
+        const int o_xm = f[0] * 64 + oxm;
+        const int o_xp = f[1] * 64 + oxp;
+        const int o_ym = y > 0 ? row - 4 : f[2] * 64 + oym;
+        const int o_yp = y < 3 ? row + 4 : f[2] * 64 + oyp;
+        const int o_zm = z > 0 ? row - 16 : f[3] * 64 + ozm;
+        const int o_zp = z < 3 ? row + 16 : f[3] * 64 + ozp;
+        const float4 c = ldg4(gu + row);
+        const float4 ym = ldg4(gu + o_ym), yp = ldg4(gu + o_yp);
+        const float4 zm = ldg4(gu + o_zm), zp = ldg4(gu + o_zp);
+        const float xm = __ldg(gu + o_xm), xp = __ldg(gu + o_xp);
+        const float4 ec = ldg4(ge + row);
+        const float4 eym = ldg4(ge + o_ym), eyp = ldg4(ge + o_yp);
+        const float4 ezm = ldg4(ge + o_zm), ezp = ldg4(ge + o_zp);
+        const float exm = __ldg(ge + o_xm), exp_ = __ldg(ge + o_xp);
+        load_meta(gi + G, nxt);  // the next group's tables, in flight while this one computes
+        const float R[6] = {xm, c.x, c.y, c.z, c.w, xp};
+        const float E[6] = {exm, ec.x, ec.y, ec.z, ec.w, exp_};
+        bool act[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) act[i] = !is_sent(R[i]);
+        float D[5];  // x differences R[i+1] - R[i], shared by neighbouring voxels
+#pragma unroll
+        for (int i = 0; i < 5; ++i) D[i] = __fsub_rn(R[i + 1], R[i]);
+        float res[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float u = R[i + 1];
+            const float nym = f4at(ym, i), nyp = f4at(yp, i), nzm = f4at(zm, i), nzp = f4at(zp, i);
+            const float vym = is_sent(nym) ? u : nym, vyp = is_sent(nyp) ? u : nyp;
+            const float vzm = is_sent(nzm) ? u : nzm, vzp = is_sent(nzp) ? u : nzp;
+            const float dp[3] = {act[i + 2] ? D[i + 1] : 0.f, __fsub_rn(vyp, u), __fsub_rn(vzp, u)};
+            const float dm[3] = {act[i] ? D[i] : 0.f, __fsub_rn(u, vym), __fsub_rn(u, vzm)};
+            const float en[6] = {E[i], E[i + 2], f4at(eym, i), f4at(eyp, i), f4at(ezm, i), f4at(ezp, i)};
+            const float nr = inh_update(u, dp, dm, E[i + 1], en, a.cf.c[0], a.cf.dt, a.cf.decay[0]);
+            res[i] = (act[i + 1] && !((held >> i) & 1u)) ? nr : u;
+        }
+        if (valid) *reinterpret_cast<float4 *>(out + (row - 64)) = make_float4(res[0], res[1], res[2], res[3]);
+        cur = nxt;
+    }
+}
+
+template <bool HELD>
+static cudaError_t launch_stream_inh_t(const StepArgs &a, int ctas_per_sm, int *err, cudaStream_t s) {
+    constexpr int MINB = 3;
+    auto kern = k_step_stream_inh<HELD, MINB>;
+    static int occ = -1, nsm = 0;
+    if (occ < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);  // all of it as L1
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStreamThreads, 0);
+        if (occ < 1) occ = 1;
+    }
+    const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
+    const int64_t ngroups = (a.nb + 15) / 16;
+    int64_t grid = (int64_t)nsm * per_sm;
+    if (grid > ngroups) grid = ngroups;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, kStreamThreads, 0, s>>>(a, err);
+    return cudaGetLastError();
+}
+
+bool stream_inh_applies(sbg_grid g, sbg_state st) {
+    return st->dtype == SBG_F32 && st->ns == 1 && g->B == 4 && st->has_ghost && g->has_eps && g->eps != nullptr &&
+           (g->nb + 2) * 64 < (int64_t(1) << 31);
+}
+
+cudaError_t launch_step_stream_inh(const StepArgs &a, sbg_grid g, int ctas_per_sm, cudaStream_t s) {
+    return a.held_mask ? launch_stream_inh_t<true>(a, ctas_per_sm, g->err, s)
+                       : launch_stream_inh_t<false>(a, ctas_per_sm, g->err, s);
+}
+
 template <int NS, bool REACT, bool HELD, bool SRC = false>
 static cudaError_t launch_stream_t(const StepArgs &a, const int2 *wmeta, const float4 *wrow, int ctas_per_sm,
                                    int *err, int n_wrows, cudaStream_t s) {

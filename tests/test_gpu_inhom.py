@@ -46,7 +46,7 @@ def test_fp32_kernels_match_the_oracle_and_each_other(block):
     phi, eps, ph, u0 = case((37, 29, 23), 12)
     ref = oracle.Problem(phi, ph, eps=eps).run(u0[None], 150)[0]
     outs = []
-    for variant in ("plain", "pipelined", "prefetch", "async"):
+    for variant in ("plain", "pipelined", "prefetch", "async", "stream"):
         g = Grid(phi, block=block).set_diffusivity(eps.astype(np.float32))
         st = State(g, 1, "f32").set_kernel(variant).set(u0)
         st.step(make_params(ph), 150)
@@ -71,6 +71,37 @@ def test_two_row_kernel_with_few_ctas(block):
     for per_sm in (1, 2, 0):
         b = State(g, 1, "f32").set_kernel("async", ctas_per_sm=per_sm).set(u0).step(p, 33).get()
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("order", ["tiled", "planes"])
+@pytest.mark.parametrize("per_sm", [1, 0])
+def test_streaming_kernel_with_a_factor(order, per_sm):
+    """u and the factor read by the streaming kernel (rows through L1, absent
+    neighbour blocks from the ghost blocks: sentinels for u, zeros for the
+    factor), with one or all CTAs per SM: the plain kernel's field bitwise."""
+    phi, eps, ph, u0 = case((64, 60, 56), 15)
+    g = Grid(phi, block=4, order=order).set_diffusivity(eps.astype(np.float32))
+    p = make_params(ph)
+    a = State(g, 1, "f32").set_kernel("plain").set(u0).step(p, 33).get()
+    b = State(g, 1, "f32").set_kernel("stream", ctas_per_sm=per_sm).set(u0).step(p, 33).get()
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (6, 1, 1), (1, 1, 9), (4, 4, 4), (17, 3, 2)])
+def test_streaming_kernel_with_a_factor_on_thin_boxes(dims):
+    rng = np.random.default_rng(sum(dims))
+    phi = np.where(rng.uniform(size=dims[::-1]) < 0.8, 1.0, -1.0).astype(np.float32)
+    phi.flat[0] = 1.0
+    eps = rng.uniform(0.2, 1.0, phi.shape).astype(np.float32)
+    ph = Physics(dims=dims, dt=0.02, D=(1.0, 0.0), decay=(0.01, 0.0))
+    u0 = rng.uniform(size=phi.shape)
+    g = Grid(phi, block=4).set_diffusivity(eps)
+    p = make_params(ph)
+    a = State(g, 1, "f32").set_kernel("plain").set(u0).step(p, 13).get()
+    b = State(g, 1, "f32").set_kernel("stream").set(u0).step(p, 13).get()
+    np.testing.assert_array_equal(a, b)
+    ref = oracle.Problem(phi, ph, eps=eps.astype(np.float64)).run(u0[None], 13)[0]
+    assert rel_err(b, ref) < 1e-5
 
 
 def test_eq6_factor_on_the_device_matches_the_oracle():
