@@ -258,8 +258,8 @@ sbg_status sbg_step_source(sbg_grid grid, sbg_state state, const sbg_params *par
 /* Step-kernel choice for a state (this library's tuning knob; no
  * counterpart in the paper).  variant: SBG_KERNEL_AUTO (the streaming kernel
  * where it applies: SBG_F32 states of one or two species, SBG_F32R states
- * without a surface reaction, and SBG_F32 states of one species with a
- * diffusivity factor, on 4^3 blocks; else
+ * without a surface reaction, SBG_F32 states of one species with a
+ * diffusivity factor, and SBG_F32X2 states, on 4^3 blocks; else
  * the pipelined kernel with cp.async halos where it exists, else the
  * one-thread-per-voxel kernel), SBG_KERNEL_PLAIN
  * (one thread per voxel, block tile in shared memory, one launch-sized grid)
@@ -276,8 +276,9 @@ sbg_status sbg_step_source(sbg_grid grid, sbg_state state, const sbg_params *par
  * z-paired rows per thread too, except in batched steps).  ctas_per_sm:
  * persistent CTAs per SM for the pipelined kernel (0 = as many as fit).
  * SBG_KERNEL_STREAM (SBG_F32 states of one or two species, SBG_F32R states
- * without a surface reaction, and one FP32 species with a diffusivity factor
- * (u and the factor read at the same offsets), on 4^3 blocks:
+ * without a surface reaction, one FP32 species with a diffusivity factor
+ * (u and the factor read at the same offsets) and SBG_F32X2 states (hi and
+ * lo read at the same offsets), on 4^3 blocks:
  * CTAs take groups of 16 blocks in turn, one
  * x-row of four voxels per thread, every neighbour row read straight from
  * global memory through L1; best with SBG_ORDER_PLANES grids, whose plane

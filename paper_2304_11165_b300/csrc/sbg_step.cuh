@@ -207,6 +207,9 @@ cudaError_t launch_step_stream(const StepArgs &a, sbg_grid g, int ns, bool react
 // The streaming kernel's inhomogeneous-diffusion form: SBG_F32 states of one
 // species on 4^3 blocks with a diffusivity factor.
 bool stream_inh_applies(sbg_grid g, sbg_state st);
+// ... and its compensated form: SBG_F32X2 states (one species) on 4^3 blocks.
+bool stream_x2_applies(sbg_grid g, sbg_state st);
+cudaError_t launch_step_stream_x2(const StepArgs &a, sbg_grid g, bool react, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_step_stream_inh(const StepArgs &a, sbg_grid g, int ctas_per_sm, cudaStream_t s);
 
 // Wavefront kernel (sbg_step_stream.cu): K steps per launch of the streaming

@@ -269,6 +269,166 @@ k_step_stream_inh(const StepArgs a, int *err) {
     }
 }
 
+// Compensated FP32 state (SBG_F32X2, value = hi + lo, one species): hi and lo
+// rows read at the same offsets, a neighbour outside Omega (sentinel hi)
+// taking the centre's hi and lo, and per voxel the plain kernel's
+// fused_update_x2 (error-free products and sums, the increment added with a
+// two-sum).  The lo array follows the hi array in the state's allocation, so
+// the 64 values before it (an absent neighbour's lo, never used: the mirror
+// replaces it) are the hi array's last block.
+template <bool REACT, bool HELD, int MINB>
+__global__ void __launch_bounds__(kStreamThreads, MINB)
+k_step_stream_x2(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__restrict__ wrow, int *err,
+                 int n_wrows) {
+    const int t = threadIdx.x;
+    const int j = t >> 4, rr = t & 15, y = rr & 3, z = rr >> 2;
+    const int nb = (int)a.nb;  // the launcher guarantees (nb + 2) * 64 < 2^31
+    const int ngroups = (nb + 15) >> 4;
+    const int G = (int)gridDim.x;
+    const float *gh = (const float *)a.in[0] - 64;
+    const float *gl = a.in_lo[0] - 64;
+    float *oh = (float *)a.out[0];
+    float *ol = a.out_lo[0];
+    const int oxm = 64 + rr * 4 + 3, oxp = 64 + rr * 4;
+    const int oym = 64 + rr * 4 + 12, oyp = 64 + rr * 4 - 12;
+    const int ozm = 64 + rr * 4 + 48, ozp = 64 + rr * 4 - 48;
+    struct Meta {
+        int f[4];
+        int woff;
+        uint32_t wmask, held;
+    };
+    auto load_meta = [&](int gi, Meta &m) {
+        const int b = gi * 16 + j;
+        if (gi < ngroups && b < nb) {
+            const int32_t *fp = a.face + (int64_t)b * 6;
+            m.f[0] = __ldg(fp + 0);
+            m.f[1] = __ldg(fp + 1);
+            m.f[2] = (y == 0) ? __ldg(fp + 2) : (y == 3) ? __ldg(fp + 3) : -1;
+            m.f[3] = (z == 0) ? __ldg(fp + 4) : (z == 3) ? __ldg(fp + 5) : -1;
+            if (REACT) {
+                const int2 wm = __ldg(wmeta + b);
+                m.woff = wm.x;
+                m.wmask = (uint32_t)wm.y;
+            } else {
+                m.woff = 0;
+                m.wmask = 0;
+            }
+            m.held = HELD ? (uint32_t)(__ldg(a.heldbits + b) >> (rr * 4)) & 0xFu : 0u;
+#if SBG_DEBUG
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (m.f[k] < -1 || m.f[k] >= nb) {
+                    atomicExch(err, (int)SBG_ERR_BOUNDS);
+                    m.f[k] = -1;
+                }
+#endif
+        } else {
+            m.f[0] = m.f[1] = m.f[2] = m.f[3] = -1;
+            m.woff = 0;
+            m.wmask = 0;
+            m.held = 0;
+        }
+    };
+    (void)err;
+    (void)n_wrows;
+    Meta cur, nxt;
+    load_meta(blockIdx.x, cur);
+    for (int gi = blockIdx.x; gi < ngroups; gi += G) {
+        const int *f = cur.f;
+        const uint32_t held = cur.held;
+        const int b = gi * 16 + j;
+        const bool valid = b < nb;
+        const int row = valid ? (b + 1) * 64 + rr * 4 : rr * 4;
+        const int o_xm = f[0] * 64 + oxm;
+        const int o_xp = f[1] * 64 + oxp;
+        const int o_ym = y > 0 ? row - 4 : f[2] * 64 + oym;
+        const int o_yp = y < 3 ? row + 4 : f[2] * 64 + oyp;
+        const int o_zm = z > 0 ? row - 16 : f[3] * 64 + ozm;
+        const int o_zp = z < 3 ? row + 16 : f[3] * 64 + ozp;
+        float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (REACT && valid && ((cur.wmask >> rr) & 1u)) {
+            const int wi = cur.woff + __popc(cur.wmask & ((1u << rr) - 1u));
+#if SBG_DEBUG
+            if (wi < 0 || wi >= n_wrows) atomicExch(err, (int)SBG_ERR_BOUNDS);
+            else
+#endif
+                w4 = __ldg(wrow + wi);
+        }
+        const float4 hc = ldg4(gh + row), lc = ldg4(gl + row);
+        const float4 hym = ldg4(gh + o_ym), hyp = ldg4(gh + o_yp), hzm = ldg4(gh + o_zm), hzp = ldg4(gh + o_zp);
+        const float4 lym = ldg4(gl + o_ym), lyp = ldg4(gl + o_yp), lzm = ldg4(gl + o_zm), lzp = ldg4(gl + o_zp);
+        const float hxm = __ldg(gh + o_xm), hxp = __ldg(gh + o_xp);
+        const float lxm = __ldg(gl + o_xm), lxp = __ldg(gl + o_xp);
+        load_meta(gi + G, nxt);  // the next group's tables, in flight while this one computes
+        const float H[6] = {hxm, hc.x, hc.y, hc.z, hc.w, hxp};
+        const float L[6] = {lxm, lc.x, lc.y, lc.z, lc.w, lxp};
+        float rh[4], rl[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float c0 = H[i + 1], c1 = L[i + 1];
+            const float h[6] = {H[i], H[i + 2], f4at(hym, i), f4at(hyp, i), f4at(hzm, i), f4at(hzp, i)};
+            const float l[6] = {L[i], L[i + 2], f4at(lym, i), f4at(lyp, i), f4at(lzm, i), f4at(lzp, i)};
+            float nh[6], nl[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const bool out = is_sent(h[q]);
+                nh[q] = out ? c0 : h[q];
+                nl[q] = out ? c1 : l[q];
+            }
+            float rate = a.cf.decay[0];
+            if (REACT) rate = __fmaf_rn(a.cf.k, f4at(w4, i), rate);
+            float vh, vl;
+            fused_update_x2(c0, c1, nh, nl, a.cf.c[0], a.cf.dt, rate, vh, vl);
+            const bool upd = !is_sent(c0) && !((held >> i) & 1u);
+            rh[i] = upd ? vh : c0;
+            rl[i] = upd ? vl : c1;
+        }
+        if (valid) {
+            *reinterpret_cast<float4 *>(oh + (row - 64)) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+            *reinterpret_cast<float4 *>(ol + (row - 64)) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+        }
+        cur = nxt;
+    }
+}
+
+template <bool REACT, bool HELD>
+static cudaError_t launch_stream_x2_t(const StepArgs &a, const int2 *wmeta, const float4 *wrow, int ctas_per_sm,
+                                      int *err, int n_wrows, cudaStream_t s) {
+    constexpr int MINB = 3;
+    auto kern = k_step_stream_x2<REACT, HELD, MINB>;
+    static int occ = -1, nsm = 0;
+    if (occ < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);  // all of it as L1
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStreamThreads, 0);
+        if (occ < 1) occ = 1;
+    }
+    const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
+    const int64_t ngroups = (a.nb + 15) / 16;
+    int64_t grid = (int64_t)nsm * per_sm;
+    if (grid > ngroups) grid = ngroups;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, kStreamThreads, 0, s>>>(a, wmeta, wrow, err, n_wrows);
+    return cudaGetLastError();
+}
+
+bool stream_x2_applies(sbg_grid g, sbg_state st) {
+    return st->dtype == SBG_F32X2 && st->ns == 1 && g->B == 4 && st->has_ghost && !g->has_eps &&
+           g->wmeta != nullptr && (g->nb + 2) * 64 < (int64_t(1) << 31) &&
+           st->lo[0][0] == (float *)st->val[0][0] + st->nslots && st->lo[1][0] == (float *)st->val[1][0] + st->nslots;
+}
+
+cudaError_t launch_step_stream_x2(const StepArgs &a, sbg_grid g, bool react, int ctas_per_sm, cudaStream_t s) {
+    const bool held = a.held_mask != 0;
+    const int nw = (int)std::min<int64_t>(g->n_wrows, INT32_MAX);
+    if (react) return held ? launch_stream_x2_t<true, true>(a, g->wmeta, g->wrow, ctas_per_sm, g->err, nw, s)
+                           : launch_stream_x2_t<true, false>(a, g->wmeta, g->wrow, ctas_per_sm, g->err, nw, s);
+    return held ? launch_stream_x2_t<false, true>(a, g->wmeta, g->wrow, ctas_per_sm, g->err, nw, s)
+                : launch_stream_x2_t<false, false>(a, g->wmeta, g->wrow, ctas_per_sm, g->err, nw, s);
+}
+
 template <bool HELD>
 static cudaError_t launch_stream_inh_t(const StepArgs &a, int ctas_per_sm, int *err, cudaStream_t s) {
     constexpr int MINB = 3;

@@ -279,7 +279,7 @@ def test_pipelined_kernel_is_bitwise_the_plain_kernel(block, dtype, ns, k):
     phi, phys, u0 = make_case((37, 29, 23), ns, k, (0, 1), 11)
     p = make_params(phys)
     outs = []
-    for variant in ("plain", "pipelined", "prefetch", "async"):
+    for variant in ("plain", "pipelined", "prefetch", "async", "stream"):
         g = Grid(phi, block=block)
         st = State(g, ns, dtype).set_kernel(variant).set_all(u0)
         st.step(p, 77)
@@ -331,3 +331,6 @@ def test_compensated_two_row_kernel_with_few_ctas(block):
     for per_sm in (1, 2, 0):
         b = State(g, 1, "f32x2").set_kernel("async", ctas_per_sm=per_sm).set_all(u0).step(p, 29).get_all()
         np.testing.assert_array_equal(a, b)
+        # the streaming kernel's compensated form (hi and lo rows at the same offsets)
+        c = State(g, 1, "f32x2").set_kernel("stream", ctas_per_sm=per_sm).set_all(u0).step(p, 29).get_all()
+        np.testing.assert_array_equal(a, c)
