@@ -459,8 +459,8 @@ def run_grf256(args):
     d_eff, tau, psi = st.effective_D(p, stream=stream)
     if args.variant == "plain":
         kernel_name = "k_step_x2" if args.dtype == "f32x2" else "k_step"
-    elif args.variant == "stream" and args.dtype in ("f32", "f32r") and args.block == 4:
-        kernel_name = "k_step_stream"
+    elif args.variant == "stream" and args.block == 4:
+        kernel_name = "k_step_stream_x2" if args.dtype == "f32x2" else "k_step_stream"
     else:  # the two-rows-per-thread kernel: single-array modes, and SBG_F32X2 with cp.async halos
         rows2 = (args.dtype in ("f32", "f32r") and args.variant != "prefetch") or args.variant == "async"
         kernel_name = "k_step_rows2" if rows2 else "k_step_pipe"
@@ -586,7 +586,7 @@ WAVE_SOURCES = ["paper_2304_11165_b300/csrc/sbg_step_wave.cu", "paper_2304_11165
 
 def step_kernel_sources(kernel_name):
     """Source files whose hash keys a committed ncu summary of that kernel."""
-    return {"k_step_stream": STREAM_SOURCES, "k_step_stream_inh": STREAM_SOURCES,
+    return {"k_step_stream": STREAM_SOURCES, "k_step_stream_inh": STREAM_SOURCES, "k_step_stream_x2": STREAM_SOURCES,
             "k_step_wave": WAVE_SOURCES}.get(kernel_name, KERNEL_SOURCES)
 
 
