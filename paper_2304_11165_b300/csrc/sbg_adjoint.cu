@@ -39,6 +39,8 @@ struct sbg_tape_s {
     sbg_dtype dtype = SBG_F32;
     int64_t nsteps = 0, K = 1;
     size_t state_bytes = 0;          // one species-set of one state, bytes
+    size_t ghost_bytes = 0;          // the ghost block before each species array of a buffer
+    size_t buf_bytes = 0;            // one buffer: per species a ghost block and the array
     std::vector<void *> ckpt;        // states at n = 0, K, 2K, ...
     std::vector<void *> seg;         // recompute buffer: up to K states
     double *partials = nullptr;      // per-CTA sums, accumulated over the adjoint steps
@@ -51,6 +53,21 @@ namespace sbg {
 
 sbg_status step_n(sbg_grid g, sbg_state st, const sbg_params *p, int64_t nsteps, cudaStream_t s);
 sbg_status launch_step(sbg_grid g, sbg_state st, const sbg_params *p, int src, cudaStream_t s);
+
+// Tape buffers hold, per species, a ghost block of sentinels and then the
+// species array (the layout of a state's buffers, so that the streaming
+// kernels can step the recompute buffers).  Species sp of buffer `buf`:
+static void *tape_sp(const sbg_tape_s *tp, const void *buf, int sp) {
+    const size_t per = tp->state_bytes / tp->ns;
+    return (char *)buf + tp->ghost_bytes + (size_t)sp * (per + tp->ghost_bytes);
+}
+
+template <typename T>
+__global__ void k_tape_ghosts(T *base, int64_t stride_elems, int ns, int ghost_elems) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns * ghost_elems) return;
+    base[(int64_t)(i / ghost_elems) * stride_elems + i % ghost_elems] = sentinel<T>();
+}
 
 template <typename T>
 struct AdjArgs {
@@ -222,11 +239,10 @@ static sbg_status launch_adj_t(sbg_tape tp, const void *u, const void *const *li
     sbg_grid g = tp->grid;
     AdjArgs<T> a;
     fill_adj<T>(g, &tp->p, a);
-    const size_t per = (size_t)g->nb * g->b3();
     for (int sp = 0; sp < NS; ++sp) {
         a.lam_in[sp] = (const T *)lin[sp];
         a.lam_out[sp] = (T *)lout[sp];
-        a.u[sp] = (const T *)u + sp * per;
+        a.u[sp] = (const T *)tape_sp(tp, u, sp);
     }
     a.partials = tp->partials;
     const int64_t nctas = (g->nb + BPC - 1) / BPC;
@@ -287,14 +303,21 @@ static sbg_status launch_adj_pipe(sbg_tape tp, const void *u, sbg_state lam, cud
     fill_step_args(g, &tp->p, a);
     PipeIO io;
     std::memset(&io, 0, sizeof(io));
-    const size_t per = (size_t)g->nb * g->b3();
     for (int sp = 0; sp < tp->ns; ++sp) {
         io.src[sp] = (const float *)lam->val[lam->cur][sp];
-        io.src[tp->ns + sp] = (const float *)u + sp * per;
+        io.src[tp->ns + sp] = (const float *)tape_sp(tp, u, sp);
         io.dst[sp] = (float *)lam->val[1 - lam->cur][sp];
     }
     io.gsum = tp->partials;
     for (int ax = 0; ax < 3; ++ax) io.inv2[ax] = (float)(1.0 / (tp->p.dx[ax] * tp->p.dx[ax]));
+    if (tp->ns == 1 && adjoint_stream_applies(g, lam)) {
+        // the streaming form (lambda bitwise the ring kernel's; 4^3 blocks, one species)
+        cudaError_t e = launch_adjoint_stream(a, io.src[0], io.src[1], io.dst[0], tp->partials, io.inv2, g, true,
+                                              (int)tp->nctas, s);
+        if (e != cudaSuccess) return cuda_fail(e, "streaming adjoint kernel launch");
+        lam->cur = 1 - lam->cur;
+        return SBG_OK;
+    }
     int grid = 0;
     // the surface terms always: dL/dk is not 0 at k = 0 (and with k = 0 they leave lambda unchanged)
     cudaError_t e = launch_adjoint_pipe(a, io, tp->ns, g->B, true, (int)tp->nctas, g->err, s, &grid);
@@ -307,7 +330,7 @@ static sbg_status launch_adj_pipe(sbg_tape tp, const void *u, sbg_state lam, cud
 static sbg_status save_state(sbg_tape tp, sbg_state st, void *dst, cudaStream_t s) {
     const size_t per = tp->state_bytes / tp->ns;
     for (int sp = 0; sp < tp->ns; ++sp)
-        SBG_CUDA(cudaMemcpyAsync((char *)dst + sp * per, st->val[st->cur][sp], per, cudaMemcpyDeviceToDevice, s));
+        SBG_CUDA(cudaMemcpyAsync(tape_sp(tp, dst, sp), st->val[st->cur][sp], per, cudaMemcpyDeviceToDevice, s));
     return SBG_OK;
 }
 
@@ -319,13 +342,25 @@ static sbg_status step_packed(sbg_tape tp, const void *src, void *dst, cudaStrea
     view.ns = tp->ns;
     view.dtype = tp->dtype;
     view.nslots = (int64_t)(tp->state_bytes / tp->ns / (tp->dtype == SBG_F64 ? 8 : 4));
-    const size_t per = tp->state_bytes / tp->ns;
     for (int sp = 0; sp < tp->ns; ++sp) {
-        view.val[0][sp] = (char *)src + sp * per;
-        view.val[1][sp] = (char *)dst + sp * per;
+        view.val[0][sp] = tape_sp(tp, src, sp);
+        view.val[1][sp] = tape_sp(tp, dst, sp);
     }
+    view.has_ghost = true;  // the tape's buffers have a state's layout
     view.variant = SBG_KERNEL_AUTO;
     return launch_step(tp->grid, &view, &tp->p, 0, s);
+}
+
+// the ghost blocks of a new tape buffer hold the sentinel
+static sbg_status fill_tape_ghosts(sbg_tape tp, void *buf, cudaStream_t s) {
+    const int elem = tp->dtype == SBG_F64 ? 8 : 4;
+    const int ghost_elems = (int)(tp->ghost_bytes / elem);
+    const int64_t stride = (int64_t)((tp->state_bytes / tp->ns + tp->ghost_bytes) / elem);
+    const int n = tp->ns * ghost_elems;
+    if (elem == 8) k_tape_ghosts<double><<<(n + 255) / 256, 256, 0, s>>>((double *)buf, stride, tp->ns, ghost_elems);
+    else k_tape_ghosts<float><<<(n + 255) / 256, 256, 0, s>>>((float *)buf, stride, tp->ns, ghost_elems);
+    SBG_LAUNCH_CHECK("tape ghost blocks");
+    return SBG_OK;
 }
 
 static void tape_free(sbg_tape tp) {
@@ -360,6 +395,8 @@ extern "C" sbg_status sbg_forward_record(sbg_grid g, sbg_state st, const sbg_par
     tp->nsteps = nsteps;
     tp->K = checkpoint_every;
     tp->state_bytes = (size_t)st->nslots * st->elem() * st->ns;
+    tp->ghost_bytes = ((size_t)g->b3() * st->elem() + 255) / 256 * 256;
+    tp->buf_bytes = tp->state_bytes + (size_t)st->ns * tp->ghost_bytes;
     const int64_t nck = nsteps == 0 ? 1 : (nsteps + checkpoint_every - 1) / checkpoint_every;
     auto alloc = [&](void **pp, size_t bytes) -> sbg_status {
         cudaError_t e = dmalloc((void **)pp, bytes > 0 ? bytes : 16);
@@ -369,7 +406,8 @@ extern "C" sbg_status sbg_forward_record(sbg_grid g, sbg_state st, const sbg_par
     };
     for (int64_t c = 0; c < nck && rc == SBG_OK; ++c) {
         void *q = nullptr;
-        rc = alloc(&q, tp->state_bytes);
+        rc = alloc(&q, tp->buf_bytes);
+        if (rc == SBG_OK) rc = fill_tape_ghosts(tp, q, s);
         tp->ckpt.push_back(q);
         if (rc == SBG_OK) rc = save_state(tp, st, q, s);
         if (rc == SBG_OK) {
@@ -405,10 +443,12 @@ extern "C" sbg_status sbg_adjoint(sbg_grid g, sbg_tape tp, sbg_state lam, double
     // recompute buffers for u^{n0+1} .. u^{n0+K-1} (u^{n0} is the checkpoint itself)
     while ((int64_t)tp->seg.size() < std::min<int64_t>(K, std::max<int64_t>(tp->nsteps, 1)) - 1) {
         void *q = nullptr;
-        cudaError_t e = dmalloc((void **)&q, tp->state_bytes);
+        cudaError_t e = dmalloc((void **)&q, tp->buf_bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (tape recompute buffer)");
-        tp->bytes += (int64_t)tp->state_bytes;
+        tp->bytes += (int64_t)tp->buf_bytes;
         tp->seg.push_back(q);
+        rc = fill_tape_ghosts(tp, q, s);
+        if (rc != SBG_OK) return rc;
     }
     const int64_t nck = (int64_t)tp->ckpt.size();
     for (int64_t c = nck - 1; c >= 0 && rc == SBG_OK; --c) {

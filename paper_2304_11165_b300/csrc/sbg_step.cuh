@@ -226,6 +226,15 @@ cudaError_t launch_step_wave(const StepArgs &a, sbg_grid g, sbg_state st, bool r
 bool wave_plan_tickets(const std::vector<int> &blocks_per_plane, int K, int L, int R, int ticket_blocks,
                        std::vector<int4> &tick, std::vector<int4> &plane, int &maxplane);
 
+// One adjoint step of one FP32 species on 4^3 blocks with the streaming
+// structure (sbg_adjoint_stream.cu): lambda^{n+1} from a state (ghost block
+// before it), u^n from a tape buffer laid out the same way; each CTA adds its
+// sums of dL/dD and dL/dk to gsum[cta * 3 + 0 / 2]; at most max_ctas CTAs.
+bool adjoint_stream_applies(sbg_grid g, sbg_state lam);
+cudaError_t launch_adjoint_stream(const StepArgs &a, const float *lam_in, const float *u_in, float *lam_out,
+                                  double *gsum, const float inv2[3], sbg_grid g, bool react, int max_ctas,
+                                  cudaStream_t s);
+
 // One adjoint step on FP32 arrays with the pipelined kernel: io.src = lambda^{n+1}
 // (NS arrays) then u^n (NS arrays), io.dst = lambda^n.  *grid_out receives the
 // number of CTAs (each adds to io.gsum[cta * 3 + q]); at most max_ctas are used.
