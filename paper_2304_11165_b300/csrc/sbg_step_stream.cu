@@ -20,11 +20,13 @@
 //    global memory (16-byte loads through L1; rows of the same block are read
 //    by the same half-warp).  An absent neighbour block reads the state's
 //    ghost block (block id nb, all sentinels), so no pointer selects;
-//  - no explicit prefetch: the +x neighbour values a group reads sit in the
-//    blocks of the next groups, so every sweep pulls the rows of the sweep
-//    after it into L2 as a side effect (bulk L2 prefetches a few sweeps ahead
-//    measured 12-29% slower on the 512^3 two-species run: they compete for L2
-//    with the sweep in flight);
+//  - the +x neighbour values a group reads sit in the blocks of the next
+//    groups, so every sweep pulls the rows of the sweep after it into L2 as a
+//    side effect; beyond that, only a per-thread L2 prefetch of its own row
+//    of the next group (one sweep ahead) for two species and SBG_F32R states,
+//    the cases where it measured faster (bulk L2 prefetches a few sweeps
+//    ahead measured 12-29% slower on the 512^3 two-species run: they compete
+//    for L2 with the sweep in flight);
 //  - the face ids, band-row metadata and held bits of the next group are
 //    loaded while the current group computes.
 // The per-voxel arithmetic is the plain kernel's (sbg_step.cu) with every
@@ -134,6 +136,14 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
                 w4 = __ldg(wrow + wi);
         }
         load_meta(gi + G, nxt);  // the next group's tables, in flight while this one computes
+        if (NS == 2 || SRC) {  // this thread's row of the next group, one sweep ahead (measured: 1.3% faster on
+                               // the 512^3 two-species run, 1.8% for SBG_F32R on grf256; slower for the others)
+            const int bn = (gi + G) * 16 + j;
+            if (bn < nb) {
+#pragma unroll
+                for (int s = 0; s < NS; ++s) prefetch_l2(gb[s] + (bn + 1) * 64 + rr * 4);
+            }
+        }
         uint32_t keep[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) keep[i] = ((held >> i) & 1u) ? ~0u : 0u;
