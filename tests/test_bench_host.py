@@ -1,7 +1,7 @@
 """Host-side pieces of bench.py that shape the reported line: the traffic
 lookup keyed by the kernel sources, the roofline extras, the interval
-statistics, the kernel naming of the two-array modes and the replica
-throughput."""
+statistics, the kernel naming of the two-array, streaming and wavefront
+modes and the replica throughput."""
 import math
 
 import pytest
@@ -50,6 +50,22 @@ def test_kernel_names_of_the_two_array_modes():
     assert bench.two_array_kernel("pipelined") == "k_step_pipe"
     assert bench.two_array_kernel("prefetch") == "k_step_pipe"
     assert bench.two_array_kernel("plain") == "k_step"
+    assert bench.two_array_kernel("stream") == "k_step_stream_inh"
+
+
+def test_streaming_and_wavefront_kernels_are_named_and_keyed():
+    """The reactive bench names the streaming kernel (or the wavefront kernel,
+    which runs 2 or 4 steps per launch) and keys its ncu summary to the hash of
+    that kernel's own sources."""
+    assert bench.step_kernel_name(2, "stream") == "k_step_stream"
+    assert bench.step_kernel_name(2, "wave") == bench.step_kernel_name(2, "wave4") == "k_step_wave"
+    assert bench.step_kernel_name(2, "async") == "k_step_rows2"
+    assert bench.step_kernel_name(1, "plain") == "k_step"
+    assert [bench.steps_per_launch(v) for v in ("stream", "wave", "wave4", "async")] == [1, 2, 4, 1]
+    for k in ("k_step_stream", "k_step_stream_inh", "k_step_stream_x2"):
+        assert bench.step_kernel_sources(k) == bench.STREAM_SOURCES
+    assert bench.step_kernel_sources("k_step_wave") == bench.WAVE_SOURCES
+    assert bench.step_kernel_sources("k_step_rows2") == bench.KERNEL_SOURCES
 
 
 def test_replica_throughput_counts_every_rank():
