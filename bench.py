@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--dtype", default="f32r", choices=["f32", "f32x2", "f32r"])
     ap.add_argument("--variant", default=None,
                     choices=["auto", "plain", "pipelined", "prefetch", "async", "stream", "wave", "wave4"],
-                    help="step kernel (default: stream for reactive512, grf256 and inhom512, async for the others)")
+                    help="step kernel (default: stream for reactive512, grf256, inhom512 and frap256, async for the others)")
     ap.add_argument("--order", default=None, choices=["tiled", "planes"],
                     help="block order of the grid (default: planes for reactive512, tiled for the others)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1024,7 +1024,8 @@ def run_frap256(args):
                                  % (n, phys.extra["side"], steps, sps),
                      "block": args.block, "kernel": args.variant, "n_active": n_act,
                      "timing": "host clock around both curves and the fit (each curve synchronises once)"},
-          "roofline": {"bound": "hbm", "kernel": "k_step_rows2" if args.variant != "prefetch" else "k_step_pipe",
+          "roofline": {"bound": "hbm", "kernel": {"stream": "k_step_stream", "prefetch": "k_step_pipe",
+                                                  "pipelined": "k_step_pipe"}.get(args.variant, "k_step_rows2"),
                        "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                        "frac": achieved / peak, "traffic": None,
                        "algorithmic_bytes_per_launch": algo_bytes,
@@ -1341,7 +1342,7 @@ def run_batch64(args):
 def main():
     args = parse()
     if args.variant is None:
-        args.variant = "stream" if args.workload in ("reactive512", "grf256", "inhom512") else "async"
+        args.variant = "stream" if args.workload in ("reactive512", "grf256", "inhom512", "frap256") else "async"
     if args.order is None:
         args.order = "planes" if args.workload == "reactive512" else "tiled"
     if args.steps is None:
