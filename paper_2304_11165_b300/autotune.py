@@ -5,9 +5,10 @@ For a set of geometries (one grid or a batch) it builds the grid at each
 block edge, times a few steps of every candidate kernel configuration with
 CUDA events on the current stream, and picks the fastest per active-voxel
 update (the block edge trades block fill against per-block overhead; the
-variant trades registers against latency hiding: halo loads when the group
-comes up, prefetched a group ahead in registers, or copied a group ahead with
-cp.async).  Results are cached in a
+variant trades registers against latency hiding: the streaming kernel's rows
+read through L1 (4^3 blocks; also over the batch solver's work lists), or the
+ring kernels' halo loads when the group comes up, prefetched a group ahead in
+registers, or copied a group ahead with cp.async).  Results are cached in a
 JSON file keyed by GPU name, state dtype, species count and a fill bucket
 (the fraction of 8^3-block slots that are pore voxels, in steps of 0.1), so
 a second solve of a similar geometry skips the timing.
@@ -30,7 +31,7 @@ import torch
 
 from .api import Grid, State, make_params
 
-DEFAULT_CANDIDATES = [(4, "pipelined", 0), (4, "prefetch", 0), (4, "async", 0), (8, "pipelined", 0),
+DEFAULT_CANDIDATES = [(4, "stream", 0), (4, "pipelined", 0), (4, "prefetch", 0), (4, "async", 0), (8, "pipelined", 0),
                       (8, "prefetch", 0), (8, "async", 0), (4, "pipelined", 4), (8, "pipelined", 4)]
 
 

@@ -688,6 +688,16 @@ sbg_status launch_step_work(sbg_grid g, sbg_state st, const sbg_params *p, int s
     a.items = items;
     a.nitems = nitems;
     cudaError_t e = cudaSuccess;
+    // the streaming kernel takes work-list spans of at most 16 blocks (the spans the batch solver
+    // makes for these states: step_work_group_voxels / B^3 <= 1024 / 64)
+    const bool react = p->k_surf != 0.0;
+    if ((st->variant == SBG_KERNEL_AUTO || st->variant == SBG_KERNEL_STREAM) && stream_kernel_applies(g, st) &&
+        !(st->dtype == SBG_F32R && react) &&
+        step_work_group_voxels(st->dtype, st->ns, g->has_eps, halo_variant_of(st->variant)) <= 16 * g->b3()) {
+        e = launch_step_stream(a, g, st->ns, react, st->ctas_per_sm, s);
+        if (e != cudaSuccess) return cuda_fail(e, "streaming step kernel launch (work list)");
+        return SBG_OK;
+    }
     if (!launch_step_pipe(a, st->dtype, st->ns, g->B, p->k_surf != 0.0,
                           halo_variant_of(st->variant), st->ctas_per_sm, g->err, s, &e))
         return fail(SBG_ERR_INVALID_ARG, "batched stepping needs an FP32-based state (SBG_F32, SBG_F32X2 or "

@@ -45,15 +45,29 @@ constexpr int kStreamThreads = 256;  // 16 blocks x 16 rows of 4 voxels
 // SRC: the correction d of an SBG_F32R state (one species, no surface
 // reaction): the stored source r = L_h b of the row takes the place of the
 // transfer term, d' = d + dt (L_h d - decay d + r), as in the plain kernel.
-template <int NS, bool REACT, bool HELD, int MINB, bool SRC = false>
+// WL: the groups are the spans of a work list (a.items: first block, blocks;
+// at most 16 blocks each, within one geometry) instead of consecutive 16-block
+// groups of the list: the batch solver's steps over its unconverged geometries.
+template <int NS, bool REACT, bool HELD, int MINB, bool SRC = false, bool WL = false>
 __global__ void __launch_bounds__(kStreamThreads, MINB)
 k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__restrict__ wrow, float negzero, int *err,
               int n_wrows) {
     const int t = threadIdx.x;
     const int j = t >> 4, rr = t & 15, y = rr & 3, z = rr >> 2;
     const int nb = (int)a.nb;  // the launcher guarantees (nb + 2) * 64 < 2^31
-    const int ngroups = (nb + 15) >> 4;
+    const int ngroups = WL ? (int)a.nitems : (nb + 15) >> 4;
     const int G = (int)gridDim.x;
+    // this thread's block in group gi (-1: none)
+    auto block_of = [&](int gi) -> int {
+        if (gi >= ngroups) return -1;
+        if (WL) {
+            const int first = (int)__ldg(a.items + 2 * (int64_t)gi);
+            const int count = (int)__ldg(a.items + 2 * (int64_t)gi + 1);
+            return j < count ? first + j : -1;
+        }
+        const int b = gi * 16 + j;
+        return b < nb ? b : -1;
+    };
     // every species array is preceded by a ghost block of sentinels, block id -1: offsets
     // below are taken from that block's start, so block f sits at (f + 1) * 64 and an
     // absent neighbour (f = -1) at 0
@@ -72,13 +86,15 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
     // per thread: the face neighbours of its block it reads (-x, +x, the y side, the z side),
     // its block's band rows and its row's held bits
     struct Meta {
+        int b;  // the block (-1: none)
         int f[4];
         int woff;
         uint32_t wmask, held;
     };
     auto load_meta = [&](int gi, Meta &m) {
-        const int b = gi * 16 + j;
-        if (gi < ngroups && b < nb) {
+        const int b = block_of(gi);
+        m.b = b;
+        if (b >= 0) {
             const int32_t *fp = a.face + (int64_t)b * 6;
             m.f[0] = __ldg(fp + 0);
             m.f[1] = __ldg(fp + 1);
@@ -115,8 +131,8 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
         const int *f = cur.f;
         const int woff = cur.woff;
         const uint32_t wmask = cur.wmask, held = cur.held;
-        const int b = gi * 16 + j;
-        const bool valid = b < nb;
+        const int b = cur.b;
+        const bool valid = b >= 0;
         // offsets from the ghost block's start of every value this row reads (a thread past the
         // end of the list reads the ghost block and stores nothing)
         const int row = valid ? (b + 1) * 64 + rr * 4 : rr * 4;
@@ -138,8 +154,8 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
         load_meta(gi + G, nxt);  // the next group's tables, in flight while this one computes
         if (NS == 2 || SRC) {  // this thread's row of the next group, one sweep ahead (measured: 1.3% faster on
                                // the 512^3 two-species run, 1.8% for SBG_F32R on grf256; slower for the others)
-            const int bn = (gi + G) * 16 + j;
-            if (bn < nb) {
+            const int bn = nxt.b;
+            if (bn >= 0) {
 #pragma unroll
                 for (int s = 0; s < NS; ++s) prefetch_l2(gb[s] + (bn + 1) * 64 + rr * 4);
             }
@@ -471,11 +487,11 @@ cudaError_t launch_step_stream_inh(const StepArgs &a, sbg_grid g, int ctas_per_s
                        : launch_stream_inh_t<false>(a, ctas_per_sm, g->err, s);
 }
 
-template <int NS, bool REACT, bool HELD, bool SRC = false>
+template <int NS, bool REACT, bool HELD, bool SRC = false, bool WL = false>
 static cudaError_t launch_stream_t(const StepArgs &a, const int2 *wmeta, const float4 *wrow, int ctas_per_sm,
                                    int *err, int n_wrows, cudaStream_t s) {
     constexpr int MINB = 3;
-    auto kern = k_step_stream<NS, REACT, HELD, MINB, SRC>;
+    auto kern = k_step_stream<NS, REACT, HELD, MINB, SRC, WL>;
     static int occ = -1, nsm = 0;
     if (occ < 0) {
         int dev = 0;
@@ -486,7 +502,7 @@ static cudaError_t launch_stream_t(const StepArgs &a, const int2 *wmeta, const f
         if (occ < 1) occ = 1;
     }
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-    const int64_t ngroups = (a.nb + 15) / 16;
+    const int64_t ngroups = WL ? a.nitems : (a.nb + 15) / 16;
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ngroups) grid = ngroups;
     if (grid < 1) return cudaSuccess;
@@ -500,27 +516,35 @@ bool stream_kernel_applies(sbg_grid g, sbg_state st) {
            (g->nb + 2) * 64 < (int64_t(1) << 31);
 }
 
-cudaError_t launch_step_stream(const StepArgs &a, sbg_grid g, int ns, bool react, int ctas_per_sm,
-                               cudaStream_t s) {
+// WL: a.items holds a work list (spans of at most 16 blocks)
+template <bool WL>
+static cudaError_t launch_step_stream_t(const StepArgs &a, sbg_grid g, int ns, bool react, int ctas_per_sm,
+                                       cudaStream_t s) {
     const bool held = a.held_mask != 0;
     const int2 *wm = g->wmeta;
     const float4 *wr = g->wrow;
     int *err = g->err;
     const int nw = (int)std::min<int64_t>(g->n_wrows, INT32_MAX);
     if (a.src_term) {  // SBG_F32R correction (the caller excludes a surface reaction)
-        return held ? launch_stream_t<1, false, true, true>(a, wm, wr, ctas_per_sm, err, nw, s)
-                    : launch_stream_t<1, false, false, true>(a, wm, wr, ctas_per_sm, err, nw, s);
+        return held ? launch_stream_t<1, false, true, true, WL>(a, wm, wr, ctas_per_sm, err, nw, s)
+                    : launch_stream_t<1, false, false, true, WL>(a, wm, wr, ctas_per_sm, err, nw, s);
     }
     if (ns == 1) {
-        if (react) return held ? launch_stream_t<1, true, true>(a, wm, wr, ctas_per_sm, err, nw, s)
-                               : launch_stream_t<1, true, false>(a, wm, wr, ctas_per_sm, err, nw, s);
-        return held ? launch_stream_t<1, false, true>(a, wm, wr, ctas_per_sm, err, nw, s)
-                    : launch_stream_t<1, false, false>(a, wm, wr, ctas_per_sm, err, nw, s);
+        if (react) return held ? launch_stream_t<1, true, true, false, WL>(a, wm, wr, ctas_per_sm, err, nw, s)
+                               : launch_stream_t<1, true, false, false, WL>(a, wm, wr, ctas_per_sm, err, nw, s);
+        return held ? launch_stream_t<1, false, true, false, WL>(a, wm, wr, ctas_per_sm, err, nw, s)
+                    : launch_stream_t<1, false, false, false, WL>(a, wm, wr, ctas_per_sm, err, nw, s);
     }
-    if (react) return held ? launch_stream_t<2, true, true>(a, wm, wr, ctas_per_sm, err, nw, s)
-                           : launch_stream_t<2, true, false>(a, wm, wr, ctas_per_sm, err, nw, s);
-    return held ? launch_stream_t<2, false, true>(a, wm, wr, ctas_per_sm, err, nw, s)
-                : launch_stream_t<2, false, false>(a, wm, wr, ctas_per_sm, err, nw, s);
+    if (react) return held ? launch_stream_t<2, true, true, false, WL>(a, wm, wr, ctas_per_sm, err, nw, s)
+                           : launch_stream_t<2, true, false, false, WL>(a, wm, wr, ctas_per_sm, err, nw, s);
+    return held ? launch_stream_t<2, false, true, false, WL>(a, wm, wr, ctas_per_sm, err, nw, s)
+                : launch_stream_t<2, false, false, false, WL>(a, wm, wr, ctas_per_sm, err, nw, s);
+}
+
+cudaError_t launch_step_stream(const StepArgs &a, sbg_grid g, int ns, bool react, int ctas_per_sm,
+                               cudaStream_t s) {
+    if (a.items) return launch_step_stream_t<true>(a, g, ns, react, ctas_per_sm, s);
+    return launch_step_stream_t<false>(a, g, ns, react, ctas_per_sm, s);
 }
 
 
