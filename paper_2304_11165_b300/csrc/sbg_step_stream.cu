@@ -8,8 +8,10 @@
 // (sbg_step_pipe.cu) stage every group through shared memory and fetch the
 // face halos of each group with extra copies; with two species they fit only
 // a few CTAs per SM and stay latency-bound.  Here:
-//  - CTAs of 256 threads take groups of 16 consecutive blocks of the list in
-//    turn (group g goes to CTA g mod gridDim), so at any moment the whole GPU
+//  - CTAs of 16 threads per block take groups of consecutive blocks of the
+//    list in turn (16 blocks; 12 for two species, in CTAs of 192 threads, four
+//    per SM, which measured 1% faster than 16 blocks at three per SM; group g
+//    goes to CTA g mod gridDim), so at any moment the whole GPU
 //    works on one window of the list.  On a grid built in plane order
 //    (SBG_ORDER_PLANES: x fastest, z slowest) that window sweeps the box plane
 //    by plane, and the face neighbours of every block (in the same plane, one
@@ -46,16 +48,17 @@ constexpr int kStreamThreads = 256;  // 16 blocks x 16 rows of 4 voxels
 // reaction): the stored source r = L_h b of the row takes the place of the
 // transfer term, d' = d + dt (L_h d - decay d + r), as in the plain kernel.
 // WL: the groups are the spans of a work list (a.items: first block, blocks;
-// at most 16 blocks each, within one geometry) instead of consecutive 16-block
-// groups of the list: the batch solver's steps over its unconverged geometries.
-template <int NS, bool REACT, bool HELD, int MINB, bool SRC = false, bool WL = false>
-__global__ void __launch_bounds__(kStreamThreads, MINB)
+// at most 16 blocks each, within one geometry) instead of consecutive groups of
+// the list: the batch solver's steps over its unconverged geometries.
+// GB: blocks per group (16 threads each); 16 with a work list.
+template <int NS, bool REACT, bool HELD, int MINB, bool SRC = false, bool WL = false, int GB = 16>
+__global__ void __launch_bounds__(16 * GB, MINB)
 k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__restrict__ wrow, float negzero, int *err,
               int n_wrows) {
     const int t = threadIdx.x;
     const int j = t >> 4, rr = t & 15, y = rr & 3, z = rr >> 2;
     const int nb = (int)a.nb;  // the launcher guarantees (nb + 2) * 64 < 2^31
-    const int ngroups = WL ? (int)a.nitems : (nb + 15) >> 4;
+    const int ngroups = WL ? (int)a.nitems : (nb + GB - 1) / GB;
     const int G = (int)gridDim.x;
     // this thread's block in group gi (-1: none)
     auto block_of = [&](int gi) -> int {
@@ -65,7 +68,7 @@ k_step_stream(const StepArgs a, const int2 *__restrict__ wmeta, const float4 *__
             const int count = (int)__ldg(a.items + 2 * (int64_t)gi + 1);
             return j < count ? first + j : -1;
         }
-        const int b = gi * 16 + j;
+        const int b = gi * GB + j;
         return b < nb ? b : -1;
     };
     // every species array is preceded by a ghost block of sentinels, block id -1: offsets
@@ -490,23 +493,27 @@ cudaError_t launch_step_stream_inh(const StepArgs &a, sbg_grid g, int ctas_per_s
 template <int NS, bool REACT, bool HELD, bool SRC = false, bool WL = false>
 static cudaError_t launch_stream_t(const StepArgs &a, const int2 *wmeta, const float4 *wrow, int ctas_per_sm,
                                    int *err, int n_wrows, cudaStream_t s) {
-    constexpr int MINB = 3;
-    auto kern = k_step_stream<NS, REACT, HELD, MINB, SRC, WL>;
+    // two species: groups of 12 blocks, 4 CTAs of 192 threads per SM (80 registers); otherwise 16
+    // blocks, 256 threads, at least 3 CTAs per SM
+    constexpr int GB = (NS == 2 && !WL) ? 12 : 16;
+    constexpr int MINB = GB == 12 ? 4 : 3;
+    constexpr int kThreads = 16 * GB;
+    auto kern = k_step_stream<NS, REACT, HELD, MINB, SRC, WL, GB>;
     static int occ = -1, nsm = 0;
     if (occ < 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);  // all of it as L1
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStreamThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0);
         if (occ < 1) occ = 1;
     }
     const int per_sm = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-    const int64_t ngroups = WL ? a.nitems : (a.nb + 15) / 16;
+    const int64_t ngroups = WL ? a.nitems : (a.nb + GB - 1) / GB;
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ngroups) grid = ngroups;
     if (grid < 1) return cudaSuccess;
-    kern<<<(unsigned)grid, kStreamThreads, 0, s>>>(a, wmeta, wrow, -0.0f, err, n_wrows);
+    kern<<<(unsigned)grid, kThreads, 0, s>>>(a, wmeta, wrow, -0.0f, err, n_wrows);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
-"""The streaming step kernel (SBG_KERNEL_STREAM: groups of 16 blocks taken by
-the CTAs in turn, one x-row per thread, neighbour rows read through L1, L2
-prefetches a few sweeps ahead) against the one-thread-per-voxel kernel,
+"""The streaming step kernel (SBG_KERNEL_STREAM: groups of 16 blocks, 12 for
+two species, taken by the CTAs in turn, one x-row per thread, neighbour rows
+read through L1, an L2 prefetch of the next group's rows) against the one-thread-per-voxel kernel,
 bitwise, and against the FP64 oracle; on grids in tiled and in plane order,
 with ragged box edges, Dirichlet faces, the surface transfer of two species,
 few CTAs walking many groups, and the degenerate geometries."""
