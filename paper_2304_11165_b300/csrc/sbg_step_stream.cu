@@ -21,7 +21,7 @@
 //    neighbour rows and the two x neighbour values are read straight from
 //    global memory (16-byte loads through L1; rows of the same block are read
 //    by the same half-warp).  An absent neighbour block reads the state's
-//    ghost block (block id nb, all sentinels), so no pointer selects;
+//    ghost block (block id -1, all sentinels), so no pointer selects;
 //  - the +x neighbour values a group reads sit in the blocks of the next
 //    groups, so every sweep pulls the rows of the sweep after it into L2 as a
 //    side effect; beyond that, only a per-thread L2 prefetch of its own row
