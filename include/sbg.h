@@ -279,7 +279,7 @@ sbg_status sbg_step_source(sbg_grid grid, sbg_state state, const sbg_params *par
  * without a surface reaction, one FP32 species with a diffusivity factor
  * (u and the factor read at the same offsets) and SBG_F32X2 states (hi and
  * lo read at the same offsets), on 4^3 blocks:
- * CTAs take groups of 16 blocks in turn, one
+ * CTAs take groups of 16 blocks (12 for two species) in turn, one
  * x-row of four voxels per thread, every neighbour row read straight from
  * global memory through L1; best with SBG_ORDER_PLANES grids, whose plane
  * order keeps the sweep's neighbour planes in L2; states of other kinds fall
